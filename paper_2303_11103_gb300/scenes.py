@@ -1,0 +1,228 @@
+"""Seeded synthetic scene and radio-device generators.
+
+This module only builds inputs: triangle meshes made of boxes and a ground
+quad, material tables and transmitter/receiver placements. It holds none of
+the propagation arithmetic, so the CUDA path and the CPU oracle can both take
+their inputs from here.
+
+The paper's own scenes (Munich and Etoile, built from OpenStreetMap, Sec. II
+and Sec. III-A) are not available; these seeded box cities stand in for them.
+Materials are described by relative permittivity and conductivity only, the
+two properties the paper names for radio materials (Sec. II).
+
+Seeds: 0 tiny, 1 city geometry, 2 transmitter/receiver placement,
+3 materials of the differentiation workload, 4 surrogate pairs.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# (eps_r, sigma [S/m]) of the named materials of the workloads.
+CONCRETE = (5.24, 0.123)
+GLASS = (6.31, 0.0036)
+GROUND = (5.13, 0.0047)
+
+ANT_ISO, ANT_DIPOLE, ANT_TR38901 = 0, 1, 2
+
+
+@dataclass
+class Antenna:
+    """Pattern kind and per-port polarization slant angles (radians)."""
+    kind: int = ANT_ISO
+    slants: tuple = (0.0,)
+
+    @property
+    def n_ports(self) -> int:
+        return len(self.slants)
+
+
+V_ISO = Antenna(ANT_ISO, (0.0,))
+TR38901_VH = Antenna(ANT_TR38901, (0.0, np.pi / 2))
+TR38901_V = Antenna(ANT_TR38901, (0.0,))
+
+
+@dataclass
+class Scene:
+    verts: np.ndarray            # float32 [T, 9]: v0, v1, v2 of each triangle
+    mat_id: np.ndarray           # int32 [T]
+    materials: np.ndarray        # float32 [M, 2]: eps_r, sigma
+    name: str = ""
+    footprints: np.ndarray = field(default_factory=lambda: np.zeros((0, 5), np.float64))
+    # footprints: [B, 5] = x0, x1, y0, y1, height of each box building
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.verts.shape[0])
+
+
+@dataclass
+class Devices:
+    pos: np.ndarray              # float32 [n, 3]
+    ypr: np.ndarray              # float32 [n, 3] yaw, pitch, roll (radians)
+    antenna: Antenna = field(default_factory=lambda: V_ISO)
+
+
+def box_triangles(x0, x1, y0, y1, z0, z1) -> np.ndarray:
+    """12 triangles (6 faces x 2) of an axis-aligned box, float64 [12, 9]."""
+    c = np.array([[x0, y0, z0], [x1, y0, z0], [x1, y1, z0], [x0, y1, z0],
+                  [x0, y0, z1], [x1, y0, z1], [x1, y1, z1], [x0, y1, z1]], np.float64)
+    faces = [(0, 1, 2, 3), (4, 5, 6, 7), (0, 1, 5, 4),
+             (1, 2, 6, 5), (2, 3, 7, 6), (3, 0, 4, 7)]
+    tris = []
+    for a, b, cc, d in faces:
+        tris.append(np.concatenate([c[a], c[b], c[cc]]))
+        tris.append(np.concatenate([c[a], c[cc], c[d]]))
+    return np.stack(tris)
+
+
+def ground_triangles(half: float) -> np.ndarray:
+    c = np.array([[-half, -half, 0.0], [half, -half, 0.0],
+                  [half, half, 0.0], [-half, half, 0.0]])
+    return np.stack([np.concatenate([c[0], c[1], c[2]]),
+                     np.concatenate([c[0], c[2], c[3]])])
+
+
+def tiny_scene() -> Scene:
+    """200 x 200 m ground plus one 20 x 20 x 30 m box at the origin, all concrete."""
+    tris = np.concatenate([ground_triangles(100.0),
+                           box_triangles(-10, 10, -10, 10, 0, 30)])
+    mats = np.array([CONCRETE], np.float32)
+    return Scene(tris.astype(np.float32), np.zeros(len(tris), np.int32), mats, "tiny",
+                 np.array([[-10, 10, -10, 10, 30.0]]))
+
+
+def tiny_devices(visible: bool = False):
+    """Tx (-60,0,25), Rx (60,10,1.5); the 'visible' variant moves Rx to (-75,0,1.5)."""
+    tx = Devices(np.array([[-60.0, 0.0, 25.0]], np.float32), np.zeros((1, 3), np.float32), V_ISO)
+    rxp = [-75.0, 0.0, 1.5] if visible else [60.0, 10.0, 1.5]
+    rx = Devices(np.array([rxp], np.float32), np.zeros((1, 3), np.float32), V_ISO)
+    return tx, rx
+
+
+def ground_only_scene(half: float = 1000.0, mat=CONCRETE) -> Scene:
+    tris = ground_triangles(half)
+    return Scene(tris.astype(np.float32), np.zeros(2, np.int32),
+                 np.array([mat], np.float32), "ground")
+
+
+def city_scene(n_side: int = 20, size: float = 500.0, seed: int = 1,
+               n_materials: int = 0, mat_seed: int = 3) -> Scene:
+    """Box city on a jittered n_side x n_side grid over a size x size ground.
+
+    Footprints are uniform in [10, 40] m, heights uniform in [10, 60] m, grid
+    jitter uniform in [-5, 5] m. Overlapping boxes are kept. With the default
+    three materials each building is concrete or glass (half each, by seed)
+    and the ground is material 2. With n_materials > 0 the materials are
+    drawn as eps_r ~ U(2, 8), sigma ~ logU(1e-3, 1) and assigned to the
+    ground (material 0) and to buildings at random.
+    """
+    rng = np.random.default_rng(seed)
+    pitch = size / n_side
+    tris, mats, fps = [], [], []
+    if n_materials > 0:
+        mrng = np.random.default_rng(mat_seed)
+        eps = mrng.uniform(2.0, 8.0, n_materials)
+        sig = 10.0 ** mrng.uniform(-3.0, 0.0, n_materials)
+        materials = np.stack([eps, sig], 1).astype(np.float32)
+        ground_mat = 0
+    else:
+        materials = np.array([CONCRETE, GLASS, GROUND], np.float32)
+        ground_mat = 2
+    g = ground_triangles(size / 2)
+    tris.append(g)
+    mats += [ground_mat] * 2
+    brng = np.random.default_rng(seed + 1000)
+    for i in range(n_side):
+        for j in range(n_side):
+            cx = -size / 2 + pitch * (i + 0.5) + rng.uniform(-5, 5)
+            cy = -size / 2 + pitch * (j + 0.5) + rng.uniform(-5, 5)
+            w, d = rng.uniform(10, 40, 2)
+            h = rng.uniform(10, 60)
+            x0, x1, y0, y1 = cx - w / 2, cx + w / 2, cy - d / 2, cy + d / 2
+            tris.append(box_triangles(x0, x1, y0, y1, 0.0, h))
+            if n_materials > 0:
+                m = int(brng.integers(0, n_materials))
+            else:
+                m = int(brng.integers(0, 2))
+            mats += [m] * 12
+            fps.append([x0, x1, y0, y1, h])
+    verts = np.concatenate(tris).astype(np.float32)
+    return Scene(verts, np.array(mats, np.int32), materials, f"city{n_side}",
+                 np.array(fps, np.float64))
+
+
+def _inside_any(fps: np.ndarray, x: float, y: float, margin: float = 0.0) -> bool:
+    if len(fps) == 0:
+        return False
+    return bool(np.any((x > fps[:, 0] - margin) & (x < fps[:, 1] + margin) &
+                       (y > fps[:, 2] - margin) & (y < fps[:, 3] + margin)))
+
+
+def _height_at(fps: np.ndarray, x: float, y: float) -> float:
+    if len(fps) == 0:
+        return 0.0
+    m = (x > fps[:, 0]) & (x < fps[:, 1]) & (y > fps[:, 2]) & (y < fps[:, 3])
+    return float(fps[m, 4].max()) if m.any() else 0.0
+
+
+def street_points(scene: Scene, n: int, rng, half: float, margin: float = 0.5):
+    """n points (x, y) by rejection from [-half, half]^2 outside every footprint."""
+    out = []
+    while len(out) < n:
+        x, y = rng.uniform(-half, half, 2)
+        if not _inside_any(scene.footprints, x, y, margin):
+            out.append((x, y))
+    return np.array(out, np.float64)
+
+
+def city_devices(scene: Scene, n_rx: int = 1000, seed: int = 2,
+                 tx_antenna: Antenna = TR38901_VH, rx_antenna: Antenna = V_ISO,
+                 half: float = 240.0):
+    """One Tx 30 m above a street point, n_rx receivers 1.5 m above streets."""
+    rng = np.random.default_rng(seed)
+    txy = street_points(scene, 1, rng, 0.6 * half)[0]
+    tx = Devices(np.array([[txy[0], txy[1], 30.0]], np.float32),
+                 np.array([[rng.uniform(-np.pi, np.pi), 0.1, 0.0]], np.float32), tx_antenna)
+    rxy = street_points(scene, n_rx, rng, half)
+    rx = Devices(np.concatenate([rxy, np.full((n_rx, 1), 1.5)], 1).astype(np.float32),
+                 np.zeros((n_rx, 3), np.float32), rx_antenna)
+    return tx, rx
+
+
+def rooftop_transmitters(scene: Scene, n_tx: int = 64, seed: int = 2,
+                         antenna: Antenna = TR38901_V, half: float = 240.0) -> Devices:
+    """n_tx Tx with z ~ U(25, 60) at xy not inside a taller building, random azimuth."""
+    rng = np.random.default_rng(seed + 100)
+    pos, ypr = [], []
+    while len(pos) < n_tx:
+        x, y = rng.uniform(-half, half, 2)
+        z = rng.uniform(25.0, 60.0)
+        if _height_at(scene.footprints, x, y) >= z - 1.0:
+            continue
+        pos.append((x, y, z))
+        ypr.append((rng.uniform(-np.pi, np.pi), 0.1, 0.0))
+    return Devices(np.array(pos, np.float32), np.array(ypr, np.float32), antenna)
+
+
+def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
+                    half: float = 240.0):
+    """Tx 1 m above a random roof centre, Rx 1.5 m above streets.
+
+    Returns tx [n_tx, 3] and rx [n_tx, n_rx_per_tx, 3] (float32).
+    """
+    rng = np.random.default_rng(seed)
+    fps = scene.footprints
+    inner = fps[(np.abs(0.5 * (fps[:, 0] + fps[:, 1])) < half) &
+                (np.abs(0.5 * (fps[:, 2] + fps[:, 3])) < half)]
+    tx = []
+    while len(tx) < n_tx:
+        b = inner[rng.integers(0, len(inner))]
+        x, y = 0.5 * (b[0] + b[1]), 0.5 * (b[2] + b[3])
+        tx.append((x, y, _height_at(fps, x, y) + 1.0))
+    rx = np.stack([np.concatenate([street_points(scene, n_rx_per_tx, rng, half),
+                                   np.full((n_rx_per_tx, 1), 1.5)], 1)
+                   for _ in range(n_tx)])
+    return np.array(tx, np.float32), rx.astype(np.float32)
+
