@@ -1,0 +1,212 @@
+/*
+ * rt.h -- C ABI of the GB300 (sm_103a) specular radio ray tracer.
+ *
+ * The calls follow the problem statement of "Sionna RT: Differentiable Ray
+ * Tracing for Radio Propagation Modeling" (arXiv 2303.11103):
+ *   load_scene          Sec. II   triangle meshes with radio materials (eps_r, sigma)
+ *   set_tx / set_rx     Sec. II-A Listing 2: positions, yaw/pitch/roll, antenna patterns
+ *   compute_paths       Sec. II-B heuristic: Fibonacci-lattice rays, specular bounces,
+ *                                 image-method refinement, duplicate removal, LOS added
+ *   cir                 Sec. II-A Listing 3: path coefficients a_i and delays tau_i
+ *   freq_response       Sec. III-A: OFDM frequency response H(f) = sum_i a_i e^{-j2 pi f tau_i}
+ *   coverage_map        Sec. II-A Listing 2, Fig. 2: path-gain map on a cell grid
+ *   *_backward          Sec. I/II: gradients w.r.t. materials and transmitter pose
+ *
+ * Conventions (every call):
+ *   - Returns RT_OK (0) or a negative RT_ERR_* code; rt_last_error() gives the
+ *     message. No exception or abort crosses the ABI.
+ *   - SI units: metres, seconds, hertz, siemens per metre; angles in radians.
+ *   - Array pointers are DEVICE pointers owned by the caller unless the
+ *     parameter name ends in _host. The library copies what it keeps.
+ *   - Work is enqueued on the context's stream (rt_create / rt_set_stream);
+ *     calls that return counts synchronise that stream.
+ *   - Complex numbers are interleaved (re, im) float32 pairs.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef RT_GB300_H
+#define RT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_OK 0
+#define RT_ERR_INVALID_ARG (-1)
+#define RT_ERR_CUDA (-2)
+#define RT_ERR_OOM (-3)
+#define RT_ERR_CAPACITY (-4)
+#define RT_ERR_TIMEOUT (-5)
+#define RT_ERR_NOT_READY (-6)
+
+/* path-type flags of rt_compute_paths / rt_cir (Listing 3: cir(los, reflection)) */
+#define RT_LOS 1u
+#define RT_REFLECTION 2u
+#define RT_RECORD_RAYS 0x100u /* keep per-ray hit lists (debug / parity) */
+
+/* antenna pattern kinds (Sec. II-A: predefined patterns, single or dual polarized) */
+#define RT_ANT_ISO 0     /* isotropic, field amplitude 1 */
+#define RT_ANT_DIPOLE 1  /* short dipole, amplitude sqrt(1.5) sin(theta) */
+#define RT_ANT_TR38901 2 /* 3GPP TR 38.901 Table 7.3-1 element, 8 dBi */
+
+typedef struct rt_ctx rt_ctx;
+
+/* One antenna: pattern kind and per-port polarization slant angle (0 = V,
+ * pi/2 = H, +-pi/4 = cross). n_ports is 1 or 2. */
+typedef struct rt_antenna {
+    int32_t kind;
+    int32_t n_ports;
+    float slant[2];
+} rt_antenna;
+
+/* Horizontal coverage grid: cells [x0 + i*cell, x0 + (i+1)*cell) x
+ * [y0 + j*cell, ...), i < nx, j < ny, on the plane z = height. */
+typedef struct rt_grid {
+    float x0, y0, cell, height;
+    int32_t nx, ny;
+} rt_grid;
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+int rt_create(rt_ctx** ctx, int device, void* cuda_stream);
+/* Free every device buffer the context owns. Safe on NULL. */
+int rt_destroy(rt_ctx* ctx);
+int rt_set_stream(rt_ctx* ctx, void* cuda_stream);
+/* Copy the last error message (NUL-terminated, truncated to len). */
+int rt_last_error(const rt_ctx* ctx, char* buf, size_t len);
+/* Carrier frequency (default 3.5e9 Hz). */
+int rt_set_frequency(rt_ctx* ctx, double fc);
+
+/*
+ * Sec. II: scene = triangle meshes, each triangle with a radio material.
+ * verts [n_tris*9] float32 (v0, v1, v2 of each triangle), mat_id [n_tris]
+ * int32 in [0, n_mat), mat_params [n_mat*2] float32 (eps_r, sigma).
+ * Builds the LBVH on the GPU. Surfaces are two-sided. n_tris may be 0
+ * (every ray misses). Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t* mat_id,
+                  const float* mat_params, int32_t n_mat);
+/* Replace the material table (same n_mat as the scene). */
+int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat);
+
+/*
+ * Sec. II-A (Listing 2): transmitters. pos [n*3], ypr [n*3] (yaw, pitch,
+ * roll; 3GPP TR 38.901 Sec. 7.1 rotation Rz(yaw) Ry(pitch) Rx(roll)),
+ * pattern pat (host struct, shared by all transmitters).
+ */
+int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const rt_antenna* pat);
+/*
+ * Receivers, as rt_set_tx. rx_set_offsets_host (HOST, may be NULL): CSR of
+ * n_tx+1 int32 giving each transmitter its own receiver range [off[t],
+ * off[t+1]) of this array (uneven receiver sets); NULL = every transmitter
+ * with every receiver. Must be called after rt_set_tx when sets are given.
+ * The (tx, rx) pairs are numbered: without sets t*m + r; with sets the
+ * receiver index itself.
+ */
+int rt_set_rx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t m, const rt_antenna* pat,
+              const int32_t* rx_set_offsets_host);
+
+/*
+ * Sec. II-B: specular paths of every (tx, rx) pair. For each transmitter,
+ * num_rays rays leave along a Fibonacci lattice on the sphere (global
+ * frame) and bounce specularly up to max_depth times; every prefix of a
+ * ray's triangle list is a candidate; duplicates are removed; the image
+ * method keeps the candidates that reach each receiver exactly and
+ * unoccluded; the LOS path is added if flags has RT_LOS. max_depth = number
+ * of reflections (0 = LOS only). The path store (owned by the context)
+ * lists the paths of each pair in canonical order (depth, triangle ids).
+ * num_paths_out (HOST) receives the path count. Synchronises the stream.
+ * Errors: RT_ERR_INVALID_ARG (no scene / devices, max_depth > 6, key width
+ * over 64 bits), RT_ERR_OOM, RT_ERR_CUDA.
+ */
+int rt_compute_paths(rt_ctx* ctx, int32_t max_depth, int64_t num_rays, uint32_t flags,
+                     int64_t* num_paths_out);
+/* Sec. II-B: the launch directions the tracer shoots, rays [first,
+ * first+n) of a lattice of num_rays: dirs [n*3] float32 (FP64 lattice
+ * formula rounded once to FP32). */
+int rt_ray_directions(rt_ctx* ctx, int64_t num_rays, int64_t first, int64_t n, float* dirs);
+/* Number of (tx, rx) pairs of the current device configuration (HOST out). */
+int rt_num_pairs(const rt_ctx* ctx, int64_t* n_pairs_out);
+/*
+ * Copy the path store. Any pointer may be NULL. offsets [n_pairs+1] int64
+ * (CSR over pairs), seq [P*max_depth] int32 triangle ids (-1 padded),
+ * points [P*max_depth*3] float32 reflection points, depth [P] int32,
+ * length [P] float64 (path length accumulated in FP64).
+ */
+int rt_get_paths(rt_ctx* ctx, int64_t* offsets, int32_t* seq, float* points, int32_t* depth,
+                 double* length);
+/*
+ * Debug / parity: the de-duplicated candidate list of the last
+ * rt_compute_paths. n_out (HOST) = count U (always written); tx [U],
+ * depth [U], seq [U*max_depth], witness_ray [U] (lowest ray index that
+ * produced the candidate, -1 for LOS). Any device pointer may be NULL.
+ */
+int rt_get_candidates(rt_ctx* ctx, int64_t* n_out, int32_t* tx, int32_t* depth, int32_t* seq,
+                      int64_t* witness_ray);
+/* Debug / parity (flag RT_RECORD_RAYS): hits [n_tx*num_rays*max_depth]
+ * int32 triangle ids per ray and bounce, -1 after a miss. */
+int rt_get_ray_hits(rt_ctx* ctx, int32_t* hits);
+
+/*
+ * Listing 3 (paths.cir): channel coefficients and delays of every stored
+ * path. a [P*nrp*ntp] complex (nrp/ntp = rx/tx ports), a = lambda/(4 pi r)
+ * exp(-j 2 pi frac(r/lambda)) F_rx . (Fresnel chain) . F_tx, tau [P] = r/c0
+ * (absolute delay). Paths excluded by flags (RT_LOS: depth 0,
+ * RT_REFLECTION: depth >= 1) get a = 0.
+ */
+int rt_cir(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
+/*
+ * Sec. III-A: H [n_pairs*nrp*ntp*K] complex, H = sum_i a_i exp(-j 2 pi f_k tau_i)
+ * over the pair's paths, from a [P*nrp*ntp] and tau [P] as returned by
+ * rt_cir; freqs [K] float64 baseband offsets (Hz).
+ */
+int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double* freqs,
+                     int32_t K, float* H);
+
+/*
+ * Sec. II-A Listing 2 / Fig. 2: coverage map of every transmitter, port
+ * tx_port, on grid g, by the ray-density estimator: each of num_rays
+ * Fibonacci rays carries the transmit field through up to max_depth
+ * specular reflections; every segment crossing z = height at x with
+ * direction d adds |F_rx(-d) . E|^2 / (num_rays |d_z|) to its cell
+ * (receiver pattern: rt_set_rx's, port 0, unrotated); cell gain =
+ * lambda^2/(4 pi cell^2) * sum. gain [n_tx*ny*nx] float32, hits
+ * [n_tx*ny*nx] uint32 (crossings per cell); both overwritten. All
+ * transmitters run in one persistent launch.
+ */
+int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
+                    int32_t tx_port, float* gain, uint32_t* hits);
+/*
+ * As rt_coverage_map, but traces only lattice rays [first_ray, first_ray +
+ * ray_count) of the num_rays lattice of every transmitter and ADDS to gain
+ * and hits (not zeroed). Summing calls over a partition of [0, num_rays)
+ * gives rt_coverage_map's result up to float summation order (used to split
+ * large jobs and to trace chosen subsets of rays).
+ */
+int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
+                               int64_t first_ray, int64_t ray_count, int32_t tx_port, float* gain,
+                               uint32_t* hits);
+
+/*
+ * Sec. I/II (differentiability): vector-Jacobian products through the
+ * stored paths (no re-trace). grad_a [P*nrp*ntp] complex and grad_tau [P]
+ * (may be NULL) are the upstream gradients of a real loss w.r.t. rt_cir's
+ * outputs (PyTorch convention dL/dRe + j dL/dIm). Accumulates (+=) into
+ * g_eps [n_mat], g_sigma [n_mat], g_txpos [n_tx*3], g_txypr [n_tx*3]; any
+ * may be NULL.
+ */
+int rt_cir_backward(rt_ctx* ctx, uint32_t flags, const float* grad_a, const float* grad_tau,
+                    float* g_eps, float* g_sigma, float* g_txpos, float* g_txypr);
+/*
+ * VJP of rt_freq_response: from grad_H [n_pairs*nrp*ntp*K] complex, writes
+ * grad_a [P*nrp*ntp] complex and grad_tau [P] (overwritten).
+ */
+int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, const double* freqs,
+                              int32_t K, const float* grad_H, float* grad_a, float* grad_tau);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

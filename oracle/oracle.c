@@ -742,17 +742,26 @@ void ora_coverage(int T, const double* V, const int* mat, int M, const double* m
                             size_t c = (size_t)iy * nx + ix;
                             g[c] += w;
                             hc[c] += 1.0;
+                            /* distance (along the ray-normal scale) to the cell's x and y edges */
                             double ex = fx - ix, ey = fy - iy;
-                            double eb = ex < 1 - ex ? ex : 1 - ex;
-                            double eb2 = ey < 1 - ey ? ey : 1 - ey;
-                            if (eb2 < eb) eb = eb2;
-                            eb *= cell * fabs(d[2]);
-                            int near = macc < eps || eb < eps || s < eps || (id >= 0 && t - s < eps);
-                            if (near) {
+                            double sc = cell * fabs(d[2]);
+                            int nxd = ex * sc < eps ? -1 : ((1 - ex) * sc < eps ? 1 : 0);
+                            int nyd = ey * sc < eps ? -1 : ((1 - ey) * sc < eps ? 1 : 0);
+                            int whole = macc < eps || s < eps || (id >= 0 && t - s < eps);
+                            if (whole) {
                                 for (long yy = iy - 1; yy <= iy + 1; yy++)
                                     for (long xx = ix - 1; xx <= ix + 1; xx++)
                                         if (xx >= 0 && yy >= 0 && xx < nx && yy < ny)
                                             mg[(size_t)yy * nx + xx] += w;
+                            } else if (nxd || nyd) {
+                                /* the crossing may land in the cell across the near edge(s) */
+                                long cx[2] = {ix, ix + nxd}, cy[2] = {iy, iy + nyd};
+                                for (int a = 0; a < (nyd ? 2 : 1); a++)
+                                    for (int b = 0; b < (nxd ? 2 : 1); b++) {
+                                        long xx = cx[b], yy = cy[a];
+                                        if (xx >= 0 && yy >= 0 && xx < nx && yy < ny)
+                                            mg[(size_t)yy * nx + xx] += w;
+                                    }
                             }
                         }
                     }

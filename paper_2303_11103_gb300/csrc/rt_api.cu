@@ -1,0 +1,344 @@
+// rt_api.cu -- the C ABI (include/rt.h): context, argument checks, buffer
+// ownership and error reporting around the kernels.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "rt_internal.h"
+
+int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* out);
+int export_candidates(rt_ctx* ctx, int32_t* tx, int32_t* depth, int32_t* seq, int64_t* wit);
+int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
+int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
+                 float* g_pos, float* g_ypr);
+int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
+              int64_t n_pairs);
+int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, const float* gH,
+                  float* ga, float* gt, int64_t n_pairs);
+int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t first, int64_t count, bool zero,
+                    int tx_port, float* gain, uint32_t* hits);
+int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out);
+
+cudaError_t buf_reserve(DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return e;
+    }
+    b.bytes = want;
+    return cudaSuccess;
+}
+
+void buf_free(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int set_err(rt_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int set_cuda(rt_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? RT_ERR_OOM : RT_ERR_CUDA, m);
+}
+
+DevScene dev_scene(rt_ctx* ctx) {
+    DevScene s;
+    s.nodes = bp<float4>(ctx->nodes);
+    s.tris = bp<float4>(ctx->tris);
+    s.tris_o = bp<float4>(ctx->tris_o);
+    s.planes = bp<float4>(ctx->planes);
+    s.mat = bp<int32_t>(ctx->mat);
+    s.mats = bp<float2>(ctx->mats);
+    s.n_tris = ctx->n_tris;
+    s.n_nodes = ctx->n_nodes;
+    s.n_mat = ctx->n_mat;
+    s.tmin = ctx->tmin;
+    return s;
+}
+
+static int use_device(rt_ctx* ctx) {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return set_cuda(ctx, e, "cudaSetDevice");
+    return RT_OK;
+}
+
+#define CHECK_CTX(c)                       \
+    do {                                   \
+        if (!(c)) return RT_ERR_INVALID_ARG; \
+        int e__ = use_device(c);           \
+        if (e__) return e__;               \
+    } while (0)
+
+static bool valid_antenna(const rt_antenna* a) {
+    return a && a->kind >= RT_ANT_ISO && a->kind <= RT_ANT_TR38901 && (a->n_ports == 1 || a->n_ports == 2);
+}
+
+extern "C" {
+
+int rt_create(rt_ctx** out, int device, void* stream) {
+    if (!out) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return RT_ERR_INVALID_ARG;
+    }
+    rt_ctx* ctx = new (std::nothrow) rt_ctx();
+    if (!ctx) return RT_ERR_OOM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return RT_ERR_CUDA;
+    }
+    if (buf_reserve(ctx->counters, 64) != cudaSuccess || buf_reserve(ctx->status, 64) != cudaSuccess) {
+        buf_free(ctx->counters);
+        delete ctx;
+        return RT_ERR_OOM;
+    }
+    *out = ctx;
+    return RT_OK;
+}
+
+int rt_destroy(rt_ctx* ctx) {
+    if (!ctx) return RT_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->mat, &ctx->mats, &ctx->tx_pos,
+                      &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->keys, &ctx->keys_alt,
+                      &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
+                      &ctx->cand_img, &ctx->path_key, &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
+                      &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
+                      &ctx->sort_hist, &ctx->counters, &ctx->status, &ctx->perm})
+        buf_free(*b);
+    delete ctx;
+    return RT_OK;
+}
+
+int rt_set_stream(rt_ctx* ctx, void* stream) {
+    CHECK_CTX(ctx);
+    ctx->stream = (cudaStream_t)stream;
+    return RT_OK;
+}
+
+int rt_last_error(const rt_ctx* ctx, char* buf, size_t len) {
+    if (!ctx || !buf || len == 0) return RT_ERR_INVALID_ARG;
+    size_t n = std::min(len - 1, ctx->err.size());
+    memcpy(buf, ctx->err.data(), n);
+    buf[n] = 0;
+    return RT_OK;
+}
+
+int rt_set_frequency(rt_ctx* ctx, double fc) {
+    CHECK_CTX(ctx);
+    if (!(fc > 0.0)) return set_err(ctx, RT_ERR_INVALID_ARG, "frequency must be positive");
+    ctx->fc = fc;
+    return RT_OK;
+}
+
+int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t* mat_id, const float* mat_params,
+                  int32_t n_mat) {
+    CHECK_CTX(ctx);
+    if (n_tris < 0 || n_tris >= (1ll << 30) || n_mat <= 0 || !mat_params || (n_tris > 0 && (!verts || !mat_id)))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "load_scene: bad arguments");
+    ctx->has_scene = false;
+    ctx->n_paths = 0;
+    ctx->n_cand = 0;
+    ctx->n_mat = n_mat;
+    RT_TRY(buf_reserve(ctx->mats, sizeof(float) * 2 * n_mat));
+    RT_TRY(cudaMemcpyAsync(ctx->mats.p, mat_params, sizeof(float) * 2 * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
+    RT_TRY(buf_reserve(ctx->mat, sizeof(int32_t) * std::max<int64_t>(n_tris, 1)));
+    if (n_tris > 0)
+        RT_TRY(cudaMemcpyAsync(ctx->mat.p, mat_id, sizeof(int32_t) * n_tris, cudaMemcpyDeviceToDevice, ctx->stream));
+    int e = bvh_build(ctx, verts, n_tris);
+    if (e) return e;
+    ctx->has_scene = true;
+    return RT_OK;
+}
+
+int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat) {
+    CHECK_CTX(ctx);
+    if (!ctx->has_scene || n_mat != ctx->n_mat || !mat_params)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "set_materials: material count differs from the scene's");
+    RT_TRY(cudaMemcpyAsync(ctx->mats.p, mat_params, sizeof(float) * 2 * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
+    return RT_OK;
+}
+
+static int set_devices(rt_ctx* ctx, DevBuf& pos, DevBuf& ypr, const float* p, const float* y, int32_t n) {
+    RT_TRY(buf_reserve(pos, sizeof(float) * 3 * std::max(n, 1)));
+    RT_TRY(buf_reserve(ypr, sizeof(float) * 3 * std::max(n, 1)));
+    if (n > 0) {
+        RT_TRY(cudaMemcpyAsync(pos.p, p, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (y)
+            RT_TRY(cudaMemcpyAsync(ypr.p, y, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+        else
+            RT_TRY(cudaMemsetAsync(ypr.p, 0, sizeof(float) * 3 * n, ctx->stream));
+    }
+    return RT_OK;
+}
+
+int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const rt_antenna* pat) {
+    CHECK_CTX(ctx);
+    if (n < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_tx: bad arguments");
+    int e = set_devices(ctx, ctx->tx_pos, ctx->tx_ypr, pos, ypr, n);
+    if (e) return e;
+    ctx->n_tx = n;
+    ctx->tx_ant = {pat->kind, pat->n_ports, {pat->slant[0], pat->slant[1]}};
+    ctx->rx_sets = false;
+    ctx->n_paths = 0;
+    return RT_OK;
+}
+
+int rt_set_rx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t m, const rt_antenna* pat,
+              const int32_t* off_host) {
+    CHECK_CTX(ctx);
+    if (m < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: bad arguments");
+    if (off_host) {
+        if (ctx->n_tx < 1) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: receiver sets need set_tx first");
+        if (off_host[0] != 0 || off_host[ctx->n_tx] != m)
+            return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: offsets must start at 0 and end at m");
+        for (int t = 0; t < ctx->n_tx; t++)
+            if (off_host[t + 1] < off_host[t]) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: decreasing offsets");
+    }
+    int e = set_devices(ctx, ctx->rx_pos, ctx->rx_ypr, pos, ypr, m);
+    if (e) return e;
+    ctx->n_rx = m;
+    ctx->rx_ant = {pat->kind, pat->n_ports, {pat->slant[0], pat->slant[1]}};
+    ctx->rx_sets = off_host != nullptr;
+    ctx->rx_off.assign(off_host ? off_host : nullptr, off_host ? off_host + ctx->n_tx + 1 : nullptr);
+    if (ctx->rx_sets) {
+        RT_TRY(buf_reserve(ctx->rx_off_d, sizeof(int32_t) * (ctx->n_tx + 1)));
+        RT_TRY(cudaMemcpyAsync(ctx->rx_off_d.p, ctx->rx_off.data(), sizeof(int32_t) * (ctx->n_tx + 1),
+                               cudaMemcpyHostToDevice, ctx->stream));
+        RT_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->n_paths = 0;
+    return RT_OK;
+}
+
+int rt_ray_directions(rt_ctx* ctx, int64_t num_rays, int64_t first, int64_t n, float* dirs) {
+    CHECK_CTX(ctx);
+    if (num_rays < 1 || first < 0 || n < 0 || first + n > num_rays || (n > 0 && !dirs))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "ray_directions: bad range");
+    return launch_dirs(ctx, num_rays, first, n, dirs);
+}
+
+int rt_num_pairs(const rt_ctx* ctx, int64_t* n) {
+    if (!ctx || !n) return RT_ERR_INVALID_ARG;
+    *n = ctx->rx_sets ? (int64_t)ctx->rx_off[ctx->n_tx] : (int64_t)ctx->n_tx * ctx->n_rx;
+    return RT_OK;
+}
+
+int rt_compute_paths(rt_ctx* ctx, int32_t max_depth, int64_t num_rays, uint32_t flags, int64_t* num_paths) {
+    CHECK_CTX(ctx);
+    if (!num_paths || max_depth < 0 || max_depth > RT_MAX_DEPTH || num_rays < 0)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "compute_paths: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "compute_paths: scene, transmitters and receivers must be set");
+    *num_paths = 0;
+    ctx->n_paths = 0;
+    return compute_paths_impl(ctx, max_depth, num_rays, flags, num_paths);
+}
+
+int rt_get_paths(rt_ctx* ctx, int64_t* offsets, int32_t* seq, float* points, int32_t* depth, double* length) {
+    CHECK_CTX(ctx);
+    int64_t np = 0;
+    rt_num_pairs(ctx, &np);
+    const int64_t P = ctx->n_paths;
+    const int D = ctx->max_depth;
+    cudaStream_t st = ctx->stream;
+    if (offsets) RT_TRY(cudaMemcpyAsync(offsets, ctx->path_off.p, sizeof(int64_t) * (np + 1), cudaMemcpyDeviceToDevice, st));
+    if (P > 0) {
+        if (seq) RT_TRY(cudaMemcpyAsync(seq, ctx->path_seq.p, sizeof(int32_t) * P * D, cudaMemcpyDeviceToDevice, st));
+        if (points) RT_TRY(cudaMemcpyAsync(points, ctx->path_pts.p, sizeof(float) * 3 * P * D, cudaMemcpyDeviceToDevice, st));
+        if (depth) RT_TRY(cudaMemcpyAsync(depth, ctx->path_depth.p, sizeof(int32_t) * P, cudaMemcpyDeviceToDevice, st));
+        if (length) RT_TRY(cudaMemcpyAsync(length, ctx->path_len.p, sizeof(double) * P, cudaMemcpyDeviceToDevice, st));
+    }
+    return RT_OK;
+}
+
+int rt_get_candidates(rt_ctx* ctx, int64_t* n_out, int32_t* tx, int32_t* depth, int32_t* seq, int64_t* wit) {
+    CHECK_CTX(ctx);
+    if (!n_out) return RT_ERR_INVALID_ARG;
+    *n_out = ctx->n_cand;
+    return export_candidates(ctx, tx, depth, seq, wit);
+}
+
+int rt_get_ray_hits(rt_ctx* ctx, int32_t* hits) {
+    CHECK_CTX(ctx);
+    if (!ctx->recorded_rays || !hits)
+        return set_err(ctx, RT_ERR_NOT_READY, "get_ray_hits: compute_paths ran without RT_RECORD_RAYS");
+    size_t n = (size_t)ctx->n_tx * ctx->num_rays * ctx->max_depth;
+    RT_TRY(cudaMemcpyAsync(hits, ctx->ray_hits.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return RT_OK;
+}
+
+int rt_cir(rt_ctx* ctx, uint32_t flags, float* a, float* tau) {
+    CHECK_CTX(ctx);
+    if ((!a || !tau) && ctx->n_paths > 0) return set_err(ctx, RT_ERR_INVALID_ARG, "cir: null output");
+    return cir_impl(ctx, flags, a, tau);
+}
+
+int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int32_t K, float* H) {
+    CHECK_CTX(ctx);
+    if (K < 0 || (K > 0 && (!freqs || !H)) || ((!a || !tau) && ctx->n_paths > 0))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "freq_response: bad arguments");
+    int64_t np = 0;
+    rt_num_pairs(ctx, &np);
+    return freq_impl(ctx, a, tau, freqs, K, H, np);
+}
+
+int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
+                    float* gain, uint32_t* hits) {
+    CHECK_CTX(ctx);
+    if (!g || !gain || !hits || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 || num_rays < 1 ||
+        tx_port < 0 || tx_port >= ctx->tx_ant.n_ports)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map: scene, transmitters and receivers must be set");
+    RT_TRY(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream));
+    return launch_coverage(ctx, g, max_depth, num_rays, 0, num_rays, true, tx_port, gain, hits);
+}
+
+int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
+                               int64_t first_ray, int64_t ray_count, int32_t tx_port, float* gain, uint32_t* hits) {
+    CHECK_CTX(ctx);
+    if (!g || !gain || !hits || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 || num_rays < 1 ||
+        first_ray < 0 || ray_count < 0 || first_ray + ray_count > num_rays || tx_port < 0 ||
+        tx_port >= ctx->tx_ant.n_ports)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_accumulate: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_accumulate: scene, transmitters and receivers must be set");
+    return launch_coverage(ctx, g, max_depth, num_rays, first_ray, ray_count, false, tx_port, gain, hits);
+}
+
+int rt_cir_backward(rt_ctx* ctx, uint32_t flags, const float* grad_a, const float* grad_tau, float* g_eps,
+                    float* g_sigma, float* g_txpos, float* g_txypr) {
+    CHECK_CTX(ctx);
+    if (!grad_a && ctx->n_paths > 0) return set_err(ctx, RT_ERR_INVALID_ARG, "cir_backward: null grad_a");
+    return cir_vjp_impl(ctx, flags, grad_a, grad_tau, g_eps, g_sigma, g_txpos, g_txypr);
+}
+
+int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int32_t K,
+                              const float* grad_H, float* grad_a, float* grad_tau) {
+    CHECK_CTX(ctx);
+    if (K < 1 || !freqs || !grad_H || ((!a || !tau || !grad_a || !grad_tau) && ctx->n_paths > 0))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "freq_response_backward: bad arguments");
+    int64_t np = 0;
+    rt_num_pairs(ctx, &np);
+    return freq_vjp_impl(ctx, a, tau, freqs, K, grad_H, grad_a, grad_tau, np);
+}
+
+}  // extern "C"

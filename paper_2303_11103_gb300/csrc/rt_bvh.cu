@@ -1,0 +1,333 @@
+// rt_bvh.cu -- GPU LBVH builder (Morton codes, radix sort, Karras radix
+// tree, bottom-up AABB refit) and conversion to the breadth-first
+// 64-byte-node traversal layout.
+//
+// The paper delegates ray/triangle intersection to Mitsuba 3 (Sec. II); the
+// acceleration structure here is a linear BVH built in parallel on the GPU:
+//   1. per triangle: records, plane, padded AABB, centroid;
+//   2. scene bounds; 30-bit Morton code of each centroid;
+//   3. stable radix sort of the codes (ties keep triangle order, which is
+//      Karras' index-augmented key);
+//   4. one thread per internal node finds its key range and split from the
+//      longest common prefix of neighbouring keys (Karras 2012);
+//   5. leaves walk to the root; the second child to arrive at a node
+//      computes its box (atomic arrival counters);
+//   6. nodes are re-numbered by depth (level order) so the top levels form
+//      a prefix that traversal blocks stage in shared memory.
+#include <algorithm>
+#include <cstring>
+
+#include "rt_internal.h"
+
+namespace {
+
+__device__ __forceinline__ unsigned ord(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// bounds layout (ordered uints): [0..2] vmin, [3..5] vmax, [6..8] cmin, [9..11] cmax
+__global__ void k_prep(const float* __restrict__ v, const int32_t* __restrict__ mat, int T,
+                       float4* __restrict__ tris_o, float4* __restrict__ planes,
+                       float* __restrict__ lbox, float* __restrict__ cent,
+                       unsigned* __restrict__ bounds) {
+    __shared__ unsigned sb[12];
+    if (threadIdx.x < 12) sb[threadIdx.x] = (threadIdx.x % 6) < 3 ? 0xffffffffu : 0u;
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < T) {
+        const float* t = v + 9 * (size_t)i;
+        f3 a = mk(t[0], t[1], t[2]), b = mk(t[3], t[4], t[5]), c = mk(t[6], t[7], t[8]);
+        f3 e1 = b - a, e2 = c - a;
+        tris_o[3 * i] = make_float4(a.x, a.y, a.z, __int_as_float(i));
+        tris_o[3 * i + 1] = make_float4(e1.x, e1.y, e1.z, __int_as_float(mat[i]));
+        tris_o[3 * i + 2] = make_float4(e2.x, e2.y, e2.z, 0.0f);
+        f3 n = cross(e1, e2);
+        float nl = sqrtf(dot(n, n));
+        n = nl > 0.0f ? n * (1.0f / nl) : mk(0.0f, 0.0f, 1.0f);
+        planes[i] = make_float4(n.x, n.y, n.z, dot(n, a));
+        float lo[3] = {fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z))};
+        float hi[3] = {fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z))};
+        float ce[3] = {(a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                       (a.z + b.z + c.z) * (1.0f / 3.0f)};
+        for (int k = 0; k < 3; k++) {
+            lbox[6 * (size_t)i + k] = lo[k];
+            lbox[6 * (size_t)i + 3 + k] = hi[k];
+            cent[3 * (size_t)i + k] = ce[k];
+            atomicMin(&sb[k], ord(lo[k]));
+            atomicMax(&sb[3 + k], ord(hi[k]));
+            atomicMin(&sb[6 + k], ord(ce[k]));
+            atomicMax(&sb[9 + k], ord(ce[k]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        if ((threadIdx.x % 6) < 3)
+            atomicMin(&bounds[threadIdx.x], sb[threadIdx.x]);
+        else
+            atomicMax(&bounds[threadIdx.x], sb[threadIdx.x]);
+    }
+}
+
+__device__ __forceinline__ unsigned expand10(unsigned x) {
+    x &= 1023u;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+__global__ void k_morton(const float* __restrict__ cent, int T, const unsigned* __restrict__ bounds,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    unsigned q[3];
+    for (int k = 0; k < 3; k++) {
+        float lo = unord(bounds[6 + k]), hi = unord(bounds[9 + k]);
+        float span = hi - lo;
+        float f = span > 0.0f ? (cent[3 * (size_t)i + k] - lo) / span : 0.5f;
+        q[k] = (unsigned)fminf(fmaxf(f * 1024.0f, 0.0f), 1023.0f);
+    }
+    keys[i] = (uint64_t)((expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]));
+    vals[i] = (uint32_t)i;
+}
+
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned a = (unsigned)k[i], b = (unsigned)k[j];
+    if (a == b) return 32 + __clz((unsigned)i ^ (unsigned)j);
+    return __clz(a ^ b);
+}
+
+// Karras 2012: internal node i of n-1; children: >= 0 internal, < 0 leaf ~k.
+__global__ void k_karras(const uint64_t* __restrict__ k, int n, int2* __restrict__ child,
+                         int* __restrict__ par_int, int* __restrict__ par_leaf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(k, n, i, i - d);
+    int lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(k, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int g = i + s * d + min(d, 0);
+    int left = (min(i, j) == g) ? ~g : g;
+    int right = (max(i, j) == g + 1) ? ~(g + 1) : g + 1;
+    child[i] = make_int2(left, right);
+    if (left < 0) par_leaf[~left] = i; else par_int[left] = i;
+    if (right < 0) par_leaf[~right] = i; else par_int[right] = i;
+    if (i == 0) par_int[0] = -1;
+}
+
+__device__ __forceinline__ void load_box(const float* b, float* o) {
+    for (int k = 0; k < 6; k++) o[k] = __ldcg(b + k);
+}
+
+// Bottom-up AABBs; leaf boxes padded by `pad`.
+__global__ void k_refit(int n, const uint32_t* __restrict__ leaf_tri, const float* __restrict__ lbox,
+                        const int2* __restrict__ child, const int* __restrict__ par_int,
+                        const int* __restrict__ par_leaf, float* __restrict__ ibox,
+                        int* __restrict__ flag, float pad) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int p = par_leaf[k];
+    for (int steps = 0; p >= 0 && steps < n; steps++) {
+        __threadfence();
+        if (atomicAdd(&flag[p], 1) == 0) return;
+        int2 c = child[p];
+        float a[6], b[6];
+        if (c.x < 0) { load_box(lbox + 6 * (size_t)leaf_tri[~c.x], a); for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; } }
+        else load_box(ibox + 6 * (size_t)c.x, a);
+        if (c.y < 0) { load_box(lbox + 6 * (size_t)leaf_tri[~c.y], b); for (int q = 0; q < 3; q++) { b[q] -= pad; b[3 + q] += pad; } }
+        else load_box(ibox + 6 * (size_t)c.y, b);
+        for (int q = 0; q < 3; q++) {
+            __stcg(ibox + 6 * (size_t)p + q, fminf(a[q], b[q]));
+            __stcg(ibox + 6 * (size_t)p + 3 + q, fmaxf(a[3 + q], b[3 + q]));
+        }
+        p = par_int[p];
+    }
+}
+
+__global__ void k_depth(int m, const int* __restrict__ par_int, uint64_t* __restrict__ keys,
+                        int* __restrict__ maxdepth) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int d = 0;
+    for (int p = par_int[i]; p >= 0 && d < m; p = par_int[p]) d++;
+    keys[i] = ((uint64_t)d << 32) | (uint32_t)i;
+    atomicMax(maxdepth, d);
+}
+
+__global__ void k_rank(int m, const uint64_t* __restrict__ keys, int* __restrict__ rank) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) rank[(uint32_t)keys[k]] = k;
+}
+
+__global__ void k_emit(int m, const uint64_t* __restrict__ order, const int* __restrict__ rank,
+                       const int2* __restrict__ child, const float* __restrict__ ibox,
+                       const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri,
+                       float pad, float4* __restrict__ nodes) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    int o = (int)(uint32_t)order[k];
+    int2 c = child[o];
+    float a[6], b[6];
+    int na, nb;
+    if (c.x < 0) { for (int q = 0; q < 6; q++) a[q] = lbox[6 * (size_t)leaf_tri[~c.x] + q]; for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; } na = c.x; }
+    else { for (int q = 0; q < 6; q++) a[q] = ibox[6 * (size_t)c.x + q]; na = rank[c.x]; }
+    if (c.y < 0) { for (int q = 0; q < 6; q++) b[q] = lbox[6 * (size_t)leaf_tri[~c.y] + q]; for (int q = 0; q < 3; q++) { b[q] -= pad; b[3 + q] += pad; } nb = c.y; }
+    else { for (int q = 0; q < 6; q++) b[q] = ibox[6 * (size_t)c.y + q]; nb = rank[c.y]; }
+    float4* p = nodes + 4 * (size_t)k;
+    p[0] = make_float4(a[0], a[1], a[2], a[3]);
+    p[1] = make_float4(a[4], a[5], b[0], b[1]);
+    p[2] = make_float4(b[2], b[3], b[4], b[5]);
+    p[3] = make_float4(__int_as_float(na), __int_as_float(nb), 0.0f, 0.0f);
+}
+
+__global__ void k_leaf_tris(int n, const uint32_t* __restrict__ leaf_tri, const float4* __restrict__ tris_o,
+                            float4* __restrict__ tris) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t t = leaf_tri[k];
+    tris[3 * (size_t)k] = tris_o[3 * (size_t)t];
+    tris[3 * (size_t)k + 1] = tris_o[3 * (size_t)t + 1];
+    tris[3 * (size_t)k + 2] = tris_o[3 * (size_t)t + 2];
+}
+
+__global__ void k_single_leaf(const float* __restrict__ lbox, float pad, float4* __restrict__ nodes) {
+    // one triangle: both children are leaf 0
+    float a[6];
+    for (int q = 0; q < 6; q++) a[q] = lbox[q];
+    for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; }
+    nodes[0] = make_float4(a[0], a[1], a[2], a[3]);
+    nodes[1] = make_float4(a[4], a[5], a[0], a[1]);
+    nodes[2] = make_float4(a[2], a[3], a[4], a[5]);
+    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
+}
+
+float host_unord(unsigned u) {
+    unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+}  // namespace
+
+int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
+    const int T = (int)n_tris;
+    cudaStream_t st = ctx->stream;
+    ctx->n_tris = T;
+    if (T == 0) {
+        ctx->n_nodes = 0;
+        ctx->bvh_depth = 0;
+        ctx->extent = 1.0f;
+        ctx->tmin = 2e-6f;
+        return RT_OK;
+    }
+    const int B = 256;
+    const int gT = (T + B - 1) / B;
+    RT_TRY(buf_reserve(ctx->tris_o, sizeof(float4) * 3 * (size_t)T));
+    RT_TRY(buf_reserve(ctx->tris, sizeof(float4) * 3 * (size_t)T));
+    RT_TRY(buf_reserve(ctx->planes, sizeof(float4) * (size_t)T));
+    int m = std::max(T - 1, 1);
+    RT_TRY(buf_reserve(ctx->nodes, sizeof(float4) * 4 * (size_t)m));
+    // build temporaries (freed at the end)
+    DevBuf lbox, cent, bounds, keys, keys2, vals, vals2, child, pint, pleaf, ibox, flag, dkeys, dkeys2,
+        rank, maxd;
+    auto cleanup = [&]() {
+        for (DevBuf* b : {&lbox, &cent, &bounds, &keys, &keys2, &vals, &vals2, &child, &pint, &pleaf,
+                          &ibox, &flag, &dkeys, &dkeys2, &rank, &maxd})
+            buf_free(*b);
+    };
+#define BT(expr)                                               \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) { cleanup(); return set_cuda(ctx, e_, #expr); } \
+    } while (0)
+    BT(buf_reserve(lbox, sizeof(float) * 6 * (size_t)T));
+    BT(buf_reserve(cent, sizeof(float) * 3 * (size_t)T));
+    BT(buf_reserve(bounds, sizeof(unsigned) * 12));
+    unsigned init[12];
+    for (int k = 0; k < 12; k++) init[k] = (k % 6) < 3 ? 0xffffffffu : 0u;
+    BT(cudaMemcpyAsync(bounds.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_prep<<<gT, B, 0, st>>>(verts, bp<int32_t>(ctx->mat), T, bp<float4>(ctx->tris_o),
+                             bp<float4>(ctx->planes), bp<float>(lbox), bp<float>(cent),
+                             bp<unsigned>(bounds));
+    BT(cudaGetLastError());
+    unsigned hb[12];
+    BT(cudaMemcpyAsync(hb, bounds.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    BT(cudaStreamSynchronize(st));
+    float ext = 0.0f;
+    for (int k = 0; k < 3; k++) ext = std::max(ext, host_unord(hb[3 + k]) - host_unord(hb[k]));
+    if (!(ext > 0.0f)) ext = 1.0f;
+    ctx->extent = ext;
+    ctx->tmin = 2e-6f * ext;
+    const float pad = 1e-6f * ext;
+    BT(buf_reserve(keys, sizeof(uint64_t) * T));
+    BT(buf_reserve(keys2, sizeof(uint64_t) * T));
+    BT(buf_reserve(vals, sizeof(uint32_t) * T));
+    BT(buf_reserve(vals2, sizeof(uint32_t) * T));
+    k_morton<<<gT, B, 0, st>>>(bp<float>(cent), T, bp<unsigned>(bounds), bp<uint64_t>(keys),
+                               bp<uint32_t>(vals));
+    BT(cudaGetLastError());
+    BT(radix_sort64(ctx, bp<uint64_t>(keys), bp<uint64_t>(keys2), bp<uint32_t>(vals),
+                    bp<uint32_t>(vals2), T, 30));
+    const uint32_t* leaf_tri = bp<uint32_t>(vals);
+    if (T == 1) {
+        k_single_leaf<<<1, 1, 0, st>>>(bp<float>(lbox), pad, bp<float4>(ctx->nodes));
+        BT(cudaGetLastError());
+        ctx->n_nodes = 1;
+        ctx->bvh_depth = 1;
+    } else {
+        BT(buf_reserve(child, sizeof(int2) * m));
+        BT(buf_reserve(pint, sizeof(int) * m));
+        BT(buf_reserve(pleaf, sizeof(int) * T));
+        BT(buf_reserve(ibox, sizeof(float) * 6 * (size_t)m));
+        BT(buf_reserve(flag, sizeof(int) * m));
+        BT(cudaMemsetAsync(flag.p, 0, sizeof(int) * m, st));
+        int gm = (m + B - 1) / B;
+        k_karras<<<gm, B, 0, st>>>(bp<uint64_t>(keys), T, bp<int2>(child), bp<int>(pint), bp<int>(pleaf));
+        BT(cudaGetLastError());
+        k_refit<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), bp<int2>(child), bp<int>(pint),
+                                  bp<int>(pleaf), bp<float>(ibox), bp<int>(flag), pad);
+        BT(cudaGetLastError());
+        BT(buf_reserve(dkeys, sizeof(uint64_t) * m));
+        BT(buf_reserve(dkeys2, sizeof(uint64_t) * m));
+        BT(buf_reserve(rank, sizeof(int) * m));
+        BT(buf_reserve(maxd, sizeof(int)));
+        BT(cudaMemsetAsync(maxd.p, 0, sizeof(int), st));
+        k_depth<<<gm, B, 0, st>>>(m, bp<int>(pint), bp<uint64_t>(dkeys), bp<int>(maxd));
+        BT(cudaGetLastError());
+        BT(radix_sort64(ctx, bp<uint64_t>(dkeys), bp<uint64_t>(dkeys2), nullptr, nullptr, m, 40));
+        k_rank<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank));
+        k_emit<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank), bp<int2>(child), bp<float>(ibox),
+                                 bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
+        BT(cudaGetLastError());
+        int hd = 0;
+        BT(cudaMemcpyAsync(&hd, maxd.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BT(cudaStreamSynchronize(st));
+        ctx->n_nodes = m;
+        ctx->bvh_depth = hd + 1;
+    }
+    k_leaf_tris<<<gT, B, 0, st>>>(T, leaf_tri, bp<float4>(ctx->tris_o), bp<float4>(ctx->tris));
+    BT(cudaGetLastError());
+    BT(cudaStreamSynchronize(st));
+    cleanup();
+#undef BT
+    if (ctx->bvh_depth + 1 >= RT_STACK)
+        return set_err(ctx, RT_ERR_CAPACITY, "BVH deeper than the traversal stack");
+    return RT_OK;
+}

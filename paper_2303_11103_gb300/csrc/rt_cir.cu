@@ -1,0 +1,439 @@
+// rt_cir.cu -- channel impulse response (Listing 3: a_i, tau_i), OFDM
+// frequency response (Sec. III-A) and their vector-Jacobian products
+// (Sec. I/II: gradients w.r.t. materials and transmitter pose).
+//
+// The field of one path is written once over a scalar type (rt_field.cuh).
+// The VJP kernel replays the stored path (no re-trace): for each group of
+// four of the path's local parameters it runs the field with Dual<4>
+// tangents and contracts the Jacobian with the upstream gradient. A path
+// depends on at most 6 + 2*depth parameters (tx xyz, yaw/pitch/roll, eps_r
+// and sigma of the materials it reflects on), so per-path forward tangents
+// are cheaper than a taped reverse pass.
+#include "rt_field.cuh"
+#include "rt_internal.h"
+
+namespace {
+
+struct CirParams {
+    DevScene s;
+    const float* tx_pos;
+    const float* tx_ypr;
+    const float* rx_pos;
+    const float* rx_ypr;
+    DevAntenna txa, rxa;
+    const int32_t* seq;      // [P*D]
+    const int32_t* depth;    // [P]
+    const double* len;       // [P]
+    const int32_t* pair_tx;  // [P*2]
+    int D;
+    int64_t P;
+    double lambda;
+    float inv_we0;
+    uint32_t flags;
+};
+
+template <class S>
+struct PathIn {
+    V3<S> tx;
+    S yaw, pitch, roll;
+    S eps[RT_MAX_DEPTH], sig[RT_MAX_DEPTH];
+};
+
+// a[p][q] (rx port p, tx port q) and the path length (as S) of path i.
+template <class S>
+__device__ __forceinline__ void path_field(const CirParams& c, int64_t i, const PathIn<S>& in, f3 rx,
+                                           f3 rx_ypr, Cx<S> a[4], S& L) {
+    const int K = c.depth[i];
+    const int32_t* ids = c.seq + i * c.D;
+    V3<S> I[RT_MAX_DEPTH + 1];
+    I[0] = in.tx;
+    for (int k = 1; k <= K; k++) {
+        float4 pl = __ldg(c.s.planes + ids[k - 1]);
+        V3<S> n = v_const<S>(xyz(pl));
+        S sd = v_dot(I[k - 1], n) - pl.w;
+        I[k] = v_sub(I[k - 1], v_scale(n, sd * 2.0f));
+    }
+    V3<S> P[RT_MAX_DEPTH + 2];
+    P[0] = in.tx;
+    P[K + 1] = v_const<S>(rx);
+    for (int k = K; k >= 1; k--) {
+        float4 pl = __ldg(c.s.planes + ids[k - 1]);
+        V3<S> n = v_const<S>(xyz(pl));
+        V3<S> dir = v_sub(I[k], P[k + 1]);
+        S sp = (pl.w - v_dot(P[k + 1], n)) / v_dot(dir, n);
+        P[k] = v_add(P[k + 1], v_scale(dir, sp));
+    }
+    V3<S> kd[RT_MAX_DEPTH + 1];
+    L = SConst<S>::make(0.0f);
+    for (int j = 0; j <= K; j++) {
+        V3<S> sg = v_sub(P[j + 1], P[j]);
+        S l = s_sqrt(v_dot(sg, sg));
+        L = L + l;
+        kd[j] = v_scale(sg, SConst<S>::make(1.0f) / l);
+    }
+    Rot<S> Rt = rot_ypr(in.yaw, in.pitch, in.roll);
+    Rot<S> Rr = rot_ypr(SConst<S>::make(rx_ypr.x), SConst<S>::make(rx_ypr.y), SConst<S>::make(rx_ypr.z));
+    Cx<S> E[2][3];
+    for (int q = 0; q < c.txa.n_ports; q++) {
+        V3<S> f = antenna_vec<S>(c.txa.kind, c.txa.slant[q], Rt, kd[0]);
+        E[q][0] = {f.x, SConst<S>::make(0.0f)};
+        E[q][1] = {f.y, SConst<S>::make(0.0f)};
+        E[q][2] = {f.z, SConst<S>::make(0.0f)};
+    }
+    for (int k = 1; k <= K; k++) {
+        f3 n = xyz(__ldg(c.s.planes + ids[k - 1]));
+        for (int q = 0; q < c.txa.n_ports; q++)
+            reflect_field<S>(E[q], kd[k - 1], kd[k], n, in.eps[k - 1], in.sig[k - 1], c.inv_we0);
+    }
+    V3<S> u = v_scale(kd[K], -1.0f);
+    // phase: value from the FP64 length reduced modulo 2 pi, tangents from L
+    double x = c.len[i] / c.lambda;
+    float ph0 = (float)(-2.0 * RT_PI_D * (x - floor(x)));
+    S ph = L * (float)(-2.0 * RT_PI_D / c.lambda);
+    S amp = SConst<S>::make((float)(c.lambda / (4.0 * RT_PI_D))) / L;
+    Cx<S> e;
+    {
+        S phv = with_value(ph, ph0);  // reduced phase value, tangents of -2 pi L / lambda
+        e.re = amp * s_cos(phv);
+        e.im = amp * s_sin(phv);
+    }
+    for (int p = 0; p < c.rxa.n_ports; p++) {
+        V3<S> F = antenna_vec<S>(c.rxa.kind, c.rxa.slant[p], Rr, u);
+        for (int q = 0; q < c.txa.n_ports; q++) {
+            Cx<S> fe = {F.x * E[q][0].re + F.y * E[q][1].re + F.z * E[q][2].re,
+                        F.x * E[q][0].im + F.y * E[q][1].im + F.z * E[q][2].im};
+            a[p * c.txa.n_ports + q] = c_mul(e, fe);
+        }
+    }
+}
+
+__device__ __forceinline__ bool path_enabled(uint32_t flags, int K) {
+    return K == 0 ? (flags & RT_LOS) != 0 : (flags & RT_REFLECTION) != 0;
+}
+
+__global__ void k_cir(CirParams c, float2* __restrict__ a_out, float* __restrict__ tau) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.P) return;
+    int t = c.pair_tx[2 * i], r = c.pair_tx[2 * i + 1];
+    PathIn<float> in;
+    in.tx = {c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]};
+    in.yaw = c.tx_ypr[3 * t];
+    in.pitch = c.tx_ypr[3 * t + 1];
+    in.roll = c.tx_ypr[3 * t + 2];
+    const int K = c.depth[i];
+    for (int k = 0; k < K; k++) {
+        int m = __ldg(c.s.mat + c.seq[i * c.D + k]);
+        float2 mp = __ldg(c.s.mats + m);
+        in.eps[k] = mp.x;
+        in.sig[k] = mp.y;
+    }
+    f3 rx = mk(c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]);
+    f3 ry = mk(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
+    Cx<float> a[4];
+    float L;
+    path_field<float>(c, i, in, rx, ry, a, L);
+    const int np = c.txa.n_ports * c.rxa.n_ports;
+    const bool on = path_enabled(c.flags, K);
+    for (int k = 0; k < np; k++) a_out[i * np + k] = on ? make_float2(a[k].re, a[k].im) : make_float2(0.0f, 0.0f);
+    tau[i] = (float)(c.len[i] / RT_C0_D);
+}
+
+// ----------------------------------------------------------------- VJP of cir
+constexpr int NT = 4;
+
+__global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const float* __restrict__ gtau,
+                          float* g_eps, float* g_sig, float* g_pos, float* g_ypr) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.P) return;
+    const int K = c.depth[i];
+    if (!path_enabled(c.flags, K) && !gtau) return;
+    int t = c.pair_tx[2 * i], r = c.pair_tx[2 * i + 1];
+    // local parameter list: 0..2 tx xyz, 3..5 yaw pitch roll, then (eps, sigma)
+    // of each distinct material along the path
+    int mats[RT_MAX_DEPTH], nm = 0, slot[RT_MAX_DEPTH];
+    for (int k = 0; k < K; k++) {
+        int m = __ldg(c.s.mat + c.seq[i * c.D + k]);
+        int j = 0;
+        while (j < nm && mats[j] != m) j++;
+        if (j == nm) mats[nm++] = m;
+        slot[k] = j;
+    }
+    const int nloc = 6 + 2 * nm;
+    const int np = c.txa.n_ports * c.rxa.n_ports;
+    const bool on = path_enabled(c.flags, K);
+    f3 rx = mk(c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]);
+    f3 ry = mk(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
+    float2 g[4];
+    for (int k = 0; k < np; k++) g[k] = on ? ga[i * np + k] : make_float2(0.0f, 0.0f);
+    const float gt = gtau ? gtau[i] : 0.0f;
+    for (int base = 0; base < nloc; base += NT) {
+        auto var = [&](float v, int idx) {
+            Dual<NT> d = dconst<NT>(v);
+            if (idx >= base && idx < base + NT) d.d[idx - base] = 1.0f;
+            return d;
+        };
+        PathIn<Dual<NT>> in;
+        in.tx = {var(c.tx_pos[3 * t], 0), var(c.tx_pos[3 * t + 1], 1), var(c.tx_pos[3 * t + 2], 2)};
+        in.yaw = var(c.tx_ypr[3 * t], 3);
+        in.pitch = var(c.tx_ypr[3 * t + 1], 4);
+        in.roll = var(c.tx_ypr[3 * t + 2], 5);
+        for (int k = 0; k < K; k++) {
+            float2 mp = __ldg(c.s.mats + mats[slot[k]]);
+            in.eps[k] = var(mp.x, 6 + 2 * slot[k]);
+            in.sig[k] = var(mp.y, 7 + 2 * slot[k]);
+        }
+        Cx<Dual<NT>> a[4];
+        Dual<NT> L;
+        path_field<Dual<NT>>(c, i, in, rx, ry, a, L);
+        for (int j = 0; j < NT && base + j < nloc; j++) {
+            float acc = gt * L.d[j] * (float)(1.0 / RT_C0_D);
+            for (int k = 0; k < np; k++) acc += g[k].x * a[k].re.d[j] + g[k].y * a[k].im.d[j];
+            int idx = base + j;
+            if (idx < 3) {
+                if (g_pos) atomicAdd(g_pos + 3 * t + idx, acc);
+            } else if (idx < 6) {
+                if (g_ypr) atomicAdd(g_ypr + 3 * t + idx - 3, acc);
+            } else {
+                int mi = mats[(idx - 6) >> 1];
+                if ((idx - 6) & 1) { if (g_sig) atomicAdd(g_sig + mi, acc); }
+                else if (g_eps) atomicAdd(g_eps + mi, acc);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- H(f)
+// One block per pair; each thread owns RUN consecutive subcarriers and keeps
+// their accumulators for every port pair in registers. Paths of the pair are
+// staged in shared memory in tiles. Twiddles: one range-reduced sincos per
+// (path, run) and a complex-rotation recurrence across the run (uniform
+// spacing), else a sincos per (path, subcarrier).
+constexpr int HF_RUN = 8;
+constexpr int HF_TILE = 64;
+
+template <int NP>
+__global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, const float2* __restrict__ a,
+                                              const float* __restrict__ tau, const double* __restrict__ freqs,
+                                              int K, int uniform, double f0, double df, float2* __restrict__ H) {
+    __shared__ float2 sa[HF_TILE][NP];
+    __shared__ float st[HF_TILE];
+    const int64_t pair = blockIdx.y;
+    const int64_t b = off[pair], e = off[pair + 1];
+    const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * HF_RUN;
+    float2 acc[HF_RUN][NP];
+#pragma unroll
+    for (int s = 0; s < HF_RUN; s++)
+#pragma unroll
+        for (int q = 0; q < NP; q++) acc[s][q] = make_float2(0.0f, 0.0f);
+    float fk0 = 0.0f;
+    float fl[HF_RUN];
+    if (uniform) {
+        fk0 = (float)(f0 + df * k0);
+    } else {
+#pragma unroll
+        for (int s = 0; s < HF_RUN; s++) fl[s] = k0 + s < K ? (float)freqs[k0 + s] : 0.0f;
+    }
+    const float dff = (float)df;
+    for (int64_t tb = b; tb < e; tb += HF_TILE) {
+        int n = (int)min((int64_t)HF_TILE, e - tb);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n * NP; j += blockDim.x) sa[j / NP][j % NP] = a[(tb + j / NP) * NP + j % NP];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) st[j] = tau[tb + j];
+        __syncthreads();
+        if (k0 >= K) continue;
+        for (int j = 0; j < n; j++) {
+            const float t = st[j];
+            if (uniform) {
+                // w_k = exp(-j 2 pi f_k tau): cycles reduced to [-0.5, 0.5) before sincos
+                float cyc = fk0 * t;
+                cyc -= rintf(cyc);
+                float s0, c0;
+                __sincosf(-2.0f * RT_PI_F * cyc, &s0, &c0);
+                float cd = dff * t;
+                cd -= rintf(cd);
+                float sd, cdd;
+                __sincosf(-2.0f * RT_PI_F * cd, &sd, &cdd);
+                float wr = c0, wi = s0;
+#pragma unroll
+                for (int s = 0; s < HF_RUN; s++) {
+#pragma unroll
+                    for (int q = 0; q < NP; q++) {
+                        float2 av = sa[j][q];
+                        acc[s][q].x = fmaf(av.x, wr, fmaf(-av.y, wi, acc[s][q].x));
+                        acc[s][q].y = fmaf(av.x, wi, fmaf(av.y, wr, acc[s][q].y));
+                    }
+                    float nr = wr * cdd - wi * sd;
+                    wi = wr * sd + wi * cdd;
+                    wr = nr;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < HF_RUN; s++) {
+                    float cyc = fl[s] * t;
+                    cyc -= rintf(cyc);
+                    float wi, wr;
+                    __sincosf(-2.0f * RT_PI_F * cyc, &wi, &wr);
+#pragma unroll
+                    for (int q = 0; q < NP; q++) {
+                        float2 av = sa[j][q];
+                        acc[s][q].x = fmaf(av.x, wr, fmaf(-av.y, wi, acc[s][q].x));
+                        acc[s][q].y = fmaf(av.x, wi, fmaf(av.y, wr, acc[s][q].y));
+                    }
+                }
+            }
+        }
+    }
+    if (k0 >= K) return;
+#pragma unroll
+    for (int q = 0; q < NP; q++)
+#pragma unroll
+        for (int s = 0; s < HF_RUN; s++)
+            if (k0 + s < K) H[(pair * NP + q) * K + k0 + s] = acc[s][q];
+}
+
+// VJP of H: grad_a_i = sum_k gH_k conj(w_ik); grad_tau_i = sum_k Re(conj(gH_k) a_i (-j 2 pi f_k) w_ik)
+template <int NP>
+__global__ void __launch_bounds__(128) k_freq_vjp(const int64_t* __restrict__ off, const float2* __restrict__ a,
+                                                  const float* __restrict__ tau, const double* __restrict__ freqs,
+                                                  int K, const float2* __restrict__ gH, float2* __restrict__ ga,
+                                                  float* __restrict__ gt) {
+    __shared__ float red[NP * 2 + 1][4];
+    const int64_t pair = blockIdx.x;
+    const int64_t b = off[pair], e = off[pair + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t i = b; i < e; i++) {
+        const float t = tau[i];
+        float2 av[NP];
+        for (int q = 0; q < NP; q++) av[q] = a[i * NP + q];
+        float sr[NP], si[NP], sg = 0.0f;
+        for (int q = 0; q < NP; q++) { sr[q] = 0.0f; si[q] = 0.0f; }
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            float f = (float)freqs[k];
+            float cyc = f * t;
+            cyc -= rintf(cyc);
+            float wi, wr;
+            __sincosf(-2.0f * RT_PI_F * cyc, &wi, &wr);
+            for (int q = 0; q < NP; q++) {
+                float2 g = gH[(pair * NP + q) * K + k];
+                // g * conj(w)
+                sr[q] += g.x * wr + g.y * wi;
+                si[q] += g.y * wr - g.x * wi;
+                // Re(conj(g) * a * (-j 2 pi f) * w)
+                float awr = av[q].x * wr - av[q].y * wi, awi = av[q].x * wi + av[q].y * wr;
+                // (-j c)(awr + j awi) = c awi - j c awr, with c = 2 pi f
+                float c = 2.0f * RT_PI_F * f;
+                float zr = c * awi, zi = -c * awr;
+                sg += g.x * zr + g.y * zi;
+            }
+        }
+        float v[NP * 2 + 1];
+        for (int q = 0; q < NP; q++) { v[2 * q] = sr[q]; v[2 * q + 1] = si[q]; }
+        v[NP * 2] = sg;
+        for (int j = 0; j < NP * 2 + 1; j++) {
+            float x = v[j];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) red[j][w] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < NP; q++) {
+                float xr = 0.0f, xi = 0.0f;
+                for (int ww = 0; ww < 4; ww++) { xr += red[2 * q][ww]; xi += red[2 * q + 1][ww]; }
+                ga[i * NP + q] = make_float2(xr, xi);
+            }
+            float s = 0.0f;
+            for (int ww = 0; ww < 4; ww++) s += red[NP * 2][ww];
+            gt[i] = s;
+        }
+        __syncthreads();
+    }
+}
+
+CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
+    CirParams c;
+    c.s = dev_scene(ctx);
+    c.tx_pos = bp<float>(ctx->tx_pos);
+    c.tx_ypr = bp<float>(ctx->tx_ypr);
+    c.rx_pos = bp<float>(ctx->rx_pos);
+    c.rx_ypr = bp<float>(ctx->rx_ypr);
+    c.txa = ctx->tx_ant;
+    c.rxa = ctx->rx_ant;
+    c.seq = bp<int32_t>(ctx->path_seq);
+    c.depth = bp<int32_t>(ctx->path_depth);
+    c.len = bp<double>(ctx->path_len);
+    c.pair_tx = bp<int32_t>(ctx->path_pair);
+    c.D = ctx->max_depth;
+    c.P = ctx->n_paths;
+    c.lambda = RT_C0_D / ctx->fc;
+    c.inv_we0 = (float)(1.0 / (2.0 * RT_PI_D * ctx->fc * RT_EPS0_D));
+    c.flags = flags;
+    return c;
+}
+
+template <int NP>
+void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, int uniform,
+                 double f0, double df, float* H, int64_t n_pairs) {
+    dim3 grid((unsigned)((K + 128 * HF_RUN - 1) / (128 * HF_RUN)), (unsigned)n_pairs);
+    k_freq<NP><<<grid, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
+                                              uniform, f0, df, (float2*)H);
+}
+
+template <int NP>
+void launch_freq_vjp(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K,
+                     const float* gH, float* ga, float* gt, int64_t n_pairs) {
+    k_freq_vjp<NP><<<(unsigned)n_pairs, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau,
+                                                               freqs, K, (const float2*)gH, (float2*)ga, gt);
+}
+
+}  // namespace
+
+int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau) {
+    if (ctx->n_paths == 0) return RT_OK;
+    CirParams c = make_cir(ctx, flags);
+    k_cir<<<(unsigned)((c.P + 127) / 128), 128, 0, ctx->stream>>>(c, (float2*)a, tau);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
+                 float* g_pos, float* g_ypr) {
+    if (ctx->n_paths == 0) return RT_OK;
+    CirParams c = make_cir(ctx, flags);
+    k_cir_vjp<<<(unsigned)((c.P + 63) / 64), 64, 0, ctx->stream>>>(c, (const float2*)ga, gtau, g_eps, g_sig, g_pos,
+                                                                  g_ypr);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
+              int64_t n_pairs) {
+    if (K <= 0 || n_pairs <= 0) return RT_OK;
+    std::vector<double> hf(K);
+    RT_TRY(cudaMemcpyAsync(hf.data(), freqs, sizeof(double) * K, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_TRY(cudaStreamSynchronize(ctx->stream));
+    int uniform = 1;
+    double f0 = hf[0], df = K > 1 ? hf[1] - hf[0] : 0.0;
+    for (int k = 1; k < K && uniform; k++)
+        if (fabs(hf[k] - (f0 + df * k)) > 1e-9 * (fabs(hf[k]) + 1.0)) uniform = 0;
+    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
+    switch (np) {
+        case 1: launch_freq<1>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
+        case 2: launch_freq<2>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
+        default: launch_freq<4>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
+    }
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, const float* gH,
+                  float* ga, float* gt, int64_t n_pairs) {
+    if (K <= 0 || n_pairs <= 0) return RT_OK;
+    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
+    switch (np) {
+        case 1: launch_freq_vjp<1>(ctx, a, tau, freqs, K, gH, ga, gt, n_pairs); break;
+        case 2: launch_freq_vjp<2>(ctx, a, tau, freqs, K, gH, ga, gt, n_pairs); break;
+        default: launch_freq_vjp<4>(ctx, a, tau, freqs, K, gH, ga, gt, n_pairs); break;
+    }
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}

@@ -1,0 +1,97 @@
+// rt_internal.h -- host-side context and launcher declarations shared by the
+// translation units of the library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+#include "rt_common.cuh"
+
+// Device buffer owned by the context; grows, never shrinks.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+cudaError_t buf_reserve(DevBuf& b, size_t bytes);
+void buf_free(DevBuf& b);
+template <class T>
+T* bp(DevBuf& b) {
+    return reinterpret_cast<T*>(b.p);
+}
+
+struct DevAntenna {
+    int kind;
+    int n_ports;
+    float slant[2];
+};
+
+struct rt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    double fc = 3.5e9;
+    int num_sms = 152;
+
+    // scene
+    bool has_scene = false;
+    int n_tris = 0, n_mat = 0, n_nodes = 0, bvh_depth = 0;
+    float tmin = 0.0f, extent = 1.0f;
+    DevBuf nodes, tris, tris_o, planes, mat, mats;
+
+    // devices
+    int n_tx = 0, n_rx = 0;
+    DevBuf tx_pos, tx_ypr, rx_pos, rx_ypr;
+    DevAntenna tx_ant{0, 1, {0, 0}}, rx_ant{0, 1, {0, 0}};
+    bool rx_sets = false;
+    std::vector<int32_t> rx_off;  // host CSR [n_tx+1] when rx_sets
+    DevBuf rx_off_d;              // device copy
+
+    // path store
+    int max_depth = 0;
+    int64_t num_rays = 0;
+    int64_t n_cand = 0, n_paths = 0;
+    int id_bits = 1, tx_bits = 0, key_bits = 0;
+    bool recorded_rays = false;
+    DevBuf keys, keys_alt, vals, vals_alt;       // SBR keys + positions
+    DevBuf ray_hits;
+    DevBuf cand_key, cand_wit, cand_off, cand_img; // candidates
+    DevBuf path_key, path_key_alt, path_cap_dummy;
+    DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
+    int64_t path_cap = 0;
+
+    // scratch
+    DevBuf sort_hist, counters, status;
+    DevBuf perm;          // direction-coherent ray order
+    int64_t perm_n = -1;
+
+    // tuning
+    int n_smem_nodes = 256;   // BVH nodes staged in shared memory
+    int trace_block = 256;
+    int warp_chunk = 256;     // rays a warp takes per refill
+};
+
+#define RT_TRY(expr)                                       \
+    do {                                                   \
+        cudaError_t e_ = (expr);                           \
+        if (e_ != cudaSuccess) return set_cuda(ctx, e_, #expr); \
+    } while (0)
+
+int set_err(rt_ctx* ctx, int code, const std::string& msg);
+int set_cuda(rt_ctx* ctx, cudaError_t e, const char* what);
+DevScene dev_scene(rt_ctx* ctx);
+
+// radix sort of 64-bit keys with an optional 32-bit payload, bits [0, end_bit)
+// result in keys/vals (alt buffers used as ping-pong), n may be 0
+cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                         uint32_t* vals_alt, int64_t n, int end_bit);
+
+cudaError_t exclusive_scan_u32(rt_ctx* ctx, uint32_t* a, int64_t m);
+
+// BVH build from the context's original-order triangle buffers
+int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris);
+
+// ray order (direction-coherent permutation of [0, N))
+int ensure_perm(rt_ctx* ctx, int64_t N);

@@ -1,0 +1,554 @@
+// rt_paths.cu -- from SBR candidates to stored specular paths (Sec. II-B):
+// duplicate removal (sorted keys + warp compare), candidate images, the
+// image-method validator with visibility tests, canonical path order, the
+// path finalisation (reflection points in FP32, path length in FP64).
+#include "rt_field.cuh"
+#include "rt_internal.h"
+
+namespace {
+
+constexpr int DD_THREADS = 256;
+constexpr int DD_IPT = 8;
+constexpr int DD_TILE = DD_THREADS * DD_IPT;
+
+// ---------------------------------------------------------- duplicate removal
+// A sorted key starts a run if it differs from its predecessor (warp shuffle
+// compare, lane 0 reads the previous key from memory) and is not a sentinel.
+__device__ __forceinline__ bool run_start(const uint64_t* __restrict__ k, int64_t n, int64_t i,
+                                          uint64_t sentinel_from, uint64_t& key) {
+    bool in = i < n;
+    key = in ? k[i] : ~0ull;
+    uint64_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    if ((threadIdx.x & 31) == 0) prev = (in && i > 0) ? k[i - 1] : ~0ull;
+    return in && key < sentinel_from && (i == 0 || prev != key);
+}
+
+__global__ void __launch_bounds__(DD_THREADS) k_dedup_count(const uint64_t* __restrict__ k, int64_t n,
+                                                            uint64_t sentinel_from, uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t wc[DD_THREADS / 32];
+    int64_t base = (int64_t)blockIdx.x * DD_TILE;
+    uint32_t c = 0;
+    for (int j = 0; j < DD_IPT; j++) {
+        uint64_t key;
+        bool f = run_start(k, n, base + j * DD_THREADS + threadIdx.x, sentinel_from, key);
+        c += __popc(__ballot_sync(0xffffffffu, f));
+    }
+    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < DD_THREADS / 32; w++) s += wc[w];
+        cnt[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(DD_THREADS) k_dedup_write(const uint64_t* __restrict__ k,
+                                                            const uint32_t* __restrict__ v, int64_t n,
+                                                            uint64_t sentinel_from,
+                                                            const uint32_t* __restrict__ off,
+                                                            uint64_t* __restrict__ out_k,
+                                                            uint32_t* __restrict__ out_v) {
+    __shared__ uint32_t wbase[DD_THREADS / 32];
+    __shared__ uint32_t run;
+    if (threadIdx.x == 0) run = off[blockIdx.x];
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * DD_TILE;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = 0; j < DD_IPT; j++) {
+        int64_t i = base + j * DD_THREADS + threadIdx.x;
+        uint64_t key;
+        bool f = run_start(k, n, i, sentinel_from, key);
+        unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wbase[w] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t s = run;
+            for (int q = 0; q < DD_THREADS / 32; q++) {
+                uint32_t t = wbase[q];
+                wbase[q] = s;
+                s += t;
+            }
+            run = s;
+        }
+        __syncthreads();
+        if (f) {
+            uint32_t pos = wbase[w] + __popc(m & lanemask_lt());
+            out_k[pos] = key;
+            out_v[pos] = v[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- candidates
+struct KeyFmt {
+    int D, id_bits, depth_shift, tx_shift;
+    __device__ __forceinline__ int depth(uint64_t k) const { return (int)((k >> depth_shift) & 7ull); }
+    __device__ __forceinline__ int tx(uint64_t k) const { return (int)(k >> tx_shift); }
+    __device__ __forceinline__ int id(uint64_t k, int b) const {
+        return (int)((k >> ((D - 1 - b) * id_bits)) & ((1ull << id_bits) - 1ull));
+    }
+};
+
+__global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, int n_tx, KeyFmt f) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tx) {
+        keys[at + t] = (uint64_t)t << f.tx_shift;
+        vals[at + t] = 0xFFFFFFFFu;
+    }
+}
+
+__global__ void k_iota(uint32_t* v, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+// per-tx candidate ranges: off[t] = first candidate with tx >= t
+__global__ void k_cand_off(const uint64_t* __restrict__ ck, int64_t U, int n_tx, KeyFmt f,
+                           int64_t* __restrict__ off) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > n_tx) return;
+    int64_t lo = 0, hi = U;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (f.tx(ck[mid]) < t) lo = mid + 1; else hi = mid;
+    }
+    off[t] = lo;
+}
+
+// images I_k of the transmitter through the candidate's planes (FP32)
+__global__ void k_cand_img(const uint64_t* __restrict__ ck, int64_t U, KeyFmt f,
+                           const float* __restrict__ tx_pos, const float4* __restrict__ planes,
+                           float* __restrict__ img) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= U) return;
+    uint64_t key = ck[c];
+    int K = f.depth(key), t = f.tx(key);
+    f3 I = mk(tx_pos[3 * t], tx_pos[3 * t + 1], tx_pos[3 * t + 2]);
+    for (int k = 0; k < K; k++) {
+        float4 pl = planes[f.id(key, k)];
+        f3 n = xyz(pl);
+        I = I - n * (2.0f * (dot(n, I) - pl.w));
+        img[(c * f.D + k) * 3] = I.x;
+        img[(c * f.D + k) * 3 + 1] = I.y;
+        img[(c * f.D + k) * 3 + 2] = I.z;
+    }
+}
+
+// ------------------------------------------------------------ image method
+struct ValParams {
+    DevScene s;
+    KeyFmt f;
+    const float* tx_pos;
+    const float* rx_pos;
+    const uint64_t* cand_key;
+    const float* cand_img;
+    const int64_t* cand_off;   // [n_tx+1]
+    const int64_t* work_off;   // [n_tx+1]
+    const int32_t* rx_off;     // [n_tx+1] or null
+    int n_tx, n_rx;
+    long long total;
+    uint64_t* out;
+    unsigned long long* count;
+    long long cap;
+    int n_sm;
+    unsigned* status;
+};
+
+// Back-projection from rx through the candidate's images (Sec. II-B image
+// method): P[K+1] = rx, P[k] = crossing of P[k+1] -> I_k with plane k, which
+// must lie inside triangle k (closed test) at line parameter in (0, 1).
+__device__ __forceinline__ bool back_project(const DevScene& s, const KeyFmt& f, uint64_t key, int K,
+                                             const float* img, f3 tx, f3 rx, f3* P, int* ids) {
+    P[0] = tx;
+    P[K + 1] = rx;
+    for (int k = 0; k < K; k++) ids[k] = f.id(key, k);
+    for (int k = 1; k < K; k++)
+        if (ids[k] == ids[k - 1]) return false;
+    for (int k = K; k >= 1; k--) {
+        f3 I = mk(img[(k - 1) * 3], img[(k - 1) * 3 + 1], img[(k - 1) * 3 + 2]);
+        f3 o = P[k + 1];
+        f3 dir = I - o;
+        const float4* tp = s.tris_o + 3 * (size_t)ids[k - 1];
+        float4 r0 = __ldg(tp), r1 = __ldg(tp + 1), r2 = __ldg(tp + 2);
+        float t = tri_hit(r0, r1, r2, o, dir);
+        if (!(t > 0.0f && t < 1.0f)) return false;
+        P[k] = o + dir * t;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool sides_ok(const DevScene& s, int K, const f3* P, const int* ids) {
+    for (int k = 1; k <= K; k++) {
+        float4 pl = __ldg(s.planes + ids[k - 1]);
+        f3 n = xyz(pl);
+        float s1 = dot(n, P[k - 1]) - pl.w, s2 = dot(n, P[k + 1]) - pl.w;
+        if (!((s1 > 0.0f && s2 > 0.0f) || (s1 < 0.0f && s2 < 0.0f))) return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_validate(ValParams p) {
+    extern __shared__ float4 sm[];
+    for (int i = threadIdx.x; i < p.n_sm * 4; i += blockDim.x) sm[i] = p.s.nodes[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < p.total;
+         base += stride) {
+        long long g = base + lane;
+        bool valid = false;
+        uint64_t rec = 0;
+        if (g < p.total) {
+            int lo = 0, hi = p.n_tx;  // largest t with work_off[t] <= g
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (p.work_off[mid] <= g) lo = mid; else hi = mid;
+            }
+            int t = lo;
+            long long R = p.rx_off ? (long long)(p.rx_off[t + 1] - p.rx_off[t]) : (long long)p.n_rx;
+            long long local = g - p.work_off[t];
+            long long cl = local / R, r = local - cl * R;
+            long long c = p.cand_off[t] + cl;
+            long long rxg = p.rx_off ? (long long)p.rx_off[t] + r : r;
+            long long pair = p.rx_off ? rxg : (long long)t * p.n_rx + r;
+            uint64_t key = p.cand_key[c];
+            int K = p.f.depth(key);
+            f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
+            f3 rx = mk(p.rx_pos[3 * rxg], p.rx_pos[3 * rxg + 1], p.rx_pos[3 * rxg + 2]);
+            f3 P[RT_MAX_DEPTH + 2];
+            int ids[RT_MAX_DEPTH];
+            valid = back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * p.f.D * 3, tx, rx, P, ids) &&
+                    sides_ok(p.s, K, P, ids);
+            for (int j = 0; valid && j <= K; j++) {
+                f3 seg = P[j + 1] - P[j];
+                float L = sqrtf(dot(seg, seg));
+                f3 d = seg * (1.0f / L);
+                int ex0 = j >= 1 ? ids[j - 1] : -1, ex1 = j < K ? ids[j] : -1;
+                if (any_hit(p.s, sm, p.n_sm, P[j], d, L - p.s.tmin, ex0, ex1, p.status)) valid = false;
+            }
+            rec = ((uint64_t)pair << 32) | (uint64_t)c;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, valid);
+        if (m) {
+            int leader = __ffs(m) - 1;
+            unsigned long long b0 = 0;
+            if (lane == leader) b0 = atomicAdd(p.count, (unsigned long long)__popc(m));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (valid) {
+                unsigned long long idx = b0 + __popc(m & lanemask_lt());
+                if ((long long)idx < p.cap) p.out[idx] = rec;
+            }
+        }
+    }
+}
+
+// offsets[p] = first path with pair >= p (paths sorted by pair, candidate)
+__global__ void k_path_off(const uint64_t* __restrict__ pk, int64_t P, int64_t n_pairs,
+                           int64_t* __restrict__ off) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q > n_pairs) return;
+    int64_t lo = 0, hi = P;
+    uint64_t want = (uint64_t)q << 32;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (pk[mid] < want) lo = mid + 1; else hi = mid;
+    }
+    off[q] = lo;
+}
+
+struct FinParams {
+    DevScene s;
+    KeyFmt f;
+    const float* tx_pos;
+    const float* rx_pos;
+    const uint64_t* cand_key;
+    const float* cand_img;
+    const uint64_t* path_key;
+    const int32_t* rx_off;
+    int n_tx, n_rx;
+    int64_t P;
+    int32_t* seq;
+    float* pts;
+    int32_t* depth;
+    double* len;
+    int32_t* pair_tx;   // [P*2]: tx, rx
+};
+
+// Reflection points (FP32) and path length accumulated in FP64: the length
+// of a specular path equals |rx - I_K| with I_K the last image of the
+// transmitter, computed here with FP64 planes from the FP32 vertices.
+__global__ void k_path_final(FinParams p) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.P) return;
+    uint64_t pk = p.path_key[i];
+    int64_t pair = (int64_t)(pk >> 32);
+    int64_t c = (int64_t)(pk & 0xFFFFFFFFull);
+    int t;
+    int64_t rxg;
+    if (p.rx_off) {
+        int lo = 0, hi = p.n_tx;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (p.rx_off[mid] <= pair) lo = mid; else hi = mid;
+        }
+        t = lo;
+        rxg = pair;
+    } else {
+        t = (int)(pair / p.n_rx);
+        rxg = pair - (int64_t)t * p.n_rx;
+    }
+    uint64_t key = p.cand_key[c];
+    int K = p.f.depth(key);
+    f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
+    f3 rx = mk(p.rx_pos[3 * rxg], p.rx_pos[3 * rxg + 1], p.rx_pos[3 * rxg + 2]);
+    f3 P[RT_MAX_DEPTH + 2];
+    int ids[RT_MAX_DEPTH];
+    back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * p.f.D * 3, tx, rx, P, ids);
+    for (int k = 0; k < p.f.D; k++) {
+        p.seq[i * p.f.D + k] = k < K ? ids[k] : -1;
+        f3 q = k < K ? P[k + 1] : mk(0.0f, 0.0f, 0.0f);
+        p.pts[(i * p.f.D + k) * 3] = q.x;
+        p.pts[(i * p.f.D + k) * 3 + 1] = q.y;
+        p.pts[(i * p.f.D + k) * 3 + 2] = q.z;
+    }
+    p.depth[i] = K;
+    p.pair_tx[2 * i] = t;
+    p.pair_tx[2 * i + 1] = (int32_t)rxg;
+    double I[3] = {(double)tx.x, (double)tx.y, (double)tx.z};
+    for (int k = 0; k < K; k++) {
+        const float4* tp = p.s.tris_o + 3 * (size_t)ids[k];
+        float4 r0 = tp[0], r1 = tp[1], r2 = tp[2];
+        double e1[3] = {r1.x, r1.y, r1.z}, e2[3] = {r2.x, r2.y, r2.z}, v0[3] = {r0.x, r0.y, r0.z};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        n[0] /= nl; n[1] /= nl; n[2] /= nl;
+        double sd = (I[0] - v0[0]) * n[0] + (I[1] - v0[1]) * n[1] + (I[2] - v0[2]) * n[2];
+        for (int q = 0; q < 3; q++) I[q] -= 2.0 * sd * n[q];
+    }
+    double dx = (double)rx.x - I[0], dy = (double)rx.y - I[1], dz = (double)rx.z - I[2];
+    p.len[i] = sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- host side
+int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits);
+
+static int key_format(rt_ctx* ctx, int D, KeyFmt& f) {
+    int idb = 1;
+    while ((1ll << idb) < (long long)std::max(ctx->n_tris, 2)) idb++;
+    int txb = 0;
+    while ((1ll << txb) < (long long)ctx->n_tx) txb++;
+    int bits = txb + 3 + std::max(D, 1) * idb;
+    if (bits > 64) return set_err(ctx, RT_ERR_INVALID_ARG, "candidate key wider than 64 bits (max_depth too large for this scene)");
+    f.D = std::max(D, 1);
+    f.id_bits = idb;
+    f.depth_shift = f.D * idb;
+    f.tx_shift = f.depth_shift + 3;
+    ctx->id_bits = idb;
+    ctx->tx_bits = txb;
+    ctx->key_bits = bits;
+    return RT_OK;
+}
+
+int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* out) {
+    cudaStream_t st = ctx->stream;
+    KeyFmt f;
+    int e = key_format(ctx, D, f);
+    if (e) return e;
+    const bool los = flags & RT_LOS, refl = (flags & RT_REFLECTION) && D > 0 && N > 0;
+    const int64_t nsbr = refl ? (int64_t)ctx->n_tx * N * D : 0;
+    const int64_t nkeys = nsbr + (los ? ctx->n_tx : 0);
+    if (nkeys >= 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "n_tx * num_rays * max_depth above 2^32");
+    ctx->max_depth = f.D;
+    ctx->num_rays = N;
+    ctx->recorded_rays = refl && (flags & RT_RECORD_RAYS);
+    RT_TRY(buf_reserve(ctx->keys, sizeof(uint64_t) * std::max<int64_t>(nkeys, 1)));
+    RT_TRY(buf_reserve(ctx->keys_alt, sizeof(uint64_t) * std::max<int64_t>(nkeys, 1)));
+    RT_TRY(buf_reserve(ctx->vals, sizeof(uint32_t) * std::max<int64_t>(nkeys, 1)));
+    RT_TRY(buf_reserve(ctx->vals_alt, sizeof(uint32_t) * std::max<int64_t>(nkeys, 1)));
+    uint64_t* keys = bp<uint64_t>(ctx->keys);
+    uint32_t* vals = bp<uint32_t>(ctx->vals);
+    RT_TRY(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), st));
+    if (refl) {
+        RT_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * nsbr, st));
+        int32_t* hits = nullptr;
+        if (ctx->recorded_rays) {
+            RT_TRY(buf_reserve(ctx->ray_hits, sizeof(int32_t) * nsbr));
+            RT_TRY(cudaMemsetAsync(ctx->ray_hits.p, 0xFF, sizeof(int32_t) * nsbr, st));
+            hits = bp<int32_t>(ctx->ray_hits);
+        }
+        e = launch_sbr(ctx, N, f.D, keys, hits);
+        if (e) return e;
+    }
+    if (nkeys > 0) {
+        k_iota<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(vals, nkeys);
+        if (los) k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nsbr, ctx->n_tx, f);
+        RT_TRY(cudaGetLastError());
+    }
+    RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
+                        ctx->key_bits));
+    // duplicate removal
+    const uint64_t sentinel_from = ctx->key_bits >= 64 ? ~0ull : ((1ull << ctx->key_bits) - 1ull);
+    int nb = (int)std::max<int64_t>((nkeys + DD_TILE - 1) / DD_TILE, 1);
+    DevBuf& cnt = ctx->sort_hist;
+    RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * (nb + 1)));
+    uint32_t* cntp = bp<uint32_t>(cnt);
+    RT_TRY(cudaMemsetAsync(cntp, 0, sizeof(uint32_t) * (nb + 1), st));
+    if (nkeys > 0) {
+        k_dedup_count<<<nb, DD_THREADS, 0, st>>>(keys, nkeys, sentinel_from, cntp);
+        RT_TRY(cudaGetLastError());
+    }
+    RT_TRY(exclusive_scan_u32(ctx, cntp, nb + 1));
+    uint32_t U32 = 0;
+    RT_TRY(cudaMemcpyAsync(&U32, cntp + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    RT_TRY(cudaStreamSynchronize(st));
+    const int64_t U = U32;
+    ctx->n_cand = U;
+    RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * std::max<int64_t>(U, 1)));
+    RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * std::max<int64_t>(U, 1)));
+    RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
+    RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * std::max<int64_t>(U, 1)));
+    if (U > 0) {
+        k_dedup_write<<<nb, DD_THREADS, 0, st>>>(keys, vals, nkeys, sentinel_from, cntp,
+                                                 bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit));
+        RT_TRY(cudaGetLastError());
+        k_cand_img<<<(unsigned)((U + 255) / 256), 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, f,
+                                                               bp<float>(ctx->tx_pos), bp<float4>(ctx->planes),
+                                                               bp<float>(ctx->cand_img));
+        RT_TRY(cudaGetLastError());
+    }
+    k_cand_off<<<(ctx->n_tx + 256) / 256, 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, ctx->n_tx, f,
+                                                         bp<int64_t>(ctx->cand_off));
+    RT_TRY(cudaGetLastError());
+    std::vector<int64_t> coff(ctx->n_tx + 1);
+    RT_TRY(cudaMemcpyAsync(coff.data(), ctx->cand_off.p, sizeof(int64_t) * (ctx->n_tx + 1),
+                           cudaMemcpyDeviceToHost, st));
+    RT_TRY(cudaStreamSynchronize(st));
+    // validation work: sum over tx of U_t * R_t
+    std::vector<int64_t> woff(ctx->n_tx + 1, 0);
+    for (int t = 0; t < ctx->n_tx; t++) {
+        int64_t R = ctx->rx_sets ? (int64_t)(ctx->rx_off[t + 1] - ctx->rx_off[t]) : (int64_t)ctx->n_rx;
+        woff[t + 1] = woff[t] + (coff[t + 1] - coff[t]) * R;
+    }
+    const int64_t total = woff[ctx->n_tx];
+    int64_t n_pairs = ctx->rx_sets ? (int64_t)ctx->rx_off[ctx->n_tx] : (int64_t)ctx->n_tx * ctx->n_rx;
+    DevBuf& woffd = ctx->path_cap_dummy;
+    RT_TRY(buf_reserve(woffd, sizeof(int64_t) * (ctx->n_tx + 1)));
+    RT_TRY(cudaMemcpyAsync(woffd.p, woff.data(), sizeof(int64_t) * (ctx->n_tx + 1), cudaMemcpyHostToDevice, st));
+    if (ctx->path_cap == 0) ctx->path_cap = 1 << 16;
+    int64_t P = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        RT_TRY(buf_reserve(ctx->path_key, sizeof(uint64_t) * ctx->path_cap));
+        RT_TRY(buf_reserve(ctx->path_key_alt, sizeof(uint64_t) * ctx->path_cap));
+        RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long) * 2, st));
+        if (total > 0) {
+            ValParams vp;
+            vp.s = dev_scene(ctx);
+            vp.f = f;
+            vp.tx_pos = bp<float>(ctx->tx_pos);
+            vp.rx_pos = bp<float>(ctx->rx_pos);
+            vp.cand_key = bp<uint64_t>(ctx->cand_key);
+            vp.cand_img = bp<float>(ctx->cand_img);
+            vp.cand_off = bp<int64_t>(ctx->cand_off);
+            vp.work_off = bp<int64_t>(woffd);
+            vp.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
+            vp.n_tx = ctx->n_tx;
+            vp.n_rx = ctx->n_rx;
+            vp.total = total;
+            vp.out = bp<uint64_t>(ctx->path_key);
+            vp.count = bp<unsigned long long>(ctx->counters) + 1;
+            vp.cap = ctx->path_cap;
+            vp.n_sm = std::min(ctx->n_smem_nodes, ctx->n_nodes);
+            vp.status = bp<unsigned>(ctx->status);
+            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm;
+            RT_TRY(cudaFuncSetAttribute(k_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_validate, 256, smem);
+            int64_t need = (total + 255) / 256;
+            int64_t grid = std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms);
+            k_validate<<<(unsigned)std::max<int64_t>(grid, 1), 256, smem, st>>>(vp);
+            RT_TRY(cudaGetLastError());
+        }
+        unsigned long long hc = 0;
+        RT_TRY(cudaMemcpyAsync(&hc, bp<unsigned long long>(ctx->counters) + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaStreamSynchronize(st));
+        P = (int64_t)hc;
+        if (P <= ctx->path_cap) break;
+        ctx->path_cap = P + P / 4 + 1024;  // retry with room for every path
+    }
+    ctx->n_paths = P;
+    int pair_bits = 1;
+    while ((1ll << pair_bits) < std::max<int64_t>(n_pairs, 2)) pair_bits++;
+    RT_TRY(radix_sort64(ctx, bp<uint64_t>(ctx->path_key), bp<uint64_t>(ctx->path_key_alt), nullptr, nullptr, P,
+                        32 + pair_bits));
+    RT_TRY(buf_reserve(ctx->path_off, sizeof(int64_t) * (n_pairs + 1)));
+    k_path_off<<<(unsigned)((n_pairs + 256) / 256), 256, 0, st>>>(bp<uint64_t>(ctx->path_key), P, n_pairs,
+                                                                  bp<int64_t>(ctx->path_off));
+    RT_TRY(cudaGetLastError());
+    int64_t Pm = std::max<int64_t>(P, 1);
+    RT_TRY(buf_reserve(ctx->path_seq, sizeof(int32_t) * Pm * f.D));
+    RT_TRY(buf_reserve(ctx->path_pts, sizeof(float) * 3 * Pm * f.D));
+    RT_TRY(buf_reserve(ctx->path_depth, sizeof(int32_t) * Pm));
+    RT_TRY(buf_reserve(ctx->path_len, sizeof(double) * Pm));
+    RT_TRY(buf_reserve(ctx->path_pair, sizeof(int32_t) * 2 * Pm));
+    if (P > 0) {
+        FinParams fp;
+        fp.s = dev_scene(ctx);
+        fp.f = f;
+        fp.tx_pos = bp<float>(ctx->tx_pos);
+        fp.rx_pos = bp<float>(ctx->rx_pos);
+        fp.cand_key = bp<uint64_t>(ctx->cand_key);
+        fp.cand_img = bp<float>(ctx->cand_img);
+        fp.path_key = bp<uint64_t>(ctx->path_key);
+        fp.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
+        fp.n_tx = ctx->n_tx;
+        fp.n_rx = ctx->n_rx;
+        fp.P = P;
+        fp.seq = bp<int32_t>(ctx->path_seq);
+        fp.pts = bp<float>(ctx->path_pts);
+        fp.depth = bp<int32_t>(ctx->path_depth);
+        fp.len = bp<double>(ctx->path_len);
+        fp.pair_tx = bp<int32_t>(ctx->path_pair);
+        k_path_final<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(fp);
+        RT_TRY(cudaGetLastError());
+    }
+    unsigned hs = 0;
+    RT_TRY(cudaMemcpyAsync(&hs, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    RT_TRY(cudaStreamSynchronize(st));
+    if (hs & RT_STAT_STACK) return set_err(ctx, RT_ERR_CAPACITY, "traversal stack overflow");
+    if (hs & RT_STAT_LOOP) return set_err(ctx, RT_ERR_CUDA, "malformed BVH (traversal budget exceeded)");
+    *out = P;
+    return RT_OK;
+}
+
+__global__ void k_cand_export(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ wit, int64_t U,
+                              KeyFmt f, int64_t N, int32_t* tx, int32_t* depth, int32_t* seq, int64_t* w) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= U) return;
+    uint64_t k = ck[c];
+    int K = f.depth(k);
+    if (tx) tx[c] = f.tx(k);
+    if (depth) depth[c] = K;
+    if (seq)
+        for (int b = 0; b < f.D; b++) seq[c * f.D + b] = b < K ? f.id(k, b) : -1;
+    if (w) {
+        uint32_t pos = wit[c];
+        w[c] = pos == 0xFFFFFFFFu ? -1 : (int64_t)((pos / f.D) % N);
+    }
+}
+
+int export_candidates(rt_ctx* ctx, int32_t* tx, int32_t* depth, int32_t* seq, int64_t* wit) {
+    if (ctx->n_cand == 0) return RT_OK;
+    KeyFmt f;
+    f.D = ctx->max_depth;
+    f.id_bits = ctx->id_bits;
+    f.depth_shift = f.D * f.id_bits;
+    f.tx_shift = f.depth_shift + 3;
+    k_cand_export<<<(unsigned)((ctx->n_cand + 255) / 256), 256, 0, ctx->stream>>>(
+        bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit), ctx->n_cand, f, std::max<int64_t>(ctx->num_rays, 1),
+        tx, depth, seq, wit);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}

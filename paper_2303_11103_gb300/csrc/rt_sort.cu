@@ -1,0 +1,146 @@
+// rt_sort.cu -- LSD radix sort of 64-bit keys (optional 32-bit payload),
+// 8-bit digits, three kernels per pass: per-tile digit histograms, one
+// exclusive scan over (digit, tile), stable scatter ranked with warp
+// match/ballot. Used for Morton codes, BVH level order, candidate keys
+// (duplicate removal) and path keys.
+#include "rt_internal.h"
+
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_IPT = 8;
+constexpr int RS_TILE = RS_THREADS * RS_IPT;
+constexpr int RS_WARPS = RS_THREADS / 32;
+
+__global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                      int shift, uint32_t* __restrict__ hist, int nb) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of m entries with one block of 1024 threads.
+__global__ void __launch_bounds__(1024) rs_scan(uint32_t* __restrict__ a, int64_t m) {
+    __shared__ uint32_t part[1024];
+    int64_t per = (m + 1023) / 1024;
+    int64_t b = threadIdx.x * per, e = min(b + per, m);
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; i++) s += a[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int64_t i = b; i < e; i++) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint64_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin,
+                                                         uint64_t* __restrict__ kout,
+                                                         uint32_t* __restrict__ vout, int64_t n,
+                                                         int shift, const uint32_t* __restrict__ off,
+                                                         int nb) {
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * 32 * RS_IPT;
+    uint64_t k[RS_IPT];
+    uint32_t v[RS_IPT];
+    uint32_t rank[RS_IPT];
+    const unsigned lt = lanemask_lt();
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        bool ok = i < n;
+        unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            k[j] = kin[i];
+            if (VALS) v[j] = vin[i];
+            unsigned dg = (unsigned)(k[j] >> shift) & 255u;
+            unsigned peers = __match_any_sync(act, dg);
+            uint32_t before = cnt[w][dg];
+            rank[j] = before + __popc(peers & lt);
+            __syncwarp(act);
+            if ((peers & lt) == 0) cnt[w][dg] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix across warps
+    {
+        int dg = threadIdx.x;
+        uint32_t run = 0;
+        for (int ww = 0; ww < RS_WARPS; ww++) {
+            uint32_t t = cnt[ww][dg];
+            cnt[ww][dg] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        if (i < n) {
+            unsigned dg = (unsigned)(k[j] >> shift) & 255u;
+            uint32_t pos = off[(size_t)dg * nb + blockIdx.x] + cnt[w][dg] + rank[j];
+            kout[pos] = k[j];
+            if (VALS) vout[pos] = v[j];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
+                         uint32_t* vals_alt, int64_t n, int end_bit) {
+    if (n <= 1 || end_bit <= 0) return cudaSuccess;
+    if (n > (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
+    int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    cudaError_t e = buf_reserve(ctx->sort_hist, sizeof(uint32_t) * 256 * (size_t)nb);
+    if (e != cudaSuccess) return e;
+    uint32_t* hist = bp<uint32_t>(ctx->sort_hist);
+    uint64_t *kin = keys, *kout = keys_alt;
+    uint32_t *vin = vals, *vout = vals_alt;
+    int passes = (end_bit + 7) / 8;
+    for (int p = 0; p < passes; p++) {
+        int shift = 8 * p;
+        rs_hist<<<nb, RS_THREADS, 0, ctx->stream>>>(kin, n, shift, hist, nb);
+        rs_scan<<<1, 1024, 0, ctx->stream>>>(hist, (int64_t)256 * nb);
+        if (vals)
+            rs_scatter<true><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, hist, nb);
+        else
+            rs_scatter<false><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, nullptr, kout, nullptr, n, shift, hist, nb);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t* tk = kin; kin = kout; kout = tk;
+        uint32_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != keys) {
+        e = cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) return e;
+        if (vals) e = cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    return e;
+}
+
+// Exclusive scan of m uint32 entries in place (single block).
+cudaError_t exclusive_scan_u32(rt_ctx* ctx, uint32_t* a, int64_t m) {
+    if (m <= 0) return cudaSuccess;
+    rs_scan<<<1, 1024, 0, ctx->stream>>>(a, m);
+    return cudaGetLastError();
+}

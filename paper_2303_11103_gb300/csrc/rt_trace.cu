@@ -1,0 +1,350 @@
+// rt_trace.cu -- ray shooting: direction-coherent ray order, shooting and
+// bouncing of candidate paths (Sec. II-B), coverage-map ray tracing with
+// field transport and binning (Sec. II-A, Fig. 2).
+//
+// Both tracing kernels are persistent: a grid of (SMs x resident blocks)
+// warps pulls chunks of rays from one global counter that spans every
+// transmitter, so all transmitters run in one launch. Each lane holds one
+// ray in registers; when lanes' rays terminate, the warp refills exactly
+// those lanes (ballot over dead lanes, popc ranks) from its chunk, so the
+// warp keeps tracing with all lanes live between bounces. The top BVH
+// levels are staged in shared memory once per block.
+#include "rt_field.cuh"
+#include "rt_internal.h"
+
+namespace {
+
+// -------------------------------------------------------------- ray ordering
+// Key = 2D Morton code of (z, phi) of the lattice direction quantised to
+// 2^12 x 2^12 cells: rays whose order is close point in close directions.
+__global__ void k_perm_keys(long long N, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    f3 d = fib_dir(N, i);
+    float u = fminf(fmaxf((d.z + 1.0f) * 0.5f, 0.0f), 0.99999f);
+    float v = (atan2f(d.y, d.x) + RT_PI_F) * (0.5f / RT_PI_F);
+    v = fminf(fmaxf(v, 0.0f), 0.99999f);
+    unsigned a = (unsigned)(u * 4096.0f), b = (unsigned)(v * 4096.0f);
+    unsigned long long code = 0;
+    for (int k = 0; k < 12; k++) code |= (unsigned long long)(((a >> k) & 1u) << (2 * k + 1)) |
+                                        (unsigned long long)(((b >> k) & 1u) << (2 * k));
+    keys[i] = code;
+    vals[i] = (uint32_t)i;
+}
+
+struct TraceCommon {
+    DevScene s;
+    const float* tx_pos;  // [n_tx*3]
+    const float* tx_ypr;  // [n_tx*3]
+    long long N;          // lattice size (rays per transmitter)
+    long long first;      // first lattice index traced
+    long long count;      // lattice indices traced per transmitter
+    long long total;      // n_tx * count
+    const uint32_t* perm; // [N] direction-coherent order (full range only) or null
+    unsigned long long* counter;
+    int chunk;            // rays per warp refill
+    int n_sm;             // staged BVH nodes
+    unsigned* status;
+};
+
+__device__ __forceinline__ void stage_nodes(const TraceCommon& c, float4* sm) {
+    for (int i = threadIdx.x; i < c.n_sm * 4; i += blockDim.x) sm[i] = c.s.nodes[i];
+    __syncthreads();
+}
+
+// Warp-level ray fetch: refill dead lanes from the warp's chunk. Returns the
+// global ray slot (tx * N + lattice index) for a refilled lane, -1 otherwise.
+struct WarpFeed {
+    long long next = 0, end = 0;
+    bool exhausted = false;
+    __device__ __forceinline__ long long refill(const TraceCommon& c, bool alive) {
+        const unsigned full = 0xffffffffu;
+        unsigned dead = __ballot_sync(full, !alive);
+        long long slot = -1;
+        if (dead == 0 || exhausted) return slot;
+        if (next >= end) {
+            unsigned long long base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(c.counter, (unsigned long long)c.chunk);
+            base = __shfl_sync(full, base, 0);
+            if ((long long)base >= c.total) {
+                exhausted = true;
+                return slot;
+            }
+            next = (long long)base;
+            end = min((long long)base + c.chunk, c.total);
+        }
+        int need = __popc(dead);
+        int take = (int)min((long long)need, end - next);
+        int r = __popc(dead & lanemask_lt());
+        if (!alive && r < take) {
+            long long q = next + r;
+            long long tx = q / c.count, k = q - tx * c.count;
+            long long i = c.perm ? (long long)c.perm[k] : c.first + k;
+            slot = tx * c.N + i;
+        }
+        next += take;
+        return slot;
+    }
+};
+
+// ------------------------------------------------------------ SBR candidates
+struct SbrParams {
+    TraceCommon c;
+    int D;
+    int id_bits, depth_shift, tx_shift;
+    uint64_t* keys;   // [total*D]
+    int32_t* hits;    // [total*D] or null
+};
+
+__global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
+    extern __shared__ float4 sm[];
+    stage_nodes(p.c, sm);
+    WarpFeed feed;
+    bool alive = false;
+    f3 o = mk(0, 0, 0), d = mk(0, 0, 1);
+    int last = -1, depth = 0;
+    long long slot = 0;
+    uint64_t key = 0;
+    while (true) {
+        long long s = feed.refill(p.c, alive);
+        if (s >= 0) {
+            slot = s;
+            long long tx = s / p.c.N, i = s - tx * p.c.N;
+            o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
+            d = fib_dir(p.c.N, i);
+            last = -1;
+            depth = 0;
+            key = (uint64_t)tx << p.tx_shift;
+            alive = true;
+        }
+        if (!__any_sync(0xffffffffu, alive)) {
+            if (feed.exhausted) break;
+            continue;
+        }
+        if (alive) {
+            float t;
+            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status);
+            if (id < 0) {
+                alive = false;
+            } else {
+                key |= (uint64_t)id << ((p.D - 1 - depth) * p.id_bits);
+                size_t pos = (size_t)slot * p.D + depth;
+                p.keys[pos] = key | ((uint64_t)(depth + 1) << p.depth_shift);
+                if (p.hits) p.hits[pos] = id;
+                float4 pl = __ldg(p.c.s.planes + id);
+                o = o + d * t;
+                d = reflect(d, xyz(pl));
+                last = id;
+                if (++depth >= p.D) alive = false;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- coverage map
+struct CovParams {
+    TraceCommon c;
+    int D;
+    DevAntenna txa, rxa;
+    int tx_port;
+    float inv_we0;
+    float x0, y0, inv_cell, h;
+    int nx, ny;
+    float wscale;          // lambda^2 / (4 pi cell^2 N)
+    float* gain;           // [n_tx*ny*nx]
+    uint32_t* hits;        // [n_tx*ny*nx]
+};
+
+__global__ void __launch_bounds__(256) k_coverage(CovParams p) {
+    extern __shared__ float4 sm[];
+    stage_nodes(p.c, sm);
+    WarpFeed feed;
+    bool alive = false;
+    f3 o = mk(0, 0, 0), d = mk(0, 0, 1);
+    int last = -1, depth = 0, tx = 0;
+    Cx<float> E[3];
+    const float zeta_t = p.txa.slant[p.tx_port], zeta_r = p.rxa.slant[0];
+    Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
+    while (true) {
+        long long s = feed.refill(p.c, alive);
+        if (s >= 0) {
+            long long t64 = s / p.c.N, i = s - t64 * p.c.N;
+            tx = (int)t64;
+            o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
+            d = fib_dir(p.c.N, i);
+            Rot<float> Rt = rot_ypr(p.c.tx_ypr[3 * tx], p.c.tx_ypr[3 * tx + 1], p.c.tx_ypr[3 * tx + 2]);
+            V3<float> f = antenna_vec<float>(p.txa.kind, zeta_t, Rt, V3<float>{d.x, d.y, d.z});
+            E[0] = {f.x, 0.0f};
+            E[1] = {f.y, 0.0f};
+            E[2] = {f.z, 0.0f};
+            last = -1;
+            depth = 0;
+            alive = true;
+        }
+        if (!__any_sync(0xffffffffu, alive)) {
+            if (feed.exhausted) break;
+            continue;
+        }
+        if (alive) {
+            float t;
+            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status);
+            if (d.z != 0.0f) {
+                float sc = (p.h - o.z) / d.z;
+                if (sc > 0.0f && (id < 0 || sc < t)) {
+                    float fx = (o.x + sc * d.x - p.x0) * p.inv_cell;
+                    float fy = (o.y + sc * d.y - p.y0) * p.inv_cell;
+                    int ix = (int)floorf(fx), iy = (int)floorf(fy);
+                    if (fx >= 0.0f && fy >= 0.0f && ix < p.nx && iy < p.ny) {
+                        V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
+                        float re = F.x * E[0].re + F.y * E[1].re + F.z * E[2].re;
+                        float im = F.x * E[0].im + F.y * E[1].im + F.z * E[2].im;
+                        float w = (re * re + im * im) * p.wscale / fabsf(d.z);
+                        size_t cell = ((size_t)tx * p.ny + iy) * p.nx + ix;
+                        atomicAdd(p.gain + cell, w);
+                        atomicAdd(p.hits + cell, 1u);
+                    }
+                }
+            }
+            if (id < 0 || depth >= p.D) {
+                alive = false;
+            } else {
+                float4 pl = __ldg(p.c.s.planes + id);
+                int m = __ldg(p.c.s.mat + id);
+                float2 mp = __ldg(p.c.s.mats + m);
+                f3 n = xyz(pl);
+                f3 r = reflect(d, n);
+                reflect_field<float>(E, V3<float>{d.x, d.y, d.z}, V3<float>{r.x, r.y, r.z}, n, mp.x, mp.y,
+                                     p.inv_we0);
+                o = o + d * t;
+                d = r;
+                last = id;
+                depth++;
+            }
+        }
+    }
+}
+
+__global__ void k_dirs(long long N, long long first, long long n, float* __restrict__ out) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    f3 d = fib_dir(N, first + k);
+    out[3 * k] = d.x;
+    out[3 * k + 1] = d.y;
+    out[3 * k + 2] = d.z;
+}
+
+int trace_grid(rt_ctx* ctx, const void* kernel, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ctx->trace_block, smem);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * ctx->num_sms;
+}
+
+}  // namespace
+
+int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out) {
+    if (n <= 0) return RT_OK;
+    k_dirs<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(N, first, n, out);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int ensure_perm(rt_ctx* ctx, int64_t N) {
+    if (ctx->perm_n == N) return RT_OK;
+    if (N > 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "num_rays above 2^32");
+    DevBuf k1, k2, v2;
+    RT_TRY(buf_reserve(ctx->perm, sizeof(uint32_t) * (size_t)N));
+    cudaError_t e = buf_reserve(k1, sizeof(uint64_t) * (size_t)N);
+    if (e == cudaSuccess) e = buf_reserve(k2, sizeof(uint64_t) * (size_t)N);
+    if (e == cudaSuccess) e = buf_reserve(v2, sizeof(uint32_t) * (size_t)N);
+    if (e == cudaSuccess) {
+        k_perm_keys<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(N, bp<uint64_t>(k1),
+                                                                         bp<uint32_t>(ctx->perm));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = radix_sort64(ctx, bp<uint64_t>(k1), bp<uint64_t>(k2), bp<uint32_t>(ctx->perm), bp<uint32_t>(v2), N, 24);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    buf_free(k1);
+    buf_free(k2);
+    buf_free(v2);
+    if (e != cudaSuccess) return set_cuda(ctx, e, "ray order");
+    ctx->perm_n = N;
+    return RT_OK;
+}
+
+static TraceCommon make_common(rt_ctx* ctx, int64_t N, int64_t first, int64_t count) {
+    TraceCommon c;
+    c.s = dev_scene(ctx);
+    c.tx_pos = bp<float>(ctx->tx_pos);
+    c.tx_ypr = bp<float>(ctx->tx_ypr);
+    c.N = N;
+    c.first = first;
+    c.count = count;
+    c.total = (long long)count * ctx->n_tx;
+    c.perm = (first == 0 && count == N && ctx->perm_n == N) ? bp<uint32_t>(ctx->perm) : nullptr;
+    c.counter = bp<unsigned long long>(ctx->counters);
+    c.chunk = ctx->warp_chunk;
+    c.n_sm = ctx->n_smem_nodes < ctx->n_nodes ? ctx->n_smem_nodes : ctx->n_nodes;
+    c.status = bp<unsigned>(ctx->status);
+    return c;
+}
+
+// Shoot and bounce: writes candidate keys at (tx*N + i)*D + depth.
+int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits) {
+    int e = ensure_perm(ctx, N);
+    if (e) return e;
+    SbrParams p;
+    p.c = make_common(ctx, N, 0, N);
+    p.D = D;
+    p.id_bits = ctx->id_bits;
+    p.depth_shift = D * ctx->id_bits;
+    p.tx_shift = p.depth_shift + 3;
+    p.keys = keys;
+    p.hits = hits;
+    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
+    RT_TRY(cudaFuncSetAttribute(k_sbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
+    int grid = trace_grid(ctx, (const void*)k_sbr, smem);
+    k_sbr<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t first, int64_t count, bool zero,
+                    int tx_port, float* gain, uint32_t* hits) {
+    if (first == 0 && count == N) {
+        int e = ensure_perm(ctx, N);
+        if (e) return e;
+    }
+    CovParams p;
+    p.c = make_common(ctx, N, first, count);
+    p.D = D;
+    p.txa = ctx->tx_ant;
+    p.rxa = ctx->rx_ant;
+    p.tx_port = tx_port;
+    p.inv_we0 = (float)(1.0 / (2.0 * RT_PI_D * ctx->fc * RT_EPS0_D));
+    p.x0 = g->x0;
+    p.y0 = g->y0;
+    p.inv_cell = 1.0f / g->cell;
+    p.h = g->height;
+    p.nx = g->nx;
+    p.ny = g->ny;
+    double lam = RT_C0_D / ctx->fc;
+    p.wscale = (float)(lam * lam / (4.0 * RT_PI_D * (double)g->cell * g->cell * (double)N));
+    p.gain = gain;
+    p.hits = hits;
+    size_t cells = (size_t)ctx->n_tx * g->nx * g->ny;
+    if (zero) {
+        RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * cells, ctx->stream));
+        RT_TRY(cudaMemsetAsync(hits, 0, sizeof(uint32_t) * cells, ctx->stream));
+    }
+    if (count == 0) return RT_OK;
+    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
+    RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
+    int grid = trace_grid(ctx, (const void*)k_coverage, smem);
+    k_coverage<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}

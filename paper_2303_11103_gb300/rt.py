@@ -1,0 +1,454 @@
+"""Python binding of the C ABI in include/rt.h (argument marshalling only).
+
+Every step of the tracing path runs in librt_gb300.so; PyTorch only
+provides device memory and the current CUDA stream. The low-level functions
+carry the C names (rt_create, rt_load_scene, ...); `Tracer` bundles them
+for convenience, and `CIR` / `FreqResponse` are autograd functions whose
+backward passes call rt_cir_backward / rt_freq_response_backward.
+
+There is no CPU fallback: if the library is missing or no GPU is present,
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librt_gb300.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "rt.h")
+
+RT_OK = 0
+RT_LOS, RT_REFLECTION, RT_RECORD_RAYS = 1, 2, 0x100
+ERRORS = {-1: "RT_ERR_INVALID_ARG", -2: "RT_ERR_CUDA", -3: "RT_ERR_OOM", -4: "RT_ERR_CAPACITY",
+          -5: "RT_ERR_TIMEOUT", -6: "RT_ERR_NOT_READY"}
+
+_lib = None
+
+
+class RtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rt_antenna(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_ports", ctypes.c_int32), ("slant", ctypes.c_float * 2)]
+
+
+class rt_grid(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_float), ("y0", ctypes.c_float), ("cell", ctypes.c_float),
+                ("height", ctypes.c_float), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+def header_symbols() -> list[str]:
+    """Names of the functions include/rt.h declares."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^int\s+(rt_\w+)\s*\(", txt, re.M)))
+
+
+def lib():
+    """Load librt_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
+        sig = {
+            "rt_create": [ctypes.POINTER(vp), ctypes.c_int, vp],
+            "rt_destroy": [vp],
+            "rt_set_stream": [vp, vp],
+            "rt_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
+            "rt_set_frequency": [vp, dbl],
+            "rt_load_scene": [vp, vp, i64, vp, vp, i32],
+            "rt_set_materials": [vp, vp, i32],
+            "rt_set_tx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna)],
+            "rt_set_rx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna), vp],
+            "rt_compute_paths": [vp, i32, i64, u32, ctypes.POINTER(i64)],
+            "rt_ray_directions": [vp, i64, i64, i64, vp],
+            "rt_num_pairs": [vp, ctypes.POINTER(i64)],
+            "rt_get_paths": [vp, vp, vp, vp, vp, vp],
+            "rt_get_candidates": [vp, ctypes.POINTER(i64), vp, vp, vp, vp],
+            "rt_get_ray_hits": [vp, vp],
+            "rt_cir": [vp, u32, vp, vp],
+            "rt_freq_response": [vp, vp, vp, vp, i32, vp],
+            "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
+            "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
+            "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
+            "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _antenna(ant) -> rt_antenna:
+    a = rt_antenna()
+    a.kind = int(ant.kind)
+    a.n_ports = len(ant.slants)
+    for i, s in enumerate(ant.slants):
+        a.slant[i] = float(s)
+    return a
+
+
+# ---------------------------------------------------------------- C-ABI names
+def rt_create(device: int = 0):
+    h = ctypes.c_void_p()
+    code = lib().rt_create(ctypes.byref(h), int(device), _stream())
+    if code:
+        raise RtError(code, "rt_create failed")
+    return h
+
+
+def rt_destroy(ctx):
+    lib().rt_destroy(ctx)
+
+
+def rt_last_error(ctx) -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().rt_last_error(ctx, buf, 1024)
+    return buf.value.decode()
+
+
+def _check(ctx, code):
+    if code != RT_OK:
+        raise RtError(code, rt_last_error(ctx))
+
+
+def rt_set_stream(ctx):
+    _check(ctx, lib().rt_set_stream(ctx, _stream()))
+
+
+def rt_set_frequency(ctx, fc: float):
+    _check(ctx, lib().rt_set_frequency(ctx, float(fc)))
+
+
+def rt_load_scene(ctx, verts, mat_id, mat_params):
+    _check(ctx, lib().rt_load_scene(ctx, _ptr(verts), int(verts.shape[0]), _ptr(mat_id), _ptr(mat_params),
+                                    int(mat_params.shape[0])))
+
+
+def rt_set_materials(ctx, mat_params):
+    _check(ctx, lib().rt_set_materials(ctx, _ptr(mat_params), int(mat_params.shape[0])))
+
+
+def rt_set_tx(ctx, pos, ypr, antenna):
+    a = _antenna(antenna)
+    _check(ctx, lib().rt_set_tx(ctx, _ptr(pos), _ptr(ypr), int(pos.shape[0]), ctypes.byref(a)))
+
+
+def rt_set_rx(ctx, pos, ypr, antenna, rx_set_offsets=None):
+    a = _antenna(antenna)
+    off = None
+    if rx_set_offsets is not None:
+        arr = (ctypes.c_int32 * len(rx_set_offsets))(*[int(x) for x in rx_set_offsets])
+        off = ctypes.cast(arr, ctypes.c_void_p)
+    _check(ctx, lib().rt_set_rx(ctx, _ptr(pos), _ptr(ypr), int(pos.shape[0]), ctypes.byref(a), off))
+
+
+def rt_compute_paths(ctx, max_depth: int, num_rays: int, flags: int) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, lib().rt_compute_paths(ctx, int(max_depth), int(num_rays), int(flags), ctypes.byref(n)))
+    return int(n.value)
+
+
+def rt_ray_directions(ctx, num_rays, first, n, dirs):
+    _check(ctx, lib().rt_ray_directions(ctx, int(num_rays), int(first), int(n), _ptr(dirs)))
+
+
+def rt_num_pairs(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, lib().rt_num_pairs(ctx, ctypes.byref(n)))
+    return int(n.value)
+
+
+def rt_get_paths(ctx, offsets=None, seq=None, points=None, depth=None, length=None):
+    _check(ctx, lib().rt_get_paths(ctx, _ptr(offsets), _ptr(seq), _ptr(points), _ptr(depth), _ptr(length)))
+
+
+def rt_get_candidates(ctx, tx=None, depth=None, seq=None, witness=None) -> int:
+    n = ctypes.c_int64()
+    _check(ctx, lib().rt_get_candidates(ctx, ctypes.byref(n), _ptr(tx), _ptr(depth), _ptr(seq), _ptr(witness)))
+    return int(n.value)
+
+
+def rt_get_ray_hits(ctx, hits):
+    _check(ctx, lib().rt_get_ray_hits(ctx, _ptr(hits)))
+
+
+def rt_cir(ctx, flags, a, tau):
+    _check(ctx, lib().rt_cir(ctx, int(flags), _ptr(a), _ptr(tau)))
+
+
+def rt_freq_response(ctx, a, tau, freqs, H):
+    _check(ctx, lib().rt_freq_response(ctx, _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]), _ptr(H)))
+
+
+def rt_coverage_map(ctx, grid: rt_grid, max_depth, num_rays, tx_port, gain, hits):
+    _check(ctx, lib().rt_coverage_map(ctx, ctypes.byref(grid), int(max_depth), int(num_rays), int(tx_port),
+                                      _ptr(gain), _ptr(hits)))
+
+
+def rt_coverage_map_accumulate(ctx, grid: rt_grid, max_depth, num_rays, first_ray, ray_count, tx_port, gain,
+                               hits):
+    _check(ctx, lib().rt_coverage_map_accumulate(ctx, ctypes.byref(grid), int(max_depth), int(num_rays),
+                                                 int(first_ray), int(ray_count), int(tx_port), _ptr(gain),
+                                                 _ptr(hits)))
+
+
+def rt_cir_backward(ctx, flags, grad_a, grad_tau, g_eps, g_sigma, g_txpos, g_txypr):
+    _check(ctx, lib().rt_cir_backward(ctx, int(flags), _ptr(grad_a), _ptr(grad_tau), _ptr(g_eps), _ptr(g_sigma),
+                                      _ptr(g_txpos), _ptr(g_txypr)))
+
+
+def rt_freq_response_backward(ctx, a, tau, freqs, grad_H, grad_a, grad_tau):
+    _check(ctx, lib().rt_freq_response_backward(ctx, _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]),
+                                                _ptr(grad_H), _ptr(grad_a), _ptr(grad_tau)))
+
+
+# --------------------------------------------------------------- convenience
+class Tracer:
+    """One rt_ctx on one device, with torch tensors in and out."""
+
+    def __init__(self, device: int = 0, fc: float = 3.5e9):
+        self.device = torch.device("cuda", device)
+        self.ctx = rt_create(device)
+        self.fc = fc
+        rt_set_frequency(self.ctx, fc)
+        self.n_tx = self.n_rx = 0
+        self.ntp = self.nrp = 1
+        self.max_depth = 0
+        self.n_paths = 0
+        self.n_mat = 0
+
+    def close(self):
+        if self.ctx is not None:
+            rt_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _t(self, x, dtype):
+        return torch.as_tensor(x, dtype=dtype).to(self.device).contiguous()
+
+    def sync_stream(self):
+        rt_set_stream(self.ctx)
+
+    def load_scene(self, scene):
+        self.sync_stream()
+        self._verts = self._t(scene.verts, torch.float32).reshape(-1, 9)
+        self._mat = self._t(scene.mat_id, torch.int32)
+        self._mats = self._t(scene.materials, torch.float32).reshape(-1, 2)
+        self.n_mat = int(self._mats.shape[0])
+        rt_load_scene(self.ctx, self._verts, self._mat, self._mats)
+
+    def set_materials(self, mats):
+        self.sync_stream()
+        self._mats = self._t(mats, torch.float32).reshape(-1, 2)
+        rt_set_materials(self.ctx, self._mats)
+
+    def set_tx(self, pos, ypr, antenna):
+        self.sync_stream()
+        pos = self._t(pos, torch.float32).reshape(-1, 3)
+        ypr = self._t(ypr, torch.float32).reshape(-1, 3)
+        rt_set_tx(self.ctx, pos, ypr, antenna)
+        self.n_tx, self.ntp, self.tx_antenna = int(pos.shape[0]), len(antenna.slants), antenna
+
+    def set_rx(self, pos, ypr, antenna, rx_set_offsets=None):
+        self.sync_stream()
+        pos = self._t(pos, torch.float32).reshape(-1, 3)
+        ypr = self._t(ypr, torch.float32).reshape(-1, 3)
+        rt_set_rx(self.ctx, pos, ypr, antenna, rx_set_offsets)
+        self.n_rx, self.nrp, self.rx_antenna = int(pos.shape[0]), len(antenna.slants), antenna
+
+    def set_devices(self, tx, rx, rx_set_offsets=None):
+        self.set_tx(tx.pos, tx.ypr, tx.antenna)
+        self.set_rx(rx.pos, rx.ypr, rx.antenna, rx_set_offsets)
+
+    def compute_paths(self, max_depth, num_rays, los=True, reflection=True, record_rays=False) -> int:
+        self.sync_stream()
+        flags = (RT_LOS if los else 0) | (RT_REFLECTION if reflection else 0) | (RT_RECORD_RAYS if record_rays else 0)
+        self.n_paths = rt_compute_paths(self.ctx, max_depth, num_rays, flags)
+        self.max_depth = max(int(max_depth), 1)
+        self.num_rays = int(num_rays)
+        return self.n_paths
+
+    @property
+    def n_pairs(self) -> int:
+        return rt_num_pairs(self.ctx)
+
+    def paths(self):
+        """offsets [pairs+1], seq [P, D], points [P, D, 3], depth [P], length [P] (float64)."""
+        P, D = self.n_paths, self.max_depth
+        dev = self.device
+        out = dict(offsets=torch.empty(self.n_pairs + 1, dtype=torch.int64, device=dev),
+                   seq=torch.empty((max(P, 1), D), dtype=torch.int32, device=dev),
+                   points=torch.empty((max(P, 1), D, 3), dtype=torch.float32, device=dev),
+                   depth=torch.empty(max(P, 1), dtype=torch.int32, device=dev),
+                   length=torch.empty(max(P, 1), dtype=torch.float64, device=dev))
+        rt_get_paths(self.ctx, out["offsets"], out["seq"], out["points"], out["depth"], out["length"])
+        for k in ("seq", "points", "depth", "length"):
+            out[k] = out[k][:P]
+        return out
+
+    def candidates(self):
+        n = rt_get_candidates(self.ctx)
+        D, dev = self.max_depth, self.device
+        tx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        dep = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        seq = torch.empty((max(n, 1), D), dtype=torch.int32, device=dev)
+        wit = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+        rt_get_candidates(self.ctx, tx, dep, seq, wit)
+        return tx[:n], dep[:n], seq[:n], wit[:n]
+
+    def ray_hits(self):
+        h = torch.empty((self.n_tx, self.num_rays, self.max_depth), dtype=torch.int32, device=self.device)
+        rt_get_ray_hits(self.ctx, h)
+        return h
+
+    def ray_directions(self, num_rays, first=0, n=None):
+        n = num_rays - first if n is None else n
+        d = torch.empty((n, 3), dtype=torch.float32, device=self.device)
+        rt_ray_directions(self.ctx, num_rays, first, n, d)
+        return d
+
+    def cir_raw(self, los=True, reflection=True):
+        """a as float32 [P, nrp, ntp, 2] (interleaved complex) and tau [P]."""
+        self.sync_stream()
+        P = self.n_paths
+        a = torch.empty((max(P, 1), self.nrp, self.ntp, 2), dtype=torch.float32, device=self.device)
+        tau = torch.empty(max(P, 1), dtype=torch.float32, device=self.device)
+        rt_cir(self.ctx, (RT_LOS if los else 0) | (RT_REFLECTION if reflection else 0), a, tau)
+        return a[:P], tau[:P]
+
+    def cir(self, los=True, reflection=True):
+        a, tau = self.cir_raw(los, reflection)
+        return torch.view_as_complex(a), tau
+
+    def freq_response_raw(self, a_raw, tau, freqs):
+        self.sync_stream()
+        freqs = self._t(freqs, torch.float64)
+        K = int(freqs.shape[0])
+        H = torch.empty((self.n_pairs, self.nrp, self.ntp, K, 2), dtype=torch.float32, device=self.device)
+        a_raw = a_raw.contiguous() if a_raw.numel() else torch.zeros((1, self.nrp, self.ntp, 2), device=self.device)
+        tau = tau.contiguous() if tau.numel() else torch.zeros(1, device=self.device)
+        rt_freq_response(self.ctx, a_raw, tau, freqs, H)
+        return H
+
+    def freq_response(self, a, tau, freqs):
+        a_raw = torch.view_as_real(a.contiguous()) if a.is_complex() else a
+        return torch.view_as_complex(self.freq_response_raw(a_raw.contiguous(), tau, freqs))
+
+    def coverage_map(self, grid: dict, max_depth: int, num_rays: int, tx_port: int = 0):
+        self.sync_stream()
+        g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
+                    int(grid["nx"]), int(grid["ny"]))
+        gain = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.float32, device=self.device)
+        hits = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.int32, device=self.device)
+        rt_coverage_map(self.ctx, g, max_depth, num_rays, tx_port, gain, hits)
+        return gain, hits
+
+    def coverage_map_ranges(self, grid: dict, max_depth: int, num_rays: int, ranges, tx_port: int = 0):
+        """Coverage map accumulated over lattice ray ranges [(first, count), ...]."""
+        self.sync_stream()
+        g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
+                    int(grid["nx"]), int(grid["ny"]))
+        gain = torch.zeros((self.n_tx, g.ny, g.nx), dtype=torch.float32, device=self.device)
+        hits = torch.zeros((self.n_tx, g.ny, g.nx), dtype=torch.int32, device=self.device)
+        for first, count in ranges:
+            rt_coverage_map_accumulate(self.ctx, g, max_depth, num_rays, first, count, tx_port, gain, hits)
+        return gain, hits
+
+    # gradients --------------------------------------------------------------
+    def cir_backward(self, grad_a, grad_tau=None, los=True, reflection=True):
+        """Returns (g_eps [M], g_sigma [M], g_txpos [n_tx, 3], g_txypr [n_tx, 3])."""
+        self.sync_stream()
+        dev = self.device
+        ge = torch.zeros(self.n_mat, dtype=torch.float32, device=dev)
+        gs = torch.zeros(self.n_mat, dtype=torch.float32, device=dev)
+        gp = torch.zeros((self.n_tx, 3), dtype=torch.float32, device=dev)
+        gy = torch.zeros((self.n_tx, 3), dtype=torch.float32, device=dev)
+        ga = torch.view_as_real(grad_a.to(torch.complex64).contiguous()).contiguous()
+        gt = grad_tau.to(torch.float32).contiguous() if grad_tau is not None else None
+        if self.n_paths:
+            rt_cir_backward(self.ctx, (RT_LOS if los else 0) | (RT_REFLECTION if reflection else 0), ga, gt,
+                            ge, gs, gp, gy)
+        return ge, gs, gp, gy
+
+    def freq_response_backward(self, a, tau, freqs, grad_H):
+        self.sync_stream()
+        freqs = self._t(freqs, torch.float64)
+        P = self.n_paths
+        ga = torch.empty((max(P, 1), self.nrp, self.ntp, 2), dtype=torch.float32, device=self.device)
+        gt = torch.empty(max(P, 1), dtype=torch.float32, device=self.device)
+        if P:
+            rt_freq_response_backward(self.ctx, torch.view_as_real(a.contiguous()).contiguous(), tau.contiguous(),
+                                      freqs, torch.view_as_real(grad_H.to(torch.complex64).contiguous()).contiguous(),
+                                      ga, gt)
+        return torch.view_as_complex(ga[:P]), gt[:P]
+
+
+class CIR(torch.autograd.Function):
+    """(eps_r [M], sigma [M], tx_pos [n,3], tx_ypr [n,3]) -> (a [P,nrp,ntp], tau [P]).
+
+    The forward uploads the parameters to the tracer and evaluates the stored
+    paths (they must have been computed for this geometry); the backward
+    replays them through rt_cir_backward.
+    """
+
+    @staticmethod
+    def forward(ctx, tracer, eps_r, sigma, tx_pos, tx_ypr):
+        tracer.set_materials(torch.stack([eps_r.detach(), sigma.detach()], 1).float())
+        tracer.set_tx(tx_pos.detach().float(), tx_ypr.detach().float(), tracer.tx_antenna)
+        a, tau = tracer.cir()
+        ctx.tracer = tracer
+        return a, tau
+
+    @staticmethod
+    def backward(ctx, grad_a, grad_tau):
+        tr = ctx.tracer
+        if grad_a is None:
+            grad_a = torch.zeros((tr.n_paths, tr.nrp, tr.ntp), dtype=torch.complex64, device=tr.device)
+        ge, gs, gp, gy = tr.cir_backward(grad_a, grad_tau)
+        return None, ge, gs, gp, gy
+
+
+class FreqResponse(torch.autograd.Function):
+    """(a [P,nrp,ntp], tau [P]) -> H [pairs, nrp, ntp, K] with rt_freq_response(_backward)."""
+
+    @staticmethod
+    def forward(ctx, tracer, a, tau, freqs):
+        ctx.tracer = tracer
+        ctx.save_for_backward(a, tau, freqs)
+        return tracer.freq_response(a, tau, freqs)
+
+    @staticmethod
+    def backward(ctx, grad_H):
+        a, tau, freqs = ctx.saved_tensors
+        ga, gt = ctx.tracer.freq_response_backward(a, tau, freqs, grad_H)
+        return None, ga, gt, None
