@@ -1,0 +1,431 @@
+"""Benchmark of the specular ray-tracing hot path on GB300.
+
+One step = one pass of the whole path over the seeded synthetic city
+(4802 triangles, 1 transmitter with a TR 38.901 dual-polarized sector
+pattern, 1000 receivers, 3.5 GHz):
+  LBVH build -> compute_paths (1e6 Fibonacci rays, max_depth 3: shooting and
+  bouncing, duplicate removal, image method, LOS) -> CIR -> H(f) at 1024
+  subcarriers of 30 kHz -> coverage map (500 x 500 cells of 1 m at 1.5 m,
+  1e6 rays, max_depth 3) -> VJP of H(f) and of the CIR w.r.t. materials and
+  transmitter pose.
+metric = rays*bounces/s: closest-hit ray queries (shooting-and-bouncing
+plus coverage tracing) of the whole job / time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: replicas only (each rank traces its own copy of the workload,
+no collective on the data path), launched with torch.distributed.run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_RAYS = 1_000_000
+MAX_DEPTH = 3
+N_RX = 1000
+N_SC = 1024
+SC_SPACING = 30e3
+FC = 3.5e9
+GRID = dict(x0=-250.0, y0=-250.0, cell=1.0, nx=500, ny=500, h=1.5)
+WORKLOAD = "city-4802tri-1tx-1000rx-1e6rays-d3-1024sc-cm500x500"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks / throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 6:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import scenes as S
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    scene = S.city_scene(20)
+    tx, rx = S.city_devices(scene, n_rx=N_RX)
+    freqs_h = (np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING
+    # pinned host inputs (end-to-end leg) and device-resident copies (kernel leg)
+    host = {"verts": torch.from_numpy(scene.verts).pin_memory(),
+            "mat": torch.from_numpy(scene.mat_id).pin_memory(),
+            "mats": torch.from_numpy(scene.materials).pin_memory(),
+            "txp": torch.from_numpy(tx.pos).pin_memory(), "txy": torch.from_numpy(tx.ypr).pin_memory(),
+            "rxp": torch.from_numpy(rx.pos).pin_memory(), "rxy": torch.from_numpy(rx.ypr).pin_memory(),
+            "freqs": torch.from_numpy(freqs_h).pin_memory()}
+    devin = {k: v.to(dev) for k, v in host.items()}
+    tr = rt.Tracer(local, FC)
+    ctx = tr.ctx
+    grid = rt.rt_grid(GRID["x0"], GRID["y0"], GRID["cell"], GRID["h"], GRID["nx"], GRID["ny"])
+    n_pairs = N_RX
+    nrp, ntp = rx.antenna.n_ports, tx.antenna.n_ports
+    H = torch.empty((n_pairs, nrp, ntp, N_SC, 2), dtype=torch.float32, device=dev)
+    gain = torch.empty((1, GRID["ny"], GRID["nx"]), dtype=torch.float32, device=dev)
+    hits = torch.empty((1, GRID["ny"], GRID["nx"]), dtype=torch.int32, device=dev)
+    g_eps = torch.zeros(3, device=dev)
+    g_sig = torch.zeros(3, device=dev)
+    g_pos = torch.zeros((1, 3), device=dev)
+    g_ypr = torch.zeros((1, 3), device=dev)
+    state = {}
+
+    def step(inp):
+        rt.rt_set_stream(ctx)
+        rt.rt_load_scene(ctx, inp["verts"], inp["mat"], inp["mats"])
+        rt.rt_set_tx(ctx, inp["txp"], inp["txy"], tx.antenna)
+        rt.rt_set_rx(ctx, inp["rxp"], inp["rxy"], rx.antenna)
+        P = rt.rt_compute_paths(ctx, MAX_DEPTH, N_RAYS, rt.RT_LOS | rt.RT_REFLECTION)
+        a = torch.empty((max(P, 1), nrp, ntp, 2), dtype=torch.float32, device=dev)
+        tau = torch.empty(max(P, 1), dtype=torch.float32, device=dev)
+        rt.rt_cir(ctx, rt.RT_LOS | rt.RT_REFLECTION, a, tau)
+        rt.rt_freq_response(ctx, a, tau, inp["freqs"], H)
+        rt.rt_coverage_map(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits)
+        # VJP of L = 0.5 ||H||^2: grad_H = H
+        ga = torch.empty_like(a)
+        gt = torch.empty_like(tau)
+        rt.rt_freq_response_backward(ctx, a, tau, inp["freqs"], H, ga, gt)
+        rt.rt_cir_backward(ctx, rt.RT_LOS | rt.RT_REFLECTION, ga, gt, g_eps, g_sig, g_pos, g_ypr)
+        state["P"] = P
+        state["a"], state["tau"] = a, tau
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    # untimed: per-kernel work counts of one step
+    for _ in range(max(args.warmup, 3)):
+        step(devin)
+    torch.cuda.synchronize()
+    rt.rt_profile_report(ctx, reset=True)
+    rt.rt_load_scene(ctx, devin["verts"], devin["mat"], devin["mats"])
+    rt.rt_set_tx(ctx, devin["txp"], devin["txy"], tx.antenna)
+    rt.rt_set_rx(ctx, devin["rxp"], devin["rxy"], rx.antenna)
+    rt.rt_compute_paths(ctx, MAX_DEPTH, N_RAYS, rt.RT_LOS | rt.RT_REFLECTION)
+    sbr_counts = rt.rt_profile_report(ctx, reset=True)
+    rt.rt_coverage_map(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits)
+    cov_counts = rt.rt_profile_report(ctx, reset=True)
+    step(devin)
+    one = rt.rt_profile_report(ctx, reset=True)
+    bounces_per_step = one["closest_hit"]
+
+    # timed kernel leg: inputs resident in HBM
+    stream = torch.cuda.current_stream()
+    times = []
+    rt.rt_profile(ctx, True)
+    rt.rt_profile_report(ctx, reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(devin)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    prof = rt.rt_profile_report(ctx, reset=True)
+    rt.rt_profile(ctx, False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = bounces_per_step * args.steps * world / (total_ms / 1e3)
+
+    # end-to-end leg: pinned host inputs copied in, results read back, every step
+    e2e_times = []
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    out_h = {"H": torch.empty(H.shape, dtype=H.dtype).pin_memory(),
+             "gain": torch.empty(gain.shape, dtype=gain.dtype).pin_memory()}
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inp = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        step(inp)
+        out_h["H"].copy_(H, non_blocking=True)
+        out_h["gain"].copy_(gain, non_blocking=True)
+        a_h = state["a"].to("cpu", non_blocking=True)
+        tau_h = state["tau"].to("cpu", non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    d2h = (H.numel() * 4 + gain.numel() * 4 + state["a"].numel() * 4 + state["tau"].numel() * 4)
+    e2e_ms = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = bounces_per_step * args.steps * world / (e2e_ms / 1e3)
+
+    # dominant kernel and its roofline
+    kern = prof["kernels"]
+    dom = max(kern, key=lambda k: kern[k][1])
+    hbm, src = peaks()
+    roof = roofline(dom, kern[dom], sbr_counts, cov_counts, hbm, src)
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = extra_measurements(tr, scene, dev, args)
+
+    if world > 1:
+        dist.barrier()
+    if rank != 0:
+        return
+    cpu = cpu_baseline(scene, tx, rx) if (world == 1 and not args.no_cpu) else None
+    line = {
+        "metric": "rays*bounces/s",
+        "value": value,
+        "unit": "rays*bounces/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded city; no dataset)",
+        "config": {"workload": WORKLOAD, "tris": int(scene.n_tris), "n_tx": 1, "n_rx": N_RX,
+                   "num_rays": N_RAYS, "max_depth": MAX_DEPTH, "subcarriers": N_SC,
+                   "coverage_cells": GRID["nx"] * GRID["ny"], "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas{world}"},
+        "paths_per_step": state["P"],
+        "ray_bounces_per_step": bounces_per_step,
+        "gpu_launches": prof["launches"],
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in sorted(kern.items(), key=lambda x: -x[1][1])},
+        "e2e": {"value": e2e_value, "unit": "rays*bounces/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    line.update(extras)
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+
+
+def roofline(name, rec, sbr_counts, cov_counts, hbm, src):
+    """Algorithmic bytes of the dominant kernel per launch / its mean duration."""
+    launches, ms = rec
+    per_launch_s = ms / launches / 1e3
+    if name == "k_coverage":
+        c = cov_counts
+        bytes_ = c["nodes"] * 64 + c["tris"] * 48 + c["closest_hit"] * 8
+        basis = "BVH node records (64 B) + triangle records (48 B) fetched + 8 B cell update per query"
+    elif name == "k_sbr":
+        c = sbr_counts
+        bytes_ = c["nodes"] * 64 + c["tris"] * 48 + c["closest_hit"] * 8
+        basis = "BVH node records (64 B) + triangle records (48 B) fetched + 8 B key per query"
+    elif name == "k_validate":
+        c = sbr_counts
+        bytes_ = c["nodes"] * 64 + c["tris"] * 48
+        basis = "BVH node + triangle records fetched by visibility queries"
+    else:
+        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+                "traffic": None, "note": "no algorithmic byte model for this kernel"}
+    ach = bytes_ / per_launch_s / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None, "peak_source": src, "bytes_per_launch": bytes_,
+            "basis": basis, "ms_per_launch": per_launch_s * 1e3}
+
+
+def extra_measurements(tr, scene, dev, args):
+    """Batched coverage maps: 64 Tx x 1e7 rays, max_depth 5, 500 x 500 cells, one launch."""
+    import torch
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import scenes as S
+    txs = S.rooftop_transmitters(scene, 64)
+    rxd = S.Devices(np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32), S.V_ISO)
+    tr.load_scene(scene)
+    tr.set_devices(txs, rxd)
+    grid = rt.rt_grid(GRID["x0"], GRID["y0"], GRID["cell"], GRID["h"], GRID["nx"], GRID["ny"])
+    gain = torch.empty((64, GRID["ny"], GRID["nx"]), dtype=torch.float32, device=dev)
+    hits = torch.empty((64, GRID["ny"], GRID["nx"]), dtype=torch.int32, device=dev)
+    n = 10_000_000
+    rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
+    torch.cuda.synchronize()
+    rt.rt_profile_report(tr.ctx, reset=True)
+    rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
+    cnt = rt.rt_profile_report(tr.ctx, reset=True)
+    ts = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = min(ts)
+    return {"coverage_map_ms": ms,
+            "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch",
+            "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
+
+
+def cpu_baseline(scene, tx, rx, seconds=15.0):
+    """The FP64 oracle on the host cores: shooting and bouncing of a ray sample."""
+    from oracle import oracle as O
+    osc = O.make_scene(scene)
+    cores = O.nthreads()
+    n = 2000
+    t0 = time.perf_counter()
+    ids = np.arange(n, dtype=np.int64) * (N_RAYS // n)
+    hits, _ = O.trace_sbr(osc, tx.pos[0], N_RAYS, MAX_DEPTH, ids)
+    dt = time.perf_counter() - t0
+    if dt < seconds / 4:
+        n = int(n * seconds / max(dt, 1e-3) / 1.2)
+        ids = (np.arange(n, dtype=np.int64) * (N_RAYS / n)).astype(np.int64)
+        t0 = time.perf_counter()
+        hits, _ = O.trace_sbr(osc, tx.pos[0], N_RAYS, MAX_DEPTH, ids)
+        dt = time.perf_counter() - t0
+    queries = int(n + (hits[:, :-1] >= 0).sum())
+    return {"value": queries / dt, "unit": "rays*bounces/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the {N_RAYS} lattice rays of the city workload, max_depth {MAX_DEPTH}, "
+                      f"brute-force FP64 closest hit ({queries} queries in {dt:.1f} s)"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    world, rank, local = dist_init()
+    if rank != 0:
+        return
+    from paper_2303_11103_gb300 import scenes as S
+    scene = S.city_scene(20)
+    tx, rx = S.city_devices(scene, n_rx=N_RX)
+    for _ in range(args.warmup):
+        cpu_baseline(scene, tx, rx, seconds=2.0)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(scene, tx, rx, seconds=6.0))
+    total = time.perf_counter() - t_all
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": "rays*bounces/s", "value": v, "unit": "rays*bounces/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded city; no dataset)",
+            "config": {"workload": WORKLOAD, "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "rays*bounces/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "rays*bounces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_kernel_case(args):
+    """One kernel of the step on its own (for ncu captures): `--only coverage|paths`."""
+    import torch
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import scenes as S
+    scene = S.city_scene(20)
+    tx, rx = S.city_devices(scene, n_rx=N_RX)
+    tr = rt.Tracer(0, FC)
+    tr.load_scene(scene)
+    tr.set_devices(tx, rx)
+    for _ in range(args.warmup + args.steps):
+        if args.only == "coverage":
+            g, h = tr.coverage_map(GRID, MAX_DEPTH, args.rays, 0)
+        else:
+            tr.compute_paths(MAX_DEPTH, args.rays)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.only, "rays": args.rays, "launches": args.warmup + args.steps}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--only", choices=["coverage", "paths"], default=None,
+                    help="run one kernel case of the step (profiling)")
+    ap.add_argument("--rays", type=int, default=N_RAYS)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.only:
+        run_kernel_case(args)
+        return
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,20 @@ int rt_cir_backward(rt_ctx* ctx, uint32_t flags, const float* grad_a, const floa
 int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, const double* freqs,
                               int32_t K, const float* grad_H, float* grad_a, float* grad_tau);
 
+/*
+ * Instrumentation (the paper describes none; used for measurement).
+ * rt_profile(enable): start or stop CUDA-event timing of every kernel the
+ * context launches (events recorded on the context's stream right around
+ * each launch); clears earlier records. rt_profile_report: synchronises and
+ * writes JSON {"launches": kernel launches since the last reset,
+ * "kernels": {name: [launches, total ms]}, "closest_hit": closest-hit
+ * queries, "any_hit": visibility queries, "nodes": BVH node records
+ * fetched, "tris": triangle records fetched}; reset != 0 zeroes the
+ * counters afterwards. RT_ERR_CAPACITY if buf is too small (truncated).
+ */
+int rt_profile(rt_ctx* ctx, int enable);
+int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset);
+
 #ifdef __cplusplus
 }
 #endif

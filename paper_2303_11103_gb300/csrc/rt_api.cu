@@ -66,6 +66,32 @@ DevScene dev_scene(rt_ctx* ctx) {
     return s;
 }
 
+static const size_t PROF_MAX = 1 << 16;
+
+void prof_begin(rt_ctx* ctx, const char* name) {
+    ctx->launches++;
+    if (!ctx->prof || ctx->prof_name.size() >= PROF_MAX) return;
+    size_t k = ctx->prof_name.size();
+    while (ctx->prof_ev.size() < 2 * (k + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        ctx->prof_ev.push_back(e);
+    }
+    cudaEventRecord(ctx->prof_ev[2 * k], ctx->stream);
+    ctx->prof_name.push_back(name);
+    ctx->prof_open = true;
+}
+
+void prof_end(rt_ctx* ctx) {
+    if (!ctx->prof_open) return;
+    ctx->prof_open = false;
+    size_t k = ctx->prof_name.size() - 1;
+    cudaEventRecord(ctx->prof_ev[2 * k + 1], ctx->stream);
+}
+
 static int use_device(rt_ctx* ctx) {
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return set_cuda(ctx, e, "cudaSetDevice");
@@ -123,6 +149,7 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->counters, &ctx->status, &ctx->perm})
         buf_free(*b);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     delete ctx;
     return RT_OK;
 }
@@ -339,6 +366,62 @@ int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, con
     int64_t np = 0;
     rt_num_pairs(ctx, &np);
     return freq_vjp_impl(ctx, a, tau, freqs, K, grad_H, grad_a, grad_tau, np);
+}
+
+int rt_profile(rt_ctx* ctx, int enable) {
+    CHECK_CTX(ctx);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->prof = enable != 0;
+    ctx->prof_open = false;
+    ctx->prof_name.clear();
+    return RT_OK;
+}
+
+int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset) {
+    CHECK_CTX(ctx);
+    if (!buf || len == 0) return set_err(ctx, RT_ERR_INVALID_ARG, "profile_report: null buffer");
+    RT_TRY(cudaStreamSynchronize(ctx->stream));
+    std::vector<std::string> names;
+    std::vector<int64_t> counts;
+    std::vector<double> ms;
+    for (size_t k = 0; k < ctx->prof_name.size(); k++) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            t = 0.0f;
+        }
+        size_t j = 0;
+        while (j < names.size() && names[j] != ctx->prof_name[k]) j++;
+        if (j == names.size()) {
+            names.push_back(ctx->prof_name[k]);
+            counts.push_back(0);
+            ms.push_back(0.0);
+        }
+        counts[j]++;
+        ms[j] += t;
+    }
+    unsigned long long c[8] = {0};
+    RT_TRY(cudaMemcpy(c, ctx->counters.p, sizeof(c), cudaMemcpyDeviceToHost));
+    std::string s = "{\"launches\": " + std::to_string(ctx->launches) + ", \"kernels\": {";
+    for (size_t j = 0; j < names.size(); j++) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": [%lld, %.6f]", j ? ", " : "", names[j].c_str(), (long long)counts[j],
+                 ms[j]);
+        s += tmp;
+    }
+    s += "}, \"closest_hit\": " + std::to_string(c[RT_CNT_CLOSEST]) + ", \"any_hit\": " +
+         std::to_string(c[RT_CNT_ANY]) + ", \"nodes\": " + std::to_string(c[RT_CNT_NODES]) +
+         ", \"tris\": " + std::to_string(c[RT_CNT_TRIS]) + "}";
+    size_t n = std::min(len - 1, s.size());
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+    if (reset) {
+        ctx->launches = 0;
+        ctx->prof_name.clear();
+        ctx->prof_open = false;
+        RT_TRY(cudaMemset(ctx->counters.p, 0, sizeof(c)));
+    }
+    return s.size() < len ? RT_OK : set_err(ctx, RT_ERR_CAPACITY, "profile_report: buffer too small");
 }
 
 }  // extern "C"

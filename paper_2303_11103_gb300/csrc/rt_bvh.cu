@@ -263,9 +263,11 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     unsigned init[12];
     for (int k = 0; k < 12; k++) init[k] = (k % 6) < 3 ? 0xffffffffu : 0u;
     BT(cudaMemcpyAsync(bounds.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    prof_begin(ctx, "k_prep");
     k_prep<<<gT, B, 0, st>>>(verts, bp<int32_t>(ctx->mat), T, bp<float4>(ctx->tris_o),
                              bp<float4>(ctx->planes), bp<float>(lbox), bp<float>(cent),
                              bp<unsigned>(bounds));
+    prof_end(ctx);
     BT(cudaGetLastError());
     unsigned hb[12];
     BT(cudaMemcpyAsync(hb, bounds.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
@@ -280,14 +282,18 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     BT(buf_reserve(keys2, sizeof(uint64_t) * T));
     BT(buf_reserve(vals, sizeof(uint32_t) * T));
     BT(buf_reserve(vals2, sizeof(uint32_t) * T));
+    prof_begin(ctx, "k_morton");
     k_morton<<<gT, B, 0, st>>>(bp<float>(cent), T, bp<unsigned>(bounds), bp<uint64_t>(keys),
                                bp<uint32_t>(vals));
+    prof_end(ctx);
     BT(cudaGetLastError());
     BT(radix_sort64(ctx, bp<uint64_t>(keys), bp<uint64_t>(keys2), bp<uint32_t>(vals),
                     bp<uint32_t>(vals2), T, 30));
     const uint32_t* leaf_tri = bp<uint32_t>(vals);
     if (T == 1) {
+        prof_begin(ctx, "k_single_leaf");
         k_single_leaf<<<1, 1, 0, st>>>(bp<float>(lbox), pad, bp<float4>(ctx->nodes));
+        prof_end(ctx);
         BT(cudaGetLastError());
         ctx->n_nodes = 1;
         ctx->bvh_depth = 1;
@@ -299,22 +305,32 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         BT(buf_reserve(flag, sizeof(int) * m));
         BT(cudaMemsetAsync(flag.p, 0, sizeof(int) * m, st));
         int gm = (m + B - 1) / B;
+        prof_begin(ctx, "k_karras");
         k_karras<<<gm, B, 0, st>>>(bp<uint64_t>(keys), T, bp<int2>(child), bp<int>(pint), bp<int>(pleaf));
+        prof_end(ctx);
         BT(cudaGetLastError());
+        prof_begin(ctx, "k_refit");
         k_refit<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), bp<int2>(child), bp<int>(pint),
                                   bp<int>(pleaf), bp<float>(ibox), bp<int>(flag), pad);
+        prof_end(ctx);
         BT(cudaGetLastError());
         BT(buf_reserve(dkeys, sizeof(uint64_t) * m));
         BT(buf_reserve(dkeys2, sizeof(uint64_t) * m));
         BT(buf_reserve(rank, sizeof(int) * m));
         BT(buf_reserve(maxd, sizeof(int)));
         BT(cudaMemsetAsync(maxd.p, 0, sizeof(int), st));
+        prof_begin(ctx, "k_depth");
         k_depth<<<gm, B, 0, st>>>(m, bp<int>(pint), bp<uint64_t>(dkeys), bp<int>(maxd));
+        prof_end(ctx);
         BT(cudaGetLastError());
         BT(radix_sort64(ctx, bp<uint64_t>(dkeys), bp<uint64_t>(dkeys2), nullptr, nullptr, m, 40));
+        prof_begin(ctx, "k_rank");
         k_rank<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank));
+        prof_end(ctx);
+        prof_begin(ctx, "k_emit");
         k_emit<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank), bp<int2>(child), bp<float>(ibox),
                                  bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
+        prof_end(ctx);
         BT(cudaGetLastError());
         int hd = 0;
         BT(cudaMemcpyAsync(&hd, maxd.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -322,7 +338,9 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         ctx->n_nodes = m;
         ctx->bvh_depth = hd + 1;
     }
+    prof_begin(ctx, "k_leaf_tris");
     k_leaf_tris<<<gT, B, 0, st>>>(T, leaf_tri, bp<float4>(ctx->tris_o), bp<float4>(ctx->tris));
+    prof_end(ctx);
     BT(cudaGetLastError());
     BT(cudaStreamSynchronize(st));
     cleanup();

@@ -374,15 +374,19 @@ template <int NP>
 void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, int uniform,
                  double f0, double df, float* H, int64_t n_pairs) {
     dim3 grid((unsigned)((K + 128 * HF_RUN - 1) / (128 * HF_RUN)), (unsigned)n_pairs);
+    prof_begin(ctx, "k_freq");
     k_freq<NP><<<grid, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
                                               uniform, f0, df, (float2*)H);
+    prof_end(ctx);
 }
 
 template <int NP>
 void launch_freq_vjp(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K,
                      const float* gH, float* ga, float* gt, int64_t n_pairs) {
+    prof_begin(ctx, "k_freq_vjp");
     k_freq_vjp<NP><<<(unsigned)n_pairs, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau,
                                                                freqs, K, (const float2*)gH, (float2*)ga, gt);
+    prof_end(ctx);
 }
 
 }  // namespace
@@ -390,7 +394,9 @@ void launch_freq_vjp(rt_ctx* ctx, const float* a, const float* tau, const double
 int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau) {
     if (ctx->n_paths == 0) return RT_OK;
     CirParams c = make_cir(ctx, flags);
+    prof_begin(ctx, "k_cir");
     k_cir<<<(unsigned)((c.P + 127) / 128), 128, 0, ctx->stream>>>(c, (float2*)a, tau);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -399,8 +405,10 @@ int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau
                  float* g_pos, float* g_ypr) {
     if (ctx->n_paths == 0) return RT_OK;
     CirParams c = make_cir(ctx, flags);
+    prof_begin(ctx, "k_cir_vjp");
     k_cir_vjp<<<(unsigned)((c.P + 63) / 64), 64, 0, ctx->stream>>>(c, (const float2*)ga, gtau, g_eps, g_sig, g_pos,
                                                                   g_ypr);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }

@@ -66,7 +66,8 @@ __device__ __forceinline__ void fetch_node(const DevScene& s, const float4* sm, 
     }
 }
 
-// Slab test of one AABB; returns entry distance (or +inf when missed).
+// Slab test of one AABB; returns the entry distance, or NaN when missed (so
+// that every `tn <= bound` test fails, also against an infinite bound).
 __device__ __forceinline__ float slab(float lox, float loy, float loz, float hix, float hiy, float hiz,
                                       f3 oi, f3 inv, float tlo, float thi) {
     float t0x = fmaf(lox, inv.x, -oi.x), t1x = fmaf(hix, inv.x, -oi.x);
@@ -74,7 +75,7 @@ __device__ __forceinline__ float slab(float lox, float loy, float loz, float hix
     float t0z = fmaf(loz, inv.z, -oi.z), t1z = fmaf(hiz, inv.z, -oi.z);
     float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tlo));
     float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), thi));
-    return tn <= tf ? tn : __int_as_float(0x7f800000);
+    return tn <= tf ? tn : __int_as_float(0x7fc00000);
 }
 
 __device__ __forceinline__ f3 safe_inv(f3 d) {
@@ -101,12 +102,41 @@ __device__ __forceinline__ float tri_hit(float4 r0, float4 r1, float4 r2, f3 o, 
     return in ? t : __int_as_float(0x7f800000);
 }
 
+// Per-lane traversal counters (BVH node records and triangle records
+// fetched, queries), flushed once per warp at kernel end.
+struct TravCount {
+    unsigned nodes = 0, tris = 0, queries = 0;
+};
+
+// Counter slots of the context's device counter array (uint64 each).
+#define RT_CNT_WORK 0
+#define RT_CNT_PATHS 1
+#define RT_CNT_CLOSEST 2
+#define RT_CNT_ANY 3
+#define RT_CNT_NODES 4
+#define RT_CNT_TRIS 5
+
+__device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* counters, int query_slot) {
+    unsigned long long n = c.nodes, t = c.tris, q = c.queries;
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_xor_sync(0xffffffffu, n, o);
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0 && counters) {
+        atomicAdd(counters + RT_CNT_NODES, n);
+        atomicAdd(counters + RT_CNT_TRIS, t);
+        atomicAdd(counters + query_slot, q);
+    }
+}
+
 // Closest hit along o + t d (d unit), t > tmin, triangle `exclude` (original
 // id) skipped; equal t resolves to the lowest original id. Returns the
 // original triangle id or -1; t_out receives the distance.
 __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                           int exclude, float& t_out, unsigned* status) {
+                                           int exclude, float& t_out, unsigned* status, TravCount& cnt) {
     t_out = __int_as_float(0x7f800000);
+    cnt.queries++;
     if (s.n_tris == 0) return -1;
     f3 inv = safe_inv(d);
     f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
@@ -126,6 +156,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
         }
         float4 a, b, c, e;
         fetch_node(s, sm, n_sm, node, a, b, c, e);
+        cnt.nodes++;
         float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tb);
         float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tb);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
@@ -134,6 +165,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
             int k = ~c0;
             const float4* tp = s.tris + 3 * (size_t)k;
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != exclude) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -145,6 +177,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
             int k = ~c1;
             const float4* tp = s.tris + 3 * (size_t)k;
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != exclude) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -177,7 +210,8 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
 // Any occluder on the open segment (tmin, tmax) along o + t d (d unit),
 // skipping original ids ex0 / ex1.
 __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                        float tmax, int ex0, int ex1, unsigned* status) {
+                                        float tmax, int ex0, int ex1, unsigned* status, TravCount& cnt) {
+    cnt.queries++;
     if (s.n_tris == 0) return false;
     f3 inv = safe_inv(d);
     f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
@@ -193,6 +227,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         }
         float4 a, b, c, e;
         fetch_node(s, sm, n_sm, node, a, b, c, e);
+        cnt.nodes++;
         float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tmax);
         float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tmax);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
@@ -200,6 +235,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         if (h0 && c0 < 0) {
             const float4* tp = s.tris + 3 * (size_t)(~c0);
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != ex0 && id != ex1) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -210,6 +246,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         if (h1 && c1 < 0) {
             const float4* tp = s.tris + 3 * (size_t)(~c1);
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != ex0 && id != ex1) {
                 float t = tri_hit(r0, r1, r2, o, d);

@@ -71,7 +71,19 @@ struct rt_ctx {
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
     int trace_block = 256;
     int warp_chunk = 256;     // rays a warp takes per refill
+
+    // instrumentation: host count of kernel launches; optional CUDA-event
+    // timing of every launch on the context's stream
+    int64_t launches = 0;
+    bool prof = false, prof_open = false;
+    std::vector<const char*> prof_name;
+    std::vector<cudaEvent_t> prof_ev;  // 2 per record
 };
+
+// Bracket one kernel launch: counts it and, when profiling, records CUDA
+// events on the context's stream right before and after it.
+void prof_begin(rt_ctx* ctx, const char* name);
+void prof_end(rt_ctx* ctx);
 
 #define RT_TRY(expr)                                       \
     do {                                                   \

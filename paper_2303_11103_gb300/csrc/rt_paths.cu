@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(256) k_validate(ValParams p) {
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
+    TravCount cnt;
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < p.total;
          base += stride) {
         long long g = base + lane;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(256) k_validate(ValParams p) {
                 float L = sqrtf(dot(seg, seg));
                 f3 d = seg * (1.0f / L);
                 int ex0 = j >= 1 ? ids[j - 1] : -1, ex1 = j < K ? ids[j] : -1;
-                if (any_hit(p.s, sm, p.n_sm, P[j], d, L - p.s.tmin, ex0, ex1, p.status)) valid = false;
+                if (any_hit(p.s, sm, p.n_sm, P[j], d, L - p.s.tmin, ex0, ex1, p.status, cnt)) valid = false;
             }
             rec = ((uint64_t)pair << 32) | (uint64_t)c;
         }
@@ -241,6 +242,7 @@ __global__ void __launch_bounds__(256) k_validate(ValParams p) {
             }
         }
     }
+    flush_counts(cnt, p.count - RT_CNT_PATHS, RT_CNT_ANY);
 }
 
 // offsets[p] = first path with pair >= p (paths sorted by pair, candidate)
@@ -383,8 +385,14 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         if (e) return e;
     }
     if (nkeys > 0) {
+        prof_begin(ctx, "k_iota");
         k_iota<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(vals, nkeys);
-        if (los) k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nsbr, ctx->n_tx, f);
+        prof_end(ctx);
+        if (los) {
+            prof_begin(ctx, "k_write_los");
+            k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nsbr, ctx->n_tx, f);
+            prof_end(ctx);
+        }
         RT_TRY(cudaGetLastError());
     }
     RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
@@ -397,7 +405,9 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     uint32_t* cntp = bp<uint32_t>(cnt);
     RT_TRY(cudaMemsetAsync(cntp, 0, sizeof(uint32_t) * (nb + 1), st));
     if (nkeys > 0) {
+        prof_begin(ctx, "k_dedup_count");
         k_dedup_count<<<nb, DD_THREADS, 0, st>>>(keys, nkeys, sentinel_from, cntp);
+        prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
     RT_TRY(exclusive_scan_u32(ctx, cntp, nb + 1));
@@ -411,16 +421,22 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
     RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * std::max<int64_t>(U, 1)));
     if (U > 0) {
+        prof_begin(ctx, "k_dedup_write");
         k_dedup_write<<<nb, DD_THREADS, 0, st>>>(keys, vals, nkeys, sentinel_from, cntp,
                                                  bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit));
+        prof_end(ctx);
         RT_TRY(cudaGetLastError());
+        prof_begin(ctx, "k_cand_img");
         k_cand_img<<<(unsigned)((U + 255) / 256), 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, f,
                                                                bp<float>(ctx->tx_pos), bp<float4>(ctx->planes),
                                                                bp<float>(ctx->cand_img));
+        prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
+    prof_begin(ctx, "k_cand_off");
     k_cand_off<<<(ctx->n_tx + 256) / 256, 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, ctx->n_tx, f,
                                                          bp<int64_t>(ctx->cand_off));
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     std::vector<int64_t> coff(ctx->n_tx + 1);
     RT_TRY(cudaMemcpyAsync(coff.data(), ctx->cand_off.p, sizeof(int64_t) * (ctx->n_tx + 1),
@@ -468,7 +484,9 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_validate, 256, smem);
             int64_t need = (total + 255) / 256;
             int64_t grid = std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms);
+            prof_begin(ctx, "k_validate");
             k_validate<<<(unsigned)std::max<int64_t>(grid, 1), 256, smem, st>>>(vp);
+            prof_end(ctx);
             RT_TRY(cudaGetLastError());
         }
         unsigned long long hc = 0;
@@ -484,8 +502,10 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     RT_TRY(radix_sort64(ctx, bp<uint64_t>(ctx->path_key), bp<uint64_t>(ctx->path_key_alt), nullptr, nullptr, P,
                         32 + pair_bits));
     RT_TRY(buf_reserve(ctx->path_off, sizeof(int64_t) * (n_pairs + 1)));
+    prof_begin(ctx, "k_path_off");
     k_path_off<<<(unsigned)((n_pairs + 256) / 256), 256, 0, st>>>(bp<uint64_t>(ctx->path_key), P, n_pairs,
                                                                   bp<int64_t>(ctx->path_off));
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     int64_t Pm = std::max<int64_t>(P, 1);
     RT_TRY(buf_reserve(ctx->path_seq, sizeof(int32_t) * Pm * f.D));
@@ -511,7 +531,9 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         fp.depth = bp<int32_t>(ctx->path_depth);
         fp.len = bp<double>(ctx->path_len);
         fp.pair_tx = bp<int32_t>(ctx->path_pair);
+        prof_begin(ctx, "k_path_final");
         k_path_final<<<(unsigned)((P + 127) / 128), 128, 0, st>>>(fp);
+        prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
     unsigned hs = 0;
@@ -546,9 +568,11 @@ int export_candidates(rt_ctx* ctx, int32_t* tx, int32_t* depth, int32_t* seq, in
     f.id_bits = ctx->id_bits;
     f.depth_shift = f.D * f.id_bits;
     f.tx_shift = f.depth_shift + 3;
+    prof_begin(ctx, "k_cand_export");
     k_cand_export<<<(unsigned)((ctx->n_cand + 255) / 256), 256, 0, ctx->stream>>>(
         bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit), ctx->n_cand, f, std::max<int64_t>(ctx->num_rays, 1),
         tx, depth, seq, wit);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }

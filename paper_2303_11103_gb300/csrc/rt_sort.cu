@@ -119,12 +119,18 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
     int passes = (end_bit + 7) / 8;
     for (int p = 0; p < passes; p++) {
         int shift = 8 * p;
+        prof_begin(ctx, "rs_hist");
         rs_hist<<<nb, RS_THREADS, 0, ctx->stream>>>(kin, n, shift, hist, nb);
+        prof_end(ctx);
+        prof_begin(ctx, "rs_scan");
         rs_scan<<<1, 1024, 0, ctx->stream>>>(hist, (int64_t)256 * nb);
+        prof_end(ctx);
+        prof_begin(ctx, "rs_scatter");
         if (vals)
             rs_scatter<true><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, hist, nb);
         else
             rs_scatter<false><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, nullptr, kout, nullptr, n, shift, hist, nb);
+        prof_end(ctx);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t* tk = kin; kin = kout; kout = tk;
@@ -141,6 +147,8 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
 // Exclusive scan of m uint32 entries in place (single block).
 cudaError_t exclusive_scan_u32(rt_ctx* ctx, uint32_t* a, int64_t m) {
     if (m <= 0) return cudaSuccess;
+    prof_begin(ctx, "rs_scan");
     rs_scan<<<1, 1024, 0, ctx->stream>>>(a, m);
+    prof_end(ctx);
     return cudaGetLastError();
 }

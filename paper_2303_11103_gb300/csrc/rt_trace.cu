@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
     int last = -1, depth = 0;
     long long slot = 0;
     uint64_t key = 0;
+    TravCount cnt;
     while (true) {
         long long s = feed.refill(p.c, alive);
         if (s >= 0) {
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
         }
         if (alive) {
             float t;
-            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status);
+            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status, cnt);
             if (id < 0) {
                 alive = false;
             } else {
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
             }
         }
     }
+    flush_counts(cnt, p.c.counter, RT_CNT_CLOSEST);
 }
 
 // ------------------------------------------------------------- coverage map
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     Cx<float> E[3];
     const float zeta_t = p.txa.slant[p.tx_port], zeta_r = p.rxa.slant[0];
     Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
+    TravCount cnt;
     while (true) {
         long long s = feed.refill(p.c, alive);
         if (s >= 0) {
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
         }
         if (alive) {
             float t;
-            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status);
+            int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status, cnt);
             if (d.z != 0.0f) {
                 float sc = (p.h - o.z) / d.z;
                 if (sc > 0.0f && (id < 0 || sc < t)) {
@@ -222,6 +225,7 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
             }
         }
     }
+    flush_counts(cnt, p.c.counter, RT_CNT_CLOSEST);
 }
 
 __global__ void k_dirs(long long N, long long first, long long n, float* __restrict__ out) {
@@ -244,7 +248,9 @@ int trace_grid(rt_ctx* ctx, const void* kernel, size_t smem) {
 
 int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out) {
     if (n <= 0) return RT_OK;
+    prof_begin(ctx, "k_dirs");
     k_dirs<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(N, first, n, out);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -258,8 +264,10 @@ int ensure_perm(rt_ctx* ctx, int64_t N) {
     if (e == cudaSuccess) e = buf_reserve(k2, sizeof(uint64_t) * (size_t)N);
     if (e == cudaSuccess) e = buf_reserve(v2, sizeof(uint32_t) * (size_t)N);
     if (e == cudaSuccess) {
+        prof_begin(ctx, "k_perm_keys");
         k_perm_keys<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(N, bp<uint64_t>(k1),
                                                                          bp<uint32_t>(ctx->perm));
+        prof_end(ctx);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -306,7 +314,9 @@ int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits) {
     RT_TRY(cudaFuncSetAttribute(k_sbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_sbr, smem);
+    prof_begin(ctx, "k_sbr");
     k_sbr<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }
@@ -344,7 +354,9 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_coverage, smem);
+    prof_begin(ctx, "k_coverage");
     k_coverage<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }

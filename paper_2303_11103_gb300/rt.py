@@ -80,6 +80,8 @@ def lib():
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
+            "rt_profile": [vp, ctypes.c_int],
+            "rt_profile_report": [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -227,6 +229,26 @@ def rt_freq_response_backward(ctx, a, tau, freqs, grad_H, grad_a, grad_tau):
                                                 _ptr(grad_H), _ptr(grad_a), _ptr(grad_tau)))
 
 
+def rt_profile(ctx, enable: bool):
+    _check(ctx, lib().rt_profile(ctx, 1 if enable else 0))
+
+
+def rt_profile_report(ctx, reset: bool = False) -> dict:
+    import json
+    size = 1 << 16
+    while True:
+        buf = ctypes.create_string_buffer(size)
+        code = lib().rt_profile_report(ctx, buf, size, 0)
+        if code == -4 and size < (1 << 24):
+            size *= 4
+            continue
+        _check(ctx, code)
+        break
+    if reset:
+        _check(ctx, lib().rt_profile_report(ctx, buf, size, 1))
+    return json.loads(buf.value.decode())
+
+
 # --------------------------------------------------------------- convenience
 class Tracer:
     """One rt_ctx on one device, with torch tensors in and out."""
@@ -258,6 +280,12 @@ class Tracer:
 
     def sync_stream(self):
         rt_set_stream(self.ctx)
+
+    def profile(self, enable: bool = True):
+        rt_profile(self.ctx, enable)
+
+    def report(self, reset: bool = False) -> dict:
+        return rt_profile_report(self.ctx, reset)
 
     def load_scene(self, scene):
         self.sync_stream()
