@@ -207,6 +207,39 @@ int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, con
                               int32_t K, const float* grad_H, float* grad_a, float* grad_tau);
 
 /*
+ * Batching (not in the paper): CUDA graph of a sequence of calls.
+ * rt_graph_begin starts capturing the context's work (on an internal stream
+ * when the context's stream is the legacy default stream); the calls that
+ * follow are recorded instead of run. Calls that read results back to the
+ * host (rt_compute_paths, rt_load_scene, rt_set_rx with receiver sets,
+ * rt_profile_report, a first rt_coverage_map at a new num_rays) fail with
+ * RT_ERR_NOT_READY while capturing. rt_graph_end instantiates the graph;
+ * rt_graph_launch replays it on the context's stream, reading the buffers
+ * the recorded calls named (update their contents in place between
+ * replays). One graph per context; rt_graph_begin replaces the previous.
+ */
+int rt_graph_begin(rt_ctx* ctx);
+int rt_graph_end(rt_ctx* ctx);
+int rt_graph_launch(rt_ctx* ctx);
+
+/*
+ * Autotuner (not in the paper): times rt_coverage_map on the current scene
+ * and transmitters for every candidate launch configuration of the
+ * persistent tracing kernels (threads per block, rays per warp refill, BVH
+ * nodes staged in shared memory), keeps the fastest for this context and,
+ * if cache_path is not NULL, records it there (a text line per workload
+ * key) and reuses a recorded choice when the key matches. gain/hits:
+ * scratch outputs of the size rt_coverage_map needs. Synchronises.
+ */
+int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, float* gain,
+                uint32_t* hits, const char* cache_path);
+/* The launch configuration in use: block threads (128|256), rays per warp
+ * refill (0 = automatic, else >= 32), BVH nodes staged in shared memory
+ * (<= 3200) (HOST out / in). */
+int rt_get_tuning(const rt_ctx* ctx, int32_t* block, int32_t* chunk, int32_t* smem_nodes);
+int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes);
+
+/*
  * Instrumentation (the paper describes none; used for measurement).
  * rt_profile(enable): start or stop CUDA-event timing of every kernel the
  * context launches (events recorded on the context's stream right around

@@ -70,7 +70,7 @@ static const size_t PROF_MAX = 1 << 16;
 
 void prof_begin(rt_ctx* ctx, const char* name) {
     ctx->launches++;
-    if (!ctx->prof || ctx->prof_name.size() >= PROF_MAX) return;
+    if (!ctx->prof || ctx->capturing || ctx->prof_name.size() >= PROF_MAX) return;
     size_t k = ctx->prof_name.size();
     while (ctx->prof_ev.size() < 2 * (k + 1)) {
         cudaEvent_t e;
@@ -103,6 +103,12 @@ static int use_device(rt_ctx* ctx) {
         if (!(c)) return RT_ERR_INVALID_ARG; \
         int e__ = use_device(c);           \
         if (e__) return e__;               \
+    } while (0)
+
+#define NO_CAPTURE(c, what)                                                        \
+    do {                                                                           \
+        if ((c)->capturing)                                                        \
+            return set_err(c, RT_ERR_NOT_READY, what ": reads results back, not allowed while capturing"); \
     } while (0)
 
 static bool valid_antenna(const rt_antenna* a) {
@@ -147,9 +153,11 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
                       &ctx->cand_img, &ctx->path_key, &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
-                      &ctx->sort_hist, &ctx->counters, &ctx->status, &ctx->perm})
+                      &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm})
         buf_free(*b);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
     return RT_OK;
 }
@@ -178,6 +186,7 @@ int rt_set_frequency(rt_ctx* ctx, double fc) {
 int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t* mat_id, const float* mat_params,
                   int32_t n_mat) {
     CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "load_scene");
     if (n_tris < 0 || n_tris >= (1ll << 30) || n_mat <= 0 || !mat_params || (n_tris > 0 && (!verts || !mat_id)))
         return set_err(ctx, RT_ERR_INVALID_ARG, "load_scene: bad arguments");
     ctx->has_scene = false;
@@ -233,6 +242,7 @@ int rt_set_rx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t m, const 
     CHECK_CTX(ctx);
     if (m < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: bad arguments");
     if (off_host) {
+        NO_CAPTURE(ctx, "set_rx with receiver sets");
         if (ctx->n_tx < 1) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: receiver sets need set_tx first");
         if (off_host[0] != 0 || off_host[ctx->n_tx] != m)
             return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: offsets must start at 0 and end at m");
@@ -270,6 +280,7 @@ int rt_num_pairs(const rt_ctx* ctx, int64_t* n) {
 
 int rt_compute_paths(rt_ctx* ctx, int32_t max_depth, int64_t num_rays, uint32_t flags, int64_t* num_paths) {
     CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "compute_paths");
     if (!num_paths || max_depth < 0 || max_depth > RT_MAX_DEPTH || num_rays < 0)
         return set_err(ctx, RT_ERR_INVALID_ARG, "compute_paths: bad arguments");
     if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
@@ -368,6 +379,133 @@ int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, con
     return freq_vjp_impl(ctx, a, tau, freqs, K, grad_H, grad_a, grad_tau, np);
 }
 
+int rt_graph_begin(rt_ctx* ctx) {
+    CHECK_CTX(ctx);
+    if (ctx->capturing) return set_err(ctx, RT_ERR_INVALID_ARG, "graph_begin: already capturing");
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    if (!ctx->cap_stream) RT_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    // the capture starts after everything already queued on the user's stream
+    RT_TRY(cudaStreamSynchronize(ctx->stream));
+    ctx->user_stream = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    RT_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    ctx->capturing = true;
+    ctx->launches_at_begin = ctx->launches;
+    return RT_OK;
+}
+
+int rt_graph_end(rt_ctx* ctx) {
+    CHECK_CTX(ctx);
+    if (!ctx->capturing) return set_err(ctx, RT_ERR_INVALID_ARG, "graph_end: not capturing");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->capturing = false;
+    ctx->stream = ctx->user_stream;
+    ctx->graph_kernels = ctx->launches - ctx->launches_at_begin;
+    ctx->launches = ctx->launches_at_begin;
+    if (e != cudaSuccess) return set_cuda(ctx, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return set_cuda(ctx, e, "cudaGraphInstantiate");
+    }
+    return RT_OK;
+}
+
+int rt_graph_launch(rt_ctx* ctx) {
+    CHECK_CTX(ctx);
+    if (!ctx->graph_exec) return set_err(ctx, RT_ERR_NOT_READY, "graph_launch: no graph");
+    RT_TRY(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->launches += ctx->graph_kernels;
+    return RT_OK;
+}
+
+int rt_get_tuning(const rt_ctx* ctx, int32_t* block, int32_t* chunk, int32_t* smem_nodes) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    if (block) *block = ctx->trace_block;
+    if (chunk) *chunk = ctx->warp_chunk;
+    if (smem_nodes) *smem_nodes = ctx->n_smem_nodes;
+    return RT_OK;
+}
+
+int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes) {
+    CHECK_CTX(ctx);
+    if ((block != 128 && block != 256) || (chunk != 0 && chunk < 32) || chunk > (1 << 20) || smem_nodes < 0 ||
+        (size_t)smem_nodes * 64 > 200 * 1024)
+        return set_err(ctx, RT_ERR_INVALID_ARG,
+                       "set_tuning: block 128|256, chunk 0 (auto) or >= 32, staged nodes <= 3200");
+    ctx->trace_block = block;
+    ctx->warp_chunk = chunk;
+    ctx->n_smem_nodes = smem_nodes;
+    return RT_OK;
+}
+
+int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, float* gain, uint32_t* hits,
+                const char* cache_path) {
+    CHECK_CTX(ctx);
+    if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "autotune while capturing a graph");
+    char key[160];
+    snprintf(key, sizeof(key), "tris=%d tx=%d rays=%lld depth=%d cells=%dx%d", ctx->n_tris, ctx->n_tx,
+             (long long)num_rays, max_depth, g ? g->nx : 0, g ? g->ny : 0);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[256];
+            while (fgets(line, sizeof(line), f)) {
+                int b, c, s;
+                char k[160];
+                if (sscanf(line, "%d %d %d %159[^\n]", &b, &c, &s, k) == 4 && strcmp(k, key) == 0) {
+                    fclose(f);
+                    return rt_set_tuning(ctx, b, c, s);
+                }
+            }
+            fclose(f);
+        }
+    }
+    const int blocks[] = {128, 256};
+    const int chunks[] = {0, 32, 128};
+    const int smems[] = {0, 256, 1024, 3072};
+    cudaEvent_t e0, e1;
+    RT_TRY(cudaEventCreate(&e0));
+    RT_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bb = ctx->trace_block, bc = ctx->warp_chunk, bs = ctx->n_smem_nodes;
+    int rc = RT_OK;
+    for (int b : blocks)
+        for (int c : chunks)
+            for (int s : smems) {
+                ctx->trace_block = b;
+                ctx->warp_chunk = c;
+                ctx->n_smem_nodes = s;
+                rc = rt_coverage_map(ctx, g, max_depth, num_rays, 0, gain, hits);  // warm (and ray order)
+                if (rc) break;
+                cudaEventRecord(e0, ctx->stream);
+                rc = rt_coverage_map(ctx, g, max_depth, num_rays, 0, gain, hits);
+                cudaEventRecord(e1, ctx->stream);
+                if (rc) break;
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; bb = b; bc = c; bs = s; }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->trace_block = bb;
+    ctx->warp_chunk = bc;
+    ctx->n_smem_nodes = bs;
+    if (rc) return rc;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%d %d %d %s\n", bb, bc, bs, key);
+            fclose(f);
+        }
+    }
+    return RT_OK;
+}
+
 int rt_profile(rt_ctx* ctx, int enable) {
     CHECK_CTX(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -379,6 +517,7 @@ int rt_profile(rt_ctx* ctx, int enable) {
 
 int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset) {
     CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "profile_report");
     if (!buf || len == 0) return set_err(ctx, RT_ERR_INVALID_ARG, "profile_report: null buffer");
     RT_TRY(cudaStreamSynchronize(ctx->stream));
     std::vector<std::string> names;

@@ -214,7 +214,7 @@ constexpr int HF_TILE = 64;
 template <int NP>
 __global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, const float2* __restrict__ a,
                                               const float* __restrict__ tau, const double* __restrict__ freqs,
-                                              int K, int uniform, double f0, double df, float2* __restrict__ H) {
+                                              int K, float2* __restrict__ H) {
     __shared__ float2 sa[HF_TILE][NP];
     __shared__ float st[HF_TILE];
     const int64_t pair = blockIdx.y;
@@ -225,15 +225,21 @@ __global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, c
     for (int s = 0; s < HF_RUN; s++)
 #pragma unroll
         for (int q = 0; q < NP; q++) acc[s][q] = make_float2(0.0f, 0.0f);
-    float fk0 = 0.0f;
+    // this thread's run of subcarriers; the recurrence needs uniform spacing
     float fl[HF_RUN];
-    if (uniform) {
-        fk0 = (float)(f0 + df * k0);
-    } else {
-#pragma unroll
-        for (int s = 0; s < HF_RUN; s++) fl[s] = k0 + s < K ? (float)freqs[k0 + s] : 0.0f;
+    bool uniform = k0 + HF_RUN <= K;
+    double f0 = 0.0, df = 0.0;
+    if (k0 < K) {
+        f0 = freqs[k0];
+        df = k0 + 1 < K ? freqs[k0 + 1] - f0 : 0.0;
     }
-    const float dff = (float)df;
+#pragma unroll
+    for (int s = 0; s < HF_RUN; s++) {
+        double fs = k0 + s < K ? freqs[k0 + s] : 0.0;
+        fl[s] = (float)fs;
+        if (fabs(fs - (f0 + s * df)) > 1e-9 * (fabs(fs) + 1.0)) uniform = false;
+    }
+    const float fk0 = (float)f0, dff = (float)df;
     for (int64_t tb = b; tb < e; tb += HF_TILE) {
         int n = (int)min((int64_t)HF_TILE, e - tb);
         __syncthreads();
@@ -371,12 +377,12 @@ CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
 }
 
 template <int NP>
-void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, int uniform,
-                 double f0, double df, float* H, int64_t n_pairs) {
+void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
+                 int64_t n_pairs) {
     dim3 grid((unsigned)((K + 128 * HF_RUN - 1) / (128 * HF_RUN)), (unsigned)n_pairs);
     prof_begin(ctx, "k_freq");
     k_freq<NP><<<grid, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
-                                              uniform, f0, df, (float2*)H);
+                                              (float2*)H);
     prof_end(ctx);
 }
 
@@ -416,18 +422,11 @@ int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
               int64_t n_pairs) {
     if (K <= 0 || n_pairs <= 0) return RT_OK;
-    std::vector<double> hf(K);
-    RT_TRY(cudaMemcpyAsync(hf.data(), freqs, sizeof(double) * K, cudaMemcpyDeviceToHost, ctx->stream));
-    RT_TRY(cudaStreamSynchronize(ctx->stream));
-    int uniform = 1;
-    double f0 = hf[0], df = K > 1 ? hf[1] - hf[0] : 0.0;
-    for (int k = 1; k < K && uniform; k++)
-        if (fabs(hf[k] - (f0 + df * k)) > 1e-9 * (fabs(hf[k]) + 1.0)) uniform = 0;
     const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
     switch (np) {
-        case 1: launch_freq<1>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
-        case 2: launch_freq<2>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
-        default: launch_freq<4>(ctx, a, tau, freqs, K, uniform, f0, df, H, n_pairs); break;
+        case 1: launch_freq<1>(ctx, a, tau, freqs, K, H, n_pairs); break;
+        case 2: launch_freq<2>(ctx, a, tau, freqs, K, H, n_pairs); break;
+        default: launch_freq<4>(ctx, a, tau, freqs, K, H, n_pairs); break;
     }
     RT_TRY(cudaGetLastError());
     return RT_OK;

@@ -63,14 +63,14 @@ struct rt_ctx {
     int64_t path_cap = 0;
 
     // scratch
-    DevBuf sort_hist, counters, status;
+    DevBuf sort_hist, scan_buf, counters, status;
     DevBuf perm;          // direction-coherent ray order
     int64_t perm_n = -1;
 
     // tuning
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
     int trace_block = 256;
-    int warp_chunk = 256;     // rays a warp takes per refill
+    int warp_chunk = 0;       // rays a warp takes per refill (0 = about 16 chunks per warp)
 
     // instrumentation: host count of kernel launches; optional CUDA-event
     // timing of every launch on the context's stream
@@ -78,6 +78,12 @@ struct rt_ctx {
     bool prof = false, prof_open = false;
     std::vector<const char*> prof_name;
     std::vector<cudaEvent_t> prof_ev;  // 2 per record
+
+    // CUDA graph capture
+    bool capturing = false;
+    cudaStream_t user_stream = nullptr, cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int64_t launches_at_begin = 0, graph_kernels = 0;
 };
 
 // Bracket one kernel launch: counts it and, when profiling, records CUDA

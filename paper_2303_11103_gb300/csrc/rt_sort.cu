@@ -26,29 +26,6 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of m entries with one block of 1024 threads.
-__global__ void __launch_bounds__(1024) rs_scan(uint32_t* __restrict__ a, int64_t m) {
-    __shared__ uint32_t part[1024];
-    int64_t per = (m + 1023) / 1024;
-    int64_t b = threadIdx.x * per, e = min(b + per, m);
-    uint32_t s = 0;
-    for (int64_t i = b; i < e; i++) s += a[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-    for (int64_t i = b; i < e; i++) {
-        uint32_t v = a[i];
-        a[i] = run;
-        run += v;
-    }
-}
-
 template <bool VALS>
 __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint64_t* __restrict__ kin,
                                                          const uint32_t* __restrict__ vin,
@@ -104,6 +81,68 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint64_t* __restr
     }
 }
 
+// Multi-block exclusive scan: each block scans a tile of SC_TILE entries in
+// place and writes the tile total; the totals are scanned recursively and
+// added back.
+constexpr int SC_THREADS = 1024, SC_IPT = 4, SC_TILE = SC_THREADS * SC_IPT;
+
+__global__ void __launch_bounds__(SC_THREADS) k_scan_tile(uint32_t* __restrict__ a, int64_t m,
+                                                          uint32_t* __restrict__ sums) {
+    __shared__ uint32_t ws[SC_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_IPT;
+    uint32_t v[SC_IPT], s = 0;
+#pragma unroll
+    for (int i = 0; i < SC_IPT; i++) {
+        v[i] = base + i < m ? a[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (w > 0 ? ws[w - 1] : 0u);
+#pragma unroll
+    for (int i = 0; i < SC_IPT; i++) {
+        if (base + i < m) a[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == SC_THREADS - 1 && sums) sums[blockIdx.x] = ws[31];
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ a, int64_t m, const uint32_t* __restrict__ offs) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] += offs[i / SC_TILE];
+}
+
+cudaError_t scan_level(rt_ctx* ctx, uint32_t* a, int64_t m, uint32_t* scratch) {
+    int64_t nb = (m + SC_TILE - 1) / SC_TILE;
+    prof_begin(ctx, "k_scan_tile");
+    k_scan_tile<<<(unsigned)nb, SC_THREADS, 0, ctx->stream>>>(a, m, nb > 1 ? scratch : nullptr);
+    prof_end(ctx);
+    if (nb == 1) return cudaGetLastError();
+    cudaError_t e = scan_level(ctx, scratch, nb, scratch + nb);
+    if (e != cudaSuccess) return e;
+    prof_begin(ctx, "k_scan_add");
+    k_scan_add<<<(unsigned)((m + 255) / 256), 256, 0, ctx->stream>>>(a, m, scratch);
+    prof_end(ctx);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
@@ -122,9 +161,8 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
         prof_begin(ctx, "rs_hist");
         rs_hist<<<nb, RS_THREADS, 0, ctx->stream>>>(kin, n, shift, hist, nb);
         prof_end(ctx);
-        prof_begin(ctx, "rs_scan");
-        rs_scan<<<1, 1024, 0, ctx->stream>>>(hist, (int64_t)256 * nb);
-        prof_end(ctx);
+        e = exclusive_scan_u32(ctx, hist, (int64_t)256 * nb);
+        if (e != cudaSuccess) return e;
         prof_begin(ctx, "rs_scatter");
         if (vals)
             rs_scatter<true><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, hist, nb);
@@ -144,11 +182,12 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
     return e;
 }
 
-// Exclusive scan of m uint32 entries in place (single block).
+// Exclusive scan of m uint32 entries in place.
 cudaError_t exclusive_scan_u32(rt_ctx* ctx, uint32_t* a, int64_t m) {
     if (m <= 0) return cudaSuccess;
-    prof_begin(ctx, "rs_scan");
-    rs_scan<<<1, 1024, 0, ctx->stream>>>(a, m);
-    prof_end(ctx);
-    return cudaGetLastError();
+    size_t need = 0;
+    for (int64_t k = (m + SC_TILE - 1) / SC_TILE; k > 1; k = (k + SC_TILE - 1) / SC_TILE) need += k;
+    cudaError_t e = buf_reserve(ctx->scan_buf, sizeof(uint32_t) * (need + 16));
+    if (e != cudaSuccess) return e;
+    return scan_level(ctx, a, m, bp<uint32_t>(ctx->scan_buf));
 }

@@ -244,6 +244,17 @@ int trace_grid(rt_ctx* ctx, const void* kernel, size_t smem) {
     return per_sm * ctx->num_sms;
 }
 
+// Rays per warp refill: the tuned value, else about 16 refills per resident
+// warp (multiple of 32, in [32, 1024]) so that the tail of the persistent
+// launch stays short.
+int pick_chunk(rt_ctx* ctx, long long total, int grid) {
+    if (ctx->warp_chunk > 0) return ctx->warp_chunk;
+    long long warps = (long long)grid * (ctx->trace_block / 32);
+    long long c = total / (warps * 16);
+    c = (c + 31) / 32 * 32;
+    return (int)std::min<long long>(std::max<long long>(c, 32), 1024);
+}
+
 }  // namespace
 
 int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out) {
@@ -257,6 +268,7 @@ int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out) {
 
 int ensure_perm(rt_ctx* ctx, int64_t N) {
     if (ctx->perm_n == N) return RT_OK;
+    if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "first trace at a new num_rays while capturing a graph");
     if (N > 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "num_rays above 2^32");
     DevBuf k1, k2, v2;
     RT_TRY(buf_reserve(ctx->perm, sizeof(uint32_t) * (size_t)N));
@@ -314,6 +326,7 @@ int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits) {
     RT_TRY(cudaFuncSetAttribute(k_sbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_sbr, smem);
+    p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     prof_begin(ctx, "k_sbr");
     k_sbr<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
     prof_end(ctx);
@@ -354,6 +367,7 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_coverage, smem);
+    p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     prof_begin(ctx, "k_coverage");
     k_coverage<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
     prof_end(ctx);

@@ -80,6 +80,12 @@ def lib():
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
+            "rt_graph_begin": [vp],
+            "rt_graph_end": [vp],
+            "rt_graph_launch": [vp],
+            "rt_autotune": [vp, ctypes.POINTER(rt_grid), i32, i64, vp, vp, ctypes.c_char_p],
+            "rt_get_tuning": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "rt_set_tuning": [vp, i32, i32, i32],
             "rt_profile": [vp, ctypes.c_int],
             "rt_profile_report": [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int],
         }
@@ -227,6 +233,33 @@ def rt_cir_backward(ctx, flags, grad_a, grad_tau, g_eps, g_sigma, g_txpos, g_txy
 def rt_freq_response_backward(ctx, a, tau, freqs, grad_H, grad_a, grad_tau):
     _check(ctx, lib().rt_freq_response_backward(ctx, _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]),
                                                 _ptr(grad_H), _ptr(grad_a), _ptr(grad_tau)))
+
+
+def rt_graph_begin(ctx):
+    _check(ctx, lib().rt_graph_begin(ctx))
+
+
+def rt_graph_end(ctx):
+    _check(ctx, lib().rt_graph_end(ctx))
+
+
+def rt_graph_launch(ctx):
+    _check(ctx, lib().rt_graph_launch(ctx))
+
+
+def rt_autotune(ctx, grid: rt_grid, max_depth, num_rays, gain, hits, cache_path=None):
+    _check(ctx, lib().rt_autotune(ctx, ctypes.byref(grid), int(max_depth), int(num_rays), _ptr(gain), _ptr(hits),
+                                  cache_path.encode() if cache_path else None))
+
+
+def rt_get_tuning(ctx):
+    b, c, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, lib().rt_get_tuning(ctx, ctypes.byref(b), ctypes.byref(c), ctypes.byref(s)))
+    return int(b.value), int(c.value), int(s.value)
+
+
+def rt_set_tuning(ctx, block, chunk, smem_nodes):
+    _check(ctx, lib().rt_set_tuning(ctx, int(block), int(chunk), int(smem_nodes)))
 
 
 def rt_profile(ctx, enable: bool):
