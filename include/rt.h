@@ -94,7 +94,11 @@ int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat);
 /*
  * Sec. II-A (Listing 2): transmitters. pos [n*3], ypr [n*3] (yaw, pitch,
  * roll; 3GPP TR 38.901 Sec. 7.1 rotation Rz(yaw) Ry(pitch) Rx(roll)),
- * pattern pat (host struct, shared by all transmitters).
+ * pattern pat (host struct, shared by all transmitters). With the same n
+ * and port count as before this is a pose update: the stored paths and
+ * receiver sets are kept and rt_cir / rt_cir_backward evaluate the same
+ * triangle sequences at the new pose (paths frozen, as gradients assume);
+ * otherwise they are dropped.
  */
 int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const rt_antenna* pat);
 /*

@@ -228,12 +228,18 @@ static int set_devices(rt_ctx* ctx, DevBuf& pos, DevBuf& ypr, const float* p, co
 int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const rt_antenna* pat) {
     CHECK_CTX(ctx);
     if (n < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_tx: bad arguments");
+    // Same count and ports: a pose update. The stored paths (triangle
+    // sequences) and receiver sets stay; rt_cir re-evaluates the paths at
+    // the new pose (replay for gradients). Otherwise both are dropped.
+    bool pose_only = n == ctx->n_tx && pat->n_ports == ctx->tx_ant.n_ports;
     int e = set_devices(ctx, ctx->tx_pos, ctx->tx_ypr, pos, ypr, n);
     if (e) return e;
     ctx->n_tx = n;
     ctx->tx_ant = {pat->kind, pat->n_ports, {pat->slant[0], pat->slant[1]}};
-    ctx->rx_sets = false;
-    ctx->n_paths = 0;
+    if (!pose_only) {
+        ctx->rx_sets = false;
+        ctx->n_paths = 0;
+    }
     return RT_OK;
 }
 

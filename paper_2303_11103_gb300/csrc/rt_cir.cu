@@ -39,10 +39,11 @@ struct PathIn {
     S eps[RT_MAX_DEPTH], sig[RT_MAX_DEPTH];
 };
 
-// a[p][q] (rx port p, tx port q) and the path length (as S) of path i.
+// a[p][q] (rx port p, tx port q) and the path length (as S) of path i;
+// len64 = the same length accumulated in FP64 (carrier phase).
 template <class S>
 __device__ __forceinline__ void path_field(const CirParams& c, int64_t i, const PathIn<S>& in, f3 rx,
-                                           f3 rx_ypr, Cx<S> a[4], S& L) {
+                                           f3 rx_ypr, double len64, Cx<S> a[4], S& L) {
     const int K = c.depth[i];
     const int32_t* ids = c.seq + i * c.D;
     V3<S> I[RT_MAX_DEPTH + 1];
@@ -87,7 +88,7 @@ __device__ __forceinline__ void path_field(const CirParams& c, int64_t i, const 
     }
     V3<S> u = v_scale(kd[K], -1.0f);
     // phase: value from the FP64 length reduced modulo 2 pi, tangents from L
-    double x = c.len[i] / c.lambda;
+    double x = len64 / c.lambda;
     float ph0 = (float)(-2.0 * RT_PI_D * (x - floor(x)));
     S ph = L * (float)(-2.0 * RT_PI_D / c.lambda);
     S amp = SConst<S>::make((float)(c.lambda / (4.0 * RT_PI_D))) / L;
@@ -131,11 +132,12 @@ __global__ void k_cir(CirParams c, float2* __restrict__ a_out, float* __restrict
     f3 ry = mk(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
     Cx<float> a[4];
     float L;
-    path_field<float>(c, i, in, rx, ry, a, L);
+    const double len64 = path_length64(c.s, c.seq + i * c.D, K, mk(in.tx.x, in.tx.y, in.tx.z), rx);
+    path_field<float>(c, i, in, rx, ry, len64, a, L);
     const int np = c.txa.n_ports * c.rxa.n_ports;
     const bool on = path_enabled(c.flags, K);
     for (int k = 0; k < np; k++) a_out[i * np + k] = on ? make_float2(a[k].re, a[k].im) : make_float2(0.0f, 0.0f);
-    tau[i] = (float)(c.len[i] / RT_C0_D);
+    tau[i] = (float)(len64 / RT_C0_D);
 }
 
 // ----------------------------------------------------------------- VJP of cir
@@ -166,6 +168,8 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
     float2 g[4];
     for (int k = 0; k < np; k++) g[k] = on ? ga[i * np + k] : make_float2(0.0f, 0.0f);
     const float gt = gtau ? gtau[i] : 0.0f;
+    const double len64 = path_length64(c.s, c.seq + i * c.D, K,
+                                       mk(c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]), rx);
     for (int base = 0; base < nloc; base += NT) {
         auto var = [&](float v, int idx) {
             Dual<NT> d = dconst<NT>(v);
@@ -184,7 +188,7 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
         }
         Cx<Dual<NT>> a[4];
         Dual<NT> L;
-        path_field<Dual<NT>>(c, i, in, rx, ry, a, L);
+        path_field<Dual<NT>>(c, i, in, rx, ry, len64, a, L);
         for (int j = 0; j < NT && base + j < nloc; j++) {
             float acc = gt * L.d[j] * (float)(1.0 / RT_C0_D);
             for (int k = 0; k < np; k++) acc += g[k].x * a[k].re.d[j] + g[k].y * a[k].im.d[j];

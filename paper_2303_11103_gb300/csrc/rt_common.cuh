@@ -287,6 +287,27 @@ __device__ __forceinline__ f3 fib_dir(long long N, long long i) {
     return {(float)(rho * cp), (float)(rho * sp), (float)z};
 }
 
+// Length of the specular path tx -> triangles ids[0..K-1] -> rx, in FP64:
+// for a specular path it equals |rx - I_K|, I_K the last image of tx, with
+// the planes' normals taken in FP64 from the stored FP32 triangle edges.
+__device__ __forceinline__ double path_length64(const DevScene& s, const int32_t* ids, int K, f3 tx, f3 rx) {
+    double I[3] = {(double)tx.x, (double)tx.y, (double)tx.z};
+    for (int k = 0; k < K; k++) {
+        const float4* tp = s.tris_o + 3 * (size_t)ids[k];
+        float4 r0 = tp[0], r1 = tp[1], r2 = tp[2];
+        double e1[3] = {r1.x, r1.y, r1.z}, e2[3] = {r2.x, r2.y, r2.z}, v0[3] = {r0.x, r0.y, r0.z};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        n[0] /= nl;
+        n[1] /= nl;
+        n[2] /= nl;
+        double sd = (I[0] - v0[0]) * n[0] + (I[1] - v0[1]) * n[1] + (I[2] - v0[2]) * n[2];
+        for (int q = 0; q < 3; q++) I[q] -= 2.0 * sd * n[q];
+    }
+    double dx = (double)rx.x - I[0], dy = (double)rx.y - I[1], dz = (double)rx.z - I[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
 // Specular reflection of d about the plane with unit normal n.
 __device__ __forceinline__ f3 reflect(f3 d, f3 n) { return d - n * (2.0f * dot(d, n)); }
 

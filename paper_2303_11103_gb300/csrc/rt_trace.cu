@@ -374,3 +374,4 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }
+

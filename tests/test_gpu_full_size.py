@@ -86,7 +86,7 @@ def test_full_size_paths_cir_freq(city):
 def test_full_size_coverage_sample(city):
     tr, sc, tx, rx, osc, P = city
     grid = dict(x0=-250.0, y0=-250.0, cell=1.0, nx=500, ny=500, h=1.5)
-    first, count = 400_000, 20_000          # a lattice sub-range of the 1e6-ray map
+    first, count = 600_000, 60_000          # a lattice sub-range of the 1e6-ray map (z < 0: downward)
     ids = np.arange(first, first + count)
     _, marg = O.trace_sbr(osc, tx.pos[0], N, D + 1, ids)
     bad = ids[marg[:, -1] < osc.eps]
@@ -104,7 +104,7 @@ def test_full_size_coverage_sample(city):
     clean = om == 0
     assert np.array_equal(h[clean], oh[clean].astype(np.int64))
     touched = clean & (oh > 0)
-    assert touched.sum() > 1000
+    assert touched.sum() > 300
     rel = np.abs(g[touched] - og[touched]) / og[touched]
     assert rel.max() < 1e-4
     assert np.all(np.abs(g - og) <= om + 1e-4 * og + 1e-30)
