@@ -194,6 +194,33 @@ int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth,
                                uint32_t* hits);
 
 /*
+ * Allocation-free coverage map. The paper has no counterpart; it exists for
+ * callers that must not allocate device memory at call time: hosts whose
+ * device memory is owned by another allocator (a framework's caching
+ * allocator can leave cudaMalloc without room, or fragment memory it
+ * manages), latency-critical loops in which cudaMalloc's implicit
+ * synchronisation is not acceptable, and plug-ins whose host application
+ * forbids device allocations. Same inputs, outputs and result as
+ * rt_coverage_map (up to float summation order), but the call allocates
+ * nothing: its scratch (work counter, status word, ray order) lives in one
+ * static device array of about 4.03 MB that every GPU which loads the library
+ * holds until the process exits. Limits and behaviour:
+ *   - num_rays <= RT_NOALLOC_MAX_RAYS (1048576) per transmitter, else
+ *     RT_ERR_INVALID_ARG with a message (use rt_coverage_map for more);
+ *   - the context must already hold the scene and devices (rt_load_scene,
+ *     rt_set_tx, rt_set_rx allocate; call them during set-up);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     during set-up, before any stream capture;
+ *   - all calls share the one array and each call clears what must start at
+ *     zero; calls whose GPU work overlaps (other streams or contexts on the
+ *     same device) race on it, so serialise them.
+ */
+#define RT_NOALLOC_MAX_RAYS 1048576
+int rt_coverage_map_noalloc(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
+                            int32_t tx_port, float* gain, uint32_t* hits);
+
+/*
  * Sec. I/II (differentiability): vector-Jacobian products through the
  * stored paths (no re-trace). grad_a [P*nrp*ntp] complex and grad_tau [P]
  * (may be NULL) are the upstream gradients of a real loss w.r.t. rt_cir's

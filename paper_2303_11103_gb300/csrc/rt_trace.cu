@@ -375,3 +375,42 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     return RT_OK;
 }
 
+// The coverage kernel on scratch the caller provides: the work counter and
+// traversal counter slots at `counters` (8 x uint64, zeroed here), the status
+// word at `status`, the ray order at `perm` (null = lattice order). Allocates
+// no device memory.
+int launch_coverage_scratch(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int tx_port, float* gain,
+                            uint32_t* hits, unsigned long long* counters, unsigned* status, const uint32_t* perm) {
+    CovParams p;
+    p.c = make_common(ctx, N, 0, N);
+    p.c.counter = counters;
+    p.c.status = status;
+    p.c.perm = perm;
+    p.D = D;
+    p.txa = ctx->tx_ant;
+    p.rxa = ctx->rx_ant;
+    p.tx_port = tx_port;
+    p.inv_we0 = (float)(1.0 / (2.0 * RT_PI_D * ctx->fc * RT_EPS0_D));
+    p.x0 = g->x0;
+    p.y0 = g->y0;
+    p.inv_cell = 1.0f / g->cell;
+    p.h = g->height;
+    p.nx = g->nx;
+    p.ny = g->ny;
+    double lam = RT_C0_D / ctx->fc;
+    p.wscale = (float)(lam * lam / (4.0 * RT_PI_D * (double)g->cell * g->cell * (double)N));
+    p.gain = gain;
+    p.hits = hits;
+    size_t cells = (size_t)ctx->n_tx * g->nx * g->ny;
+    RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * cells, ctx->stream));
+    RT_TRY(cudaMemsetAsync(hits, 0, sizeof(uint32_t) * cells, ctx->stream));
+    RT_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned long long), ctx->stream));
+    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
+    RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = trace_grid(ctx, (const void*)k_coverage, smem);
+    p.c.chunk = pick_chunk(ctx, p.c.total, grid);
+    ctx->launches++;
+    k_coverage<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}

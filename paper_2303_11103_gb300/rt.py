@@ -78,6 +78,7 @@ def lib():
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
+            "rt_coverage_map_noalloc": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
             "rt_graph_begin": [vp],
@@ -223,6 +224,12 @@ def rt_coverage_map_accumulate(ctx, grid: rt_grid, max_depth, num_rays, first_ra
     _check(ctx, lib().rt_coverage_map_accumulate(ctx, ctypes.byref(grid), int(max_depth), int(num_rays),
                                                  int(first_ray), int(ray_count), int(tx_port), _ptr(gain),
                                                  _ptr(hits)))
+
+
+def rt_coverage_map_noalloc(ctx, grid: rt_grid, max_depth, num_rays, tx_port, gain, hits):
+    """rt_coverage_map without device allocation (static scratch, num_rays <= 2^20)."""
+    _check(ctx, lib().rt_coverage_map_noalloc(ctx, ctypes.byref(grid), int(max_depth), int(num_rays),
+                                              int(tx_port), _ptr(gain), _ptr(hits)))
 
 
 def rt_cir_backward(ctx, flags, grad_a, grad_tau, g_eps, g_sigma, g_txpos, g_txypr):
