@@ -279,29 +279,43 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+# Algorithmic FP32/ALU operations of the traversal: two slab tests per BVH
+# node record (2 x (6 FMA + 6 per-axis min/max + 4 combining min/max + 1
+# compare) = 34) and one Moller-Trumbore test per triangle record (35).
+OPS_PER_NODE, OPS_PER_TRI = 34, 35
+# FP32/ALU lane-operation peak: 152 SMs x 128 lanes x 2070 MHz (one op per
+# lane per clock, an FMA counted as one operation).
+ALU_PEAK_GOPS = 152 * 128 * 2.070
+# DRAM bytes (read + write) of one k_coverage launch of this workload, from
+# the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
+# None whenever the kernel changes until it is captured again.
+K_COVERAGE_TRAFFIC = 4.49e6
+
+
 def roofline(name, rec, sbr_counts, cov_counts, hbm, src):
-    """Algorithmic bytes of the dominant kernel per launch / its mean duration."""
+    """Roofline of the dominant kernel: algorithmic work per launch / mean duration.
+
+    The traversal kernels keep the BVH and triangles in L1/L2 (ncu: 98 % L1
+    hits, 4.5 MB of DRAM traffic per coverage launch), so their bound is ALU
+    issue, not HBM; the node/triangle record bytes they request are reported
+    beside it (`requested_gbs`) for comparison with the HBM peak.
+    """
     launches, ms = rec
     per_launch_s = ms / launches / 1e3
-    if name == "k_coverage":
-        c = cov_counts
-        bytes_ = c["nodes"] * 64 + c["tris"] * 48 + c["closest_hit"] * 8
-        basis = "BVH node records (64 B) + triangle records (48 B) fetched + 8 B cell update per query"
-    elif name == "k_sbr":
-        c = sbr_counts
-        bytes_ = c["nodes"] * 64 + c["tris"] * 48 + c["closest_hit"] * 8
-        basis = "BVH node records (64 B) + triangle records (48 B) fetched + 8 B key per query"
-    elif name == "k_validate":
-        c = sbr_counts
-        bytes_ = c["nodes"] * 64 + c["tris"] * 48
-        basis = "BVH node + triangle records fetched by visibility queries"
-    else:
-        return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                "traffic": None, "note": "no algorithmic byte model for this kernel"}
-    ach = bytes_ / per_launch_s / 1e9
-    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None, "peak_source": src, "bytes_per_launch": bytes_,
-            "basis": basis, "ms_per_launch": per_launch_s * 1e3}
+    counts = {"k_coverage": cov_counts, "k_sbr": sbr_counts, "k_validate": sbr_counts}.get(name)
+    if counts is None:
+        return {"kernel": name, "bound": "alu", "achieved": None, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+                "frac": None, "traffic": None, "note": "no algorithmic model for this kernel"}
+    ops = counts["nodes"] * OPS_PER_NODE + counts["tris"] * OPS_PER_TRI
+    req_bytes = counts["nodes"] * 64 + counts["tris"] * 48
+    ach = ops / per_launch_s / 1e9
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+            "frac": ach / ALU_PEAK_GOPS,
+            "traffic": K_COVERAGE_TRAFFIC if name == "k_coverage" else None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+            "ops_per_launch": ops, "ops_basis": f"{OPS_PER_NODE} per BVH node record, {OPS_PER_TRI} per triangle record",
+            "requested_gbs": req_bytes / per_launch_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+            "ms_per_launch": per_launch_s * 1e3}
 
 
 def extra_measurements(tr, scene, dev, args):
