@@ -162,6 +162,14 @@ int rt_get_ray_hits(rt_ctx* ctx, int32_t* hits);
  */
 int rt_cir(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
 /*
+ * Path gain of every (tx, rx) pair from rt_cir's a [P*nrp*ntp]: out
+ * [n_pairs*2] = (1 if the pair has a path else 0, 10 log10(sum over paths
+ * and port pairs of |a|^2), or floor_db without paths). The incoherent
+ * received power the paper's transmitter-orientation example maximises
+ * (Sec. III-B) and the label of the path-gain surrogate.
+ */
+int rt_pair_gain(rt_ctx* ctx, const float* a, float floor_db, float* out);
+/*
  * Sec. III-A: H [n_pairs*nrp*ntp*K] complex, H = sum_i a_i exp(-j 2 pi f_k tau_i)
  * over the pair's paths, from a [P*nrp*ntp] and tau [P] as returned by
  * rt_cir; freqs [K] float64 baseband offsets (Hz).
@@ -269,6 +277,46 @@ int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_ra
  * (<= 3200) (HOST out / in). */
 int rt_get_tuning(const rt_ctx* ctx, int32_t* block, int32_t* chunk, int32_t* smem_nodes);
 int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes);
+
+/*
+ * Learned path-gain surrogate (not in the paper; Sec. I cites neural
+ * path-loss prediction as related work). f(tx, rx) = MLP(Fourier features):
+ * x' = 2 (x - lo)/(hi - lo) - 1 for the 6 coordinates (tx xyz, rx xyz),
+ * features [sin 2 pi B x', cos 2 pi B x'] with B [n_freq x 6] ~ N(0,
+ * sigma^2), n_hidden ReLU layers of `width`, a 2-wide head: (logit of "the
+ * tracer finds a path", path gain in dB). Dense layers run as tcgen05 BF16
+ * GEMMs with FP32 accumulation; parameters are FP32 (Adam), BF16 copies feed
+ * the GEMMs. All pointers are device pointers except *_host.
+ */
+typedef struct rt_mlp rt_mlp;
+/* n_freq % 4 == 0, width in {64, 128, 192, 256}, 1 <= n_hidden <= 16;
+ * lo_host/hi_host [6]: the normalisation box of (tx xyz, rx xyz). */
+int rt_mlp_create(rt_mlp** m, int device, void* cuda_stream, int32_t n_freq, int32_t width, int32_t n_hidden,
+                  float sigma, uint64_t seed, const float* lo_host, const float* hi_host);
+int rt_mlp_destroy(rt_mlp* m);
+int rt_mlp_set_stream(rt_mlp* m, void* cuda_stream);
+int rt_mlp_last_error(const rt_mlp* m, char* buf, size_t len);
+/* One Adam step on a batch: x [batch*6], target [batch*2] = (1 if the
+ * tracer found a path else 0, path gain dB); loss = mean over the batch of
+ * BCE(logit, has_path) + has_path ((gain_pred - gain)/20 dB)^2, ADDED to
+ * loss_out[0] (device; may be NULL). batch % 128 == 0. */
+int rt_mlp_train_step(rt_mlp* m, const float* x, const float* target, int32_t batch, float lr, float* loss_out);
+/* out [n*2] = (path logit, path gain dB) for x [n*6]. */
+int rt_mlp_infer(rt_mlp* m, const float* x, int64_t n, float* out);
+/* Parameter vector layout: per layer W [out x in] then b [out] (hidden
+ * layers, then the head), then the Fourier matrix [n_freq x 6]. */
+int rt_mlp_num_params(const rt_mlp* m, int64_t* n_host);
+int rt_mlp_get_params(rt_mlp* m, float* dst);
+int rt_mlp_set_params(rt_mlp* m, const float* src);
+/* Gradients of the last training step (before its update), parameter layout. */
+int rt_mlp_get_grads(rt_mlp* m, float* dst);
+/* Error bits of the GEMM kernels (1 = a bounded wait timed out) (HOST out). */
+int rt_mlp_status(rt_mlp* m, uint32_t* status_host);
+/* C [M x N] = act(A [M x K] B [N x K]^T + bias [N]) with BF16 A, B (row-major)
+ * on tcgen05; act = ReLU if relu; C BF16 if out_bf16 else FP32; N % 8 == 0,
+ * K % 8 == 0; status (device, may be NULL) receives timeout bits. */
+int rt_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                 const float* bias, int32_t relu, int32_t out_bf16, void* C, uint32_t* status);
 
 /*
  * Instrumentation (the paper describes none; used for measurement).

@@ -18,6 +18,7 @@ int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* f
 int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t first, int64_t count, bool zero,
                     int tx_port, float* gain, uint32_t* hits);
 int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out);
+int pair_gain_impl(rt_ctx* ctx, const float* a, float floor_db, float* out, int64_t n_pairs);
 
 cudaError_t buf_reserve(DevBuf& b, size_t bytes) {
     if (bytes <= b.bytes && b.p) return cudaSuccess;
@@ -383,6 +384,14 @@ int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, con
     int64_t np = 0;
     rt_num_pairs(ctx, &np);
     return freq_vjp_impl(ctx, a, tau, freqs, K, grad_H, grad_a, grad_tau, np);
+}
+
+int rt_pair_gain(rt_ctx* ctx, const float* a, float floor_db, float* out) {
+    CHECK_CTX(ctx);
+    if (!out || (!a && ctx->n_paths > 0)) return set_err(ctx, RT_ERR_INVALID_ARG, "pair_gain: null pointer");
+    int64_t np = 0;
+    rt_num_pairs(ctx, &np);
+    return pair_gain_impl(ctx, a, floor_db, out, np);
 }
 
 int rt_graph_begin(rt_ctx* ctx) {

@@ -436,6 +436,32 @@ int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs
     return RT_OK;
 }
 
+// Per pair: incoherent path gain sum_paths sum_ports |a|^2 in dB, and whether
+// the pair has any path (out [pair*2] = (has_path, gain dB or floor_db)).
+__global__ void k_pair_gain(const int64_t* __restrict__ off, const float2* __restrict__ a, int np, int64_t n_pairs,
+                            float floor_db, float* __restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_pairs) return;
+    double s = 0.0;
+    for (int64_t i = off[q] * np; i < off[q + 1] * np; i++) {
+        float2 v = a[i];
+        s += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    out[2 * q] = s > 0.0 ? 1.0f : 0.0f;
+    out[2 * q + 1] = s > 0.0 ? (float)(10.0 * log10(s)) : floor_db;
+}
+
+int pair_gain_impl(rt_ctx* ctx, const float* a, float floor_db, float* out, int64_t n_pairs) {
+    if (n_pairs <= 0) return RT_OK;
+    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
+    prof_begin(ctx, "k_pair_gain");
+    k_pair_gain<<<(unsigned)((n_pairs + 255) / 256), 256, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off),
+                                                                            (const float2*)a, np, n_pairs, floor_db, out);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
 int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, const float* gH,
                   float* ga, float* gt, int64_t n_pairs) {
     if (K <= 0 || n_pairs <= 0) return RT_OK;

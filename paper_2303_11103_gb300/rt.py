@@ -81,12 +81,26 @@ def lib():
             "rt_coverage_map_noalloc": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
+            "rt_pair_gain": [vp, vp, ctypes.c_float, vp],
             "rt_graph_begin": [vp],
             "rt_graph_end": [vp],
             "rt_graph_launch": [vp],
             "rt_autotune": [vp, ctypes.POINTER(rt_grid), i32, i64, vp, vp, ctypes.c_char_p],
             "rt_get_tuning": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "rt_set_tuning": [vp, i32, i32, i32],
+            "rt_mlp_create": [ctypes.POINTER(vp), ctypes.c_int, vp, i32, i32, i32, ctypes.c_float,
+                              ctypes.c_uint64, vp, vp],
+            "rt_mlp_destroy": [vp],
+            "rt_mlp_set_stream": [vp, vp],
+            "rt_mlp_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
+            "rt_mlp_train_step": [vp, vp, vp, i32, ctypes.c_float, vp],
+            "rt_mlp_infer": [vp, vp, i64, vp],
+            "rt_mlp_num_params": [vp, ctypes.POINTER(i64)],
+            "rt_mlp_get_params": [vp, vp],
+            "rt_mlp_set_params": [vp, vp],
+            "rt_mlp_get_grads": [vp, vp],
+            "rt_mlp_status": [vp, ctypes.POINTER(u32)],
+            "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, vp, i32, i32, vp, vp],
             "rt_profile": [vp, ctypes.c_int],
             "rt_profile_report": [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int],
         }
@@ -212,6 +226,10 @@ def rt_cir(ctx, flags, a, tau):
 
 def rt_freq_response(ctx, a, tau, freqs, H):
     _check(ctx, lib().rt_freq_response(ctx, _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]), _ptr(H)))
+
+
+def rt_pair_gain(ctx, a, floor_db, out):
+    _check(ctx, lib().rt_pair_gain(ctx, _ptr(a), float(floor_db), _ptr(out)))
 
 
 def rt_coverage_map(ctx, grid: rt_grid, max_depth, num_rays, tx_port, gain, hits):
@@ -418,6 +436,14 @@ class Tracer:
         a, tau = self.cir_raw(los, reflection)
         return torch.view_as_complex(a), tau
 
+    def pair_gain(self, a_raw, floor_db=-400.0):
+        """[pairs, 2] = (has path, incoherent path gain dB) from cir_raw's a."""
+        self.sync_stream()
+        out = torch.empty((self.n_pairs, 2), dtype=torch.float32, device=self.device)
+        a_raw = a_raw.contiguous() if a_raw.numel() else torch.zeros((1, self.nrp, self.ntp, 2), device=self.device)
+        rt_pair_gain(self.ctx, a_raw, floor_db, out)
+        return out
+
     def freq_response_raw(self, a_raw, tau, freqs):
         self.sync_stream()
         freqs = self._t(freqs, torch.float64)
@@ -520,3 +546,87 @@ class FreqResponse(torch.autograd.Function):
         a, tau, freqs = ctx.saved_tensors
         ga, gt = ctx.tracer.freq_response_backward(a, tau, freqs, grad_H)
         return None, ga, gt, None
+
+
+# ------------------------------------------------------------ surrogate MLP
+def rt_gemm_bf16(A, B, bias=None, relu=False, out_bf16=False, status=None):
+    """C = act(A B^T + bias) on tcgen05 (A [M, K], B [N, K] bfloat16 CUDA tensors)."""
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.bfloat16 if out_bf16 else torch.float32, device=A.device)
+    code = lib().rt_gemm_bf16(_stream(), _ptr(A), _ptr(B), int(M), int(N), int(K), _ptr(bias), int(bool(relu)),
+                              int(bool(out_bf16)), _ptr(C), _ptr(status))
+    if code:
+        raise RtError(code, "rt_gemm_bf16 failed")
+    return C
+
+
+class Surrogate:
+    """Fourier-feature MLP path-gain surrogate (rt_mlp_* C ABI)."""
+
+    def __init__(self, lo, hi, n_freq=32, width=256, n_hidden=8, sigma=1.0, seed=0, device=0):
+        self.F, self.W, self.L = n_freq, width, n_hidden
+        self.device = torch.device("cuda", device)
+        self.h = ctypes.c_void_p()
+        lo = (ctypes.c_float * 6)(*[float(v) for v in lo])
+        hi = (ctypes.c_float * 6)(*[float(v) for v in hi])
+        code = lib().rt_mlp_create(ctypes.byref(self.h), device, _stream(), n_freq, width, n_hidden,
+                                   float(sigma), int(seed), ctypes.cast(lo, ctypes.c_void_p),
+                                   ctypes.cast(hi, ctypes.c_void_p))
+        if code:
+            raise RtError(code, "rt_mlp_create failed")
+        n = ctypes.c_int64()
+        lib().rt_mlp_num_params(self.h, ctypes.byref(n))
+        self.n_params = int(n.value)
+
+    def _check(self, code):
+        if code:
+            buf = ctypes.create_string_buffer(512)
+            lib().rt_mlp_last_error(self.h, buf, 512)
+            raise RtError(code, buf.value.decode())
+
+    def close(self):
+        if self.h:
+            lib().rt_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync(self):
+        lib().rt_mlp_set_stream(self.h, _stream())
+
+    def train_step(self, x, target, lr, loss_acc=None):
+        self._sync()
+        self._check(lib().rt_mlp_train_step(self.h, _ptr(x.contiguous()), _ptr(target.contiguous()),
+                                            int(x.shape[0]), float(lr), _ptr(loss_acc)))
+
+    def infer(self, x):
+        self._sync()
+        out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=self.device)
+        self._check(lib().rt_mlp_infer(self.h, _ptr(x.contiguous()), int(x.shape[0]), _ptr(out)))
+        return out
+
+    def params(self):
+        p = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        self._sync()
+        self._check(lib().rt_mlp_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_params(self, p):
+        self._sync()
+        self._check(lib().rt_mlp_set_params(self.h, _ptr(p.to(torch.float32).contiguous())))
+
+    def grads(self):
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        self._sync()
+        self._check(lib().rt_mlp_get_grads(self.h, _ptr(g)))
+        return g
+
+    def status(self) -> int:
+        s = ctypes.c_uint32()
+        self._check(lib().rt_mlp_status(self.h, ctypes.byref(s)))
+        return int(s.value)
