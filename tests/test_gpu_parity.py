@@ -247,8 +247,11 @@ def test_coverage_matches_oracle(tracer, case):
         assert sel.sum() > 50
         db = 10 * np.abs(np.log10(g[sel] / og[sel]))
         assert db.max() <= CM_DB
-        # cells with crossings near a cell edge: bounded by that marginal mass
-        assert np.all(np.abs(g - og) <= om + 1e-4 * og + 1e-30)
+        # every cell: the marginal mass (crossings near a cell edge) plus the
+        # FP32 bound of the a_i rule applied to power (2e-3 relative, and a
+        # floor relative to the strongest cell for cross-polarised residues
+        # where the receive projection cancels)
+        assert np.all(np.abs(g - og) <= om + 2 * A_REL * og + 1e-10 * og.max() + 1e-30)
     # the full map equals the sum over the partition of the lattice
     g_full, h_full = tracer.coverage_map(grid, D, N, 0)
     g_part, h_part = tracer.coverage_map_ranges(grid, D, N, [(0, N // 3), (N // 3, N - N // 3)], 0)
