@@ -109,6 +109,7 @@ def run_ours(args):
     import torch.distributed as dist
     from paper_2303_11103_gb300 import rt
     from paper_2303_11103_gb300 import scenes as S
+    from paper_2303_11103_gb300.shard import max_over_ranks, sum_over_ranks
 
     world, rank, local = dist_init()
     torch.cuda.set_device(local)
@@ -117,8 +118,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     scene = S.city_scene(20)
-    tx, rx = S.city_devices(scene, n_rx=N_RX)
-    freqs_h = (np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING
+    # replicas: every rank traces its own transmitter (independent problems, no collective)
+    tx, rx = S.city_devices(scene, n_rx=N_RX, seed=2 + rank)
+    freqs_h =(np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING
     # pinned host inputs (end-to-end leg) and device-resident copies (kernel leg)
     host = {"verts": torch.from_numpy(scene.verts).pin_memory(),
             "mat": torch.from_numpy(scene.mat_id).pin_memory(),
@@ -199,12 +201,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     prof = rt.rt_profile_report(ctx, reset=True)
     rt.rt_profile(ctx, False)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = bounces_per_step * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(times), dev)
+    job_bounces = sum_over_ranks(bounces_per_step * args.steps, dev)
+    value = job_bounces / (total_ms / 1e3)
 
     # end-to-end leg: pinned host inputs copied in, results read back, every step
     e2e_times = []
@@ -226,12 +225,8 @@ def run_ours(args):
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     d2h = (H.numel() * 4 + gain.numel() * 4 + state["a"].numel() * 4 + state["tau"].numel() * 4)
-    e2e_ms = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = bounces_per_step * args.steps * world / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(sum(e2e_times), dev)
+    e2e_value = job_bounces / (e2e_ms / 1e3)
 
     # dominant kernel and its roofline
     kern = prof["kernels"]
@@ -241,6 +236,9 @@ def run_ours(args):
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = extra_measurements(tr, scene, dev, args)
+        if not args.no_surrogate:
+            extras.update(surrogate_measurement(tr, scene, n_tx=args.sur_tx, n_rx=args.sur_rx,
+                                                epochs=args.sur_epochs))
 
     if world > 1:
         dist.barrier()
@@ -351,6 +349,43 @@ def extra_measurements(tr, scene, dev, args):
             "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
 
 
+def surrogate_measurement(tr, scene, n_tx=2500, n_rx=4000, num_rays=200_000, max_depth=3, epochs=6,
+                          n_query=100_000_000, n_heldout=100_000):
+    """Learned surrogate on the city: tracer labels, training, held-out error, q/s vs the tracer."""
+    import torch
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import surrogate as SG
+    from paper_2303_11103_gb300 import scenes as S
+    t0 = time.perf_counter()
+    tr.load_scene(scene)
+    tx, rx = S.surrogate_pairs(scene, n_tx, n_rx, seed=4)
+    x, t = SG.tracer_labels(tr, tx, rx, num_rays, max_depth)
+    torch.cuda.synchronize()
+    t_label = time.perf_counter() - t0
+    n = x.shape[0]
+    g = torch.Generator(device=x.device).manual_seed(11)
+    perm = torch.randperm(n, generator=g, device=x.device)
+    held, train_idx = perm[:n_heldout], perm[n_heldout:]
+    lo = np.array([-250, -250, 0, -250, -250, 0], np.float32)
+    hi = np.array([250, 250, 70, 250, 250, 3], np.float32)
+    sur = rt.Surrogate(lo, hi, n_freq=32, width=256, n_hidden=8, sigma=8.0, seed=1)
+    t1 = time.perf_counter()
+    losses = SG.train(sur, x[train_idx], t[train_idx], epochs=epochs, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    ev = SG.evaluate(sur, x[held], t[held])
+    q_sur, ms_sur = SG.time_inference(sur, n_query, lo, hi, reps=2)
+    q_tr, s_tr = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth)
+    sur.close()
+    return {"surrogate": {
+        "train_pairs": int(len(train_idx)), "epochs": epochs, "final_loss": losses[-1],
+        "label_s": t_label, "train_s": t_train, "heldout": ev,
+        "queries": n_query, "infer_ms": ms_sur, "queries_per_s": q_sur,
+        "tracer_queries_per_s": q_tr, "speedup_vs_tracer": q_sur / q_tr,
+        "config": f"city 4802 tris; {n_tx} rooftop Tx x {n_rx} street Rx; labels: {num_rays} rays, "
+                  f"max_depth {max_depth}; MLP 64 Fourier features, 8 x 256 ReLU, BF16 tcgen05"}}
+
+
 def cpu_baseline(scene, tx, rx, seconds=15.0):
     """The FP64 oracle on the host cores: shooting and bouncing of a ray sample."""
     from oracle import oracle as O
@@ -425,11 +460,15 @@ def main():
                     help="run one kernel case of the step (profiling)")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-tx", type=int, default=2500, help="surrogate label transmitters")
+    ap.add_argument("--sur-rx", type=int, default=4000, help="surrogate receivers per transmitter")
+    ap.add_argument("--sur-epochs", type=int, default=6)
     args = ap.parse_args()
     if args.only:
         run_kernel_case(args)

@@ -88,6 +88,20 @@ int rt_set_frequency(rt_ctx* ctx, double fc);
  */
 int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t* mat_id,
                   const float* mat_params, int32_t n_mat);
+/*
+ * Hierarchy built over the Morton-sorted triangles by rt_load_scene (not in
+ * the paper, which leaves intersection to Mitsuba 3): RT_BVH_KARRAS = radix
+ * tree from the longest common prefixes of the codes (Karras 2012);
+ * RT_BVH_PLOC (default) = agglomerative clustering of Morton-order
+ * neighbours by merged surface area (Meister & Bittner 2018), a lower-cost
+ * tree for the same leaves. Both give the same intersections (every query's
+ * closest hit is independent of the tree). Takes effect at the next
+ * rt_load_scene. Errors: RT_ERR_INVALID_ARG for another value.
+ */
+#define RT_BVH_KARRAS 0
+#define RT_BVH_PLOC 1
+int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder);
+
 /* Replace the material table (same n_mat as the scene). */
 int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat);
 
@@ -144,8 +158,8 @@ int rt_get_paths(rt_ctx* ctx, int64_t* offsets, int32_t* seq, float* points, int
 /*
  * Debug / parity: the de-duplicated candidate list of the last
  * rt_compute_paths. n_out (HOST) = count U (always written); tx [U],
- * depth [U], seq [U*max_depth], witness_ray [U] (lowest ray index that
- * produced the candidate, -1 for LOS). Any device pointer may be NULL.
+ * depth [U], seq [U*max_depth], witness_ray [U] (the lattice index of a ray
+ * that produced the candidate, -1 for LOS). Any device pointer may be NULL.
  */
 int rt_get_candidates(rt_ctx* ctx, int64_t* n_out, int32_t* tx, int32_t* depth, int32_t* seq,
                       int64_t* witness_ray);
@@ -301,8 +315,13 @@ int rt_mlp_last_error(const rt_mlp* m, char* buf, size_t len);
  * BCE(logit, has_path) + has_path ((gain_pred - gain)/20 dB)^2, ADDED to
  * loss_out[0] (device; may be NULL). batch % 128 == 0. */
 int rt_mlp_train_step(rt_mlp* m, const float* x, const float* target, int32_t batch, float lr, float* loss_out);
-/* out [n*2] = (path logit, path gain dB) for x [n*6]. */
+/* out [n*2] = (path logit, path gain dB) for x [n*6]. One fused persistent
+ * kernel (all layers per 128-query tile, activations kept on chip) when
+ * 2*n_freq and width are multiples of 64, else rt_mlp_infer_layers. */
 int rt_mlp_infer(rt_mlp* m, const float* x, int64_t n, float* out);
+/* The same outputs layer by layer through rt_gemm_bf16's kernel
+ * (activations through device memory). */
+int rt_mlp_infer_layers(rt_mlp* m, const float* x, int64_t n, float* out);
 /* Parameter vector layout: per layer W [out x in] then b [out] (hidden
  * layers, then the head), then the Fourier matrix [n_freq x 6]. */
 int rt_mlp_num_params(const rt_mlp* m, int64_t* n_host);

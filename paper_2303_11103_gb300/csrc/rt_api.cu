@@ -2,7 +2,10 @@
 // ownership and error reporting around the kernels.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "rt_internal.h"
 
@@ -60,6 +63,8 @@ DevScene dev_scene(rt_ctx* ctx) {
     s.planes = bp<float4>(ctx->planes);
     s.mat = bp<int32_t>(ctx->mat);
     s.mats = bp<float2>(ctx->mats);
+    s.big = bp<float4>(ctx->tris) + 3 * (size_t)ctx->n_bvh;
+    s.n_big = ctx->n_big;
     s.n_tris = ctx->n_tris;
     s.n_nodes = ctx->n_nodes;
     s.n_mat = ctx->n_mat;
@@ -68,6 +73,20 @@ DevScene dev_scene(rt_ctx* ctx) {
 }
 
 static const size_t PROF_MAX = 1 << 16;
+
+cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = done[{dev, kernel}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 void prof_begin(rt_ctx* ctx, const char* name) {
     ctx->launches++;
@@ -202,6 +221,14 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
     int e = bvh_build(ctx, verts, n_tris);
     if (e) return e;
     ctx->has_scene = true;
+    return RT_OK;
+}
+
+int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder) {
+    CHECK_CTX(ctx);
+    if (builder != RT_BVH_KARRAS && builder != RT_BVH_PLOC)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "unknown BVH builder");
+    ctx->bvh_builder = builder;
     return RT_OK;
 }
 

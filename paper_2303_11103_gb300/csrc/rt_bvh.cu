@@ -21,6 +21,10 @@
 
 namespace {
 
+// Triangles with an AABB side above this fraction of the scene extent are
+// kept out of the hierarchy and tested by every query.
+constexpr float BIG_FRAC = 0.25f;
+
 __device__ __forceinline__ unsigned ord(float f) {
     unsigned u = __float_as_uint(f);
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -81,19 +85,35 @@ __device__ __forceinline__ unsigned expand10(unsigned x) {
     return x;
 }
 
-__global__ void k_morton(const float* __restrict__ cent, int T, const unsigned* __restrict__ bounds,
-                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Morton key of each triangle's centroid; a "large" triangle (an AABB side
+// above big_side, e.g. a ground quad half) gets the key 2^31 instead, so the
+// stable sort moves large triangles behind all others: they are tested
+// directly by every query rather than inflating the boxes of the BVH.
+__global__ void k_morton(const float* __restrict__ cent, const float* __restrict__ lbox, int T,
+                         const unsigned* __restrict__ bounds, float big_side, uint64_t* __restrict__ keys,
+                         uint32_t* __restrict__ vals, unsigned* __restrict__ n_big) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
+    vals[i] = (uint32_t)i;
+    const float* b = lbox + 6 * (size_t)i;
+    float side = fmaxf(fmaxf(b[3] - b[0], b[4] - b[1]), b[5] - b[2]);
+    if (side > big_side) {
+        keys[i] = 1ull << 31;
+        atomicAdd(n_big, 1u);
+        return;
+    }
+    // one scale for all axes (the centroid bounds' largest side): a flat
+    // city keeps its few height bits low in the code instead of splitting
+    // buildings horizontally near the root
+    float span = 0.0f;
+    for (int k = 0; k < 3; k++) span = fmaxf(span, unord(bounds[9 + k]) - unord(bounds[6 + k]));
     unsigned q[3];
     for (int k = 0; k < 3; k++) {
-        float lo = unord(bounds[6 + k]), hi = unord(bounds[9 + k]);
-        float span = hi - lo;
+        float lo = unord(bounds[6 + k]);
         float f = span > 0.0f ? (cent[3 * (size_t)i + k] - lo) / span : 0.5f;
         q[k] = (unsigned)fminf(fmaxf(f * 1024.0f, 0.0f), 1023.0f);
     }
     keys[i] = (uint64_t)((expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]));
-    vals[i] = (uint32_t)i;
 }
 
 __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int n, int i, int j) {
@@ -129,6 +149,152 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int n, int2* __restrict
     if (left < 0) par_leaf[~left] = i; else par_int[left] = i;
     if (right < 0) par_leaf[~right] = i; else par_int[right] = i;
     if (i == 0) par_int[0] = -1;
+}
+
+// ------------------------------------------------------------------ PLOC
+// Locally-ordered agglomerative clustering (Meister & Bittner 2018) over the
+// Morton-sorted leaves: each round, every cluster picks the neighbour within
+// +-PLOC_R positions whose merged box has the smallest surface area; mutual
+// nearest neighbours merge into a new internal node that takes the lower
+// position; the cluster list is compacted in order. Ties resolve to the
+// lower index, so the pair that is smallest in the order (area, lower index,
+// higher index) is always mutual and every round merges at least one pair.
+//
+// Each block clusters a chunk of PLOC_C consecutive clusters in shared
+// memory until one remains (one cluster per thread, double-buffered lists);
+// the chunk roots form the next, PLOC_C times shorter list, until a single
+// block produces the root. Merges across chunk borders are thereby
+// postponed to the next level. Internal nodes are numbered m-1-c for the
+// c-th merge in (level, chunk, round, position) order, so the root is node
+// 0, the layout the Karras builder produces; boxes come out of the merges
+// (leaf boxes padded as in the refit), so no refit pass is needed.
+constexpr int PLOC_C = 1024;
+constexpr int PLOC_R = 16;
+
+__device__ __forceinline__ float half_area(float lx, float ly, float lz, float hx, float hy, float hz) {
+    float dx = hx - lx, dy = hy - ly, dz = hz - lz;
+    return fmaf(dx, dy, fmaf(dy, dz, dz * dx));
+}
+
+// Padded leaf boxes as six planes of n floats (lo x, y, z, hi x, y, z) and
+// leaf ids ~k, in Morton order.
+__global__ void k_ploc_leaves(int n, const uint32_t* __restrict__ leaf_tri, const float* __restrict__ lbox,
+                              float pad, float* __restrict__ box, int* __restrict__ id) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* b = lbox + 6 * (size_t)leaf_tri[i];
+    for (int q = 0; q < 3; q++) {
+        box[q * (size_t)n + i] = b[q] - pad;
+        box[(3 + q) * (size_t)n + i] = b[3 + q] + pad;
+    }
+    id[i] = ~i;
+}
+
+__global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* __restrict__ in_box,
+                                                     const int* __restrict__ in_id, float* __restrict__ out_box,
+                                                     int* __restrict__ out_id, int stride, int id_base0, int m,
+                                                     int2* __restrict__ child, int* __restrict__ par_int,
+                                                     int* __restrict__ par_leaf, float* __restrict__ ibox,
+                                                     unsigned* __restrict__ status) {
+    extern __shared__ float ploc_sm[];
+    float* sb = ploc_sm;                                          // [2][6][PLOC_C]
+    int* sid = reinterpret_cast<int*>(ploc_sm + 12 * PLOC_C);    // [2][PLOC_C]
+    int* snn = sid + 2 * PLOC_C;                                  // [PLOC_C]
+    __shared__ unsigned wk[PLOC_C / 32], wm[PLOC_C / 32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int c0 = blockIdx.x * PLOC_C;
+    const int L = min(PLOC_C, count - c0);
+    if (t < L) {
+        for (int q = 0; q < 6; q++) sb[q * PLOC_C + t] = in_box[q * (size_t)stride + c0 + t];
+        sid[t] = in_id[c0 + t];
+    }
+    __syncthreads();
+    const int id_base = id_base0 + blockIdx.x * (PLOC_C - 1);
+    int cur = L, created = 0, buf = 0;
+    for (int round = 0; cur > 1; round++) {
+        if (round >= PLOC_C) {   // unreachable for finite boxes
+            if (t == 0) atomicOr(status, 1u);
+            return;
+        }
+        const float* rb = sb + buf * 6 * PLOC_C;
+        const int* ri = sid + buf * PLOC_C;
+        float* wb = sb + (buf ^ 1) * 6 * PLOC_C;
+        int* wi = sid + (buf ^ 1) * PLOC_C;
+        float lx = 0, ly = 0, lz = 0, hx = 0, hy = 0, hz = 0;
+        if (t < cur) {
+            lx = rb[t]; ly = rb[PLOC_C + t]; lz = rb[2 * PLOC_C + t];
+            hx = rb[3 * PLOC_C + t]; hy = rb[4 * PLOC_C + t]; hz = rb[5 * PLOC_C + t];
+            float best = __int_as_float(0x7f800000);
+            int bj = t > 0 ? t - 1 : 1;
+            const int j0 = max(0, t - PLOC_R), j1 = min(cur - 1, t + PLOC_R);
+            for (int j = j0; j <= j1; j++) {
+                if (j == t) continue;
+                float c = half_area(fminf(lx, rb[j]), fminf(ly, rb[PLOC_C + j]), fminf(lz, rb[2 * PLOC_C + j]),
+                                    fmaxf(hx, rb[3 * PLOC_C + j]), fmaxf(hy, rb[4 * PLOC_C + j]),
+                                    fmaxf(hz, rb[5 * PLOC_C + j]));
+                if (c < best) { best = c; bj = j; }
+            }
+            snn[t] = bj;
+        }
+        __syncthreads();
+        int j = -1;
+        bool keep = false, merge = false;
+        if (t < cur) {
+            j = snn[t];
+            const bool mutual = snn[j] == t;
+            keep = !(mutual && j < t);
+            merge = mutual && t < j;
+        }
+        // block-wide exclusive ranks of keep and merge
+        const unsigned bk = __ballot_sync(0xffffffffu, keep), bm = __ballot_sync(0xffffffffu, merge);
+        if (lane == 0) { wk[w] = __popc(bk); wm[w] = __popc(bm); }
+        __syncthreads();
+        if (w == 0) {
+            unsigned a = wk[lane], b = wm[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
+                if (lane >= o) { a += ya; b += yb; }
+            }
+            wk[lane] = a;   // inclusive
+            wm[lane] = b;
+        }
+        __syncthreads();
+        const unsigned lt = lanemask_lt();
+        const int K = (int)wk[31], M = (int)wm[31];
+        if (keep) {
+            const int kpos = (w > 0 ? (int)wk[w - 1] : 0) + __popc(bk & lt);
+            if (merge) {
+                const int mpos = (w > 0 ? (int)wm[w - 1] : 0) + __popc(bm & lt);
+                const int node = m - 1 - (id_base + created + mpos);
+                float u[6] = {fminf(lx, rb[j]), fminf(ly, rb[PLOC_C + j]), fminf(lz, rb[2 * PLOC_C + j]),
+                              fmaxf(hx, rb[3 * PLOC_C + j]), fmaxf(hy, rb[4 * PLOC_C + j]),
+                              fmaxf(hz, rb[5 * PLOC_C + j])};
+                const int ca = ri[t], cb = ri[j];
+                child[node] = make_int2(ca, cb);
+                if (ca < 0) par_leaf[~ca] = node; else par_int[ca] = node;
+                if (cb < 0) par_leaf[~cb] = node; else par_int[cb] = node;
+                for (int q = 0; q < 6; q++) { ibox[6 * (size_t)node + q] = u[q]; wb[q * PLOC_C + kpos] = u[q]; }
+                wi[kpos] = node;
+            } else {
+                wb[kpos] = lx; wb[PLOC_C + kpos] = ly; wb[2 * PLOC_C + kpos] = lz;
+                wb[3 * PLOC_C + kpos] = hx; wb[4 * PLOC_C + kpos] = hy; wb[5 * PLOC_C + kpos] = hz;
+                wi[kpos] = ri[t];
+            }
+        }
+        __syncthreads();
+        if (M == 0) {   // unreachable for finite boxes
+            if (t == 0) atomicOr(status, 1u);
+            return;
+        }
+        created += M;
+        cur = K;
+        buf ^= 1;
+    }
+    if (t == 0 && L > 0) {
+        for (int q = 0; q < 6; q++) out_box[q * (size_t)stride + blockIdx.x] = sb[(buf * 6 + q) * PLOC_C];
+        out_id[blockIdx.x] = sid[buf * PLOC_C];
+        if (gridDim.x == 1) par_int[0] = -1;   // one chunk left: its cluster is the root
+    }
 }
 
 __device__ __forceinline__ void load_box(const float* b, float* o) {
@@ -206,10 +372,11 @@ __global__ void k_leaf_tris(int n, const uint32_t* __restrict__ leaf_tri, const 
     tris[3 * (size_t)k + 2] = tris_o[3 * (size_t)t + 2];
 }
 
-__global__ void k_single_leaf(const float* __restrict__ lbox, float pad, float4* __restrict__ nodes) {
-    // one triangle: both children are leaf 0
+__global__ void k_single_leaf(const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri, float pad,
+                              float4* __restrict__ nodes) {
+    // one triangle in the hierarchy: both children are leaf 0
     float a[6];
-    for (int q = 0; q < 6; q++) a[q] = lbox[q];
+    for (int q = 0; q < 6; q++) a[q] = lbox[6 * (size_t)leaf_tri[0] + q];
     for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; }
     nodes[0] = make_float4(a[0], a[1], a[2], a[3]);
     nodes[1] = make_float4(a[4], a[5], a[0], a[1]);
@@ -232,6 +399,7 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     ctx->n_tris = T;
     if (T == 0) {
         ctx->n_nodes = 0;
+        ctx->n_bvh = ctx->n_big = 0;
         ctx->bvh_depth = 0;
         ctx->extent = 1.0f;
         ctx->tmin = 2e-6f;
@@ -282,43 +450,89 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     BT(buf_reserve(keys2, sizeof(uint64_t) * T));
     BT(buf_reserve(vals, sizeof(uint32_t) * T));
     BT(buf_reserve(vals2, sizeof(uint32_t) * T));
+    // [0] tree depth, [1] large-triangle count, [2] clustering status
+    BT(buf_reserve(maxd, sizeof(int) * 3));
+    BT(cudaMemsetAsync(maxd.p, 0, sizeof(int) * 3, st));
     prof_begin(ctx, "k_morton");
-    k_morton<<<gT, B, 0, st>>>(bp<float>(cent), T, bp<unsigned>(bounds), bp<uint64_t>(keys),
-                               bp<uint32_t>(vals));
+    k_morton<<<gT, B, 0, st>>>(bp<float>(cent), bp<float>(lbox), T, bp<unsigned>(bounds), BIG_FRAC * ext,
+                               bp<uint64_t>(keys), bp<uint32_t>(vals), bp<unsigned>(maxd) + 1);
     prof_end(ctx);
     BT(cudaGetLastError());
     BT(radix_sort64(ctx, bp<uint64_t>(keys), bp<uint64_t>(keys2), bp<uint32_t>(vals),
-                    bp<uint32_t>(vals2), T, 30));
+                    bp<uint32_t>(vals2), T, 32));
+    unsigned n_big = 0;
+    BT(cudaMemcpyAsync(&n_big, bp<unsigned>(maxd) + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    BT(cudaStreamSynchronize(st));
+    // sorted order: triangles of the hierarchy (Morton order), then the large ones (id order)
+    const int n = T - (int)n_big;
+    ctx->n_big = (int)n_big;
+    ctx->n_bvh = n;
+    m = std::max(n - 1, 1);
     const uint32_t* leaf_tri = bp<uint32_t>(vals);
-    if (T == 1) {
+    if (n == 0) {
+        ctx->n_nodes = 0;
+        ctx->bvh_depth = 0;
+    } else if (n == 1) {
         prof_begin(ctx, "k_single_leaf");
-        k_single_leaf<<<1, 1, 0, st>>>(bp<float>(lbox), pad, bp<float4>(ctx->nodes));
+        k_single_leaf<<<1, 1, 0, st>>>(bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
         prof_end(ctx);
         BT(cudaGetLastError());
         ctx->n_nodes = 1;
         ctx->bvh_depth = 1;
     } else {
+        const int T = n;   // the hierarchy's triangles
+        const int gT = (T + B - 1) / B;
         BT(buf_reserve(child, sizeof(int2) * m));
         BT(buf_reserve(pint, sizeof(int) * m));
         BT(buf_reserve(pleaf, sizeof(int) * T));
         BT(buf_reserve(ibox, sizeof(float) * 6 * (size_t)m));
-        BT(buf_reserve(flag, sizeof(int) * m));
-        BT(cudaMemsetAsync(flag.p, 0, sizeof(int) * m, st));
         int gm = (m + B - 1) / B;
-        prof_begin(ctx, "k_karras");
-        k_karras<<<gm, B, 0, st>>>(bp<uint64_t>(keys), T, bp<int2>(child), bp<int>(pint), bp<int>(pleaf));
-        prof_end(ctx);
-        BT(cudaGetLastError());
-        prof_begin(ctx, "k_refit");
-        k_refit<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), bp<int2>(child), bp<int>(pint),
-                                  bp<int>(pleaf), bp<float>(ibox), bp<int>(flag), pad);
-        prof_end(ctx);
-        BT(cudaGetLastError());
+        if (ctx->bvh_builder == RT_BVH_PLOC) {
+            // two cluster lists (six box planes + ids each)
+            BT(buf_reserve(flag, (sizeof(float) * 12 + sizeof(int) * 2) * (size_t)T));
+            float* boxA = bp<float>(flag);
+            float* boxB = boxA + 6 * (size_t)T;
+            int* idA = reinterpret_cast<int*>(boxB + 6 * (size_t)T);
+            int* idB = idA + T;
+            prof_begin(ctx, "k_ploc_leaves");
+            k_ploc_leaves<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), pad, boxA, idA);
+            prof_end(ctx);
+            BT(cudaGetLastError());
+            const size_t smem = (sizeof(float) * 12 + sizeof(int) * 3) * PLOC_C;
+            BT(ensure_smem_attr((const void*)k_ploc_chunk, smem));
+            int count = T, id_base = 0;
+            float *bi = boxA, *bo = boxB;
+            int *ii = idA, *io = idB;
+            while (true) {
+                const int K = (count + PLOC_C - 1) / PLOC_C;
+                prof_begin(ctx, "k_ploc_chunk");
+                k_ploc_chunk<<<K, PLOC_C, smem, st>>>(count, bi, ii, bo, io, T, id_base, m, bp<int2>(child),
+                                                      bp<int>(pint), bp<int>(pleaf), bp<float>(ibox),
+                                                      bp<unsigned>(maxd) + 2);
+                prof_end(ctx);
+                BT(cudaGetLastError());
+                id_base += count - K;
+                if (K == 1) break;
+                count = K;
+                std::swap(bi, bo);
+                std::swap(ii, io);
+            }
+        } else {
+            BT(buf_reserve(flag, sizeof(int) * m));
+            BT(cudaMemsetAsync(flag.p, 0, sizeof(int) * m, st));
+            prof_begin(ctx, "k_karras");
+            k_karras<<<gm, B, 0, st>>>(bp<uint64_t>(keys), T, bp<int2>(child), bp<int>(pint), bp<int>(pleaf));
+            prof_end(ctx);
+            BT(cudaGetLastError());
+            prof_begin(ctx, "k_refit");
+            k_refit<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), bp<int2>(child), bp<int>(pint),
+                                      bp<int>(pleaf), bp<float>(ibox), bp<int>(flag), pad);
+            prof_end(ctx);
+            BT(cudaGetLastError());
+        }
         BT(buf_reserve(dkeys, sizeof(uint64_t) * m));
         BT(buf_reserve(dkeys2, sizeof(uint64_t) * m));
         BT(buf_reserve(rank, sizeof(int) * m));
-        BT(buf_reserve(maxd, sizeof(int)));
-        BT(cudaMemsetAsync(maxd.p, 0, sizeof(int), st));
         prof_begin(ctx, "k_depth");
         k_depth<<<gm, B, 0, st>>>(m, bp<int>(pint), bp<uint64_t>(dkeys), bp<int>(maxd));
         prof_end(ctx);
@@ -332,12 +546,17 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
                                  bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
         prof_end(ctx);
         BT(cudaGetLastError());
-        int hd = 0;
-        BT(cudaMemcpyAsync(&hd, maxd.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int hd[3] = {0, 0, 0};
+        BT(cudaMemcpyAsync(hd, maxd.p, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
         BT(cudaStreamSynchronize(st));
+        if (hd[2] != 0) {   // the clustering found no pair to merge: non-finite geometry
+            cleanup();
+            return set_err(ctx, RT_ERR_INVALID_ARG, "BVH build: non-finite triangle boxes");
+        }
         ctx->n_nodes = m;
-        ctx->bvh_depth = hd + 1;
+        ctx->bvh_depth = hd[0] + 1;
     }
+    // leaf records in sorted order: the hierarchy's leaves, then the large triangles
     prof_begin(ctx, "k_leaf_tris");
     k_leaf_tris<<<gT, B, 0, st>>>(T, leaf_tri, bp<float4>(ctx->tris_o), bp<float4>(ctx->tris));
     prof_end(ctx);

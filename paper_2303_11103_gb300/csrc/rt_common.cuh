@@ -44,11 +44,12 @@ __device__ __forceinline__ f3 xyz(float4 v) { return {v.x, v.y, v.z}; }
 struct DevScene {
     const float4* __restrict__ nodes;   // [n_nodes*4]
     const float4* __restrict__ tris;    // [T*3] leaf order
+    const float4* __restrict__ big;     // [n_big*3] large triangles, tested by every query
     const float4* __restrict__ tris_o;  // [T*3] original order (same record layout)
     const float4* __restrict__ planes;  // [T] original order: n, n.v0
     const int32_t* __restrict__ mat;    // [T] original order
     const float2* __restrict__ mats;    // [M] eps_r, sigma
-    int n_tris, n_nodes, n_mat;
+    int n_tris, n_nodes, n_mat, n_big;
     float tmin;                         // self-intersection offset (metres)
 };
 
@@ -86,20 +87,21 @@ __device__ __forceinline__ f3 safe_inv(f3 d) {
     return {x, y, z};
 }
 
-// Moller-Trumbore, closed barycentric test. Returns t or +inf.
+// Moller-Trumbore, closed barycentric test. Returns t or +inf. The
+// barycentric tests run on the numerators scaled by sign(det) (u det >= 0,
+// v det >= 0, (u + v) det <= det^2 written as |.| <= |det|), so the one
+// division is taken only for rays that pass inside the triangle.
 __device__ __forceinline__ float tri_hit(float4 r0, float4 r1, float4 r2, f3 o, f3 d) {
     f3 v0 = xyz(r0), e1 = xyz(r1), e2 = xyz(r2);
     f3 p = cross(d, e2);
     float det = dot(e1, p);
-    if (det == 0.0f) return __int_as_float(0x7f800000);
-    float inv = 1.0f / det;
     f3 s = o - v0;
-    float u = dot(s, p) * inv;
     f3 q = cross(s, e1);
-    float v = dot(d, q) * inv;
-    float t = dot(e2, q) * inv;
-    bool in = (u >= 0.0f) & (v >= 0.0f) & (u + v <= 1.0f);
-    return in ? t : __int_as_float(0x7f800000);
+    const float sg = det < 0.0f ? -1.0f : 1.0f;
+    float us = dot(s, p) * sg, vs = dot(d, q) * sg;
+    bool in = (det != 0.0f) & (us >= 0.0f) & (vs >= 0.0f) & (us + vs <= fabsf(det));
+    if (!in) return __int_as_float(0x7f800000);
+    return dot(e2, q) / det;
 }
 
 // Per-lane traversal counters (BVH node records and triangle records
@@ -115,6 +117,7 @@ struct TravCount {
 #define RT_CNT_ANY 3
 #define RT_CNT_NODES 4
 #define RT_CNT_TRIS 5
+#define RT_CNT_KEYS 6
 
 __device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* counters, int query_slot) {
     unsigned long long n = c.nodes, t = c.tris, q = c.queries;
@@ -146,10 +149,21 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
     float tb = __int_as_float(0x7f800000);
     int best = -1;
     const float tmin = s.tmin;
+    // large triangles first: a hit there also bounds the traversal below
+    for (int k = 0; k < s.n_big; k++) {
+        const float4* tp = s.big + 3 * k;
+        float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+        cnt.tris++;
+        int id = __float_as_int(r0.w);
+        if (id != exclude) {
+            float t = tri_hit(r0, r1, r2, o, d);
+            if (t > tmin && (t < tb || (t == tb && id < best))) { tb = t; best = id; }
+        }
+    }
     // a tree visits each node at most once per query; the cap only guards
     // against a malformed hierarchy
     int budget = 2 * s.n_nodes + 16;
-    while (true) {
+    while (s.n_nodes > 0) {
         if (--budget < 0) {
             if (status) atomicOr(status, RT_STAT_LOOP);
             break;
@@ -219,8 +233,18 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
     int sp = 0;
     int node = 0;
     const float tmin = s.tmin;
+    for (int k = 0; k < s.n_big; k++) {
+        const float4* tp = s.big + 3 * k;
+        float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+        cnt.tris++;
+        int id = __float_as_int(r0.w);
+        if (id != ex0 && id != ex1) {
+            float t = tri_hit(r0, r1, r2, o, d);
+            if (t > tmin && t < tmax) return true;
+        }
+    }
     int budget = 2 * s.n_nodes + 16;
-    while (true) {
+    while (s.n_nodes > 0) {
         if (--budget < 0) {
             if (status) atomicOr(status, RT_STAT_LOOP);
             return false;

@@ -38,6 +38,7 @@ struct rt_ctx {
     // scene
     bool has_scene = false;
     int n_tris = 0, n_mat = 0, n_nodes = 0, bvh_depth = 0;
+    int n_bvh = 0, n_big = 0;  // triangles in the hierarchy / tested directly (large)
     float tmin = 0.0f, extent = 1.0f;
     DevBuf nodes, tris, tris_o, planes, mat, mats;
 
@@ -69,6 +70,7 @@ struct rt_ctx {
 
     // tuning
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
+    int bvh_builder = RT_BVH_PLOC;  // hierarchy over the Morton order: RT_BVH_KARRAS or RT_BVH_PLOC
     int trace_block = 256;
     int warp_chunk = 0;       // rays a warp takes per refill (0 = about 16 chunks per warp)
 
@@ -88,6 +90,11 @@ struct rt_ctx {
 
 // Bracket one kernel launch: counts it and, when profiling, records CUDA
 // events on the context's stream right before and after it.
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes` (the attribute call is made once per kernel, device and size
+// increase; thread-safe).
+cudaError_t ensure_smem_attr(const void* kernel, size_t bytes);
+
 void prof_begin(rt_ctx* ctx, const char* name);
 void prof_end(rt_ctx* ctx);
 

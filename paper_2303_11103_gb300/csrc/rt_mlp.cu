@@ -319,6 +319,176 @@ __global__ void k_to_bf16(const float* __restrict__ w, int64_t n, int in_dim, __
     wtb[i * out_dim + o] = __float2bfloat16_rn(w[k]);
 }
 
+// ------------------------------------------------------ fused inference
+// All layers for a tile of 128 queries per iteration of a persistent CTA:
+// activations stay in shared memory (written by the epilogue in the same
+// 128-byte-swizzled K-major layout TMA produces), each layer's weights are
+// streamed by TMA into one buffer while the previous layer's epilogue runs,
+// the accumulator lives in TMEM, the 2-wide head runs in registers.
+constexpr int FM_MAX_L = 16;
+struct alignas(64) FusedMaps {
+    CUtensorMap w[FM_MAX_L];  // BF16 weights [W x K_l], box 64 x W
+};
+
+struct FusedArgs {
+    const float* x;      // [n x 6]
+    float* out;          // [n x 2]
+    int64_t n;
+    int F, W, L;
+    const float* Bf;     // [F x 6]
+    const float* lo;
+    const float* hi;
+    const float* const* bias;  // [L] device pointers to [W]
+    const float* head_w;       // [2 x W]
+    const float* head_b;       // [2]
+    float db_scale, db_offset;
+    unsigned* err;
+};
+
+__device__ __forceinline__ uint32_t sw128_off(int r, int c) {
+    // byte offset of element (r, c) inside a 64-column K-chunk (128 B rows)
+    return (uint32_t)r * 128u + ((((uint32_t)c >> 3) ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c & 7u) << 1);
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps, FusedArgs a) {
+    extern __shared__ uint8_t dyn[];
+    __shared__ __align__(8) uint64_t wbar, mbar;
+    __shared__ uint32_t tmem_slot;
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const int W = a.W, L = a.L, F = a.F;
+    const int kmax = (2 * F > W ? 2 * F : W) / 64;           // K-chunks of the widest layer input
+    uint8_t* act = base;                                     // kmax chunks x 16 KB (<= 64 KB)
+    uint8_t* wbuf = base + 64 * 1024;                        // kmax chunks x (W rows x 128 B)
+    float* s_bias = (float*)(base + 64 * 1024 + (size_t)kmax * W * 128);  // [L x W]
+    float* s_head = s_bias + L * W;                          // [2 x W + 2]
+    float* s_bf = s_head + 2 * W + 2;                        // [F x 6] + lo[6] + hi[6]
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t wchunk = (uint32_t)W * 128u;
+    for (int i = tid; i < L * W; i += 128) s_bias[i] = a.bias[i / W][i % W];
+    for (int i = tid; i < 2 * W; i += 128) s_head[i] = a.head_w[i];
+    if (tid < 2) s_head[2 * W + tid] = a.head_b[tid];
+    for (int i = tid; i < 6 * F; i += 128) s_bf[i] = a.Bf[i];
+    if (tid < 6) {
+        s_bf[6 * F + tid] = a.lo[tid];
+        s_bf[6 * F + 6 + tid] = a.hi[tid];
+    }
+    const uint32_t tcols = W <= 64 ? 64u : (W <= 128 ? 128u : 256u);
+    if (warp == 0) {
+        tmem_alloc(su32(&tmem_slot), tcols);
+        tmem_relinquish();
+    }
+    if (tid == 32) {
+        mbar_init(su32(&wbar), 1);
+        mbar_init(su32(&mbar), 1);
+        mbar_fence_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int64_t ntiles = (a.n + 127) / 128;
+    uint32_t wcount = 0, mcount = 0;
+    bool ok = true;
+    auto load_weights = [&](int l) {
+        const int K = l == 0 ? 2 * F : W;
+        mbar_expect_tx(su32(&wbar), (uint32_t)W * K * 2u);
+        for (int kc = 0; kc < K / 64; kc++) tma_load_2d(su32(wbuf + kc * wchunk), &maps.w[l], kc * 64, 0, su32(&wbar));
+    };
+    if (tid == 0 && blockIdx.x < ntiles) load_weights(0);
+    const uint32_t idesc = idesc_bf16(128, W);
+    // Every thread runs the same loop trips (block barriers inside); after a
+    // timed-out wait `ok` only suppresses work and the error bit is set.
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t q = tile * 128 + tid;
+        // Fourier features of this thread's query into K-chunk(s) of act
+        {
+            float xn[6];
+            for (int k = 0; k < 6; k++) {
+                float xv = q < a.n ? a.x[6 * q + k] : 0.0f;
+                xn[k] = 2.0f * (xv - s_bf[6 * F + k]) / (s_bf[6 * F + 6 + k] - s_bf[6 * F + k]) - 1.0f;
+            }
+            for (int j = 0; j < F; j += 2) {
+                float s2[2], c2[2];
+                for (int h = 0; h < 2; h++) {
+                    float v = 0.0f;
+                    for (int k = 0; k < 6; k++) v = fmaf(s_bf[6 * (j + h) + k], xn[k], v);
+                    v -= rintf(v);
+                    sincospif(2.0f * v, &s2[h], &c2[h]);
+                }
+                *(uint32_t*)(act + (j / 64) * 16384 + sw128_off(tid, j % 64)) = pack_bf16(s2[0], s2[1]);
+                *(uint32_t*)(act + ((F + j) / 64) * 16384 + sw128_off(tid, (F + j) % 64)) = pack_bf16(c2[0], c2[1]);
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        float h0 = 0.0f, h1 = 0.0f;
+        for (int l = 0; l < L; l++) {
+            const int K = l == 0 ? 2 * F : W;
+            if (tid == 0) {
+                if (ok) ok = mbar_wait(su32(&wbar), wcount & 1u, a.err);
+                wcount++;
+                tc_fence_after();
+                if (ok) {
+                    for (int kc = 0; kc < K / 64; kc++)
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            mma_bf16(tmem, desc_sw128(su32(act + kc * 16384) + k * 32),
+                                     desc_sw128(su32(wbuf + kc * wchunk) + k * 32), idesc, (kc | k) != 0 ? 1u : 0u);
+                }
+                mma_commit(su32(&mbar));
+            }
+            __syncwarp();
+            if (warp == 0) ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // warp-uniform for tcgen05.ld
+            const bool done = ok && mbar_wait(su32(&mbar), mcount & 1u, a.err);
+            mcount++;
+            tc_fence_after();
+            // the weight buffer is free again: stream the next layer's weights
+            const bool more = (l + 1 < L) || (tile + gridDim.x < ntiles);
+            if (tid == 0 && done && more) load_weights((l + 1) % L);
+            if (!done) ok = false;
+            if (ok) {
+                for (int c0 = 0; c0 < W; c0 += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+                    tmem_wait_ld();
+                    uint32_t packed[16];
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        float v0 = fmaxf(__uint_as_float(r[j]) + s_bias[l * W + c0 + j], 0.0f);
+                        float v1 = fmaxf(__uint_as_float(r[j + 1]) + s_bias[l * W + c0 + j + 1], 0.0f);
+                        packed[j / 2] = pack_bf16(v0, v1);
+                        if (l == L - 1) {
+                            __nv_bfloat162 b2 = *reinterpret_cast<__nv_bfloat162*>(&packed[j / 2]);
+                            float r0 = __low2float(b2), r1 = __high2float(b2);
+                            h0 = fmaf(r0, s_head[c0 + j], fmaf(r1, s_head[c0 + j + 1], h0));
+                            h1 = fmaf(r0, s_head[W + c0 + j], fmaf(r1, s_head[W + c0 + j + 1], h1));
+                        }
+                    }
+                    if (l < L - 1) {
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int c = c0 + 8 * u;
+                            *(uint4*)(act + (c / 64) * 16384 + sw128_off(tid, c % 64)) =
+                                make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
+                        }
+                    }
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (ok && q < a.n) {
+            a.out[2 * q] = h0 + s_head[2 * W];
+            a.out[2 * q + 1] = (h1 + s_head[2 * W + 1]) * a.db_scale + a.db_offset;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, tcols);
+}
+
 // ------------------------------------------------------------- tensor maps
 typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -362,7 +532,7 @@ template <int BN>
 cudaError_t launch_gemm_t(cudaStream_t st, const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K,
                           const float* bias, int relu, int out_bf16, void* C, int ldc, unsigned* err) {
     size_t smem = gemm_smem<BN>();
-    cudaError_t e = cudaFuncSetAttribute(k_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_attr((const void*)k_gemm<BN>, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((N + BN - 1) / BN));
     k_gemm<BN><<<grid, 128, smem, st>>>(ta, tb, M, N, K, bias, relu, out_bf16, C, ldc, err);
@@ -393,6 +563,7 @@ struct rt_mlp {
     DevBuf Bf, lo, hi, errw, loss;
     std::vector<DevBuf> w, b, mw, vw, mb, vb, gw, gb, wbf, wtbf;  // per layer, head = index L
     std::vector<DevBuf> H;                                         // H[0] features, H[l] hidden outputs
+    DevBuf bias_ptrs;                                              // [L] device pointers (fused kernel)
     DevBuf y, dy, dZ, dH, dZt, Ht;
     int64_t cap = 0;
     int step = 0;
@@ -520,7 +691,8 @@ int rt_mlp_destroy(rt_mlp* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     for (auto* v : {&m->w, &m->b, &m->mw, &m->vw, &m->mb, &m->vb, &m->gw, &m->gb, &m->wbf, &m->wtbf, &m->H})
         for (auto& d : *v) buf_free(d);
-    for (DevBuf* d : {&m->Bf, &m->lo, &m->hi, &m->errw, &m->loss, &m->y, &m->dy, &m->dZ, &m->dH, &m->dZt, &m->Ht})
+    for (DevBuf* d : {&m->Bf, &m->lo, &m->hi, &m->errw, &m->loss, &m->y, &m->dy, &m->dZ, &m->dH, &m->dZt, &m->Ht,
+                      &m->bias_ptrs})
         buf_free(*d);
     delete m;
     return RT_OK;
@@ -541,6 +713,52 @@ int rt_mlp_last_error(const rt_mlp* m, char* buf, size_t len) {
 }
 
 int rt_mlp_infer(rt_mlp* m, const float* x, int64_t n, float* out) {
+    if (!m || (n > 0 && (!x || !out))) return RT_ERR_INVALID_ARG;
+    if (cudaSetDevice(m->device) != cudaSuccess) return RT_ERR_CUDA;
+    if ((2 * m->F) % 64 || m->W % 64 || m->L > FM_MAX_L) return rt_mlp_infer_layers(m, x, n, out);
+    if (n == 0) return RT_OK;
+    alignas(64) FusedMaps maps;
+    for (int l = 0; l < m->L; l++)
+        if (!make_map(&maps.w[l], m->wbf[l].p, m->W, m->in_dim(l), m->W))
+            return mlp_err(m, RT_ERR_CUDA, "tensor map of a weight matrix");
+    if (!m->bias_ptrs.p) {
+        std::vector<const float*> bp_h(m->L);
+        for (int l = 0; l < m->L; l++) bp_h[l] = bp<float>(m->b[l]);
+        MT(buf_reserve(m->bias_ptrs, sizeof(float*) * m->L));
+        MT(cudaMemcpy(m->bias_ptrs.p, bp_h.data(), sizeof(float*) * m->L, cudaMemcpyHostToDevice));
+    }
+    FusedArgs a;
+    a.x = x;
+    a.out = out;
+    a.n = n;
+    a.F = m->F;
+    a.W = m->W;
+    a.L = m->L;
+    a.Bf = bp<float>(m->Bf);
+    a.lo = bp<float>(m->lo);
+    a.hi = bp<float>(m->hi);
+    a.bias = (const float* const*)m->bias_ptrs.p;
+    a.head_w = bp<float>(m->w[m->L]);
+    a.head_b = bp<float>(m->b[m->L]);
+    a.db_scale = m->db_scale;
+    a.db_offset = m->db_offset;
+    a.err = bp<unsigned>(m->errw);
+    const int kmax = std::max(2 * m->F, m->W) / 64;
+    size_t smem = 1024 + 64 * 1024 + (size_t)kmax * m->W * 128 +
+                  sizeof(float) * ((size_t)m->L * m->W + 2 * m->W + 2 + 6 * m->F + 12);
+    MT(ensure_smem_attr((const void*)k_mlp_fused, smem));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+    int64_t ntiles = (n + 127) / 128;
+    int grid = (int)std::min<int64_t>(ntiles, sms);
+    k_mlp_fused<<<grid, 128, smem, m->stream>>>(maps, a);
+    MT(cudaGetLastError());
+    return RT_OK;
+}
+
+// Layer-by-layer inference through the generic GEMM (activations in HBM):
+// the reference path the fused kernel is checked against.
+int rt_mlp_infer_layers(rt_mlp* m, const float* x, int64_t n, float* out) {
     if (!m || (n > 0 && (!x || !out))) return RT_ERR_INVALID_ARG;
     if (cudaSetDevice(m->device) != cudaSuccess) return RT_ERR_CUDA;
     const int64_t chunk = 1 << 18;

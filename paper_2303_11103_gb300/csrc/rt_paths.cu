@@ -98,11 +98,6 @@ __global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, int n_tx
     }
 }
 
-__global__ void k_iota(uint32_t* v, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = (uint32_t)i;
-}
-
 // per-tx candidate ranges: off[t] = first candidate with tx >= t
 __global__ void k_cand_off(const uint64_t* __restrict__ ck, int64_t U, int n_tx, KeyFmt f,
                            int64_t* __restrict__ off) {
@@ -323,7 +318,7 @@ __global__ void k_path_final(FinParams p) {
 }  // namespace
 
 // ----------------------------------------------------------------- host side
-int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits);
+int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, uint32_t* vals, int32_t* hits);
 
 static int key_format(rt_ctx* ctx, int D, KeyFmt& f) {
     int idb = 1;
@@ -349,38 +344,39 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     if (e) return e;
     const bool los = flags & RT_LOS, refl = (flags & RT_REFLECTION) && D > 0 && N > 0;
     const int64_t nsbr = refl ? (int64_t)ctx->n_tx * N * D : 0;
-    const int64_t nkeys = nsbr + (los ? ctx->n_tx : 0);
-    if (nkeys >= 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "n_tx * num_rays * max_depth above 2^32");
+    const int64_t ncap = nsbr + (los ? ctx->n_tx : 0);
+    if (ncap >= 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "n_tx * num_rays * max_depth above 2^32");
     ctx->max_depth = f.D;
     ctx->num_rays = N;
     ctx->recorded_rays = refl && (flags & RT_RECORD_RAYS);
-    RT_TRY(buf_reserve(ctx->keys, sizeof(uint64_t) * std::max<int64_t>(nkeys, 1)));
-    RT_TRY(buf_reserve(ctx->keys_alt, sizeof(uint64_t) * std::max<int64_t>(nkeys, 1)));
-    RT_TRY(buf_reserve(ctx->vals, sizeof(uint32_t) * std::max<int64_t>(nkeys, 1)));
-    RT_TRY(buf_reserve(ctx->vals_alt, sizeof(uint32_t) * std::max<int64_t>(nkeys, 1)));
+    RT_TRY(buf_reserve(ctx->keys, sizeof(uint64_t) * std::max<int64_t>(ncap, 1)));
+    RT_TRY(buf_reserve(ctx->keys_alt, sizeof(uint64_t) * std::max<int64_t>(ncap, 1)));
+    RT_TRY(buf_reserve(ctx->vals, sizeof(uint32_t) * std::max<int64_t>(ncap, 1)));
+    RT_TRY(buf_reserve(ctx->vals_alt, sizeof(uint32_t) * std::max<int64_t>(ncap, 1)));
     uint64_t* keys = bp<uint64_t>(ctx->keys);
     uint32_t* vals = bp<uint32_t>(ctx->vals);
     RT_TRY(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), st));
+    int64_t nhit = 0;  // candidate keys the rays produced (one per hit)
     if (refl) {
-        RT_TRY(cudaMemsetAsync(keys, 0xFF, sizeof(uint64_t) * nsbr, st));
         int32_t* hits = nullptr;
         if (ctx->recorded_rays) {
             RT_TRY(buf_reserve(ctx->ray_hits, sizeof(int32_t) * nsbr));
             RT_TRY(cudaMemsetAsync(ctx->ray_hits.p, 0xFF, sizeof(int32_t) * nsbr, st));
             hits = bp<int32_t>(ctx->ray_hits);
         }
-        e = launch_sbr(ctx, N, f.D, keys, hits);
+        e = launch_sbr(ctx, N, f.D, keys, vals, hits);
         if (e) return e;
+        unsigned long long hk = 0;
+        RT_TRY(cudaMemcpyAsync(&hk, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS, sizeof(hk),
+                               cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaStreamSynchronize(st));
+        nhit = (int64_t)hk;
     }
-    if (nkeys > 0) {
-        prof_begin(ctx, "k_iota");
-        k_iota<<<(unsigned)((nkeys + 255) / 256), 256, 0, st>>>(vals, nkeys);
+    const int64_t nkeys = nhit + (los ? ctx->n_tx : 0);
+    if (los) {
+        prof_begin(ctx, "k_write_los");
+        k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nhit, ctx->n_tx, f);
         prof_end(ctx);
-        if (los) {
-            prof_begin(ctx, "k_write_los");
-            k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nsbr, ctx->n_tx, f);
-            prof_end(ctx);
-        }
         RT_TRY(cudaGetLastError());
     }
     RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
@@ -467,7 +463,7 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             vp.n_sm = std::min(ctx->n_smem_nodes, ctx->n_nodes);
             vp.status = bp<unsigned>(ctx->status);
             size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm;
-            RT_TRY(cudaFuncSetAttribute(k_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            RT_TRY(ensure_smem_attr((const void*)k_validate, smem));
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_validate, 256, smem);
             int64_t need = (total + 255) / 256;

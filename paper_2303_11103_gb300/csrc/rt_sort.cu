@@ -18,9 +18,18 @@ __global__ void __launch_bounds__(RS_THREADS) rs_hist(const uint64_t* __restrict
     h[threadIdx.x] = 0;
     __syncthreads();
     int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const unsigned lt = lanemask_lt();
     for (int j = 0; j < RS_IPT; j++) {
         int64_t i = base + j * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1u);
+        bool ok = i < n;
+        unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            // one shared atomic per distinct digit in the warp (keys are
+            // often heavily repeated)
+            unsigned dg = (unsigned)(keys[i] >> shift) & 255u;
+            unsigned peers = __match_any_sync(act, dg);
+            if ((peers & lt) == 0) atomicAdd(&h[dg], (uint32_t)__popc(peers));
+        }
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];
@@ -143,12 +152,120 @@ cudaError_t scan_level(rt_ctx* ctx, uint32_t* a, int64_t m, uint32_t* scratch) {
     return cudaGetLastError();
 }
 
+// Small inputs (<= SS_MAX keys): one block sorts in shared memory, all
+// passes in one launch. Each warp owns a contiguous chunk of the keys. Per
+// pass: the warps count their chunk's digits (warp match, one shared update
+// per distinct digit), one exclusive scan over (digit, warp) gives every
+// warp its first slot per digit, then the warps walk their chunks again in
+// order and scatter (stable: warp order, then step order, then lane order).
+constexpr int SS_THREADS = 1024, SS_WARPS = SS_THREADS / 32, SS_MAX = 6144;
+
+template <bool VALS>
+__global__ void __launch_bounds__(SS_THREADS) k_sort_small(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                         int n, int passes) {
+    extern __shared__ __align__(16) unsigned char ss_raw[];
+    uint64_t* ka = reinterpret_cast<uint64_t*>(ss_raw);
+    uint64_t* kb = ka + SS_MAX;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(kb + SS_MAX);   // [SS_WARPS][256]
+    uint32_t* base = cnt + SS_WARPS * 256;                        // [256]
+    uint32_t* va = base + 256;
+    uint32_t* vb = va + SS_MAX;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int chunk = (n + SS_WARPS - 1) / SS_WARPS;
+    const int c0 = min(w * chunk, n), c1 = min(c0 + chunk, n);
+    for (int i = threadIdx.x; i < n; i += SS_THREADS) {
+        ka[i] = keys[i];
+        if (VALS) va[i] = vals[i];
+    }
+    for (int p = 0; p < passes; p++) {
+        const int shift = 8 * p;
+        uint32_t* row = cnt + w * 256;
+        for (int q = lane; q < 256; q += 32) row[q] = 0;
+        __syncthreads();   // also orders the previous pass's scatter before these reads
+        for (int t = c0; t < c1; t += 32) {
+            int i = t + lane;
+            bool ok = i < c1;
+            unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                unsigned dg = (unsigned)(ka[i] >> shift) & 255u;
+                unsigned peers = __match_any_sync(act, dg);
+                if ((peers & lt) == 0) row[dg] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        uint32_t run = 0;
+        if (threadIdx.x < 256) {   // per digit: exclusive over warps, total to base
+            for (int ww = 0; ww < SS_WARPS; ww++) {
+                uint32_t c = cnt[ww * 256 + threadIdx.x];
+                cnt[ww * 256 + threadIdx.x] = run;
+                run += c;
+            }
+            base[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (w == 0) {   // exclusive scan of the 256 digit totals, 8 per lane
+            uint32_t v[8], sum = 0;
+            for (int q = 0; q < 8; q++) { v[q] = base[lane * 8 + q]; sum += v[q]; }
+            uint32_t x = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            uint32_t r = x - sum;
+            for (int q = 0; q < 8; q++) { base[lane * 8 + q] = r; r += v[q]; }
+        }
+        __syncthreads();
+        for (int t = c0; t < c1; t += 32) {
+            int i = t + lane;
+            bool ok = i < c1;
+            unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                uint64_t k = ka[i];
+                unsigned dg = (unsigned)(k >> shift) & 255u;
+                unsigned peers = __match_any_sync(act, dg);
+                uint32_t pos = base[dg] + row[dg] + __popc(peers & lt);
+                kb[pos] = k;
+                if (VALS) vb[pos] = va[i];
+                __syncwarp(act);
+                if ((peers & lt) == 0) row[dg] += __popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+    for (int i = threadIdx.x; i < n; i += SS_THREADS) {
+        keys[i] = ka[i];
+        if (VALS) vals[i] = va[i];
+    }
+}
+
 }  // namespace
 
 cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32_t* vals,
                          uint32_t* vals_alt, int64_t n, int end_bit) {
     if (n <= 1 || end_bit <= 0) return cudaSuccess;
     if (n > (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
+    if (n <= SS_MAX) {
+        const size_t smem = sizeof(uint64_t) * 2 * SS_MAX + sizeof(uint32_t) * (SS_WARPS * 256 + 256) +
+                            (vals ? sizeof(uint32_t) * 2 * SS_MAX : 0);
+        cudaError_t e;
+        prof_begin(ctx, "k_sort_small");
+        if (vals) {
+            e = ensure_smem_attr((const void*)k_sort_small<true>, smem);
+            if (e == cudaSuccess)
+                k_sort_small<true><<<1, SS_THREADS, smem, ctx->stream>>>(keys, vals, (int)n, (end_bit + 7) / 8);
+        } else {
+            e = ensure_smem_attr((const void*)k_sort_small<false>, smem);
+            if (e == cudaSuccess)
+                k_sort_small<false><<<1, SS_THREADS, smem, ctx->stream>>>(keys, nullptr, (int)n, (end_bit + 7) / 8);
+        }
+        prof_end(ctx);
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     int nb = (int)((n + RS_TILE - 1) / RS_TILE);
     cudaError_t e = buf_reserve(ctx->sort_hist, sizeof(uint32_t) * 256 * (size_t)nb);
     if (e != cudaSuccess) return e;

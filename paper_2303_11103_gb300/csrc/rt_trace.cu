@@ -92,8 +92,10 @@ struct SbrParams {
     TraceCommon c;
     int D;
     int id_bits, depth_shift, tx_shift;
-    uint64_t* keys;   // [total*D]
-    int32_t* hits;    // [total*D] or null
+    uint64_t* keys;                // compacted candidate keys (capacity total*D)
+    uint32_t* vals;                // their (ray slot * D + depth) positions
+    unsigned long long* n_keys;    // append counter
+    int32_t* hits;                 // [total*D] or null
 };
 
 __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
@@ -122,6 +124,9 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
             if (feed.exhausted) break;
             continue;
         }
+        bool emit = false;
+        uint64_t ekey = 0;
+        uint32_t epos = 0;
         if (alive) {
             float t;
             int id = closest_hit(p.c.s, sm, p.c.n_sm, o, d, last, t, p.c.status, cnt);
@@ -130,13 +135,34 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
             } else {
                 key |= (uint64_t)id << ((p.D - 1 - depth) * p.id_bits);
                 size_t pos = (size_t)slot * p.D + depth;
-                p.keys[pos] = key | ((uint64_t)(depth + 1) << p.depth_shift);
+                ekey = key | ((uint64_t)(depth + 1) << p.depth_shift);
+                epos = (uint32_t)pos;
+                emit = true;
                 if (p.hits) p.hits[pos] = id;
                 float4 pl = __ldg(p.c.s.planes + id);
                 o = o + d * t;
                 d = reflect(d, xyz(pl));
                 last = id;
                 if (++depth >= p.D) alive = false;
+            }
+        }
+        // append this bounce's candidate keys: equal keys within the warp
+        // are appended once (the lowest lane is the witness), one atomic per
+        // warp, ballot ranks
+        const unsigned em = __ballot_sync(0xffffffffu, emit);
+        if (em) {
+            const int lane = threadIdx.x & 31;
+            bool keep = false;
+            if (emit) keep = (__match_any_sync(em, (unsigned long long)ekey) & lanemask_lt()) == 0;
+            const unsigned km = __ballot_sync(0xffffffffu, keep);
+            const int leader = __ffs(km) - 1;
+            unsigned long long b0 = 0;
+            if (lane == leader) b0 = atomicAdd(p.n_keys, (unsigned long long)__popc(km));
+            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            if (keep) {
+                unsigned long long k = b0 + __popc(km & lanemask_lt());
+                p.keys[k] = ekey;
+                p.vals[k] = epos;
             }
         }
     }
@@ -310,8 +336,9 @@ static TraceCommon make_common(rt_ctx* ctx, int64_t N, int64_t first, int64_t co
     return c;
 }
 
-// Shoot and bounce: writes candidate keys at (tx*N + i)*D + depth.
-int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits) {
+// Shoot and bounce: appends every hit's candidate key with its position
+// (tx*N + i)*D + depth; the key count goes to counter slot RT_CNT_KEYS.
+int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, uint32_t* vals, int32_t* hits) {
     int e = ensure_perm(ctx, N);
     if (e) return e;
     SbrParams p;
@@ -321,10 +348,13 @@ int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, int32_t* hits) {
     p.depth_shift = D * ctx->id_bits;
     p.tx_shift = p.depth_shift + 3;
     p.keys = keys;
+    p.vals = vals;
+    p.n_keys = bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS;
     p.hits = hits;
     size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    RT_TRY(cudaFuncSetAttribute(k_sbr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RT_TRY(ensure_smem_attr((const void*)k_sbr, smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
+    RT_TRY(cudaMemsetAsync(p.n_keys, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_sbr, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     prof_begin(ctx, "k_sbr");
@@ -364,7 +394,7 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     }
     if (count == 0) return RT_OK;
     size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RT_TRY(ensure_smem_attr((const void*)k_coverage, smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)k_coverage, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
@@ -406,7 +436,7 @@ int launch_coverage_scratch(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int
     RT_TRY(cudaMemsetAsync(hits, 0, sizeof(uint32_t) * cells, ctx->stream));
     RT_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned long long), ctx->stream));
     size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    RT_TRY(cudaFuncSetAttribute(k_coverage, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RT_TRY(ensure_smem_attr((const void*)k_coverage, smem));
     int grid = trace_grid(ctx, (const void*)k_coverage, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     ctx->launches++;

@@ -66,6 +66,7 @@ def lib():
             "rt_set_frequency": [vp, dbl],
             "rt_load_scene": [vp, vp, i64, vp, vp, i32],
             "rt_set_materials": [vp, vp, i32],
+            "rt_set_bvh_builder": [vp, i32],
             "rt_set_tx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna)],
             "rt_set_rx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna), vp],
             "rt_compute_paths": [vp, i32, i64, u32, ctypes.POINTER(i64)],
@@ -95,6 +96,7 @@ def lib():
             "rt_mlp_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
             "rt_mlp_train_step": [vp, vp, vp, i32, ctypes.c_float, vp],
             "rt_mlp_infer": [vp, vp, i64, vp],
+            "rt_mlp_infer_layers": [vp, vp, i64, vp],
             "rt_mlp_num_params": [vp, ctypes.POINTER(i64)],
             "rt_mlp_get_params": [vp, vp],
             "rt_mlp_set_params": [vp, vp],
@@ -174,6 +176,13 @@ def rt_load_scene(ctx, verts, mat_id, mat_params):
 
 def rt_set_materials(ctx, mat_params):
     _check(ctx, lib().rt_set_materials(ctx, _ptr(mat_params), int(mat_params.shape[0])))
+
+
+BVH_KARRAS, BVH_PLOC = 0, 1
+
+
+def rt_set_bvh_builder(ctx, builder):
+    _check(ctx, lib().rt_set_bvh_builder(ctx, int(builder)))
 
 
 def rt_set_tx(ctx, pos, ypr, antenna):
@@ -352,6 +361,10 @@ class Tracer:
         self._mats = self._t(scene.materials, torch.float32).reshape(-1, 2)
         self.n_mat = int(self._mats.shape[0])
         rt_load_scene(self.ctx, self._verts, self._mat, self._mats)
+
+    def set_bvh_builder(self, builder):
+        """Hierarchy for the next load_scene: BVH_KARRAS or BVH_PLOC."""
+        rt_set_bvh_builder(self.ctx, builder)
 
     def set_materials(self, mats):
         self.sync_stream()
@@ -608,6 +621,13 @@ class Surrogate:
         self._sync()
         out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=self.device)
         self._check(lib().rt_mlp_infer(self.h, _ptr(x.contiguous()), int(x.shape[0]), _ptr(out)))
+        return out
+
+    def infer_layers(self, x):
+        """Layer-by-layer GEMM path (the reference of the fused inference kernel)."""
+        self._sync()
+        out = torch.empty((x.shape[0], 2), dtype=torch.float32, device=self.device)
+        self._check(lib().rt_mlp_infer_layers(self.h, _ptr(x.contiguous()), int(x.shape[0]), _ptr(out)))
         return out
 
     def params(self):

@@ -167,14 +167,63 @@ def _height_at(fps: np.ndarray, x: float, y: float) -> float:
     return float(fps[m, 4].max()) if m.any() else 0.0
 
 
-def street_points(scene: Scene, n: int, rng, half: float, margin: float = 0.5):
-    """n points (x, y) by rejection from [-half, half]^2 outside every footprint."""
-    out = []
+class _FootprintRaster:
+    """Exact point-in-(dilated)-footprint test accelerated by a 1 m raster:
+    cells fully inside a footprint reject, cells touching none accept, the
+    rest fall back to the exact test."""
+
+    def __init__(self, fps, margin, cell=1.0):
+        self.fps, self.margin, self.cell = fps, margin, cell
+        lo = np.floor(min(fps[:, 0].min(), fps[:, 2].min()) - margin - 1)
+        hi = np.ceil(max(fps[:, 1].max(), fps[:, 3].max()) + margin + 1)
+        self.lo, self.n = lo, int((hi - lo) / cell) + 1
+        self.touch = np.zeros((self.n, self.n), bool)
+        self.full = np.zeros((self.n, self.n), bool)
+        for x0, x1, y0, y1, _ in fps:
+            a = (np.array([x0 - margin, x1 + margin, y0 - margin, y1 + margin]) - lo) / cell
+            i0, i1, j0, j1 = int(np.floor(a[0])), int(np.floor(a[1])), int(np.floor(a[2])), int(np.floor(a[3]))
+            self.touch[i0:i1 + 1, j0:j1 + 1] = True
+            f0, f1, g0, g1 = int(np.ceil(a[0])), int(np.floor(a[1])) - 1, int(np.ceil(a[2])), int(np.floor(a[3])) - 1
+            if f1 >= f0 and g1 >= g0:
+                self.full[f0:f1 + 1, g0:g1 + 1] = True
+
+    def inside(self, p):
+        ij = np.floor((p - self.lo) / self.cell).astype(np.int64)
+        ok = (ij >= 0).all(1) & (ij < self.n).all(1)
+        res = np.zeros(len(p), bool)
+        t = np.zeros(len(p), bool)
+        f = np.zeros(len(p), bool)
+        t[ok] = self.touch[ij[ok, 0], ij[ok, 1]]
+        f[ok] = self.full[ij[ok, 0], ij[ok, 1]]
+        res[f] = True
+        amb = t & ~f
+        if amb.any():
+            q, m, fps = p[amb], self.margin, self.fps
+            res[amb] = ((q[:, None, 0] > fps[None, :, 0] - m) & (q[:, None, 0] < fps[None, :, 1] + m) &
+                        (q[:, None, 1] > fps[None, :, 2] - m) & (q[:, None, 1] < fps[None, :, 3] + m)).any(1)
+        return res
+
+
+def street_points(scene: Scene, n: int, rng, half: float, margin: float = 0.5, center=(0.0, 0.0)):
+    """n points (x, y) by rejection from center + [-half, half]^2 outside every footprint."""
+    fps = scene.footprints
+    raster = None
+    if len(fps):
+        key = (id(fps), margin)
+        raster = _RASTERS.get(key)
+        if raster is None:
+            raster = _RASTERS[key] = _FootprintRaster(fps, margin)
+    out = np.zeros((0, 2))
     while len(out) < n:
-        x, y = rng.uniform(-half, half, 2)
-        if not _inside_any(scene.footprints, x, y, margin):
-            out.append((x, y))
-    return np.array(out, np.float64)
+        m = max(2 * (n - len(out)), 64)
+        p = rng.uniform(-half, half, (m, 2)) + np.asarray(center, np.float64)
+        if raster is not None:
+            p = p[~raster.inside(p)]
+        out = np.concatenate([out, p])
+    return out[:n]
+
+
+_RASTERS = {}
 
 
 def city_devices(scene: Scene, n_rx: int = 1000, seed: int = 2,
@@ -207,9 +256,14 @@ def rooftop_transmitters(scene: Scene, n_tx: int = 64, seed: int = 2,
 
 
 def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
-                    half: float = 240.0):
-    """Tx 1 m above a random roof centre, Rx 1.5 m above streets.
+                    half: float = 240.0, mast: float = 3.0, rx_radius: float = 100.0):
+    """Tx on a 3 m mast at a random roof corner, Rx 1.5 m above nearby streets.
 
+    The transmitter stands 1 m diagonally outside a corner of a random
+    building, `mast` metres above that roof (a mast at the roof centre sees
+    no street: the roof hides it), and not inside a taller building. Its
+    receivers are street points within a square of half-side rx_radius
+    around it (clipped to the city).
     Returns tx [n_tx, 3] and rx [n_tx, n_rx_per_tx, 3] (float32).
     """
     rng = np.random.default_rng(seed)
@@ -219,10 +273,18 @@ def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
     tx = []
     while len(tx) < n_tx:
         b = inner[rng.integers(0, len(inner))]
-        x, y = 0.5 * (b[0] + b[1]), 0.5 * (b[2] + b[3])
-        tx.append((x, y, _height_at(fps, x, y) + 1.0))
-    rx = np.stack([np.concatenate([street_points(scene, n_rx_per_tx, rng, half),
-                                   np.full((n_rx_per_tx, 1), 1.5)], 1)
-                   for _ in range(n_tx)])
-    return np.array(tx, np.float32), rx.astype(np.float32)
+        cx, cy = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+        x = b[1] + 1.0 if cx else b[0] - 1.0
+        y = b[3] + 1.0 if cy else b[2] - 1.0
+        z = b[4] + mast
+        if _height_at(fps, x, y) >= z - 0.5:
+            continue
+        tx.append((x, y, z))
+    rx = []
+    for t in tx:
+        r = min(rx_radius, half)
+        c = np.clip([t[0], t[1]], -half + r, half - r)
+        rx.append(np.concatenate([street_points(scene, n_rx_per_tx, rng, r, center=c),
+                                  np.full((n_rx_per_tx, 1), 1.5)], 1))
+    return np.array(tx, np.float32), np.stack(rx).astype(np.float32)
 

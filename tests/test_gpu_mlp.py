@@ -85,6 +85,13 @@ def test_mlp_inference_matches_reference_and_learns():
         S.train_step(xt[(it % 8) * 512:(it % 8 + 1) * 512], tt[(it % 8) * 512:(it % 8 + 1) * 512], 1e-3, loss)
         losses.append(loss.item())
     assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+    # fused all-layer kernel == layer-by-layer GEMMs (same BF16 rounding points)
+    big = torch.cat([xt] * 3)[:10007]                    # several tiles per CTA, ragged tail
+    fused = S.infer(big)
+    layered = S.infer_layers(big)
+    torch.cuda.synchronize()
+    assert S.status() == 0
+    assert torch.allclose(fused, layered, rtol=1e-4, atol=1e-3)
     out = S.infer(xt[:777]).cpu().numpy()             # ragged count
     p = S.params().cpu().numpy()
     y, _, _, _ = R.forward(p, x[:777], S.F, S.W, S.L, lo, hi, bf16=True)
