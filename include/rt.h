@@ -315,6 +315,11 @@ int rt_mlp_last_error(const rt_mlp* m, char* buf, size_t len);
  * BCE(logit, has_path) + has_path ((gain_pred - gain)/20 dB)^2, ADDED to
  * loss_out[0] (device; may be NULL). batch % 128 == 0. */
 int rt_mlp_train_step(rt_mlp* m, const float* x, const float* target, int32_t batch, float lr, float* loss_out);
+/* Free-space baseline (wavelength in m; 0, the default, = none): with it
+ * the gain output is the network's residual plus the Friis gain
+ * 20 log10(lambda / (4 pi d)), d = |rx - tx| (at least 1 m), in training
+ * (the loss compares the residual) and inference alike. */
+int rt_mlp_set_baseline(rt_mlp* m, float wavelength);
 /* out [n*2] = (path logit, path gain dB) for x [n*6]. One fused persistent
  * kernel (all layers per 128-query tile, activations kept on chip) when
  * 2*n_freq and width are multiples of 64, else rt_mlp_infer_layers. */
@@ -350,6 +355,10 @@ int rt_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int
  */
 int rt_profile(rt_ctx* ctx, int enable);
 int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset);
+/* Restrict the event timing of rt_profile to the kernels named in `names`
+ * (HOST, comma-separated, e.g. "k_coverage,k_sbr"); NULL or "" times every
+ * kernel again. Launch counting is unaffected. */
+int rt_profile_select(rt_ctx* ctx, const char* names);
 
 #ifdef __cplusplus
 }

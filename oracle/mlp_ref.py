@@ -58,14 +58,29 @@ def forward(params, x, F, W, L, lo, hi, bf16=True):
     return y, H, ws, bs
 
 
-def loss_and_grads(params, x, target, F, W, L, lo, hi, bf16=True):
-    """Mean loss and its gradient (parameter layout; Fourier part zero)."""
+def friis_db(x, lam):
+    """Free-space gain 20 log10(lam / (4 pi d)) of queries x [n, 6], d = |rx - tx|
+    clamped to at least 1 m (the surrogate's optional baseline); 0 if lam == 0."""
+    if lam <= 0:
+        return np.zeros(len(x))
+    d = np.maximum(np.linalg.norm(np.asarray(x, np.float64)[:, 3:] - np.asarray(x, np.float64)[:, :3], axis=1), 1.0)
+    return 20.0 * np.log10(lam / (4.0 * np.pi * d))
+
+
+def gain_db(y, x, lam=0.0):
+    """Gain output in dB from the head's second value."""
+    return y[:, 1] * DB_SCALE + DB_OFFSET + friis_db(x, lam)
+
+
+def loss_and_grads(params, x, target, F, W, L, lo, hi, bf16=True, lam=0.0):
+    """Mean loss and its gradient (parameter layout; Fourier part zero). With
+    lam > 0 the gain head is the residual over the free-space gain."""
     dt = np.float32 if bf16 else np.float64
     rnd = to_bf16 if bf16 else (lambda v: v)
     y, H, ws, bs = forward(params, x, F, W, L, lo, hi, bf16)
     n = len(x)
     z, has = y[:, 0], target[:, 0].astype(dt)
-    t = (target[:, 1].astype(dt) - DB_OFFSET) / DB_SCALE
+    t = ((target[:, 1].astype(np.float64) - DB_OFFSET - friis_db(x, lam)) / DB_SCALE).astype(dt)
     p = 1.0 / (1.0 + np.exp(-z))
     e = y[:, 1] - t
     loss = np.mean(np.maximum(z, 0) - z * has + np.log1p(np.exp(-np.abs(z))) + has * e * e)

@@ -91,6 +91,9 @@ cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
 void prof_begin(rt_ctx* ctx, const char* name) {
     ctx->launches++;
     if (!ctx->prof || ctx->capturing || ctx->prof_name.size() >= PROF_MAX) return;
+    if (!ctx->prof_only.empty() &&
+        std::find(ctx->prof_only.begin(), ctx->prof_only.end(), name) == ctx->prof_only.end())
+        return;
     size_t k = ctx->prof_name.size();
     while (ctx->prof_ev.size() < 2 * (k + 1)) {
         cudaEvent_t e;
@@ -155,8 +158,11 @@ int rt_create(rt_ctx** out, int device, void* stream) {
         delete ctx;
         return RT_ERR_CUDA;
     }
-    if (buf_reserve(ctx->counters, 64) != cudaSuccess || buf_reserve(ctx->status, 64) != cudaSuccess) {
+    if (buf_reserve(ctx->counters, 64) != cudaSuccess || buf_reserve(ctx->status, 64) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->host_rb, sizeof(uint64_t) * RB_WORDS) != cudaSuccess) {
+        cudaGetLastError();
         buf_free(ctx->counters);
+        buf_free(ctx->status);
         delete ctx;
         return RT_ERR_OOM;
     }
@@ -173,8 +179,12 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
                       &ctx->cand_img, &ctx->path_key, &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
-                      &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm})
+                      &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
+                      &ctx->b_lbox, &ctx->b_cent, &ctx->b_info, &ctx->b_keys, &ctx->b_keys2, &ctx->b_vals,
+                      &ctx->b_vals2, &ctx->b_child, &ctx->b_pint, &ctx->b_pleaf, &ctx->b_ibox, &ctx->b_flag,
+                      &ctx->b_dkeys, &ctx->b_dkeys2, &ctx->b_rank})
         buf_free(*b);
+    if (ctx->host_rb) cudaFreeHost(ctx->host_rb);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -554,6 +564,23 @@ int rt_profile(rt_ctx* ctx, int enable) {
     ctx->prof = enable != 0;
     ctx->prof_open = false;
     ctx->prof_name.clear();
+    return RT_OK;
+}
+
+int rt_profile_select(rt_ctx* ctx, const char* names) {
+    CHECK_CTX(ctx);
+    ctx->prof_only.clear();
+    if (!names) return RT_OK;
+    std::string cur;
+    for (const char* c = names;; c++) {
+        if (*c == ',' || *c == 0) {
+            if (!cur.empty()) ctx->prof_only.push_back(cur);
+            cur.clear();
+            if (*c == 0) break;
+        } else if (*c != ' ') {
+            cur.push_back(*c);
+        }
+    }
     return RT_OK;
 }
 

@@ -76,6 +76,22 @@ __global__ void k_prep(const float* __restrict__ v, const int32_t* __restrict__ 
     }
 }
 
+// Largest side of the vertex bounds (1 for a degenerate scene); the host
+// computes the same value from the same words.
+__device__ __forceinline__ float bounds_extent(const unsigned* __restrict__ b) {
+    float e = 0.0f;
+    for (int k = 0; k < 3; k++) e = fmaxf(e, unord(b[3 + k]) - unord(b[k]));
+    return e > 0.0f ? e : 1.0f;
+}
+
+// Build info words: [0..11] bounds (min words all ones, max words zero),
+// [12] large-triangle count, [13] tree depth, [14] clustering status.
+constexpr int INFO_WORDS = 16;
+__global__ void k_info_init(unsigned* __restrict__ info) {
+    int k = threadIdx.x;
+    if (k < INFO_WORDS) info[k] = (k < 12 && (k % 6) < 3) ? 0xffffffffu : 0u;
+}
+
 __device__ __forceinline__ unsigned expand10(unsigned x) {
     x &= 1023u;
     x = (x | (x << 16)) & 0x030000FFu;
@@ -90,11 +106,12 @@ __device__ __forceinline__ unsigned expand10(unsigned x) {
 // stable sort moves large triangles behind all others: they are tested
 // directly by every query rather than inflating the boxes of the BVH.
 __global__ void k_morton(const float* __restrict__ cent, const float* __restrict__ lbox, int T,
-                         const unsigned* __restrict__ bounds, float big_side, uint64_t* __restrict__ keys,
+                         const unsigned* __restrict__ bounds, uint64_t* __restrict__ keys,
                          uint32_t* __restrict__ vals, unsigned* __restrict__ n_big) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= T) return;
     vals[i] = (uint32_t)i;
+    const float big_side = BIG_FRAC * bounds_extent(bounds);
     const float* b = lbox + 6 * (size_t)i;
     float side = fmaxf(fmaxf(b[3] - b[0], b[4] - b[1]), b[5] - b[2]);
     if (side > big_side) {
@@ -326,28 +343,30 @@ __global__ void k_refit(int n, const uint32_t* __restrict__ leaf_tri, const floa
     }
 }
 
-__global__ void k_depth(int m, const int* __restrict__ par_int, uint64_t* __restrict__ keys,
+// Level-order key (depth << shift) | node, depth clamped to 255 in the key
+// (a deeper tree is rejected by the stack check anyway).
+__global__ void k_depth(int m, int shift, const int* __restrict__ par_int, uint64_t* __restrict__ keys,
                         int* __restrict__ maxdepth) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int d = 0;
     for (int p = par_int[i]; p >= 0 && d < m; p = par_int[p]) d++;
-    keys[i] = ((uint64_t)d << 32) | (uint32_t)i;
+    keys[i] = ((uint64_t)min(d, 255) << shift) | (uint32_t)i;
     atomicMax(maxdepth, d);
 }
 
-__global__ void k_rank(int m, const uint64_t* __restrict__ keys, int* __restrict__ rank) {
+__global__ void k_rank(int m, uint32_t mask, const uint64_t* __restrict__ keys, int* __restrict__ rank) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < m) rank[(uint32_t)keys[k]] = k;
+    if (k < m) rank[(uint32_t)keys[k] & mask] = k;
 }
 
 __global__ void k_emit(int m, const uint64_t* __restrict__ order, const int* __restrict__ rank,
                        const int2* __restrict__ child, const float* __restrict__ ibox,
                        const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri,
-                       float pad, float4* __restrict__ nodes) {
+                       float pad, uint32_t mask, float4* __restrict__ nodes) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
-    int o = (int)(uint32_t)order[k];
+    int o = (int)((uint32_t)order[k] & mask);
     int2 c = child[o];
     float a[6], b[6];
     int na, nb;
@@ -412,105 +431,95 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     RT_TRY(buf_reserve(ctx->planes, sizeof(float4) * (size_t)T));
     int m = std::max(T - 1, 1);
     RT_TRY(buf_reserve(ctx->nodes, sizeof(float4) * 4 * (size_t)m));
-    // build temporaries (freed at the end)
-    DevBuf lbox, cent, bounds, keys, keys2, vals, vals2, child, pint, pleaf, ibox, flag, dkeys, dkeys2,
-        rank, maxd;
-    auto cleanup = [&]() {
-        for (DevBuf* b : {&lbox, &cent, &bounds, &keys, &keys2, &vals, &vals2, &child, &pint, &pleaf,
-                          &ibox, &flag, &dkeys, &dkeys2, &rank, &maxd})
-            buf_free(*b);
-    };
-#define BT(expr)                                               \
-    do {                                                       \
-        cudaError_t e_ = (expr);                               \
-        if (e_ != cudaSuccess) { cleanup(); return set_cuda(ctx, e_, #expr); } \
-    } while (0)
-    BT(buf_reserve(lbox, sizeof(float) * 6 * (size_t)T));
-    BT(buf_reserve(cent, sizeof(float) * 3 * (size_t)T));
-    BT(buf_reserve(bounds, sizeof(unsigned) * 12));
-    unsigned init[12];
-    for (int k = 0; k < 12; k++) init[k] = (k % 6) < 3 ? 0xffffffffu : 0u;
-    BT(cudaMemcpyAsync(bounds.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
-    prof_begin(ctx, "k_prep");
-    k_prep<<<gT, B, 0, st>>>(verts, bp<int32_t>(ctx->mat), T, bp<float4>(ctx->tris_o),
-                             bp<float4>(ctx->planes), bp<float>(lbox), bp<float>(cent),
-                             bp<unsigned>(bounds));
+    // build scratch, kept in the context between builds
+    RT_TRY(buf_reserve(ctx->b_lbox, sizeof(float) * 6 * (size_t)T));
+    RT_TRY(buf_reserve(ctx->b_cent, sizeof(float) * 3 * (size_t)T));
+    RT_TRY(buf_reserve(ctx->b_info, sizeof(unsigned) * INFO_WORDS));
+    RT_TRY(buf_reserve(ctx->b_keys, sizeof(uint64_t) * T));
+    RT_TRY(buf_reserve(ctx->b_keys2, sizeof(uint64_t) * T));
+    RT_TRY(buf_reserve(ctx->b_vals, sizeof(uint32_t) * T));
+    RT_TRY(buf_reserve(ctx->b_vals2, sizeof(uint32_t) * T));
+    float* lbox = bp<float>(ctx->b_lbox);
+    unsigned* info = bp<unsigned>(ctx->b_info);
+    uint64_t* keys = bp<uint64_t>(ctx->b_keys);
+    uint32_t* vals = bp<uint32_t>(ctx->b_vals);
+    prof_begin(ctx, "k_info_init");
+    k_info_init<<<1, 32, 0, st>>>(info);
     prof_end(ctx);
-    BT(cudaGetLastError());
-    unsigned hb[12];
-    BT(cudaMemcpyAsync(hb, bounds.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
-    BT(cudaStreamSynchronize(st));
+    prof_begin(ctx, "k_prep");
+    k_prep<<<gT, B, 0, st>>>(verts, bp<int32_t>(ctx->mat), T, bp<float4>(ctx->tris_o), bp<float4>(ctx->planes),
+                             lbox, bp<float>(ctx->b_cent), info);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    prof_begin(ctx, "k_morton");
+    k_morton<<<gT, B, 0, st>>>(bp<float>(ctx->b_cent), lbox, T, info, keys, vals, info + 12);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->b_keys2), vals, bp<uint32_t>(ctx->b_vals2), T, 32));
+    // bounds and large-triangle count in one read
+    unsigned hi[13];
+    RT_TRY(cudaMemcpyAsync(ctx->host_rb, info, sizeof(hi), cudaMemcpyDeviceToHost, st));
+    RT_TRY(cudaStreamSynchronize(st));
+    memcpy(hi, ctx->host_rb, sizeof(hi));
     float ext = 0.0f;
-    for (int k = 0; k < 3; k++) ext = std::max(ext, host_unord(hb[3 + k]) - host_unord(hb[k]));
+    for (int k = 0; k < 3; k++) ext = std::max(ext, host_unord(hi[3 + k]) - host_unord(hi[k]));
     if (!(ext > 0.0f)) ext = 1.0f;
     ctx->extent = ext;
     ctx->tmin = 2e-6f * ext;
     const float pad = 1e-6f * ext;
-    BT(buf_reserve(keys, sizeof(uint64_t) * T));
-    BT(buf_reserve(keys2, sizeof(uint64_t) * T));
-    BT(buf_reserve(vals, sizeof(uint32_t) * T));
-    BT(buf_reserve(vals2, sizeof(uint32_t) * T));
-    // [0] tree depth, [1] large-triangle count, [2] clustering status
-    BT(buf_reserve(maxd, sizeof(int) * 3));
-    BT(cudaMemsetAsync(maxd.p, 0, sizeof(int) * 3, st));
-    prof_begin(ctx, "k_morton");
-    k_morton<<<gT, B, 0, st>>>(bp<float>(cent), bp<float>(lbox), T, bp<unsigned>(bounds), BIG_FRAC * ext,
-                               bp<uint64_t>(keys), bp<uint32_t>(vals), bp<unsigned>(maxd) + 1);
-    prof_end(ctx);
-    BT(cudaGetLastError());
-    BT(radix_sort64(ctx, bp<uint64_t>(keys), bp<uint64_t>(keys2), bp<uint32_t>(vals),
-                    bp<uint32_t>(vals2), T, 32));
-    unsigned n_big = 0;
-    BT(cudaMemcpyAsync(&n_big, bp<unsigned>(maxd) + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    BT(cudaStreamSynchronize(st));
     // sorted order: triangles of the hierarchy (Morton order), then the large ones (id order)
+    const unsigned n_big = hi[12];
     const int n = T - (int)n_big;
     ctx->n_big = (int)n_big;
     ctx->n_bvh = n;
     m = std::max(n - 1, 1);
-    const uint32_t* leaf_tri = bp<uint32_t>(vals);
+    const uint32_t* leaf_tri = vals;
+    int hd[2] = {0, 0};   // tree depth, clustering status
     if (n == 0) {
         ctx->n_nodes = 0;
         ctx->bvh_depth = 0;
     } else if (n == 1) {
         prof_begin(ctx, "k_single_leaf");
-        k_single_leaf<<<1, 1, 0, st>>>(bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
+        k_single_leaf<<<1, 1, 0, st>>>(lbox, leaf_tri, pad, bp<float4>(ctx->nodes));
         prof_end(ctx);
-        BT(cudaGetLastError());
+        RT_TRY(cudaGetLastError());
         ctx->n_nodes = 1;
         ctx->bvh_depth = 1;
     } else {
         const int T = n;   // the hierarchy's triangles
         const int gT = (T + B - 1) / B;
-        BT(buf_reserve(child, sizeof(int2) * m));
-        BT(buf_reserve(pint, sizeof(int) * m));
-        BT(buf_reserve(pleaf, sizeof(int) * T));
-        BT(buf_reserve(ibox, sizeof(float) * 6 * (size_t)m));
+        RT_TRY(buf_reserve(ctx->b_child, sizeof(int2) * m));
+        RT_TRY(buf_reserve(ctx->b_pint, sizeof(int) * m));
+        RT_TRY(buf_reserve(ctx->b_pleaf, sizeof(int) * T));
+        RT_TRY(buf_reserve(ctx->b_ibox, sizeof(float) * 6 * (size_t)m));
+        int2* child = bp<int2>(ctx->b_child);
+        int* pint = bp<int>(ctx->b_pint);
+        int* pleaf = bp<int>(ctx->b_pleaf);
+        float* ibox = bp<float>(ctx->b_ibox);
         int gm = (m + B - 1) / B;
         if (ctx->bvh_builder == RT_BVH_PLOC) {
             // two cluster lists (six box planes + ids each)
-            BT(buf_reserve(flag, (sizeof(float) * 12 + sizeof(int) * 2) * (size_t)T));
-            float* boxA = bp<float>(flag);
+            RT_TRY(buf_reserve(ctx->b_flag, (sizeof(float) * 12 + sizeof(int) * 2) * (size_t)T));
+            float* boxA = bp<float>(ctx->b_flag);
             float* boxB = boxA + 6 * (size_t)T;
             int* idA = reinterpret_cast<int*>(boxB + 6 * (size_t)T);
             int* idB = idA + T;
             prof_begin(ctx, "k_ploc_leaves");
-            k_ploc_leaves<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), pad, boxA, idA);
+            k_ploc_leaves<<<gT, B, 0, st>>>(T, leaf_tri, lbox, pad, boxA, idA);
             prof_end(ctx);
-            BT(cudaGetLastError());
+            RT_TRY(cudaGetLastError());
             const size_t smem = (sizeof(float) * 12 + sizeof(int) * 3) * PLOC_C;
-            BT(ensure_smem_attr((const void*)k_ploc_chunk, smem));
+            RT_TRY(ensure_smem_attr((const void*)k_ploc_chunk, smem));
             int count = T, id_base = 0;
             float *bi = boxA, *bo = boxB;
             int *ii = idA, *io = idB;
             while (true) {
                 const int K = (count + PLOC_C - 1) / PLOC_C;
                 prof_begin(ctx, "k_ploc_chunk");
-                k_ploc_chunk<<<K, PLOC_C, smem, st>>>(count, bi, ii, bo, io, T, id_base, m, bp<int2>(child),
-                                                      bp<int>(pint), bp<int>(pleaf), bp<float>(ibox),
-                                                      bp<unsigned>(maxd) + 2);
+                k_ploc_chunk<<<K, PLOC_C, smem, st>>>(count, bi, ii, bo, io, T, id_base, m, child, pint, pleaf,
+                                                      ibox, info + 14);
                 prof_end(ctx);
-                BT(cudaGetLastError());
+                RT_TRY(cudaGetLastError());
                 id_base += count - K;
                 if (K == 1) break;
                 count = K;
@@ -518,52 +527,53 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
                 std::swap(ii, io);
             }
         } else {
-            BT(buf_reserve(flag, sizeof(int) * m));
-            BT(cudaMemsetAsync(flag.p, 0, sizeof(int) * m, st));
+            RT_TRY(buf_reserve(ctx->b_flag, sizeof(int) * m));
+            RT_TRY(cudaMemsetAsync(ctx->b_flag.p, 0, sizeof(int) * m, st));
             prof_begin(ctx, "k_karras");
-            k_karras<<<gm, B, 0, st>>>(bp<uint64_t>(keys), T, bp<int2>(child), bp<int>(pint), bp<int>(pleaf));
+            k_karras<<<gm, B, 0, st>>>(keys, T, child, pint, pleaf);
             prof_end(ctx);
-            BT(cudaGetLastError());
+            RT_TRY(cudaGetLastError());
             prof_begin(ctx, "k_refit");
-            k_refit<<<gT, B, 0, st>>>(T, leaf_tri, bp<float>(lbox), bp<int2>(child), bp<int>(pint),
-                                      bp<int>(pleaf), bp<float>(ibox), bp<int>(flag), pad);
+            k_refit<<<gT, B, 0, st>>>(T, leaf_tri, lbox, child, pint, pleaf, ibox, bp<int>(ctx->b_flag), pad);
             prof_end(ctx);
-            BT(cudaGetLastError());
+            RT_TRY(cudaGetLastError());
         }
-        BT(buf_reserve(dkeys, sizeof(uint64_t) * m));
-        BT(buf_reserve(dkeys2, sizeof(uint64_t) * m));
-        BT(buf_reserve(rank, sizeof(int) * m));
+        // level order: sort internal nodes by (depth, id)
+        RT_TRY(buf_reserve(ctx->b_dkeys, sizeof(uint64_t) * m));
+        RT_TRY(buf_reserve(ctx->b_dkeys2, sizeof(uint64_t) * m));
+        RT_TRY(buf_reserve(ctx->b_rank, sizeof(int) * m));
+        uint64_t* dkeys = bp<uint64_t>(ctx->b_dkeys);
+        int* rank = bp<int>(ctx->b_rank);
+        int shift = 1;
+        while ((1ll << shift) < m) shift++;
+        const uint32_t mask = (uint32_t)((1ull << shift) - 1);
         prof_begin(ctx, "k_depth");
-        k_depth<<<gm, B, 0, st>>>(m, bp<int>(pint), bp<uint64_t>(dkeys), bp<int>(maxd));
+        k_depth<<<gm, B, 0, st>>>(m, shift, pint, dkeys, reinterpret_cast<int*>(info + 13));
         prof_end(ctx);
-        BT(cudaGetLastError());
-        BT(radix_sort64(ctx, bp<uint64_t>(dkeys), bp<uint64_t>(dkeys2), nullptr, nullptr, m, 40));
+        RT_TRY(cudaGetLastError());
+        RT_TRY(radix_sort64(ctx, dkeys, bp<uint64_t>(ctx->b_dkeys2), nullptr, nullptr, m, shift + 8));
         prof_begin(ctx, "k_rank");
-        k_rank<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank));
+        k_rank<<<gm, B, 0, st>>>(m, mask, dkeys, rank);
         prof_end(ctx);
         prof_begin(ctx, "k_emit");
-        k_emit<<<gm, B, 0, st>>>(m, bp<uint64_t>(dkeys), bp<int>(rank), bp<int2>(child), bp<float>(ibox),
-                                 bp<float>(lbox), leaf_tri, pad, bp<float4>(ctx->nodes));
+        k_emit<<<gm, B, 0, st>>>(m, dkeys, rank, child, ibox, lbox, leaf_tri, pad, mask, bp<float4>(ctx->nodes));
         prof_end(ctx);
-        BT(cudaGetLastError());
-        int hd[3] = {0, 0, 0};
-        BT(cudaMemcpyAsync(hd, maxd.p, sizeof(int) * 3, cudaMemcpyDeviceToHost, st));
-        BT(cudaStreamSynchronize(st));
-        if (hd[2] != 0) {   // the clustering found no pair to merge: non-finite geometry
-            cleanup();
-            return set_err(ctx, RT_ERR_INVALID_ARG, "BVH build: non-finite triangle boxes");
-        }
+        RT_TRY(cudaGetLastError());
         ctx->n_nodes = m;
-        ctx->bvh_depth = hd[0] + 1;
     }
     // leaf records in sorted order: the hierarchy's leaves, then the large triangles
     prof_begin(ctx, "k_leaf_tris");
     k_leaf_tris<<<gT, B, 0, st>>>(T, leaf_tri, bp<float4>(ctx->tris_o), bp<float4>(ctx->tris));
     prof_end(ctx);
-    BT(cudaGetLastError());
-    BT(cudaStreamSynchronize(st));
-    cleanup();
-#undef BT
+    RT_TRY(cudaGetLastError());
+    if (n >= 2) {
+        RT_TRY(cudaMemcpyAsync(ctx->host_rb, info + 13, sizeof(hd), cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaStreamSynchronize(st));
+        memcpy(hd, ctx->host_rb, sizeof(hd));
+        if (hd[1] != 0)   // the clustering found no pair to merge: non-finite geometry
+            return set_err(ctx, RT_ERR_INVALID_ARG, "BVH build: non-finite triangle boxes");
+        ctx->bvh_depth = hd[0] + 1;
+    }
     if (ctx->bvh_depth + 1 >= RT_STACK)
         return set_err(ctx, RT_ERR_CAPACITY, "BVH deeper than the traversal stack");
     return RT_OK;

@@ -168,9 +168,12 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
     float2 g[4];
     for (int k = 0; k < np; k++) g[k] = on ? ga[i * np + k] : make_float2(0.0f, 0.0f);
     const float gt = gtau ? gtau[i] : 0.0f;
+    // one group of NT local parameters per grid row (blockIdx.y)
+    const int base = blockIdx.y * NT;
+    if (base >= nloc) return;
     const double len64 = path_length64(c.s, c.seq + i * c.D, K,
                                        mk(c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]), rx);
-    for (int base = 0; base < nloc; base += NT) {
+    {
         auto var = [&](float v, int idx) {
             Dual<NT> d = dconst<NT>(v);
             if (idx >= base && idx < base + NT) d.d[idx - base] = 1.0f;
@@ -207,39 +210,54 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
 }
 
 // ---------------------------------------------------------------- H(f)
-// One block per pair; each thread owns RUN consecutive subcarriers and keeps
-// their accumulators for every port pair in registers. Paths of the pair are
-// staged in shared memory in tiles. Twiddles: one range-reduced sincos per
-// (path, run) and a complex-rotation recurrence across the run (uniform
-// spacing), else a sincos per (path, subcarrier).
+// One block column per pair; block y covers 128 * HF_RUN subcarriers, thread t
+// the subcarriers kb + t + 128 s (s < HF_RUN), so every store instruction
+// writes 128 consecutive values. Accumulators for every port pair stay in
+// registers; the pair's paths are staged in shared memory in tiles.
+// Twiddles: with uniform spacing one range-reduced sincos for the first
+// subcarrier and one for the 128-subcarrier step per (path, thread), then a
+// complex-rotation recurrence; otherwise a sincos per (path, subcarrier).
+// Pairs without paths write zeros.
 constexpr int HF_RUN = 8;
 constexpr int HF_TILE = 64;
+constexpr int HF_THREADS = 128;
 
 template <int NP>
-__global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, const float2* __restrict__ a,
-                                              const float* __restrict__ tau, const double* __restrict__ freqs,
-                                              int K, float2* __restrict__ H) {
+__global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__ off, const float2* __restrict__ a,
+                                                     const float* __restrict__ tau, const double* __restrict__ freqs,
+                                                     int K, float2* __restrict__ H) {
     __shared__ float2 sa[HF_TILE][NP];
     __shared__ float st[HF_TILE];
-    const int64_t pair = blockIdx.y;
+    const int64_t pair = blockIdx.x;
     const int64_t b = off[pair], e = off[pair + 1];
-    const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * HF_RUN;
+    const int kb = blockIdx.y * HF_THREADS * HF_RUN + threadIdx.x;
+    if (b == e) {
+#pragma unroll
+        for (int q = 0; q < NP; q++)
+#pragma unroll
+            for (int s = 0; s < HF_RUN; s++) {
+                const int k = kb + s * HF_THREADS;
+                if (k < K) H[(pair * NP + q) * K + k] = make_float2(0.0f, 0.0f);
+            }
+        return;
+    }
     float2 acc[HF_RUN][NP];
 #pragma unroll
     for (int s = 0; s < HF_RUN; s++)
 #pragma unroll
         for (int q = 0; q < NP; q++) acc[s][q] = make_float2(0.0f, 0.0f);
-    // this thread's run of subcarriers; the recurrence needs uniform spacing
+    // this thread's subcarriers; the recurrence needs them evenly spaced
     float fl[HF_RUN];
-    bool uniform = k0 + HF_RUN <= K;
     double f0 = 0.0, df = 0.0;
-    if (k0 < K) {
-        f0 = freqs[k0];
-        df = k0 + 1 < K ? freqs[k0 + 1] - f0 : 0.0;
+    if (kb < K) {
+        f0 = freqs[kb];
+        df = kb + HF_THREADS < K ? freqs[kb + HF_THREADS] - f0 : 0.0;
     }
+    bool uniform = true;
 #pragma unroll
     for (int s = 0; s < HF_RUN; s++) {
-        double fs = k0 + s < K ? freqs[k0 + s] : 0.0;
+        const int k = kb + s * HF_THREADS;
+        double fs = k < K ? freqs[k] : f0 + s * df;
         fl[s] = (float)fs;
         if (fabs(fs - (f0 + s * df)) > 1e-9 * (fabs(fs) + 1.0)) uniform = false;
     }
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, c
         for (int j = threadIdx.x; j < n * NP; j += blockDim.x) sa[j / NP][j % NP] = a[(tb + j / NP) * NP + j % NP];
         for (int j = threadIdx.x; j < n; j += blockDim.x) st[j] = tau[tb + j];
         __syncthreads();
-        if (k0 >= K) continue;
+        if (kb >= K) continue;
         for (int j = 0; j < n; j++) {
             const float t = st[j];
             if (uniform) {
@@ -293,12 +311,14 @@ __global__ void __launch_bounds__(128) k_freq(const int64_t* __restrict__ off, c
             }
         }
     }
-    if (k0 >= K) return;
+    if (kb >= K) return;
 #pragma unroll
     for (int q = 0; q < NP; q++)
 #pragma unroll
-        for (int s = 0; s < HF_RUN; s++)
-            if (k0 + s < K) H[(pair * NP + q) * K + k0 + s] = acc[s][q];
+        for (int s = 0; s < HF_RUN; s++) {
+            const int k = kb + s * HF_THREADS;
+            if (k < K) H[(pair * NP + q) * K + k] = acc[s][q];
+        }
 }
 
 // VJP of H: grad_a_i = sum_k gH_k conj(w_ik); grad_tau_i = sum_k Re(conj(gH_k) a_i (-j 2 pi f_k) w_ik)
@@ -383,9 +403,9 @@ CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
 template <int NP>
 void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
                  int64_t n_pairs) {
-    dim3 grid((unsigned)((K + 128 * HF_RUN - 1) / (128 * HF_RUN)), (unsigned)n_pairs);
+    dim3 grid((unsigned)n_pairs, (unsigned)((K + HF_THREADS * HF_RUN - 1) / (HF_THREADS * HF_RUN)));
     prof_begin(ctx, "k_freq");
-    k_freq<NP><<<grid, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
+    k_freq<NP><<<grid, HF_THREADS, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
                                               (float2*)H);
     prof_end(ctx);
 }
@@ -416,8 +436,8 @@ int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau
     if (ctx->n_paths == 0) return RT_OK;
     CirParams c = make_cir(ctx, flags);
     prof_begin(ctx, "k_cir_vjp");
-    k_cir_vjp<<<(unsigned)((c.P + 63) / 64), 64, 0, ctx->stream>>>(c, (const float2*)ga, gtau, g_eps, g_sig, g_pos,
-                                                                  g_ypr);
+    dim3 grid((unsigned)((c.P + 63) / 64), (unsigned)((6 + 2 * c.D + NT - 1) / NT));
+    k_cir_vjp<<<grid, 64, 0, ctx->stream>>>(c, (const float2*)ga, gtau, g_eps, g_sig, g_pos, g_ypr);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;

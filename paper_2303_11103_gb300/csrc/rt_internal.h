@@ -28,6 +28,8 @@ struct DevAntenna {
     float slant[2];
 };
 
+constexpr int RB_WORDS = 16;
+
 struct rt_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -63,8 +65,13 @@ struct rt_ctx {
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
     int64_t path_cap = 0;
 
+    // BVH build scratch (kept between builds: no allocation per rt_load_scene)
+    DevBuf b_lbox, b_cent, b_info, b_keys, b_keys2, b_vals, b_vals2, b_child, b_pint, b_pleaf, b_ibox, b_flag,
+        b_dkeys, b_dkeys2, b_rank;
+
     // scratch
     DevBuf sort_hist, scan_buf, counters, status;
+    uint64_t* host_rb = nullptr;  // pinned host words for device -> host reads (RB_WORDS)
     DevBuf perm;          // direction-coherent ray order
     int64_t perm_n = -1;
 
@@ -80,6 +87,7 @@ struct rt_ctx {
     bool prof = false, prof_open = false;
     std::vector<const char*> prof_name;
     std::vector<cudaEvent_t> prof_ev;  // 2 per record
+    std::vector<std::string> prof_only;  // kernels timed (empty = all)
 
     // CUDA graph capture
     bool capturing = false;

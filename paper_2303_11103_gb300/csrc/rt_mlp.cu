@@ -174,22 +174,32 @@ __global__ void k_head(const __nv_bfloat16* __restrict__ H, int64_t n, int W, co
     }
 }
 
-// outputs in user units: (path logit, gain dB = y1 * scale + offset)
-__global__ void k_head_out(const float* __restrict__ y, int64_t n, float scale, float offset, float* __restrict__ out) {
+// Free-space gain 20 log10(lambda / (4 pi d)) in dB of the query x [6]
+// (d = |rx - tx|, at least 1 m); 0 when lam == 0 (no baseline).
+__device__ __forceinline__ float fspl_db(const float* __restrict__ x, float lam) {
+    if (lam <= 0.0f) return 0.0f;
+    float dx = x[3] - x[0], dy = x[4] - x[1], dz = x[5] - x[2];
+    float d = fmaxf(sqrtf(dx * dx + dy * dy + dz * dz), 1.0f);
+    return 20.0f * log10f(lam / (4.0f * RT_PI_F * d));
+}
+
+// outputs in user units: (path logit, gain dB = y1 * scale + offset + baseline)
+__global__ void k_head_out(const float* __restrict__ y, const float* __restrict__ x, int64_t n, float scale,
+                           float offset, float lam, float* __restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[2 * i] = y[2 * i];
-    out[2 * i + 1] = y[2 * i + 1] * scale + offset;
+    out[2 * i + 1] = y[2 * i + 1] * scale + offset + fspl_db(x + 6 * i, lam);
 }
 
 // loss = mean_b [BCE(logit, has) + has * (y1 - t)^2], t = (gain_db - offset) / scale;
 // dy = d loss / d y
-__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ tgt, int n, float scale, float offset,
-                       float* __restrict__ dy, float* __restrict__ loss) {
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ tgt, const float* __restrict__ x, int n,
+                       float scale, float offset, float lam, float* __restrict__ dy, float* __restrict__ loss) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     float l = 0.0f;
     if (i < n) {
-        float z = y[2 * i], has = tgt[2 * i], t = (tgt[2 * i + 1] - offset) / scale;
+        float z = y[2 * i], has = tgt[2 * i], t = (tgt[2 * i + 1] - offset - fspl_db(x + 6 * i, lam)) / scale;
         float p = 1.0f / (1.0f + __expf(-z));
         // BCE with logits, stable form: max(z,0) - z has + log(1 + e^-|z|)
         l = fmaxf(z, 0.0f) - z * has + log1pf(__expf(-fabsf(z)));
@@ -342,6 +352,7 @@ struct FusedArgs {
     const float* head_w;       // [2 x W]
     const float* head_b;       // [2]
     float db_scale, db_offset;
+    float lam;           // free-space baseline wavelength (0 = none)
     unsigned* err;
 };
 
@@ -481,7 +492,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fused(const __grid_constant__ Fu
         }
         if (ok && q < a.n) {
             a.out[2 * q] = h0 + s_head[2 * W];
-            a.out[2 * q + 1] = (h1 + s_head[2 * W + 1]) * a.db_scale + a.db_offset;
+            a.out[2 * q + 1] = (h1 + s_head[2 * W + 1]) * a.db_scale + a.db_offset + fspl_db(a.x + 6 * q, a.lam);
         }
     }
     tc_fence_before();
@@ -559,6 +570,7 @@ struct rt_mlp {
     cudaStream_t stream = nullptr;
     int F = 32, W = 256, L = 8;  // Fourier frequencies, width, hidden layers
     float db_scale = 20.0f, db_offset = -100.0f;
+    float lam = 0.0f;            // free-space baseline wavelength (0 = none)
     std::string err;
     DevBuf Bf, lo, hi, errw, loss;
     std::vector<DevBuf> w, b, mw, vw, mb, vb, gw, gb, wbf, wtbf;  // per layer, head = index L
@@ -742,6 +754,7 @@ int rt_mlp_infer(rt_mlp* m, const float* x, int64_t n, float* out) {
     a.head_b = bp<float>(m->b[m->L]);
     a.db_scale = m->db_scale;
     a.db_offset = m->db_offset;
+    a.lam = m->lam;
     a.err = bp<unsigned>(m->errw);
     const int kmax = std::max(2 * m->F, m->W) / 64;
     size_t smem = 1024 + 64 * 1024 + (size_t)kmax * m->W * 128 +
@@ -768,10 +781,16 @@ int rt_mlp_infer_layers(rt_mlp* m, const float* x, int64_t n, float* out) {
         int64_t c = std::min(chunk, n - s);
         rc = mlp_forward(m, x + 6 * s, c);
         if (rc) return rc;
-        k_head_out<<<(unsigned)((c + 255) / 256), 256, 0, m->stream>>>(bp<float>(m->y), c, m->db_scale, m->db_offset,
-                                                                       out + 2 * s);
+        k_head_out<<<(unsigned)((c + 255) / 256), 256, 0, m->stream>>>(bp<float>(m->y), x + 6 * s, c, m->db_scale,
+                                                                       m->db_offset, m->lam, out + 2 * s);
         MT(cudaGetLastError());
     }
+    return RT_OK;
+}
+
+int rt_mlp_set_baseline(rt_mlp* m, float wavelength) {
+    if (!m || !(wavelength >= 0.0f)) return RT_ERR_INVALID_ARG;
+    m->lam = wavelength;
     return RT_OK;
 }
 
@@ -785,8 +804,8 @@ int rt_mlp_train_step(rt_mlp* m, const float* x, const float* target, int32_t B,
     rc = mlp_forward(m, x, B);
     if (rc) return rc;
     float* loss = loss_out ? loss_out : bp<float>(m->loss);
-    k_loss<<<(B + 255) / 256, 256, 0, st>>>(bp<float>(m->y), target, B, m->db_scale, m->db_offset, bp<float>(m->dy),
-                                           loss);
+    k_loss<<<(B + 255) / 256, 256, 0, st>>>(bp<float>(m->y), target, x, B, m->db_scale, m->db_offset, m->lam,
+                                           bp<float>(m->dy), loss);
     const int W = m->W, L = m->L;
     k_head_wgrad<<<(W + 31) / 32, dim3(32, 8), 0, st>>>(bp<__nv_bfloat16>(m->H[L]), bp<float>(m->dy), B, W,
                                                          bp<float>(m->gw[L]), bp<float>(m->gb[L]));

@@ -99,11 +99,11 @@ __global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, int n_tx
 }
 
 // per-tx candidate ranges: off[t] = first candidate with tx >= t
-__global__ void k_cand_off(const uint64_t* __restrict__ ck, int64_t U, int n_tx, KeyFmt f,
+__global__ void k_cand_off(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ Up, int n_tx, KeyFmt f,
                            int64_t* __restrict__ off) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t > n_tx) return;
-    int64_t lo = 0, hi = U;
+    int64_t lo = 0, hi = *Up;
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
         if (f.tx(ck[mid]) < t) lo = mid + 1; else hi = mid;
@@ -112,11 +112,9 @@ __global__ void k_cand_off(const uint64_t* __restrict__ ck, int64_t U, int n_tx,
 }
 
 // images I_k of the transmitter through the candidate's planes (FP32)
-__global__ void k_cand_img(const uint64_t* __restrict__ ck, int64_t U, KeyFmt f,
-                           const float* __restrict__ tx_pos, const float4* __restrict__ planes,
-                           float* __restrict__ img) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= U) return;
+__device__ __forceinline__ void cand_img_one(const uint64_t* __restrict__ ck, int64_t c, KeyFmt f,
+                                             const float* __restrict__ tx_pos, const float4* __restrict__ planes,
+                                             float* __restrict__ img) {
     uint64_t key = ck[c];
     int K = f.depth(key), t = f.tx(key);
     f3 I = mk(tx_pos[3 * t], tx_pos[3 * t + 1], tx_pos[3 * t + 2]);
@@ -130,6 +128,54 @@ __global__ void k_cand_img(const uint64_t* __restrict__ ck, int64_t U, KeyFmt f,
     }
 }
 
+
+__global__ void k_cand_img(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ Up, KeyFmt f,
+                           const float* __restrict__ tx_pos, const float4* __restrict__ planes,
+                           float* __restrict__ img) {
+    const int64_t U = *Up;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < U; c += (int64_t)gridDim.x * blockDim.x)
+        cand_img_one(ck, c, f, tx_pos, planes, img);
+}
+
+// Validation work offsets: work_off[t] = sum over t' < t of U_t' R_t' (one
+// block; n_tx entries scanned in thread-contiguous runs).
+__global__ void __launch_bounds__(1024) k_work_off(const int64_t* __restrict__ cand_off,
+                                                   const int32_t* __restrict__ rx_off, int n_tx, int n_rx,
+                                                   int64_t* __restrict__ work_off) {
+    __shared__ long long ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int seg = (n_tx + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int s0 = min((int)threadIdx.x * seg, n_tx), s1 = min(s0 + seg, n_tx);
+    long long sum = 0;
+    for (int t = s0; t < s1; t++) {
+        long long R = rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx;
+        sum += (cand_off[t + 1] - cand_off[t]) * R;
+    }
+    long long x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        long long v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        ws[lane] = v;
+    }
+    __syncthreads();
+    long long run = x - sum + (w > 0 ? ws[w - 1] : 0);
+    for (int t = s0; t < s1; t++) {
+        work_off[t] = run;
+        long long R = rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx;
+        run += (cand_off[t + 1] - cand_off[t]) * R;
+    }
+    if (threadIdx.x == blockDim.x - 1) work_off[n_tx] = run;
+}
+
 // ------------------------------------------------------------ image method
 struct ValParams {
     DevScene s;
@@ -141,8 +187,7 @@ struct ValParams {
     const int64_t* cand_off;   // [n_tx+1]
     const int64_t* work_off;   // [n_tx+1]
     const int32_t* rx_off;     // [n_tx+1] or null
-    int n_tx, n_rx;
-    long long total;
+    int n_tx, n_rx;            // total work = work_off[n_tx]
     uint64_t* out;
     unsigned long long* count;
     long long cap;
@@ -183,19 +228,37 @@ __device__ __forceinline__ bool sides_ok(const DevScene& s, int K, const f3* P, 
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_validate(ValParams p) {
+// Per-warp scratch of k_validate: the 32 work items' path points and ids,
+// and the queue of their segments still to be tested for occluders.
+struct ValWarp {
+    float pts[32][RT_MAX_DEPTH + 2][3];
+    int ids[32][RT_MAX_DEPTH];
+    int K[32];
+    unsigned char q[32 * (RT_MAX_DEPTH + 1)];   // lane << 3 | segment
+};
+
+// One (candidate, receiver) work item per lane. Back-projection and side
+// tests run per lane; the segments of the items that pass go to a per-warp
+// queue, and all 32 lanes then test queued segments for occluders (any hit)
+// in rounds, skipping segments of items already found occluded, so that
+// the traversals of a round run side by side.
+__global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
     extern __shared__ float4 sm[];
     for (int i = threadIdx.x; i < p.n_sm * 4; i += blockDim.x) sm[i] = p.s.nodes[i];
+    ValWarp& W = reinterpret_cast<ValWarp*>(sm + 4 * p.n_sm)[threadIdx.x >> 5];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu, lt = lanemask_lt();
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long total = p.work_off[p.n_tx];
     TravCount cnt;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < p.total;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
          base += stride) {
         long long g = base + lane;
         bool valid = false;
         uint64_t rec = 0;
-        if (g < p.total) {
+        int K = 0;
+        if (g < total) {
             int lo = 0, hi = p.n_tx;  // largest t with work_off[t] <= g
             while (hi - lo > 1) {
                 int mid = (lo + hi) >> 1;
@@ -209,30 +272,68 @@ __global__ void __launch_bounds__(256) k_validate(ValParams p) {
             long long rxg = p.rx_off ? (long long)p.rx_off[t] + r : r;
             long long pair = p.rx_off ? rxg : (long long)t * p.n_rx + r;
             uint64_t key = p.cand_key[c];
-            int K = p.f.depth(key);
+            K = p.f.depth(key);
             f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
             f3 rx = mk(p.rx_pos[3 * rxg], p.rx_pos[3 * rxg + 1], p.rx_pos[3 * rxg + 2]);
             f3 P[RT_MAX_DEPTH + 2];
             int ids[RT_MAX_DEPTH];
             valid = back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * p.f.D * 3, tx, rx, P, ids) &&
                     sides_ok(p.s, K, P, ids);
-            for (int j = 0; valid && j <= K; j++) {
-                f3 seg = P[j + 1] - P[j];
-                float L = sqrtf(dot(seg, seg));
-                f3 d = seg * (1.0f / L);
-                int ex0 = j >= 1 ? ids[j - 1] : -1, ex1 = j < K ? ids[j] : -1;
-                if (any_hit(p.s, sm, p.n_sm, P[j], d, L - p.s.tmin, ex0, ex1, p.status, cnt)) valid = false;
+            if (valid) {
+                for (int k = 0; k <= K + 1; k++) {
+                    W.pts[lane][k][0] = P[k].x;
+                    W.pts[lane][k][1] = P[k].y;
+                    W.pts[lane][k][2] = P[k].z;
+                }
+                for (int k = 0; k < K; k++) W.ids[lane][k] = ids[k];
+                W.K[lane] = K;
             }
             rec = ((uint64_t)pair << 32) | (uint64_t)c;
         }
-        unsigned m = __ballot_sync(0xffffffffu, valid);
+        // queue the K+1 segments of every item that passed
+        int nq_l = valid ? K + 1 : 0, qo = nq_l;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(full, qo, o);
+            if (lane >= o) qo += y;
+        }
+        const int nq = __shfl_sync(full, qo, 31);
+        qo -= nq_l;
+        for (int j = 0; j < nq_l; j++) W.q[qo + j] = (unsigned char)((lane << 3) | j);
+        __syncwarp();
+        unsigned occluded = 0;   // items with an occluded segment (warp-uniform)
+        for (int qb = 0; qb < nq; qb += 32) {
+            const int qi = qb + lane;
+            bool act = qi < nq;
+            int il = 0, j = 0;
+            if (act) {
+                const unsigned code = W.q[qi];
+                il = (int)(code >> 3);
+                j = (int)(code & 7u);
+                act = !((occluded >> il) & 1u);
+            }
+            bool hit = false;
+            if (act) {
+                const int Ki = W.K[il];
+                f3 a = mk(W.pts[il][j][0], W.pts[il][j][1], W.pts[il][j][2]);
+                f3 b = mk(W.pts[il][j + 1][0], W.pts[il][j + 1][1], W.pts[il][j + 1][2]);
+                f3 seg = b - a;
+                float L = sqrtf(dot(seg, seg));
+                f3 d = seg * (1.0f / L);
+                int ex0 = j >= 1 ? W.ids[il][j - 1] : -1, ex1 = j < Ki ? W.ids[il][j] : -1;
+                hit = any_hit(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, p.status, cnt);
+            }
+            occluded |= __reduce_or_sync(full, hit ? (1u << il) : 0u);
+        }
+        valid = valid && !((occluded >> lane) & 1u);
+        __syncwarp();
+        unsigned m = __ballot_sync(full, valid);
         if (m) {
             int leader = __ffs(m) - 1;
             unsigned long long b0 = 0;
             if (lane == leader) b0 = atomicAdd(p.count, (unsigned long long)__popc(m));
-            b0 = __shfl_sync(0xffffffffu, b0, leader);
+            b0 = __shfl_sync(full, b0, leader);
             if (valid) {
-                unsigned long long idx = b0 + __popc(m & lanemask_lt());
+                unsigned long long idx = b0 + __popc(m & lt);
                 if ((long long)idx < p.cap) p.out[idx] = rec;
             }
         }
@@ -366,11 +467,10 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         }
         e = launch_sbr(ctx, N, f.D, keys, vals, hits);
         if (e) return e;
-        unsigned long long hk = 0;
-        RT_TRY(cudaMemcpyAsync(&hk, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS, sizeof(hk),
-                               cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaMemcpyAsync(ctx->host_rb, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS,
+                               sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         RT_TRY(cudaStreamSynchronize(st));
-        nhit = (int64_t)hk;
+        nhit = (int64_t)ctx->host_rb[0];
     }
     const int64_t nkeys = nhit + (los ? ctx->n_tx : 0);
     if (los) {
@@ -395,55 +495,48 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         RT_TRY(cudaGetLastError());
     }
     RT_TRY(exclusive_scan_u32(ctx, cntp, nb + 1));
-    uint32_t U32 = 0;
-    RT_TRY(cudaMemcpyAsync(&U32, cntp + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    RT_TRY(cudaStreamSynchronize(st));
-    const int64_t U = U32;
-    ctx->n_cand = U;
-    RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * std::max<int64_t>(U, 1)));
-    RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * std::max<int64_t>(U, 1)));
+    // From here the candidate count U = cntp[nb] stays on the device until
+    // the path count is read: buffers are sized for U <= nkeys.
+    const uint32_t* Ud = cntp + nb;
+    const int64_t Ucap = std::max<int64_t>(nkeys, 1);
+    RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * Ucap));
+    RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * Ucap));
     RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
-    RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * std::max<int64_t>(U, 1)));
-    if (U > 0) {
+    RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * Ucap));
+    if (nkeys > 0) {
         prof_begin(ctx, "k_dedup_write");
         k_dedup_write<<<nb, DD_THREADS, 0, st>>>(keys, vals, nkeys, sentinel_from, cntp,
                                                  bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit));
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
         prof_begin(ctx, "k_cand_img");
-        k_cand_img<<<(unsigned)((U + 255) / 256), 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, f,
-                                                               bp<float>(ctx->tx_pos), bp<float4>(ctx->planes),
-                                                               bp<float>(ctx->cand_img));
+        k_cand_img<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
+            bp<uint64_t>(ctx->cand_key), Ud, f, bp<float>(ctx->tx_pos), bp<float4>(ctx->planes),
+            bp<float>(ctx->cand_img));
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
     prof_begin(ctx, "k_cand_off");
-    k_cand_off<<<(ctx->n_tx + 256) / 256, 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), U, ctx->n_tx, f,
+    k_cand_off<<<(ctx->n_tx + 256) / 256, 256, 0, st>>>(bp<uint64_t>(ctx->cand_key), Ud, ctx->n_tx, f,
                                                          bp<int64_t>(ctx->cand_off));
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
-    std::vector<int64_t> coff(ctx->n_tx + 1);
-    RT_TRY(cudaMemcpyAsync(coff.data(), ctx->cand_off.p, sizeof(int64_t) * (ctx->n_tx + 1),
-                           cudaMemcpyDeviceToHost, st));
-    RT_TRY(cudaStreamSynchronize(st));
-    // validation work: sum over tx of U_t * R_t
-    std::vector<int64_t> woff(ctx->n_tx + 1, 0);
-    for (int t = 0; t < ctx->n_tx; t++) {
-        int64_t R = ctx->rx_sets ? (int64_t)(ctx->rx_off[t + 1] - ctx->rx_off[t]) : (int64_t)ctx->n_rx;
-        woff[t + 1] = woff[t] + (coff[t + 1] - coff[t]) * R;
-    }
-    const int64_t total = woff[ctx->n_tx];
+    // validation work (sum over tx of U_t * R_t), offsets on the device
     int64_t n_pairs = ctx->rx_sets ? (int64_t)ctx->rx_off[ctx->n_tx] : (int64_t)ctx->n_tx * ctx->n_rx;
     DevBuf& woffd = ctx->path_cap_dummy;
     RT_TRY(buf_reserve(woffd, sizeof(int64_t) * (ctx->n_tx + 1)));
-    RT_TRY(cudaMemcpyAsync(woffd.p, woff.data(), sizeof(int64_t) * (ctx->n_tx + 1), cudaMemcpyHostToDevice, st));
+    prof_begin(ctx, "k_work_off");
+    k_work_off<<<1, 1024, 0, st>>>(bp<int64_t>(ctx->cand_off), ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr,
+                                   ctx->n_tx, ctx->n_rx, bp<int64_t>(woffd));
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
     if (ctx->path_cap == 0) ctx->path_cap = 1 << 16;
     int64_t P = 0;
     for (int attempt = 0; attempt < 2; attempt++) {
         RT_TRY(buf_reserve(ctx->path_key, sizeof(uint64_t) * ctx->path_cap));
         RT_TRY(buf_reserve(ctx->path_key_alt, sizeof(uint64_t) * ctx->path_cap));
         RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long) * 2, st));
-        if (total > 0) {
+        if (nkeys > 0 && n_pairs > 0) {
             ValParams vp;
             vp.s = dev_scene(ctx);
             vp.f = f;
@@ -456,27 +549,36 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             vp.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
             vp.n_tx = ctx->n_tx;
             vp.n_rx = ctx->n_rx;
-            vp.total = total;
             vp.out = bp<uint64_t>(ctx->path_key);
             vp.count = bp<unsigned long long>(ctx->counters) + 1;
             vp.cap = ctx->path_cap;
             vp.n_sm = std::min(ctx->n_smem_nodes, ctx->n_nodes);
             vp.status = bp<unsigned>(ctx->status);
-            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm;
+            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm + sizeof(ValWarp) * 8;
             RT_TRY(ensure_smem_attr((const void*)k_validate, smem));
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_validate, 256, smem);
-            int64_t need = (total + 255) / 256;
-            int64_t grid = std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms);
+            // persistent grid: the work total is read on the device
+            const int64_t need = (nkeys * std::max<int64_t>(n_pairs / std::max(ctx->n_tx, 1), 1) + 255) / 256;
+            const int64_t grid = std::max<int64_t>(std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms), 1);
             prof_begin(ctx, "k_validate");
-            k_validate<<<(unsigned)std::max<int64_t>(grid, 1), 256, smem, st>>>(vp);
+            k_validate<<<(unsigned)grid, 256, smem, st>>>(vp);
             prof_end(ctx);
             RT_TRY(cudaGetLastError());
         }
-        unsigned long long hc = 0;
-        RT_TRY(cudaMemcpyAsync(&hc, bp<unsigned long long>(ctx->counters) + 1, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        // one read: path count, candidate count, status
+        RT_TRY(cudaMemcpyAsync(ctx->host_rb, bp<unsigned long long>(ctx->counters) + 1, sizeof(uint64_t),
+                               cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(ctx->host_rb + 1), Ud, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(ctx->host_rb + 2), ctx->status.p, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, st));
         RT_TRY(cudaStreamSynchronize(st));
-        P = (int64_t)hc;
+        P = (int64_t)ctx->host_rb[0];
+        ctx->n_cand = *reinterpret_cast<uint32_t*>(ctx->host_rb + 1);
+        const unsigned hs = *reinterpret_cast<uint32_t*>(ctx->host_rb + 2);
+        if (hs & RT_STAT_STACK) return set_err(ctx, RT_ERR_CAPACITY, "traversal stack overflow");
+        if (hs & RT_STAT_LOOP) return set_err(ctx, RT_ERR_CUDA, "malformed BVH (traversal budget exceeded)");
         if (P <= ctx->path_cap) break;
         ctx->path_cap = P + P / 4 + 1024;  // retry with room for every path
     }
@@ -520,11 +622,6 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
-    unsigned hs = 0;
-    RT_TRY(cudaMemcpyAsync(&hs, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    RT_TRY(cudaStreamSynchronize(st));
-    if (hs & RT_STAT_STACK) return set_err(ctx, RT_ERR_CAPACITY, "traversal stack overflow");
-    if (hs & RT_STAT_LOOP) return set_err(ctx, RT_ERR_CUDA, "malformed BVH (traversal budget exceeded)");
     *out = P;
     return RT_OK;
 }

@@ -95,6 +95,7 @@ def lib():
             "rt_mlp_set_stream": [vp, vp],
             "rt_mlp_last_error": [vp, ctypes.c_char_p, ctypes.c_size_t],
             "rt_mlp_train_step": [vp, vp, vp, i32, ctypes.c_float, vp],
+            "rt_mlp_set_baseline": [vp, ctypes.c_float],
             "rt_mlp_infer": [vp, vp, i64, vp],
             "rt_mlp_infer_layers": [vp, vp, i64, vp],
             "rt_mlp_num_params": [vp, ctypes.POINTER(i64)],
@@ -104,6 +105,7 @@ def lib():
             "rt_mlp_status": [vp, ctypes.POINTER(u32)],
             "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, vp, i32, i32, vp, vp],
             "rt_profile": [vp, ctypes.c_int],
+            "rt_profile_select": [vp, ctypes.c_char_p],
             "rt_profile_report": [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int],
         }
         for name, args in sig.items():
@@ -298,6 +300,12 @@ def rt_set_tuning(ctx, block, chunk, smem_nodes):
 
 def rt_profile(ctx, enable: bool):
     _check(ctx, lib().rt_profile(ctx, 1 if enable else 0))
+
+
+def rt_profile_select(ctx, names=None):
+    """Time only the named kernels (iterable of names; None = all)."""
+    arg = ",".join(names).encode() if names else None
+    _check(ctx, lib().rt_profile_select(ctx, arg))
 
 
 def rt_profile_report(ctx, reset: bool = False) -> dict:
@@ -611,6 +619,10 @@ class Surrogate:
 
     def _sync(self):
         lib().rt_mlp_set_stream(self.h, _stream())
+
+    def set_baseline(self, wavelength):
+        """Free-space (Friis) baseline: the gain head learns the residual."""
+        self._check(lib().rt_mlp_set_baseline(self.h, float(wavelength)))
 
     def train_step(self, x, target, lr, loss_acc=None):
         self._sync()

@@ -41,6 +41,26 @@ def tracer_labels(tracer: rt.Tracer, tx_pos, rx_pos, num_rays: int, max_depth: i
     return torch.cat(xs), torch.cat(ts)
 
 
+def set_fourier(sur: rt.Surrogate, sigma: float, sigma_rel: float, rel_frac: float = 0.5, seed: int = 0):
+    """Seeded Fourier matrix B [F x 6] on the normalised (tx, rx): the first
+    rel_frac of the rows see only the horizontal Tx -> Rx offset (rows
+    (-bx, -by, 0, bx, by, 0), b ~ N(0, sigma_rel^2)), the others all six
+    coordinates (N(0, sigma^2)). The network then gets the relative geometry,
+    which the path gain mostly depends on, without having to build it from
+    products of absolute-coordinate sinusoids."""
+    rng = np.random.default_rng(seed)
+    F = sur.F
+    n_rel = int(round(rel_frac * F))
+    B = rng.normal(0.0, sigma, (F, 6))
+    b = rng.normal(0.0, sigma_rel, (n_rel, 2))
+    B[:n_rel] = 0.0
+    B[:n_rel, 0:2] = -b
+    B[:n_rel, 3:5] = b
+    p = sur.params().clone()
+    p[-6 * F:] = torch.as_tensor(B.astype(np.float32).ravel(), device=p.device)
+    sur.set_params(p)
+
+
 def train(sur: rt.Surrogate, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, lr_end: float = 5e-5,
           seed: int = 0):
     """Adam with a cosine learning-rate schedule; returns per-epoch mean losses."""

@@ -48,8 +48,10 @@ def _batch(n, seed):
     return x, np.stack([has, gain], 1).astype(np.float32)
 
 
-def test_mlp_gradients_match_reference():
+@pytest.mark.parametrize("lam", [0.0, 299792458.0 / 3.5e9])
+def test_mlp_gradients_match_reference(lam):
     S, lo, hi = _surrogate()
+    S.set_baseline(lam)
     x, t = _batch(256, 0)
     p0 = S.params().cpu().numpy().astype(np.float64)
     loss = torch.zeros(1, device="cuda")
@@ -58,7 +60,7 @@ def test_mlp_gradients_match_reference():
     p1 = S.params().cpu().numpy()
     torch.cuda.synchronize()
     assert S.status() == 0
-    ref_loss, g_ref = R.loss_and_grads(p0.astype(np.float32), x, t, S.F, S.W, S.L, lo, hi, bf16=True)
+    ref_loss, g_ref = R.loss_and_grads(p0.astype(np.float32), x, t, S.F, S.W, S.L, lo, hi, bf16=True, lam=lam)
     assert abs(loss.item() - ref_loss) <= 2e-3 * abs(ref_loss)
     # per layer: relative L2 error of the gradient at BF16 tolerance
     o = 0
@@ -97,4 +99,24 @@ def test_mlp_inference_matches_reference_and_learns():
     y, _, _, _ = R.forward(p, x[:777], S.F, S.W, S.L, lo, hi, bf16=True)
     assert np.allclose(out[:, 0], y[:, 0], rtol=2e-2, atol=2e-2)
     assert np.allclose(out[:, 1], y[:, 1] * R.DB_SCALE + R.DB_OFFSET, rtol=2e-3, atol=0.2)
+    S.close()
+
+
+def test_baseline_outputs_match_reference():
+    """With the free-space baseline the fused kernel, the layer-by-layer path
+    and the CPU reference give the same gain output (residual + Friis)."""
+    S, lo, hi = _surrogate(seed=9)
+    lam = 299792458.0 / 3.5e9
+    S.set_baseline(lam)
+    x, _ = _batch(1000, 4)
+    xt = torch.as_tensor(x).cuda()
+    fused = S.infer(xt)
+    layered = S.infer_layers(xt)
+    torch.cuda.synchronize()
+    assert torch.allclose(fused, layered, rtol=1e-4, atol=1e-3)
+    p = S.params().cpu().numpy()
+    y, _, _, _ = R.forward(p, x, S.F, S.W, S.L, lo, hi, bf16=True)
+    assert np.allclose(fused.cpu().numpy()[:, 1], R.gain_db(y, x, lam), rtol=2e-3, atol=0.2)
+    with pytest.raises(rt.RtError):
+        S.set_baseline(-1.0)
     S.close()
