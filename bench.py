@@ -164,10 +164,11 @@ def run_ours(args):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    # untimed: per-kernel work counts of one step
+    # untimed: per-kernel work counts of one step (counting kernel variants)
     for _ in range(max(args.warmup, 3)):
         step(devin)
     torch.cuda.synchronize()
+    rt.rt_profile(ctx, rt.PROFILE_COUNT)
     rt.rt_profile_report(ctx, reset=True)
     rt.rt_load_scene(ctx, devin["verts"], devin["mat"], devin["mats"])
     rt.rt_set_tx(ctx, devin["txp"], devin["txy"], tx.antenna)
@@ -179,6 +180,7 @@ def run_ours(args):
     step(devin)
     one = rt.rt_profile_report(ctx, reset=True)
     bounces_per_step = one["closest_hit"]
+    rt.rt_profile(ctx, False)
 
     # per-kernel breakdown: every launch bracketed by CUDA events, outside the timed region
     stream = torch.cuda.current_stream()
@@ -342,23 +344,40 @@ def extra_measurements(tr, scene, dev, args):
     gain = torch.empty((64, GRID["ny"], GRID["nx"]), dtype=torch.float32, device=dev)
     hits = torch.empty((64, GRID["ny"], GRID["nx"]), dtype=torch.int32, device=dev)
     n = 10_000_000
-    rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
+    ctx = tr.ctx
+    # launch configuration picked by the autotuner (timed on 2e6 rays per Tx)
+    tuning_default = rt.rt_get_tuning(ctx)
+    rt.rt_autotune(ctx, grid, 5, 2_000_000, gain, hits)
+    tuning = rt.rt_get_tuning(ctx)
+    # closest-hit queries of one map (counting variant, untimed)
+    rt.rt_profile(ctx, rt.PROFILE_COUNT)
+    rt.rt_profile_report(ctx, reset=True)
+    rt.rt_coverage_map(ctx, grid, 5, n, 0, gain, hits)
+    cnt = rt.rt_profile_report(ctx, reset=True)
+    rt.rt_profile(ctx, False)
+    # the whole map (zeroing + one persistent launch over all 64 Tx) as a CUDA graph, replayed
+    stream = torch.cuda.current_stream()
+    rt.rt_set_stream(ctx)
+    rt.rt_graph_begin(ctx)
+    rt.rt_coverage_map(ctx, grid, 5, n, 0, gain, hits)
+    rt.rt_graph_end(ctx)
+    rt.rt_graph_launch(ctx)
     torch.cuda.synchronize()
-    rt.rt_profile_report(tr.ctx, reset=True)
-    rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
-    cnt = rt.rt_profile_report(tr.ctx, reset=True)
     ts = []
-    for _ in range(2):
+    for _ in range(10):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        rt.rt_coverage_map(tr.ctx, grid, 5, n, 0, gain, hits)
-        e1.record()
+        e0.record(stream)
+        rt.rt_graph_launch(ctx)
+        e1.record(stream)
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-    ms = min(ts)
+    ms = statistics.median(ts)
+    rt.rt_set_tuning(ctx, *tuning_default)
     return {"coverage_map_ms": ms,
-            "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch",
+            "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch "
+                                   "in a captured CUDA graph, median of 10 replays",
+            "coverage_map_tuning": {"block": tuning[0], "chunk": tuning[1], "smem_nodes": tuning[2]},
             "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
 
 

@@ -344,16 +344,21 @@ int rt_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int
 
 /*
  * Instrumentation (the paper describes none; used for measurement).
- * rt_profile(enable): start or stop CUDA-event timing of every kernel the
- * context launches (events recorded on the context's stream right around
- * each launch); clears earlier records. rt_profile_report: synchronises and
+ * rt_profile(flags): bit 0 (RT_PROFILE_TIME) = CUDA-event timing of every
+ * kernel the context launches (events recorded on the context's stream right
+ * around each launch); bit 1 (RT_PROFILE_COUNT) = the traversal kernels
+ * count BVH node / triangle records and queries (a separately compiled
+ * variant; without the bit they count nothing); 0 stops both; clears earlier
+ * records. rt_profile_report: synchronises and
  * writes JSON {"launches": kernel launches since the last reset,
  * "kernels": {name: [launches, total ms]}, "closest_hit": closest-hit
  * queries, "any_hit": visibility queries, "nodes": BVH node records
  * fetched, "tris": triangle records fetched}; reset != 0 zeroes the
  * counters afterwards. RT_ERR_CAPACITY if buf is too small (truncated).
  */
-int rt_profile(rt_ctx* ctx, int enable);
+#define RT_PROFILE_TIME 1
+#define RT_PROFILE_COUNT 2
+int rt_profile(rt_ctx* ctx, int flags);
 int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset);
 /* Restrict the event timing of rt_profile to the kernels named in `names`
  * (HOST, comma-separated, e.g. "k_coverage,k_sbr"); NULL or "" times every

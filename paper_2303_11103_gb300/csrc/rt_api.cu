@@ -518,7 +518,7 @@ int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_ra
         }
     }
     const int blocks[] = {128, 256};
-    const int chunks[] = {0, 32, 128};
+    const int chunks[] = {0, 64, 256};   // 0 = automatic (32 rays per refill)
     const int smems[] = {0, 256, 1024, 3072};
     cudaEvent_t e0, e1;
     RT_TRY(cudaEventCreate(&e0));
@@ -561,7 +561,8 @@ int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_ra
 int rt_profile(rt_ctx* ctx, int enable) {
     CHECK_CTX(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    ctx->prof = enable != 0;
+    ctx->prof = (enable & 1) != 0;
+    ctx->count_work = (enable & 2) != 0;
     ctx->prof_open = false;
     ctx->prof_name.clear();
     return RT_OK;

@@ -85,7 +85,8 @@ __device__ __forceinline__ float bounds_extent(const unsigned* __restrict__ b) {
 }
 
 // Build info words: [0..11] bounds (min words all ones, max words zero),
-// [12] large-triangle count, [13] tree depth, [14] clustering status.
+// [12] large-triangle count, [13] tree depth, [14] clustering status,
+// [15] tree check.
 constexpr int INFO_WORDS = 16;
 __global__ void k_info_init(unsigned* __restrict__ info) {
     int k = threadIdx.x;
@@ -381,6 +382,34 @@ __global__ void k_emit(int m, const uint64_t* __restrict__ order, const int* __r
     p[3] = make_float4(__int_as_float(na), __int_as_float(nb), 0.0f, 0.0f);
 }
 
+// Tree check of the emitted hierarchy (level order): every child index is
+// larger than its parent's and in range, and every node but the root and
+// every leaf has exactly one parent. Traversal relies on it: each node is
+// then visited at most once per query, with no iteration cap.
+__global__ void k_check_tree(int m, int n_leaves, const float4* __restrict__ nodes, int* __restrict__ indeg,
+                             unsigned* __restrict__ bad) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const float4 e = nodes[4 * (size_t)k + 3];
+    const int cs[2] = {__float_as_int(e.x), __float_as_int(e.y)};
+    for (int j = 0; j < 2; j++) {
+        const int c = cs[j];
+        if (c >= 0) {
+            if (c <= k || c >= m) atomicOr(bad, 1u);
+            else atomicAdd(&indeg[c], 1);
+        } else {
+            if (~c >= n_leaves) atomicOr(bad, 1u);
+            else atomicAdd(&indeg[m + ~c], 1);
+        }
+    }
+}
+
+__global__ void k_check_degree(int m, int n_leaves, const int* __restrict__ indeg, unsigned* __restrict__ bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m + n_leaves) return;
+    if (indeg[i] != (i == 0 ? 0 : 1)) atomicOr(bad, 1u);
+}
+
 __global__ void k_leaf_tris(int n, const uint32_t* __restrict__ leaf_tri, const float4* __restrict__ tris_o,
                             float4* __restrict__ tris) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -474,7 +503,7 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     ctx->n_bvh = n;
     m = std::max(n - 1, 1);
     const uint32_t* leaf_tri = vals;
-    int hd[2] = {0, 0};   // tree depth, clustering status
+    int hd[3] = {0, 0, 0};   // tree depth, clustering status, tree check
     if (n == 0) {
         ctx->n_nodes = 0;
         ctx->bvh_depth = 0;
@@ -559,6 +588,17 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         k_emit<<<gm, B, 0, st>>>(m, dkeys, rank, child, ibox, lbox, leaf_tri, pad, mask, bp<float4>(ctx->nodes));
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
+        // tree check (the cluster lists / refit flags are free again)
+        RT_TRY(buf_reserve(ctx->b_flag, sizeof(int) * (size_t)(m + T)));
+        int* indeg = bp<int>(ctx->b_flag);
+        RT_TRY(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)(m + T), st));
+        prof_begin(ctx, "k_check_tree");
+        k_check_tree<<<gm, B, 0, st>>>(m, T, bp<float4>(ctx->nodes), indeg, info + 15);
+        prof_end(ctx);
+        prof_begin(ctx, "k_check_degree");
+        k_check_degree<<<(m + T + B - 1) / B, B, 0, st>>>(m, T, indeg, info + 15);
+        prof_end(ctx);
+        RT_TRY(cudaGetLastError());
         ctx->n_nodes = m;
     }
     // leaf records in sorted order: the hierarchy's leaves, then the large triangles
@@ -572,6 +612,11 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         memcpy(hd, ctx->host_rb, sizeof(hd));
         if (hd[1] != 0)   // the clustering found no pair to merge: non-finite geometry
             return set_err(ctx, RT_ERR_INVALID_ARG, "BVH build: non-finite triangle boxes");
+        if (hd[2] != 0) {
+            ctx->n_nodes = 0;
+            ctx->n_tris = 0;
+            return set_err(ctx, RT_ERR_CUDA, "BVH build: hierarchy failed the tree check");
+        }
         ctx->bvh_depth = hd[0] + 1;
     }
     if (ctx->bvh_depth + 1 >= RT_STACK)

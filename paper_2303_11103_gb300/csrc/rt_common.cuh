@@ -67,15 +67,28 @@ __device__ __forceinline__ void fetch_node(const DevScene& s, const float4* sm, 
     }
 }
 
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Slab test of one AABB; returns the entry distance, or NaN when missed (so
 // that every `tn <= bound` test fails, also against an infinite bound).
+// Three-input min/max: near = max(tlo, per-axis near planes), far =
+// min(thi, per-axis far planes).
 __device__ __forceinline__ float slab(float lox, float loy, float loz, float hix, float hiy, float hiz,
                                       f3 oi, f3 inv, float tlo, float thi) {
     float t0x = fmaf(lox, inv.x, -oi.x), t1x = fmaf(hix, inv.x, -oi.x);
     float t0y = fmaf(loy, inv.y, -oi.y), t1y = fmaf(hiy, inv.y, -oi.y);
     float t0z = fmaf(loz, inv.z, -oi.z), t1z = fmaf(hiz, inv.z, -oi.z);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), tlo));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), thi));
+    float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), tlo));
+    float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), thi));
     return tn <= tf ? tn : __int_as_float(0x7fc00000);
 }
 
@@ -136,10 +149,16 @@ __device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* c
 // Closest hit along o + t d (d unit), t > tmin, triangle `exclude` (original
 // id) skipped; equal t resolves to the lowest original id. Returns the
 // original triangle id or -1; t_out receives the distance.
+//
+// The hierarchy is checked at build time to be a tree whose children have
+// larger indices than their parent (level order), with depth below
+// RT_STACK, so the loop visits each node at most once and the stack cannot
+// overflow. C: count node / triangle records and queries in cnt.
+template <bool C>
 __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                           int exclude, float& t_out, unsigned* status, TravCount& cnt) {
+                                           int exclude, float& t_out, TravCount& cnt) {
     t_out = __int_as_float(0x7f800000);
-    cnt.queries++;
+    if (C) cnt.queries++;
     if (s.n_tris == 0) return -1;
     f3 inv = safe_inv(d);
     f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
@@ -153,24 +172,17 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
     for (int k = 0; k < s.n_big; k++) {
         const float4* tp = s.big + 3 * k;
         float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-        cnt.tris++;
+        if (C) cnt.tris++;
         int id = __float_as_int(r0.w);
         if (id != exclude) {
             float t = tri_hit(r0, r1, r2, o, d);
             if (t > tmin && (t < tb || (t == tb && id < best))) { tb = t; best = id; }
         }
     }
-    // a tree visits each node at most once per query; the cap only guards
-    // against a malformed hierarchy
-    int budget = 2 * s.n_nodes + 16;
     while (s.n_nodes > 0) {
-        if (--budget < 0) {
-            if (status) atomicOr(status, RT_STAT_LOOP);
-            break;
-        }
         float4 a, b, c, e;
         fetch_node(s, sm, n_sm, node, a, b, c, e);
-        cnt.nodes++;
+        if (C) cnt.nodes++;
         float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tb);
         float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tb);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
@@ -179,7 +191,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
             int k = ~c0;
             const float4* tp = s.tris + 3 * (size_t)k;
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-            cnt.tris++;
+            if (C) cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != exclude) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -191,7 +203,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
             int k = ~c1;
             const float4* tp = s.tris + 3 * (size_t)k;
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-            cnt.tris++;
+            if (C) cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != exclude) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -202,11 +214,7 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
         if (h0 && h1) {
             int nearc = tn0 <= tn1 ? c0 : c1;
             int farc = tn0 <= tn1 ? c1 : c0;
-            if (sp < RT_STACK) {
-                stack[sp++] = farc;
-            } else if (status) {
-                atomicOr(status, RT_STAT_STACK);
-            }
+            stack[sp++] = farc;
             node = nearc;
         } else if (h0) {
             node = c0;
@@ -223,9 +231,10 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
 
 // Any occluder on the open segment (tmin, tmax) along o + t d (d unit),
 // skipping original ids ex0 / ex1.
+template <bool C>
 __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                        float tmax, int ex0, int ex1, unsigned* status, TravCount& cnt) {
-    cnt.queries++;
+                                        float tmax, int ex0, int ex1, TravCount& cnt) {
+    if (C) cnt.queries++;
     if (s.n_tris == 0) return false;
     f3 inv = safe_inv(d);
     f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
@@ -236,22 +245,17 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
     for (int k = 0; k < s.n_big; k++) {
         const float4* tp = s.big + 3 * k;
         float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-        cnt.tris++;
+        if (C) cnt.tris++;
         int id = __float_as_int(r0.w);
         if (id != ex0 && id != ex1) {
             float t = tri_hit(r0, r1, r2, o, d);
             if (t > tmin && t < tmax) return true;
         }
     }
-    int budget = 2 * s.n_nodes + 16;
     while (s.n_nodes > 0) {
-        if (--budget < 0) {
-            if (status) atomicOr(status, RT_STAT_LOOP);
-            return false;
-        }
         float4 a, b, c, e;
         fetch_node(s, sm, n_sm, node, a, b, c, e);
-        cnt.nodes++;
+        if (C) cnt.nodes++;
         float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tmax);
         float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tmax);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
@@ -259,7 +263,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         if (h0 && c0 < 0) {
             const float4* tp = s.tris + 3 * (size_t)(~c0);
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-            cnt.tris++;
+            if (C) cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != ex0 && id != ex1) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -270,7 +274,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         if (h1 && c1 < 0) {
             const float4* tp = s.tris + 3 * (size_t)(~c1);
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
-            cnt.tris++;
+            if (C) cnt.tris++;
             int id = __float_as_int(r0.w);
             if (id != ex0 && id != ex1) {
                 float t = tri_hit(r0, r1, r2, o, d);
@@ -279,11 +283,7 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
             h1 = false;
         }
         if (h0 && h1) {
-            if (sp < RT_STACK) {
-                stack[sp++] = c1;
-            } else if (status) {
-                atomicOr(status, RT_STAT_STACK);
-            }
+            stack[sp++] = c1;
             node = c0;
         } else if (h0) {
             node = c0;

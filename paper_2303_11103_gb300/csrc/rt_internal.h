@@ -79,12 +79,13 @@ struct rt_ctx {
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
     int bvh_builder = RT_BVH_PLOC;  // hierarchy over the Morton order: RT_BVH_KARRAS or RT_BVH_PLOC
     int trace_block = 256;
-    int warp_chunk = 0;       // rays a warp takes per refill (0 = about 16 chunks per warp)
+    int warp_chunk = 0;       // rays a warp takes per refill (0 = automatic: 32)
 
     // instrumentation: host count of kernel launches; optional CUDA-event
     // timing of every launch on the context's stream
     int64_t launches = 0;
     bool prof = false, prof_open = false;
+    bool count_work = false;  // traversal kernels count node / triangle records and queries
     std::vector<const char*> prof_name;
     std::vector<cudaEvent_t> prof_ev;  // 2 per record
     std::vector<std::string> prof_only;  // kernels timed (empty = all)

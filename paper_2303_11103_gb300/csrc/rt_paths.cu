@@ -228,24 +228,29 @@ __device__ __forceinline__ bool sides_ok(const DevScene& s, int K, const f3* P, 
     return true;
 }
 
-// Per-warp scratch of k_validate: the 32 work items' path points and ids,
-// and the queue of their segments still to be tested for occluders.
-struct ValWarp {
-    float pts[32][RT_MAX_DEPTH + 2][3];
-    int ids[32][RT_MAX_DEPTH];
-    int K[32];
-    unsigned char q[32 * (RT_MAX_DEPTH + 1)];   // lane << 3 | segment
-};
+// Per-warp scratch of k_validate, sized by the candidates' depth D: the 32
+// work items' path points [32][D+2][3], ids [32][D], depths [32], and the
+// queue of their segments still to be tested for occluders [32 (D+1)]
+// (lane << 3 | segment).
+__host__ __device__ __forceinline__ size_t val_warp_bytes(int D) {
+    return ((size_t)32 * (D + 2) * 3 * 4 + (size_t)32 * D * 4 + 32 * 4 + (size_t)32 * (D + 1) + 15) & ~(size_t)15;
+}
 
 // One (candidate, receiver) work item per lane. Back-projection and side
 // tests run per lane; the segments of the items that pass go to a per-warp
 // queue, and all 32 lanes then test queued segments for occluders (any hit)
 // in rounds, skipping segments of items already found occluded, so that
 // the traversals of a round run side by side.
+template <bool C>
 __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
     extern __shared__ float4 sm[];
     for (int i = threadIdx.x; i < p.n_sm * 4; i += blockDim.x) sm[i] = p.s.nodes[i];
-    ValWarp& W = reinterpret_cast<ValWarp*>(sm + 4 * p.n_sm)[threadIdx.x >> 5];
+    const int D = p.f.D;
+    uint8_t* wbase = reinterpret_cast<uint8_t*>(sm + 4 * p.n_sm) + (threadIdx.x >> 5) * val_warp_bytes(D);
+    float* Wpts = reinterpret_cast<float*>(wbase);                    // [32][D+2][3]
+    int* Wids = reinterpret_cast<int*>(Wpts + 32 * (D + 2) * 3);      // [32][D]
+    int* WK = Wids + 32 * D;                                          // [32]
+    unsigned char* Wq = reinterpret_cast<unsigned char*>(WK + 32);    // [32 (D+1)]
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
@@ -280,13 +285,14 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
             valid = back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * p.f.D * 3, tx, rx, P, ids) &&
                     sides_ok(p.s, K, P, ids);
             if (valid) {
+                float* pl = Wpts + lane * (D + 2) * 3;
                 for (int k = 0; k <= K + 1; k++) {
-                    W.pts[lane][k][0] = P[k].x;
-                    W.pts[lane][k][1] = P[k].y;
-                    W.pts[lane][k][2] = P[k].z;
+                    pl[3 * k] = P[k].x;
+                    pl[3 * k + 1] = P[k].y;
+                    pl[3 * k + 2] = P[k].z;
                 }
-                for (int k = 0; k < K; k++) W.ids[lane][k] = ids[k];
-                W.K[lane] = K;
+                for (int k = 0; k < K; k++) Wids[lane * D + k] = ids[k];
+                WK[lane] = K;
             }
             rec = ((uint64_t)pair << 32) | (uint64_t)c;
         }
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
         }
         const int nq = __shfl_sync(full, qo, 31);
         qo -= nq_l;
-        for (int j = 0; j < nq_l; j++) W.q[qo + j] = (unsigned char)((lane << 3) | j);
+        for (int j = 0; j < nq_l; j++) Wq[qo + j] = (unsigned char)((lane << 3) | j);
         __syncwarp();
         unsigned occluded = 0;   // items with an occluded segment (warp-uniform)
         for (int qb = 0; qb < nq; qb += 32) {
@@ -306,21 +312,22 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
             bool act = qi < nq;
             int il = 0, j = 0;
             if (act) {
-                const unsigned code = W.q[qi];
+                const unsigned code = Wq[qi];
                 il = (int)(code >> 3);
                 j = (int)(code & 7u);
                 act = !((occluded >> il) & 1u);
             }
             bool hit = false;
             if (act) {
-                const int Ki = W.K[il];
-                f3 a = mk(W.pts[il][j][0], W.pts[il][j][1], W.pts[il][j][2]);
-                f3 b = mk(W.pts[il][j + 1][0], W.pts[il][j + 1][1], W.pts[il][j + 1][2]);
+                const int Ki = WK[il];
+                const float* pl = Wpts + (il * (D + 2) + j) * 3;
+                f3 a = mk(pl[0], pl[1], pl[2]);
+                f3 b = mk(pl[3], pl[4], pl[5]);
                 f3 seg = b - a;
                 float L = sqrtf(dot(seg, seg));
                 f3 d = seg * (1.0f / L);
-                int ex0 = j >= 1 ? W.ids[il][j - 1] : -1, ex1 = j < Ki ? W.ids[il][j] : -1;
-                hit = any_hit(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, p.status, cnt);
+                int ex0 = j >= 1 ? Wids[il * D + j - 1] : -1, ex1 = j < Ki ? Wids[il * D + j] : -1;
+                hit = any_hit<C>(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, cnt);
             }
             occluded |= __reduce_or_sync(full, hit ? (1u << il) : 0u);
         }
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
             }
         }
     }
-    flush_counts(cnt, p.count - RT_CNT_PATHS, RT_CNT_ANY);
+    if (C) flush_counts(cnt, p.count - RT_CNT_PATHS, RT_CNT_ANY);
 }
 
 // offsets[p] = first path with pair >= p (paths sorted by pair, candidate)
@@ -554,15 +561,16 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             vp.cap = ctx->path_cap;
             vp.n_sm = std::min(ctx->n_smem_nodes, ctx->n_nodes);
             vp.status = bp<unsigned>(ctx->status);
-            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm + sizeof(ValWarp) * 8;
-            RT_TRY(ensure_smem_attr((const void*)k_validate, smem));
+            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm + val_warp_bytes(f.D) * 8;
+            auto kern = ctx->count_work ? k_validate<true> : k_validate<false>;
+            RT_TRY(ensure_smem_attr((const void*)kern, smem));
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_validate, 256, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
             // persistent grid: the work total is read on the device
             const int64_t need = (nkeys * std::max<int64_t>(n_pairs / std::max(ctx->n_tx, 1), 1) + 255) / 256;
             const int64_t grid = std::max<int64_t>(std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms), 1);
             prof_begin(ctx, "k_validate");
-            k_validate<<<(unsigned)grid, 256, smem, st>>>(vp);
+            kern<<<(unsigned)grid, 256, smem, st>>>(vp);
             prof_end(ctx);
             RT_TRY(cudaGetLastError());
         }

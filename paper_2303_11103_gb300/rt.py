@@ -298,8 +298,13 @@ def rt_set_tuning(ctx, block, chunk, smem_nodes):
     _check(ctx, lib().rt_set_tuning(ctx, int(block), int(chunk), int(smem_nodes)))
 
 
-def rt_profile(ctx, enable: bool):
-    _check(ctx, lib().rt_profile(ctx, 1 if enable else 0))
+PROFILE_TIME, PROFILE_COUNT = 1, 2
+
+
+def rt_profile(ctx, enable):
+    """enable: bool (kernel timing) or flags PROFILE_TIME | PROFILE_COUNT."""
+    flags = int(enable) if not isinstance(enable, bool) else (PROFILE_TIME if enable else 0)
+    _check(ctx, lib().rt_profile(ctx, flags))
 
 
 def rt_profile_select(ctx, names=None):
