@@ -175,6 +175,7 @@ def run_ours(args):
     rt.rt_set_rx(ctx, devin["rxp"], devin["rxy"], rx.antenna)
     rt.rt_compute_paths(ctx, MAX_DEPTH, N_RAYS, rt.RT_LOS | rt.RT_REFLECTION)
     sbr_counts = rt.rt_profile_report(ctx, reset=True)
+    path_stats = {k: sbr_counts[k] for k in ("sbr_keys", "candidates", "paths")}
     rt.rt_coverage_map(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits)
     cov_counts = rt.rt_profile_report(ctx, reset=True)
     step(devin)
@@ -277,6 +278,7 @@ def run_ours(args):
                    "coverage_cells": GRID["nx"] * GRID["ny"], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "paths_per_step": state["P"],
+        "compute_paths_counts": path_stats,
         "ray_bounces_per_step": bounces_per_step,
         "gpu_launches": prof["launches"],
         "kernel_ms_per_step": {k: v[1] / n_prof for k, v in sorted(breakdown.items(), key=lambda x: -x[1][1])},
@@ -381,8 +383,8 @@ def extra_measurements(tr, scene, dev, args):
             "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
 
 
-def surrogate_measurement(tr, scene, n_tx=2500, n_rx=4000, num_rays=200_000, max_depth=3, epochs=6,
-                          n_query=100_000_000, n_heldout=100_000):
+def surrogate_measurement(tr, scene, n_tx=2500, n_rx=4000, num_rays=200_000, max_depth=3, epochs=40,
+                          n_query=100_000_000, n_heldout=100_000, batch=16384, lr=1.5e-3, oversample=4):
     """Learned surrogate on the city: tracer labels, training, held-out error, q/s vs the tracer."""
     import torch
     from paper_2303_11103_gb300 import rt
@@ -402,7 +404,7 @@ def surrogate_measurement(tr, scene, n_tx=2500, n_rx=4000, num_rays=200_000, max
     hi = np.array([250, 250, 70, 250, 250, 3], np.float32)
     sur = rt.Surrogate(lo, hi, n_freq=32, width=256, n_hidden=8, sigma=8.0, seed=1)
     t1 = time.perf_counter()
-    losses = SG.train(sur, x[train_idx], t[train_idx], epochs=epochs, batch=8192, lr=1e-3)
+    losses = SG.train(sur, x[train_idx], t[train_idx], epochs=epochs, batch=batch, lr=lr, oversample=oversample)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t1
     ev = SG.evaluate(sur, x[held], t[held])
@@ -410,7 +412,8 @@ def surrogate_measurement(tr, scene, n_tx=2500, n_rx=4000, num_rays=200_000, max
     q_tr, s_tr = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth)
     sur.close()
     return {"surrogate": {
-        "train_pairs": int(len(train_idx)), "epochs": epochs, "final_loss": losses[-1],
+        "train_pairs": int(len(train_idx)), "epochs": epochs, "batch": batch, "lr": lr,
+        "path_pair_oversample": oversample, "final_loss": losses[-1],
         "label_s": t_label, "train_s": t_train, "heldout": ev,
         "queries": n_query, "infer_ms": ms_sur, "queries_per_s": q_sur,
         "tracer_queries_per_s": q_tr, "speedup_vs_tracer": q_sur / q_tr,
@@ -527,7 +530,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--sur-tx", type=int, default=2500, help="surrogate label transmitters")
     ap.add_argument("--sur-rx", type=int, default=4000, help="surrogate receivers per transmitter")
-    ap.add_argument("--sur-epochs", type=int, default=6)
+    ap.add_argument("--sur-epochs", type=int, default=40)
     args = ap.parse_args()
     if args.only:
         run_kernel_case(args)

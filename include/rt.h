@@ -353,7 +353,9 @@ int rt_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int
  * writes JSON {"launches": kernel launches since the last reset,
  * "kernels": {name: [launches, total ms]}, "closest_hit": closest-hit
  * queries, "any_hit": visibility queries, "nodes": BVH node records
- * fetched, "tris": triangle records fetched}; reset != 0 zeroes the
+ * fetched, "tris": triangle records fetched, "sbr_keys": candidate keys the
+ * last shooting pass appended, "candidates": distinct candidates, "paths":
+ * valid paths of the last rt_compute_paths}; reset != 0 zeroes the
  * counters afterwards. RT_ERR_CAPACITY if buf is too small (truncated).
  */
 #define RT_PROFILE_TIME 1

@@ -472,6 +472,7 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     unsigned* info = bp<unsigned>(ctx->b_info);
     uint64_t* keys = bp<uint64_t>(ctx->b_keys);
     uint32_t* vals = bp<uint32_t>(ctx->b_vals);
+    RT_TRY(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), st));
     prof_begin(ctx, "k_info_init");
     k_info_init<<<1, 32, 0, st>>>(info);
     prof_end(ctx);
@@ -488,8 +489,11 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     // bounds and large-triangle count in one read
     unsigned hi[13];
     RT_TRY(cudaMemcpyAsync(ctx->host_rb, info, sizeof(hi), cudaMemcpyDeviceToHost, st));
+    RT_TRY(cudaMemcpyAsync(ctx->host_rb + 7, ctx->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     RT_TRY(cudaStreamSynchronize(st));
     memcpy(hi, ctx->host_rb, sizeof(hi));
+    if (*reinterpret_cast<unsigned*>(ctx->host_rb + 7) & RT_STAT_SORT)
+        return set_err(ctx, RT_ERR_TIMEOUT, "BVH build: radix sort look-back timed out");
     float ext = 0.0f;
     for (int k = 0; k < 3; k++) ext = std::max(ext, host_unord(hi[3 + k]) - host_unord(hi[k]));
     if (!(ext > 0.0f)) ext = 1.0f;

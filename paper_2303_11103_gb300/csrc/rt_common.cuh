@@ -24,6 +24,7 @@
 #define RT_STAT_STACK 1u
 #define RT_STAT_CAPACITY 2u
 #define RT_STAT_LOOP 4u
+#define RT_STAT_SORT 8u   // a radix-sort tile look-back timed out
 
 struct f3 {
     float x, y, z;

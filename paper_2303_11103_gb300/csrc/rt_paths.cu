@@ -587,6 +587,7 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         const unsigned hs = *reinterpret_cast<uint32_t*>(ctx->host_rb + 2);
         if (hs & RT_STAT_STACK) return set_err(ctx, RT_ERR_CAPACITY, "traversal stack overflow");
         if (hs & RT_STAT_LOOP) return set_err(ctx, RT_ERR_CUDA, "malformed BVH (traversal budget exceeded)");
+        if (hs & RT_STAT_SORT) return set_err(ctx, RT_ERR_TIMEOUT, "radix sort: tile look-back timed out");
         if (P <= ctx->path_cap) break;
         ctx->path_cap = P + P / 4 + 1024;  // retry with room for every path
     }

@@ -1,8 +1,16 @@
 // rt_sort.cu -- LSD radix sort of 64-bit keys (optional 32-bit payload),
-// 8-bit digits, three kernels per pass: per-tile digit histograms, one
-// exclusive scan over (digit, tile), stable scatter ranked with warp
-// match/ballot. Used for Morton codes, BVH level order, candidate keys
-// (duplicate removal) and path keys.
+// 8-bit digits. Used for Morton codes, BVH level order, candidate keys
+// (duplicate removal) and path keys. Three forms:
+//   - up to SS_MAX keys: one block, all passes in shared memory;
+//   - up to 2^30 keys: one histogram kernel for every digit position, then
+//     one kernel per pass whose tiles find their global offsets by
+//     decoupled look-back over the preceding tiles (Merrill & Garland's
+//     single-pass prefix scan, as used by Adinets & Merrill's Onesweep);
+//   - larger: per pass a histogram kernel, a multi-block scan over
+//     (digit, tile) and a scatter kernel.
+// Every form ranks keys stably with warp match/ballot.
+#include <algorithm>
+
 #include "rt_internal.h"
 
 namespace {
@@ -152,6 +160,135 @@ cudaError_t scan_level(rt_ctx* ctx, uint32_t* a, int64_t m, uint32_t* scratch) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------- one sweep
+// Digit histograms of every pass in one read of the keys: hist [passes x 256].
+__global__ void __launch_bounds__(RS_THREADS) os_hist(const uint64_t* __restrict__ keys, int64_t n, int passes,
+                                                      uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[8][256];
+    for (int i = threadIdx.x; i < 8 * 256; i += RS_THREADS) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+    for (int64_t i0 = (int64_t)blockIdx.x * RS_TILE; i0 < n; i0 += (int64_t)gridDim.x * RS_TILE) {
+        for (int j = 0; j < RS_IPT; j++) {
+            int64_t i = i0 + j * RS_THREADS + threadIdx.x;
+            bool ok = i < n;
+            unsigned act = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const uint64_t k = keys[i];
+                for (int p = 0; p < passes; p++) {
+                    unsigned dg = (unsigned)(k >> (8 * p)) & 255u;
+                    unsigned peers = __match_any_sync(act, dg);
+                    if ((peers & lt) == 0) atomicAdd(&h[p][dg], (uint32_t)__popc(peers));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += RS_THREADS) {
+        uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(hist + i, v);
+    }
+}
+
+// Tile status word: bits 31..30 = 0 not yet published, 1 tile count only,
+// 2 inclusive prefix through this tile; bits 29..0 = the count.
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_VAL = (1u << 30) - 1u;
+constexpr int OS_SPIN_MAX = 1 << 22;   // polls per predecessor before giving up
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_THREADS) os_scatter(const uint64_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin,
+                                                         uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         int64_t n, int shift, const uint32_t* __restrict__ hist,
+                                                         uint32_t* status, unsigned* tile_ctr, unsigned* err) {
+    __shared__ uint32_t cnt[RS_WARPS][256];
+    __shared__ uint32_t s_off[256];
+    __shared__ unsigned s_tile;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, d = threadIdx.x;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&cnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);   // tiles in start order: no deadlock
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const int64_t base = (int64_t)tile * RS_TILE + (int64_t)w * 32 * RS_IPT;
+    uint64_t k[RS_IPT];
+    uint32_t v[RS_IPT];
+    uint32_t rank[RS_IPT];
+    const unsigned lt = lanemask_lt();
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        bool ok = i < n;
+        unsigned act = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            k[j] = kin[i];
+            if (VALS) v[j] = vin[i];
+            unsigned dg = (unsigned)(k[j] >> shift) & 255u;
+            unsigned peers = __match_any_sync(act, dg);
+            uint32_t before = cnt[w][dg];
+            rank[j] = before + __popc(peers & lt);
+            __syncwarp(act);
+            if ((peers & lt) == 0) cnt[w][dg] = before + __popc(peers);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: exclusive prefix across this tile's warps, tile total
+    uint32_t run = 0;
+    for (int ww = 0; ww < RS_WARPS; ww++) {
+        uint32_t t = cnt[ww][d];
+        cnt[ww][d] = run;
+        run += t;
+    }
+    // exclusive digit base of this pass (scan of the 256 totals)
+    uint32_t tot = hist[d], x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    s_off[d] = x;   // inclusive within the warp
+    __syncthreads();
+    uint32_t wsum = 0;
+    for (int ww = 0; ww < w; ww++) wsum += s_off[ww * 32 + 31];
+    const uint32_t digit_base = wsum + x - tot;
+    // publish this tile's count, look back over the preceding tiles, publish the prefix
+    volatile uint32_t* st = status;
+    uint32_t excl = 0;
+    if (tile == 0) {
+        st[d] = OS_INC | run;
+    } else {
+        st[(size_t)tile * 256 + d] = OS_AGG | run;
+        int64_t p = (int64_t)tile - 1;
+        int spins = 0;
+        while (p >= 0) {
+            uint32_t s = st[(size_t)p * 256 + d];
+            if ((s & ~OS_VAL) == 0) {
+                if (++spins > OS_SPIN_MAX) {   // a predecessor never published: give up, flag it
+                    atomicOr(err, RT_STAT_SORT);
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            spins = 0;
+            excl += s & OS_VAL;
+            if (s & OS_INC) break;
+            p--;
+        }
+        st[(size_t)tile * 256 + d] = OS_INC | ((excl + run) & OS_VAL);
+    }
+    __syncthreads();   // s_off reads above are done
+    s_off[d] = digit_base + excl;
+    __syncthreads();
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        if (i < n) {
+            unsigned dg = (unsigned)(k[j] >> shift) & 255u;
+            uint32_t pos = s_off[dg] + cnt[w][dg] + rank[j];
+            kout[pos] = k[j];
+            if (VALS) vout[pos] = v[j];
+        }
+    }
+}
+
 // Small inputs (<= SS_MAX keys): one block sorts in shared memory, all
 // passes in one launch. Each warp owns a contiguous chunk of the keys. Per
 // pass: the warps count their chunk's digits (warp match, one shared update
@@ -267,6 +404,46 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    const int passes_all = (end_bit + 7) / 8;
+    if (n < (int64_t)OS_VAL && passes_all <= 8) {
+        // scratch: [passes x 256] histograms, [passes] tile counters, error word,
+        // [passes x nb x 256] tile status words; zeroed with one memset
+        const size_t words = (size_t)passes_all * 256 + 16 + (size_t)passes_all * nb * 256;
+        cudaError_t e = buf_reserve(ctx->sort_hist, sizeof(uint32_t) * words);
+        if (e != cudaSuccess) return e;
+        uint32_t* hist = bp<uint32_t>(ctx->sort_hist);
+        unsigned* ctr = hist + passes_all * 256;
+        unsigned* err = bp<unsigned>(ctx->status);   // RT_STAT_SORT if a look-back gave up
+        uint32_t* status = ctr + 16;
+        e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * words, ctx->stream);
+        if (e != cudaSuccess) return e;
+        prof_begin(ctx, "os_hist");
+        os_hist<<<std::min(nb, 4 * ctx->num_sms), RS_THREADS, 0, ctx->stream>>>(keys, n, passes_all, hist);
+        prof_end(ctx);
+        uint64_t *kin = keys, *kout = keys_alt;
+        uint32_t *vin = vals, *vout = vals_alt;
+        for (int p = 0; p < passes_all; p++) {
+            prof_begin(ctx, "os_scatter");
+            uint32_t* stp = status + (size_t)p * nb * 256;
+            if (vals)
+                os_scatter<true><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, vin, kout, vout, n, 8 * p, hist + 256 * p,
+                                                                      stp, ctr + p, err);
+            else
+                os_scatter<false><<<nb, RS_THREADS, 0, ctx->stream>>>(kin, nullptr, kout, nullptr, n, 8 * p,
+                                                                       hist + 256 * p, stp, ctr + p, err);
+            prof_end(ctx);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            std::swap(kin, kout);
+            std::swap(vin, vout);
+        }
+        if (kin != keys) {
+            e = cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+            if (e != cudaSuccess) return e;
+            if (vals) e = cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+        }
+        return e;
+    }
     cudaError_t e = buf_reserve(ctx->sort_hist, sizeof(uint32_t) * 256 * (size_t)nb);
     if (e != cudaSuccess) return e;
     uint32_t* hist = bp<uint32_t>(ctx->sort_hist);

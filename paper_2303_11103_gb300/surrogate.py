@@ -61,9 +61,33 @@ def set_fourier(sur: rt.Surrogate, sigma: float, sigma_rel: float, rel_frac: flo
     sur.set_params(p)
 
 
+def head_logit_bias_index(sur: rt.Surrogate) -> int:
+    """Index of the path-logit bias in the parameter vector."""
+    F, W, L = sur.F, sur.W, sur.L
+    return sum((2 * F if l == 0 else W) * W + W for l in range(L)) + 2 * W
+
+
 def train(sur: rt.Surrogate, x, t, epochs: int, batch: int = 8192, lr: float = 1e-3, lr_end: float = 5e-5,
-          seed: int = 0):
-    """Adam with a cosine learning-rate schedule; returns per-epoch mean losses."""
+          seed: int = 0, oversample: int = 1):
+    """Adam with a cosine learning-rate schedule; returns per-epoch mean losses.
+
+    oversample > 1 repeats the pairs that have a path that many times (the
+    gain term of the loss then sees that many more samples per epoch) and
+    afterwards subtracts log(oversample) from the path-logit bias, which
+    undoes the shift of the class prior that the repetition causes."""
+    if oversample > 1:
+        hp = t[:, 0] > 0.5
+        x = torch.cat([x] + [x[hp]] * (oversample - 1))
+        t = torch.cat([t] + [t[hp]] * (oversample - 1))
+    losses = _train(sur, x, t, epochs, batch, lr, lr_end, seed)
+    if oversample > 1:
+        p = sur.params().clone()
+        p[head_logit_bias_index(sur)] -= float(np.log(oversample))
+        sur.set_params(p)
+    return losses
+
+
+def _train(sur, x, t, epochs, batch, lr, lr_end, seed):
     n = (x.shape[0] // batch) * batch
     g = torch.Generator(device=x.device).manual_seed(seed)
     steps = epochs * (n // batch)
@@ -96,11 +120,14 @@ def evaluate(sur: rt.Surrogate, x, t, margin: float = 2.0):
     both = ans_gain & has
     err = (pred[both] - t[both, 1])
     rms = float(torch.sqrt((err ** 2).mean()).item()) if both.any() else float("nan")
+    q = (torch.quantile(err.abs(), torch.tensor([0.5, 0.9, 0.99], device=err.device)).tolist()
+         if both.any() else [float("nan")] * 3)
     rms_all = float(torch.sqrt(((pred[has] - t[has, 1]) ** 2).mean()).item()) if has.any() else float("nan")
     return {
         "pairs": int(x.shape[0]),
         "pairs_with_path": int(has.sum().item()),
         "rms_db_answered": rms,
+        "abs_err_db_p50_p90_p99": q,
         "rms_db_all_path_pairs": rms_all,
         "fallback_fraction": float((~sure).float().mean().item()),
         "false_path": int((ans_gain & ~has).sum().item()),
