@@ -410,6 +410,27 @@ __global__ void k_check_degree(int m, int n_leaves, const int* __restrict__ inde
     if (indeg[i] != (i == 0 ? 0 : 1)) atomicOr(bad, 1u);
 }
 
+// Nodes in the clustering's own numbering (node m-1-c for the c-th merge:
+// parents after children, root 0, the last merges, i.e. the top of the
+// tree, first): child indices are kept as they are.
+__global__ void k_emit_direct(int m, const int2* __restrict__ child, const float* __restrict__ ibox,
+                              const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri, float pad,
+                              float4* __restrict__ nodes) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    int2 c = child[k];
+    float a[6], b[6];
+    if (c.x < 0) { for (int q = 0; q < 6; q++) a[q] = lbox[6 * (size_t)leaf_tri[~c.x] + q]; for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; } }
+    else { for (int q = 0; q < 6; q++) a[q] = ibox[6 * (size_t)c.x + q]; }
+    if (c.y < 0) { for (int q = 0; q < 6; q++) b[q] = lbox[6 * (size_t)leaf_tri[~c.y] + q]; for (int q = 0; q < 3; q++) { b[q] -= pad; b[3 + q] += pad; } }
+    else { for (int q = 0; q < 6; q++) b[q] = ibox[6 * (size_t)c.y + q]; }
+    float4* p = nodes + 4 * (size_t)k;
+    p[0] = make_float4(a[0], a[1], a[2], a[3]);
+    p[1] = make_float4(a[4], a[5], b[0], b[1]);
+    p[2] = make_float4(b[2], b[3], b[4], b[5]);
+    p[3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.0f, 0.0f);
+}
+
 __global__ void k_leaf_tris(int n, const uint32_t* __restrict__ leaf_tri, const float4* __restrict__ tris_o,
                             float4* __restrict__ tris) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -571,7 +592,7 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
             prof_end(ctx);
             RT_TRY(cudaGetLastError());
         }
-        // level order: sort internal nodes by (depth, id)
+        // depths (the deepest bounds the traversal stack)
         RT_TRY(buf_reserve(ctx->b_dkeys, sizeof(uint64_t) * m));
         RT_TRY(buf_reserve(ctx->b_dkeys2, sizeof(uint64_t) * m));
         RT_TRY(buf_reserve(ctx->b_rank, sizeof(int) * m));
@@ -584,13 +605,22 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         k_depth<<<gm, B, 0, st>>>(m, shift, pint, dkeys, reinterpret_cast<int*>(info + 13));
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
-        RT_TRY(radix_sort64(ctx, dkeys, bp<uint64_t>(ctx->b_dkeys2), nullptr, nullptr, m, shift + 8));
-        prof_begin(ctx, "k_rank");
-        k_rank<<<gm, B, 0, st>>>(m, mask, dkeys, rank);
-        prof_end(ctx);
-        prof_begin(ctx, "k_emit");
-        k_emit<<<gm, B, 0, st>>>(m, dkeys, rank, child, ibox, lbox, leaf_tri, pad, mask, bp<float4>(ctx->nodes));
-        prof_end(ctx);
+        if (ctx->bvh_builder == RT_BVH_PLOC) {
+            // the clustering's numbering already puts parents before children
+            // and the top of the tree first
+            prof_begin(ctx, "k_emit");
+            k_emit_direct<<<gm, B, 0, st>>>(m, child, ibox, lbox, leaf_tri, pad, bp<float4>(ctx->nodes));
+            prof_end(ctx);
+        } else {
+            // level order: sort internal nodes by (depth, id)
+            RT_TRY(radix_sort64(ctx, dkeys, bp<uint64_t>(ctx->b_dkeys2), nullptr, nullptr, m, shift + 8));
+            prof_begin(ctx, "k_rank");
+            k_rank<<<gm, B, 0, st>>>(m, mask, dkeys, rank);
+            prof_end(ctx);
+            prof_begin(ctx, "k_emit");
+            k_emit<<<gm, B, 0, st>>>(m, dkeys, rank, child, ibox, lbox, leaf_tri, pad, mask, bp<float4>(ctx->nodes));
+            prof_end(ctx);
+        }
         RT_TRY(cudaGetLastError());
         // tree check (the cluster lists / refit flags are free again)
         RT_TRY(buf_reserve(ctx->b_flag, sizeof(int) * (size_t)(m + T)));

@@ -137,7 +137,8 @@ __global__ void k_cand_img(const uint64_t* __restrict__ ck, const uint32_t* __re
         cand_img_one(ck, c, f, tx_pos, planes, img);
 }
 
-// Validation work offsets: work_off[t] = sum over t' < t of U_t' R_t' (one
+// Validation work offsets in warp units: work_off[t] = sum over t' < t of
+// U_t' ceil(R_t' / 32), a unit being one candidate against 32 receivers (one
 // block; n_tx entries scanned in thread-contiguous runs).
 __global__ void __launch_bounds__(1024) k_work_off(const int64_t* __restrict__ cand_off,
                                                    const int32_t* __restrict__ rx_off, int n_tx, int n_rx,
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_work_off(const int64_t* __restrict__ c
     const int s0 = min((int)threadIdx.x * seg, n_tx), s1 = min(s0 + seg, n_tx);
     long long sum = 0;
     for (int t = s0; t < s1; t++) {
-        long long R = rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx;
+        long long R = ((rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx) + 31) >> 5;
         sum += (cand_off[t + 1] - cand_off[t]) * R;
     }
     long long x = sum;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(1024) k_work_off(const int64_t* __restrict__ c
     long long run = x - sum + (w > 0 ? ws[w - 1] : 0);
     for (int t = s0; t < s1; t++) {
         work_off[t] = run;
-        long long R = rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx;
+        long long R = ((rx_off ? (long long)(rx_off[t + 1] - rx_off[t]) : (long long)n_rx) + 31) >> 5;
         run += (cand_off[t + 1] - cand_off[t]) * R;
     }
     if (threadIdx.x == blockDim.x - 1) work_off[n_tx] = run;
@@ -254,25 +255,26 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long total = p.work_off[p.n_tx];
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long total = p.work_off[p.n_tx];   // warp units: (candidate, 32 receivers)
     TravCount cnt;
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += stride) {
-        long long g = base + lane;
+    for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += wstride) {
+        // the unit's transmitter, candidate and first receiver (warp-uniform)
+        int lo = 0, hi = p.n_tx;  // largest t with work_off[t] <= u
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (p.work_off[mid] <= u) lo = mid; else hi = mid;
+        }
+        const int t = lo;
+        const long long R = p.rx_off ? (long long)(p.rx_off[t + 1] - p.rx_off[t]) : (long long)p.n_rx;
+        const long long chunks = (R + 31) >> 5;
+        const long long local = u - p.work_off[t];
+        const long long cl = local / chunks;
+        const long long r = ((local - cl * chunks) << 5) + lane;
         bool valid = false;
         uint64_t rec = 0;
         int K = 0;
-        if (g < total) {
-            int lo = 0, hi = p.n_tx;  // largest t with work_off[t] <= g
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (p.work_off[mid] <= g) lo = mid; else hi = mid;
-            }
-            int t = lo;
-            long long R = p.rx_off ? (long long)(p.rx_off[t + 1] - p.rx_off[t]) : (long long)p.n_rx;
-            long long local = g - p.work_off[t];
-            long long cl = local / R, r = local - cl * R;
+        if (r < R) {
             long long c = p.cand_off[t] + cl;
             long long rxg = p.rx_off ? (long long)p.rx_off[t] + r : r;
             long long pair = p.rx_off ? rxg : (long long)t * p.n_rx + r;
@@ -567,7 +569,8 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
             // persistent grid: the work total is read on the device
-            const int64_t need = (nkeys * std::max<int64_t>(n_pairs / std::max(ctx->n_tx, 1), 1) + 255) / 256;
+            const int64_t units = nkeys * std::max<int64_t>((n_pairs / std::max(ctx->n_tx, 1) + 31) / 32, 1);
+            const int64_t need = (units + 7) / 8;   // 8 warps per block
             const int64_t grid = std::max<int64_t>(std::min<int64_t>(need, (int64_t)std::max(per_sm, 1) * ctx->num_sms), 1);
             prof_begin(ctx, "k_validate");
             kern<<<(unsigned)grid, 256, smem, st>>>(vp);

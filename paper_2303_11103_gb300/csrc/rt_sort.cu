@@ -59,13 +59,18 @@ __global__ void __launch_bounds__(RS_THREADS) rs_scatter(const uint64_t* __restr
     uint32_t v[RS_IPT];
     uint32_t rank[RS_IPT];
     const unsigned lt = lanemask_lt();
+    // all loads first (independent), then the ranking
+#pragma unroll
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        k[j] = i < n ? kin[i] : 0ull;
+        if (VALS) v[j] = i < n ? vin[i] : 0u;
+    }
     for (int j = 0; j < RS_IPT; j++) {
         int64_t i = base + j * 32 + lane;
         bool ok = i < n;
         unsigned act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
-            k[j] = kin[i];
-            if (VALS) v[j] = vin[i];
             unsigned dg = (unsigned)(k[j] >> shift) & 255u;
             unsigned peers = __match_any_sync(act, dg);
             uint32_t before = cnt[w][dg];
@@ -214,13 +219,18 @@ __global__ void __launch_bounds__(RS_THREADS) os_scatter(const uint64_t* __restr
     uint32_t v[RS_IPT];
     uint32_t rank[RS_IPT];
     const unsigned lt = lanemask_lt();
+    // all loads first (independent), then the ranking
+#pragma unroll
+    for (int j = 0; j < RS_IPT; j++) {
+        int64_t i = base + j * 32 + lane;
+        k[j] = i < n ? kin[i] : 0ull;
+        if (VALS) v[j] = i < n ? vin[i] : 0u;
+    }
     for (int j = 0; j < RS_IPT; j++) {
         int64_t i = base + j * 32 + lane;
         bool ok = i < n;
         unsigned act = __ballot_sync(0xffffffffu, ok);
         if (ok) {
-            k[j] = kin[i];
-            if (VALS) v[j] = vin[i];
             unsigned dg = (unsigned)(k[j] >> shift) & 255u;
             unsigned peers = __match_any_sync(act, dg);
             uint32_t before = cnt[w][dg];

@@ -390,6 +390,7 @@ class Tracer:
         ypr = self._t(ypr, torch.float32).reshape(-1, 3)
         rt_set_tx(self.ctx, pos, ypr, antenna)
         self.n_tx, self.ntp, self.tx_antenna = int(pos.shape[0]), len(antenna.slants), antenna
+        self._tx_pos, self._tx_ypr = pos, ypr
 
     def set_rx(self, pos, ypr, antenna, rx_set_offsets=None):
         self.sync_stream()
@@ -427,6 +428,11 @@ class Tracer:
         for k in ("seq", "points", "depth", "length"):
             out[k] = out[k][:P]
         return out
+
+    def path_pairs(self):
+        """int64 [P]: the (tx, rx) pair index of every stored path."""
+        off = self.paths()["offsets"]
+        return torch.repeat_interleave(torch.arange(off.numel() - 1, device=self.device), off[1:] - off[:-1])
 
     def candidates(self):
         n = rt_get_candidates(self.ctx)
