@@ -229,35 +229,148 @@ __device__ __forceinline__ bool sides_ok(const DevScene& s, int K, const f3* P, 
     return true;
 }
 
-// Per-warp scratch of k_validate, sized by the candidates' depth D: the 32
-// work items' path points [32][D+2][3], ids [32][D], depths [32], and the
-// queue of their segments still to be tested for occluders [32 (D+1)]
-// (lane << 3 | segment).
+// Per-warp scratch of k_validate, sized by the candidates' depth D: the
+// queue of work items that passed the last-reflection test [VQ] (candidate,
+// receiver, transmitter), the 32 batch items' path points [32][D+2][3], ids
+// [32][D], depths [32], and the queue of their segments still to be tested
+// for occluders [32 (D+1)] (lane << 3 | segment).
+constexpr int VQ = 64;
 __host__ __device__ __forceinline__ size_t val_warp_bytes(int D) {
-    return ((size_t)32 * (D + 2) * 3 * 4 + (size_t)32 * D * 4 + 32 * 4 + (size_t)32 * (D + 1) + 15) & ~(size_t)15;
+    return ((size_t)VQ * 16 + (size_t)32 * (D + 2) * 3 * 4 + (size_t)32 * D * 4 + 32 * 4 + (size_t)32 * (D + 1) +
+            15) & ~(size_t)15;
 }
 
-// One (candidate, receiver) work item per lane. Back-projection and side
-// tests run per lane; the segments of the items that pass go to a per-warp
-// queue, and all 32 lanes then test queued segments for occluders (any hit)
-// in rounds, skipping segments of items already found occluded, so that
-// the traversals of a round run side by side.
+struct ValWarpPtrs {
+    uint32_t* qc;      // [VQ] candidate
+    uint32_t* qr;      // [VQ] receiver (global index)
+    uint32_t* qt;      // [VQ] transmitter
+    float* pts;        // [32][D+2][3]
+    int* ids;          // [32][D]
+    int* K;            // [32]
+    unsigned char* sq; // [32 (D+1)]
+};
+
+__device__ __forceinline__ ValWarpPtrs val_warp(float4* sm, int n_sm, int D) {
+    uint8_t* b = reinterpret_cast<uint8_t*>(sm + 4 * n_sm) + (threadIdx.x >> 5) * val_warp_bytes(D);
+    ValWarpPtrs w;
+    w.qc = reinterpret_cast<uint32_t*>(b);
+    w.qr = w.qc + VQ;
+    w.qt = w.qr + VQ;
+    w.pts = reinterpret_cast<float*>(w.qt + 2 * VQ);
+    w.ids = reinterpret_cast<int*>(w.pts + 32 * (D + 2) * 3);
+    w.K = w.ids + 32 * D;
+    w.sq = reinterpret_cast<unsigned char*>(w.K + 32);
+    return w;
+}
+
+// Full validation of up to 32 queued items (lane < n takes item (head +
+// lane) % VQ): back-projection through every image, side tests, then the
+// occluder tests of all passing items' segments, queued so that the lanes
+// run them side by side, skipping segments of items already occluded;
+// valid paths are appended. Called by all 32 lanes.
+template <bool C>
+__device__ void validate_batch(const ValParams& p, const float4* sm, const ValWarpPtrs& W, int head, int n,
+                               TravCount& cnt) {
+    const int lane = threadIdx.x & 31, D = p.f.D;
+    const unsigned full = 0xffffffffu, lt = lanemask_lt();
+    bool valid = false;
+    uint64_t rec = 0;
+    int K = 0;
+    if (lane < n) {
+        const int e = (head + lane) % VQ;
+        const long long c = W.qc[e], rxg = W.qr[e];
+        const int t = (int)W.qt[e];
+        const long long pair = p.rx_off ? rxg : (long long)t * p.n_rx + rxg;
+        const uint64_t key = p.cand_key[c];
+        K = p.f.depth(key);
+        f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
+        f3 rx = mk(p.rx_pos[3 * rxg], p.rx_pos[3 * rxg + 1], p.rx_pos[3 * rxg + 2]);
+        f3 P[RT_MAX_DEPTH + 2];
+        int ids[RT_MAX_DEPTH];
+        valid = back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * D * 3, tx, rx, P, ids) &&
+                sides_ok(p.s, K, P, ids);
+        if (valid) {
+            float* pl = W.pts + lane * (D + 2) * 3;
+            for (int k = 0; k <= K + 1; k++) {
+                pl[3 * k] = P[k].x;
+                pl[3 * k + 1] = P[k].y;
+                pl[3 * k + 2] = P[k].z;
+            }
+            for (int k = 0; k < K; k++) W.ids[lane * D + k] = ids[k];
+            W.K[lane] = K;
+        }
+        rec = ((uint64_t)pair << 32) | (uint64_t)c;
+    }
+    // queue the K+1 segments of every item that passed
+    int nq_l = valid ? K + 1 : 0, qo = nq_l;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(full, qo, o);
+        if (lane >= o) qo += y;
+    }
+    const int nq = __shfl_sync(full, qo, 31);
+    qo -= nq_l;
+    for (int j = 0; j < nq_l; j++) W.sq[qo + j] = (unsigned char)((lane << 3) | j);
+    __syncwarp();
+    unsigned occluded = 0;   // items with an occluded segment (warp-uniform)
+    for (int qb = 0; qb < nq; qb += 32) {
+        const int qi = qb + lane;
+        bool act = qi < nq;
+        int il = 0, j = 0;
+        if (act) {
+            const unsigned code = W.sq[qi];
+            il = (int)(code >> 3);
+            j = (int)(code & 7u);
+            act = !((occluded >> il) & 1u);
+        }
+        bool hit = false;
+        if (act) {
+            const int Ki = W.K[il];
+            const float* pl = W.pts + (il * (D + 2) + j) * 3;
+            f3 a = mk(pl[0], pl[1], pl[2]);
+            f3 b = mk(pl[3], pl[4], pl[5]);
+            f3 seg = b - a;
+            float L = sqrtf(dot(seg, seg));
+            f3 d = seg * (1.0f / L);
+            int ex0 = j >= 1 ? W.ids[il * D + j - 1] : -1, ex1 = j < Ki ? W.ids[il * D + j] : -1;
+            hit = any_hit<C>(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, cnt);
+        }
+        occluded |= __reduce_or_sync(full, hit ? (1u << il) : 0u);
+    }
+    valid = valid && !((occluded >> lane) & 1u);
+    __syncwarp();
+    unsigned m = __ballot_sync(full, valid);
+    if (m) {
+        int leader = __ffs(m) - 1;
+        unsigned long long b0 = 0;
+        if (lane == leader) b0 = atomicAdd(p.count, (unsigned long long)__popc(m));
+        b0 = __shfl_sync(full, b0, leader);
+        if (valid) {
+            unsigned long long idx = b0 + __popc(m & lt);
+            if ((long long)idx < p.cap) p.out[idx] = rec;
+        }
+    }
+}
+
+// Image method for every (candidate, receiver) pair (Sec. II-B). A warp
+// takes one candidate against 32 receivers (warp units) and first applies
+// only the last reflection's test: the segment from the receiver towards the
+// candidate's last image must cross the last triangle (closed test, line
+// parameter in (0, 1)). Most pairs fail it; the ones that pass go to a
+// per-warp queue, and whenever 32 are queued they are validated in full
+// (validate_batch) with all lanes busy.
 template <bool C>
 __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
     extern __shared__ float4 sm[];
     for (int i = threadIdx.x; i < p.n_sm * 4; i += blockDim.x) sm[i] = p.s.nodes[i];
     const int D = p.f.D;
-    uint8_t* wbase = reinterpret_cast<uint8_t*>(sm + 4 * p.n_sm) + (threadIdx.x >> 5) * val_warp_bytes(D);
-    float* Wpts = reinterpret_cast<float*>(wbase);                    // [32][D+2][3]
-    int* Wids = reinterpret_cast<int*>(Wpts + 32 * (D + 2) * 3);      // [32][D]
-    int* WK = Wids + 32 * D;                                          // [32]
-    unsigned char* Wq = reinterpret_cast<unsigned char*>(WK + 32);    // [32 (D+1)]
+    const ValWarpPtrs W = val_warp(sm, p.n_sm, D);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
     const long long total = p.work_off[p.n_tx];   // warp units: (candidate, 32 receivers)
     TravCount cnt;
+    int head = 0, count = 0;   // survivor queue (warp-uniform)
     for (long long u = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += wstride) {
         // the unit's transmitter, candidate and first receiver (warp-uniform)
         int lo = 0, hi = p.n_tx;  // largest t with work_off[t] <= u
@@ -271,82 +384,41 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
         const long long local = u - p.work_off[t];
         const long long cl = local / chunks;
         const long long r = ((local - cl * chunks) << 5) + lane;
-        bool valid = false;
-        uint64_t rec = 0;
-        int K = 0;
+        const long long c = p.cand_off[t] + cl;
+        const uint64_t key = p.cand_key[c];
+        const int K = p.f.depth(key);
+        bool pass = false;
+        long long rxg = 0;
         if (r < R) {
-            long long c = p.cand_off[t] + cl;
-            long long rxg = p.rx_off ? (long long)p.rx_off[t] + r : r;
-            long long pair = p.rx_off ? rxg : (long long)t * p.n_rx + r;
-            uint64_t key = p.cand_key[c];
-            K = p.f.depth(key);
-            f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
+            rxg = p.rx_off ? (long long)p.rx_off[t] + r : r;
             f3 rx = mk(p.rx_pos[3 * rxg], p.rx_pos[3 * rxg + 1], p.rx_pos[3 * rxg + 2]);
-            f3 P[RT_MAX_DEPTH + 2];
-            int ids[RT_MAX_DEPTH];
-            valid = back_project(p.s, p.f, key, K, p.cand_img + (size_t)c * p.f.D * 3, tx, rx, P, ids) &&
-                    sides_ok(p.s, K, P, ids);
-            if (valid) {
-                float* pl = Wpts + lane * (D + 2) * 3;
-                for (int k = 0; k <= K + 1; k++) {
-                    pl[3 * k] = P[k].x;
-                    pl[3 * k + 1] = P[k].y;
-                    pl[3 * k + 2] = P[k].z;
-                }
-                for (int k = 0; k < K; k++) Wids[lane * D + k] = ids[k];
-                WK[lane] = K;
+            if (K == 0) {
+                pass = true;
+            } else {
+                const float* img = p.cand_img + ((size_t)c * D + (K - 1)) * 3;
+                f3 dir = mk(img[0], img[1], img[2]) - rx;
+                const float4* tp = p.s.tris_o + 3 * (size_t)p.f.id(key, K - 1);
+                float th = tri_hit(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2), rx, dir);
+                pass = th > 0.0f && th < 1.0f;
             }
-            rec = ((uint64_t)pair << 32) | (uint64_t)c;
         }
-        // queue the K+1 segments of every item that passed
-        int nq_l = valid ? K + 1 : 0, qo = nq_l;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(full, qo, o);
-            if (lane >= o) qo += y;
+        const unsigned m = __ballot_sync(full, pass);
+        if (pass) {
+            const int e = (head + count + __popc(m & lt)) % VQ;
+            W.qc[e] = (uint32_t)c;
+            W.qr[e] = (uint32_t)rxg;
+            W.qt[e] = (uint32_t)t;
         }
-        const int nq = __shfl_sync(full, qo, 31);
-        qo -= nq_l;
-        for (int j = 0; j < nq_l; j++) Wq[qo + j] = (unsigned char)((lane << 3) | j);
+        count += __popc(m);
         __syncwarp();
-        unsigned occluded = 0;   // items with an occluded segment (warp-uniform)
-        for (int qb = 0; qb < nq; qb += 32) {
-            const int qi = qb + lane;
-            bool act = qi < nq;
-            int il = 0, j = 0;
-            if (act) {
-                const unsigned code = Wq[qi];
-                il = (int)(code >> 3);
-                j = (int)(code & 7u);
-                act = !((occluded >> il) & 1u);
-            }
-            bool hit = false;
-            if (act) {
-                const int Ki = WK[il];
-                const float* pl = Wpts + (il * (D + 2) + j) * 3;
-                f3 a = mk(pl[0], pl[1], pl[2]);
-                f3 b = mk(pl[3], pl[4], pl[5]);
-                f3 seg = b - a;
-                float L = sqrtf(dot(seg, seg));
-                f3 d = seg * (1.0f / L);
-                int ex0 = j >= 1 ? Wids[il * D + j - 1] : -1, ex1 = j < Ki ? Wids[il * D + j] : -1;
-                hit = any_hit<C>(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, cnt);
-            }
-            occluded |= __reduce_or_sync(full, hit ? (1u << il) : 0u);
-        }
-        valid = valid && !((occluded >> lane) & 1u);
-        __syncwarp();
-        unsigned m = __ballot_sync(full, valid);
-        if (m) {
-            int leader = __ffs(m) - 1;
-            unsigned long long b0 = 0;
-            if (lane == leader) b0 = atomicAdd(p.count, (unsigned long long)__popc(m));
-            b0 = __shfl_sync(full, b0, leader);
-            if (valid) {
-                unsigned long long idx = b0 + __popc(m & lt);
-                if ((long long)idx < p.cap) p.out[idx] = rec;
-            }
+        if (count >= 32) {
+            validate_batch<C>(p, sm, W, head, 32, cnt);
+            head = (head + 32) % VQ;
+            count -= 32;
+            __syncwarp();
         }
     }
+    if (count > 0) validate_batch<C>(p, sm, W, head, count, cnt);
     if (C) flush_counts(cnt, p.count - RT_CNT_PATHS, RT_CNT_ANY);
 }
 
