@@ -1,19 +1,26 @@
-// rt_bvh.cu -- GPU LBVH builder (Morton codes, radix sort, Karras radix
-// tree, bottom-up AABB refit) and conversion to the breadth-first
-// 64-byte-node traversal layout.
+// rt_bvh.cu -- GPU BVH builders over Morton-ordered triangles (Karras radix
+// tree with bottom-up AABB refit, or PLOC clustering) and the 64-byte-node
+// traversal layout.
 //
 // The paper delegates ray/triangle intersection to Mitsuba 3 (Sec. II); the
 // acceleration structure here is a linear BVH built in parallel on the GPU:
 //   1. per triangle: records, plane, padded AABB, centroid;
-//   2. scene bounds; 30-bit Morton code of each centroid;
+//   2. scene bounds; 30-bit Morton code of each centroid (large triangles
+//      are set aside and tested directly by every query);
 //   3. stable radix sort of the codes (ties keep triangle order, which is
 //      Karras' index-augmented key);
-//   4. one thread per internal node finds its key range and split from the
-//      longest common prefix of neighbouring keys (Karras 2012);
-//   5. leaves walk to the root; the second child to arrive at a node
-//      computes its box (atomic arrival counters);
-//   6. nodes are re-numbered by depth (level order) so the top levels form
-//      a prefix that traversal blocks stage in shared memory.
+//   4. either one thread per internal node finds its key range and split
+//      from the longest common prefix of neighbouring keys (Karras 2012),
+//      and leaves walk to the root, the second child to arrive at a node
+//      computing its box (atomic arrival counters); or
+//   5. (default) mutual nearest neighbours of the Morton order merge by
+//      smallest merged surface area, round by round (PLOC, below);
+//   6. the radix tree's nodes are re-numbered by depth (level order); the
+//      clustering builder's own numbering already has parents before
+//      children and the top of the tree first. Either way the top levels
+//      form a prefix that traversal blocks stage in shared memory;
+//   7. a device check that the result is a tree with children after their
+//      parents (the traversal loop relies on it instead of an iteration cap).
 #include <algorithm>
 #include <cstring>
 

@@ -23,6 +23,13 @@ namespace {
 
 constexpr int GM = 128, GK = 64, GSTAGES = 4;
 
+// sin and cos of 2 pi a for a in [-0.5, 0.5] (the reduced Fourier phase):
+// the hardware approximation, absolute error about 4e-7 on [-pi, pi], far
+// below the BF16 rounding the features then get.
+__device__ __forceinline__ void feature_sincos(float a, float* s, float* c) {
+    __sincosf(6.283185307179586f * a, s, c);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&v);
@@ -146,7 +153,7 @@ __global__ void k_features(const float* __restrict__ x, int64_t n, const float* 
         for (int k = 0; k < 6; k++) a = fmaf(Bf[6 * j + k], xn[k], a);
         a -= rintf(a);  // integer periods drop out of sin/cos(2 pi a)
         float s, c;
-        sincospif(2.0f * a, &s, &c);
+        feature_sincos(a, &s, &c);
         out[(size_t)i * 2 * F + j] = __float2bfloat16_rn(s);
         out[(size_t)i * 2 * F + F + j] = __float2bfloat16_rn(c);
     }
@@ -330,12 +337,28 @@ __global__ void k_to_bf16(const float* __restrict__ w, int64_t n, int in_dim, __
 }
 
 // ------------------------------------------------------ fused inference
-// All layers for a tile of 128 queries per iteration of a persistent CTA:
-// activations stay in shared memory (written by the epilogue in the same
-// 128-byte-swizzled K-major layout TMA produces), each layer's weights are
-// streamed by TMA into one buffer while the previous layer's epilogue runs,
-// the accumulator lives in TMEM, the 2-wide head runs in registers.
+// All layers for a pair of 128-query tiles (A, B; one query per row) in a
+// persistent CTA, with warp roles and mbarrier handshakes:
+//   warp 8 (one lane)  streams each layer's weights by TMA in K-chunks
+//                      (W output rows x 64 inputs) through a ring of NS
+//                      slots; every chunk serves both tiles, so weight
+//                      traffic per query is half of a one-tile design;
+//   warp 9 (one lane)  issues tcgen05.mma (M = 128, N = W, K = 16) per chunk,
+//                      first for tile A then for tile B, into TMEM columns
+//                      [0, W) and [W, 2W); commits each slot back to the
+//                      producer and each tile's last chunk to its epilogue;
+//   warps 0-3 / 4-7    tile A / tile B: the Fourier features, then per layer
+//                      the epilogue: read the accumulator (one TMEM lane
+//                      quarter per warp), add the bias, apply ReLU, round to
+//                      BF16 and write the next layer's input in place
+//                      (128-byte-swizzled K-major, the layout TMA produces);
+//                      after the last layer the 2-wide head.
+// Tile A's epilogue overlaps tile B's last chunk, tile B's epilogue overlaps
+// tile A's next layer. Every wait is bounded; after a timeout all roles
+// skip their remaining work.
 constexpr int FM_MAX_L = 16;
+constexpr int FM_NS = 2;          // weight ring slots (W x 64 BF16 each)
+constexpr int FM_THREADS = 320;   // 8 epilogue warps + producer + MMA issuer
 struct alignas(64) FusedMaps {
     CUtensorMap w[FM_MAX_L];  // BF16 weights [W x K_l], box 64 x W
 };
@@ -361,115 +384,196 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int c) {
     return (uint32_t)r * 128u + ((((uint32_t)c >> 3) ^ ((uint32_t)r & 7u)) << 4) + (((uint32_t)c & 7u) << 1);
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps, FusedArgs a) {
+// Shared-memory layout (offsets from a 1024-aligned base).
+struct FusedLayout {
+    uint32_t act_bytes, act0, act1, ring, bias, head, bf, bars;
+    __host__ __device__ FusedLayout(int F, int W, int L) {
+        const int kmax = (2 * F > W ? 2 * F : W) / 64;
+        act_bytes = (uint32_t)kmax * 16384u;
+        act0 = 0;
+        act1 = act_bytes;
+        ring = 2 * act_bytes;
+        bias = ring + FM_NS * (uint32_t)W * 128u;
+        head = bias + 4u * (uint32_t)(L * W);
+        bf = head + 4u * (uint32_t)(2 * W + 2);
+        bars = (bf + 4u * (uint32_t)(6 * F + 12) + 7u) & ~7u;
+    }
+    // ring full/empty, per tile: MMA done, input ready; MMA drain
+    __host__ __device__ uint32_t bytes() const { return bars + 8u * (2 * FM_NS + 5); }
+};
+
+__global__ void __launch_bounds__(FM_THREADS, 1) k_mlp_fused(const __grid_constant__ FusedMaps maps, FusedArgs a) {
     extern __shared__ uint8_t dyn[];
-    __shared__ __align__(8) uint64_t wbar, mbar;
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
     const int W = a.W, L = a.L, F = a.F;
-    const int kmax = (2 * F > W ? 2 * F : W) / 64;           // K-chunks of the widest layer input
-    uint8_t* act = base;                                     // kmax chunks x 16 KB (<= 64 KB)
-    uint8_t* wbuf = base + 64 * 1024;                        // kmax chunks x (W rows x 128 B)
-    float* s_bias = (float*)(base + 64 * 1024 + (size_t)kmax * W * 128);  // [L x W]
-    float* s_head = s_bias + L * W;                          // [2 x W + 2]
-    float* s_bf = s_head + 2 * W + 2;                        // [F x 6] + lo[6] + hi[6]
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t wchunk = (uint32_t)W * 128u;
-    for (int i = tid; i < L * W; i += 128) s_bias[i] = a.bias[i / W][i % W];
-    for (int i = tid; i < 2 * W; i += 128) s_head[i] = a.head_w[i];
+    const FusedLayout lay(F, W, L);
+    uint8_t* act[2] = {base + lay.act0, base + lay.act1};   // tile A, tile B
+    uint8_t* ring = base + lay.ring;
+    float* s_bias = (float*)(base + lay.bias);
+    float* s_head = (float*)(base + lay.head);
+    float* s_bf = (float*)(base + lay.bf);
+    uint64_t* bars = (uint64_t*)(base + lay.bars);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + FM_NS);
+    const uint32_t mma_done0 = su32(bars + 2 * FM_NS), in_ready0 = su32(bars + 2 * FM_NS + 2);
+    const uint32_t drain = su32(bars + 2 * FM_NS + 4);
+    const uint32_t slot_bytes = (uint32_t)W * 128u;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < L * W; i += FM_THREADS) s_bias[i] = a.bias[i / W][i % W];
+    for (int i = tid; i < 2 * W; i += FM_THREADS) s_head[i] = a.head_w[i];
     if (tid < 2) s_head[2 * W + tid] = a.head_b[tid];
-    for (int i = tid; i < 6 * F; i += 128) s_bf[i] = a.Bf[i];
+    for (int i = tid; i < 6 * F; i += FM_THREADS) s_bf[i] = a.Bf[i];
     if (tid < 6) {
         s_bf[6 * F + tid] = a.lo[tid];
         s_bf[6 * F + 6 + tid] = a.hi[tid];
     }
-    const uint32_t tcols = W <= 64 ? 64u : (W <= 128 ? 128u : 256u);
+    const uint32_t tcols = 2u * (uint32_t)W <= 256u ? 256u : 512u;
     if (warp == 0) {
         tmem_alloc(su32(&tmem_slot), tcols);
         tmem_relinquish();
     }
     if (tid == 32) {
-        mbar_init(su32(&wbar), 1);
-        mbar_init(su32(&mbar), 1);
+        for (int s = 0; s < FM_NS; s++) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int t = 0; t < 2; t++) {
+            mbar_init(mma_done0 + 8 * t, 1);
+            mbar_init(in_ready0 + 8 * t, 128);
+        }
+        mbar_init(drain, 1);
         mbar_fence_init();
+        abort_flag = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const int64_t ntiles = (a.n + 127) / 128;
-    uint32_t wcount = 0, mcount = 0;
-    bool ok = true;
-    auto load_weights = [&](int l) {
-        const int K = l == 0 ? 2 * F : W;
-        mbar_expect_tx(su32(&wbar), (uint32_t)W * K * 2u);
-        for (int kc = 0; kc < K / 64; kc++) tma_load_2d(su32(wbuf + kc * wchunk), &maps.w[l], kc * 64, 0, su32(&wbar));
-    };
-    if (tid == 0 && blockIdx.x < ntiles) load_weights(0);
-    const uint32_t idesc = idesc_bf16(128, W);
-    // Every thread runs the same loop trips (block barriers inside); after a
-    // timed-out wait `ok` only suppresses work and the error bit is set.
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t q = tile * 128 + tid;
-        // Fourier features of this thread's query into K-chunk(s) of act
-        {
-            float xn[6];
-            for (int k = 0; k < 6; k++) {
-                float xv = q < a.n ? a.x[6 * q + k] : 0.0f;
-                xn[k] = 2.0f * (xv - s_bf[6 * F + k]) / (s_bf[6 * F + 6 + k] - s_bf[6 * F + k]) - 1.0f;
-            }
-            for (int j = 0; j < F; j += 2) {
-                float s2[2], c2[2];
-                for (int h = 0; h < 2; h++) {
-                    float v = 0.0f;
-                    for (int k = 0; k < 6; k++) v = fmaf(s_bf[6 * (j + h) + k], xn[k], v);
-                    v -= rintf(v);
-                    sincospif(2.0f * v, &s2[h], &c2[h]);
+    const int64_t npairs = (ntiles + 1) / 2;
+    auto fail = [&]() { abort_flag = 1; };
+
+    if (warp == 8) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t pr = blockIdx.x; pr < npairs && !abort_flag; pr += gridDim.x) {
+                for (int l = 0; l < L && !abort_flag; l++) {
+                    const int nkc = (l == 0 ? 2 * F : W) / 64;
+                    for (int kc = 0; kc < nkc; kc++, it++) {
+                        const uint32_t s = it % FM_NS, ph = (it / FM_NS) & 1u;
+                        if (it >= FM_NS && !mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err)) {
+                            fail();
+                            break;
+                        }
+                        mbar_expect_tx(full0 + 8 * s, slot_bytes);
+                        tma_load_2d(su32(ring + s * slot_bytes), &maps.w[l], kc * 64, 0, full0 + 8 * s);
+                    }
                 }
-                *(uint32_t*)(act + (j / 64) * 16384 + sw128_off(tid, j % 64)) = pack_bf16(s2[0], s2[1]);
-                *(uint32_t*)(act + ((F + j) / 64) * 16384 + sw128_off(tid, (F + j) % 64)) = pack_bf16(c2[0], c2[1]);
             }
+            // drain: the last loads issued have landed before the CTA ends
+            for (uint32_t j = it > FM_NS ? it - FM_NS : 0; j < it; j++)
+                mbar_wait(full0 + 8 * (j % FM_NS), (j / FM_NS) & 1u, a.err);
         }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        float h0 = 0.0f, h1 = 0.0f;
-        for (int l = 0; l < L; l++) {
-            const int K = l == 0 ? 2 * F : W;
-            if (tid == 0) {
-                if (ok) ok = mbar_wait(su32(&wbar), wcount & 1u, a.err);
-                wcount++;
-                tc_fence_after();
-                if (ok) {
-                    for (int kc = 0; kc < K / 64; kc++)
+    } else if (warp == 9) {
+        // -------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, W);
+            uint32_t it = 0, in_ph[2] = {0, 0};
+            for (int64_t pr = blockIdx.x; pr < npairs && !abort_flag; pr += gridDim.x) {
+                for (int l = 0; l < L && !abort_flag; l++) {
+                    const int nkc = (l == 0 ? 2 * F : W) / 64;
+                    for (int kc = 0; kc < nkc; kc++, it++) {
+                        const uint32_t s = it % FM_NS, ph = (it / FM_NS) & 1u;
+                        if (!mbar_wait(full0 + 8 * s, ph, a.err)) { fail(); break; }
+                        bool okk = true;
+                        for (int t = 0; t < 2; t++) {
+                            // a layer's input (features for layer 0) and free TMEM columns
+                            if (kc == 0) {
+                                if (!mbar_wait(in_ready0 + 8 * t, in_ph[t], a.err)) { okk = false; break; }
+                                in_ph[t] ^= 1u;
+                            }
+                            tc_fence_after();
 #pragma unroll
-                        for (int k = 0; k < 4; k++)
-                            mma_bf16(tmem, desc_sw128(su32(act + kc * 16384) + k * 32),
-                                     desc_sw128(su32(wbuf + kc * wchunk) + k * 32), idesc, (kc | k) != 0 ? 1u : 0u);
+                            for (int k = 0; k < 4; k++)
+                                mma_bf16(tmem + (uint32_t)(t * W), desc_sw128(su32(act[t] + kc * 16384) + k * 32),
+                                         desc_sw128(su32(ring + s * slot_bytes) + k * 32), idesc,
+                                         (kc | k) != 0 ? 1u : 0u);
+                            if (kc == nkc - 1) mma_commit(mma_done0 + 8 * t);
+                        }
+                        mma_commit(empty0 + 8 * s);
+                        if (!okk) { fail(); break; }
+                    }
                 }
-                mma_commit(su32(&mbar));
             }
-            __syncwarp();
-            if (warp == 0) ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // warp-uniform for tcgen05.ld
-            const bool done = ok && mbar_wait(su32(&mbar), mcount & 1u, a.err);
-            mcount++;
-            tc_fence_after();
-            // the weight buffer is free again: stream the next layer's weights
-            const bool more = (l + 1 < L) || (tile + gridDim.x < ntiles);
-            if (tid == 0 && done && more) load_weights((l + 1) % L);
-            if (!done) ok = false;
-            if (ok) {
-                for (int c0 = 0; c0 < W; c0 += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            // drain: every MMA issued has completed before TMEM is released
+            mma_commit(drain);
+            mbar_wait(drain, 0, a.err);
+        }
+    } else {
+        // ---------------------------------------- features + epilogue, per tile
+        const int t = warp >> 2;                       // 0: tile A, 1: tile B
+        const int row = (warp & 3) * 32 + lane;        // query row = TMEM lane
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        const uint32_t col0 = (uint32_t)(t * W);
+        uint8_t* buf = act[t];
+        uint32_t done_ph = 0;
+        for (int64_t pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+            const int64_t q = (2 * pr + t) * 128 + row;
+            {
+                float xn[6];
+                for (int k = 0; k < 6; k++) {
+                    float xv = q < a.n ? a.x[6 * q + k] : 0.0f;
+                    xn[k] = 2.0f * (xv - s_bf[6 * F + k]) / (s_bf[6 * F + 6 + k] - s_bf[6 * F + k]) - 1.0f;
+                }
+                for (int j = 0; j < F; j += 2) {
+                    float s2[2], c2[2];
+                    for (int hh = 0; hh < 2; hh++) {
+                        float v = 0.0f;
+                        for (int k = 0; k < 6; k++) v = fmaf(s_bf[6 * (j + hh) + k], xn[k], v);
+                        v -= rintf(v);
+                        feature_sincos(v, &s2[hh], &c2[hh]);
+                    }
+                    *(uint32_t*)(buf + (j / 64) * 16384 + sw128_off(row, j % 64)) = pack_bf16(s2[0], s2[1]);
+                    *(uint32_t*)(buf + ((F + j) / 64) * 16384 + sw128_off(row, (F + j) % 64)) =
+                        pack_bf16(c2[0], c2[1]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(in_ready0 + 8 * t);
+            float h0 = 0.0f, h1 = 0.0f;
+            bool ok = true;
+            for (int l = 0; l < L; l++) {
+                bool got = !abort_flag && mbar_wait(mma_done0 + 8 * t, done_ph, a.err);
+                done_ph ^= 1u;
+                got = __all_sync(0xffffffffu, got);
+                if (!got) { fail(); ok = false; break; }
+                tc_fence_after();
+                for (int cc = 0; cc < W; cc += 64) {
+                    // two 32-column loads in flight per wait
+                    uint32_t r2[2][32];
+                    tmem_ld32(tmem + lane_base + col0 + (uint32_t)cc, r2[0]);
+                    tmem_ld32(tmem + lane_base + col0 + (uint32_t)cc + 32u, r2[1]);
                     tmem_wait_ld();
-                    uint32_t packed[16];
 #pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        float v0 = fmaxf(__uint_as_float(r[j]) + s_bias[l * W + c0 + j], 0.0f);
-                        float v1 = fmaxf(__uint_as_float(r[j + 1]) + s_bias[l * W + c0 + j + 1], 0.0f);
-                        packed[j / 2] = pack_bf16(v0, v1);
-                        if (l == L - 1) {
+                    for (int hh = 0; hh < 2; hh++) {
+                    const int c0 = cc + 32 * hh;
+                    const uint32_t* r = r2[hh];
+                    uint32_t packed[16];
+                    const float4* bv = reinterpret_cast<const float4*>(s_bias + l * W + c0);
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 b = bv[j4];
+                        const int j = 4 * j4;
+                        packed[2 * j4] = add2_relu_bf16x2(__uint_as_float(r[j]), b.x, __uint_as_float(r[j + 1]), b.y);
+                        packed[2 * j4 + 1] =
+                            add2_relu_bf16x2(__uint_as_float(r[j + 2]), b.z, __uint_as_float(r[j + 3]), b.w);
+                    }
+                    if (l == L - 1) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
                             __nv_bfloat162 b2 = *reinterpret_cast<__nv_bfloat162*>(&packed[j / 2]);
                             float r0 = __low2float(b2), r1 = __high2float(b2);
                             h0 = fmaf(r0, s_head[c0 + j], fmaf(r1, s_head[c0 + j + 1], h0));
@@ -480,19 +584,24 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fused(const __grid_constant__ Fu
 #pragma unroll
                         for (int u = 0; u < 4; u++) {
                             const int c = c0 + 8 * u;
-                            *(uint4*)(act + (c / 64) * 16384 + sw128_off(tid, c % 64)) =
+                            *(uint4*)(buf + (c / 64) * 16384 + sw128_off(row, c % 64)) =
                                 make_uint4(packed[4 * u], packed[4 * u + 1], packed[4 * u + 2], packed[4 * u + 3]);
                         }
                     }
+                    }
+                }
+                if (l < L - 1) {
+                    // the next layer's input is in place and this tile's TMEM columns are free
+                    fence_async_smem();
+                    tc_fence_before();
+                    mbar_arrive(in_ready0 + 8 * t);
                 }
             }
-            fence_async_smem();
-            tc_fence_before();
-            __syncthreads();
-        }
-        if (ok && q < a.n) {
-            a.out[2 * q] = h0 + s_head[2 * W];
-            a.out[2 * q + 1] = (h1 + s_head[2 * W + 1]) * a.db_scale + a.db_offset + fspl_db(a.x + 6 * q, a.lam);
+            if (!ok) break;
+            if (q < a.n) {
+                a.out[2 * q] = h0 + s_head[2 * W];
+                a.out[2 * q + 1] = (h1 + s_head[2 * W + 1]) * a.db_scale + a.db_offset + fspl_db(a.x + 6 * q, a.lam);
+            }
         }
     }
     tc_fence_before();
@@ -756,15 +865,14 @@ int rt_mlp_infer(rt_mlp* m, const float* x, int64_t n, float* out) {
     a.db_offset = m->db_offset;
     a.lam = m->lam;
     a.err = bp<unsigned>(m->errw);
-    const int kmax = std::max(2 * m->F, m->W) / 64;
-    size_t smem = 1024 + 64 * 1024 + (size_t)kmax * m->W * 128 +
-                  sizeof(float) * ((size_t)m->L * m->W + 2 * m->W + 2 + 6 * m->F + 12);
+    const size_t smem = 1024 + FusedLayout(m->F, m->W, m->L).bytes();
+    if (smem > 227 * 1024) return rt_mlp_infer_layers(m, x, n, out);
     MT(ensure_smem_attr((const void*)k_mlp_fused, smem));
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
-    int64_t ntiles = (n + 127) / 128;
-    int grid = (int)std::min<int64_t>(ntiles, sms);
-    k_mlp_fused<<<grid, 128, smem, m->stream>>>(maps, a);
+    int64_t npairs = ((n + 127) / 128 + 1) / 2;
+    int grid = (int)std::min<int64_t>(npairs, sms);
+    k_mlp_fused<<<grid, FM_THREADS, smem, m->stream>>>(maps, a);
     MT(cudaGetLastError());
     return RT_OK;
 }
