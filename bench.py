@@ -304,7 +304,7 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = 4.264e6
+K_COVERAGE_TRAFFIC = 4.267e6
 
 
 def roofline(name, rec, sbr_counts, cov_counts, hbm, src):

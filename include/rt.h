@@ -243,6 +243,19 @@ int rt_coverage_map_noalloc(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, in
                             int32_t tx_port, float* gain, uint32_t* hits);
 
 /*
+ * Sec. III-B: VJP of rt_coverage_map with respect to the transmitters'
+ * orientation. grad_gain [n_tx*ny*nx] (device) is the upstream gradient of
+ * the gain map (same grid, depth, ray count and port as the forward call);
+ * grad_ypr [n_tx*3] (device) receives d(sum grad_gain * gain)/d(yaw, pitch,
+ * roll), overwritten. The rays are traced again; the ray geometry does not
+ * depend on the orientation, so the gradient is exact for the sampled rays.
+ * Not allowed while capturing a graph (it may build the ray order).
+ * Errors: RT_ERR_INVALID_ARG.
+ */
+int rt_coverage_map_backward(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
+                             const float* grad_gain, float* grad_ypr);
+
+/*
  * Sec. I/II (differentiability): vector-Jacobian products through the
  * stored paths (no re-trace). grad_a [P*nrp*ntp] complex and grad_tau [P]
  * (may be NULL) are the upstream gradients of a real loss w.r.t. rt_cir's

@@ -18,6 +18,8 @@ int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs
               int64_t n_pairs);
 int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, const float* gH,
                   float* ga, float* gt, int64_t n_pairs);
+int launch_coverage_vjp(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int tx_port, const float* grad_gain,
+                        float* grad_ypr);
 int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t first, int64_t count, bool zero,
                     int tx_port, float* gain, uint32_t* hits);
 int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out);
@@ -404,6 +406,18 @@ int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth,
     if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
         return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_accumulate: scene, transmitters and receivers must be set");
     return launch_coverage(ctx, g, max_depth, num_rays, first_ray, ray_count, false, tx_port, gain, hits);
+}
+
+int rt_coverage_map_backward(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
+                             const float* grad_gain, float* grad_ypr) {
+    CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "coverage_map_backward");
+    if (!g || !grad_gain || !grad_ypr || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 ||
+        num_rays < 1 || tx_port < 0 || tx_port >= ctx->tx_ant.n_ports)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_backward: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_backward: scene, transmitters and receivers must be set");
+    return launch_coverage_vjp(ctx, g, max_depth, num_rays, tx_port, grad_gain, grad_ypr);
 }
 
 int rt_cir_backward(rt_ctx* ctx, uint32_t flags, const float* grad_a, const float* grad_tau, float* g_eps,

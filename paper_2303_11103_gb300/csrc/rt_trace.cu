@@ -256,6 +256,125 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     if (C) flush_counts(cnt, p.c.counter, RT_CNT_CLOSEST);
 }
 
+// VJP of the coverage map with respect to the transmitters' orientation
+// (yaw, pitch, roll): the rays are traced again exactly as in k_coverage
+// (the geometry does not depend on the orientation), the field is carried
+// as Dual<3> seeded by the transmit pattern at R(yaw, pitch, roll), and every
+// crossing of the plane adds g[cell] * d w / d(yaw, pitch, roll) to the
+// lane's accumulators, flushed per transmitter (warp-reduced when the warp
+// shares one). Sec. III-B optimises an orientation with this gradient.
+struct CovVjpParams {
+    CovParams p;
+    const float* grad_gain;   // [n_tx*ny*nx] upstream gradient of the gain map
+    float* grad_ypr;          // [n_tx*3], accumulated
+};
+
+__device__ __forceinline__ void flush_ypr(float* g, int tx, float (&acc)[3]) {
+    const unsigned full = 0xffffffffu;
+    const int t0 = __shfl_sync(full, tx, 0);
+    if (__all_sync(full, tx == t0)) {
+        for (int k = 0; k < 3; k++) {
+            float v = acc[k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(full, v, o);
+            if ((threadIdx.x & 31) == 0 && t0 >= 0 && v != 0.0f) atomicAdd(g + 3 * t0 + k, v);
+        }
+    } else if (tx >= 0) {
+        for (int k = 0; k < 3; k++)
+            if (acc[k] != 0.0f) atomicAdd(g + 3 * tx + k, acc[k]);
+    }
+    acc[0] = acc[1] = acc[2] = 0.0f;
+}
+
+__global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
+    extern __shared__ float4 sm[];
+    const CovParams& p = q.p;
+    stage_nodes(p.c, sm);
+    typedef Dual<3> D3;
+    WarpFeed feed;
+    bool alive = false;
+    f3 o = mk(0, 0, 0), d = mk(0, 0, 1);
+    int last = -1, depth = 0, tx = -1;
+    Cx<D3> E[3];
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+    const float zeta_t = p.txa.slant[p.tx_port], zeta_r = p.rxa.slant[0];
+    Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
+    TravCount cnt;
+    while (true) {
+        long long s = feed.refill(p.c, alive);
+        // a lane moving to another transmitter flushes its accumulators first
+        const int next_tx = s >= 0 ? (int)(s / p.c.N) : tx;
+        if (__any_sync(0xffffffffu, next_tx != tx && tx >= 0)) {
+            int ftx = (next_tx != tx) ? tx : -1;
+            float keep[3] = {acc[0], acc[1], acc[2]};
+            if (ftx < 0) acc[0] = acc[1] = acc[2] = 0.0f;
+            flush_ypr(q.grad_ypr, ftx, acc);
+            if (ftx < 0) { acc[0] = keep[0]; acc[1] = keep[1]; acc[2] = keep[2]; }
+        }
+        if (s >= 0) {
+            long long i = s - (long long)next_tx * p.c.N;
+            tx = next_tx;
+            o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
+            d = fib_dir(p.c.N, i);
+            D3 yaw = dconst<3>(p.c.tx_ypr[3 * tx]), pitch = dconst<3>(p.c.tx_ypr[3 * tx + 1]),
+               roll = dconst<3>(p.c.tx_ypr[3 * tx + 2]);
+            yaw.d[0] = 1.0f;
+            pitch.d[1] = 1.0f;
+            roll.d[2] = 1.0f;
+            Rot<D3> Rt = rot_ypr(yaw, pitch, roll);
+            V3<D3> f = antenna_vec<D3>(p.txa.kind, zeta_t, Rt, v_const<D3>(d));
+            E[0] = {f.x, dconst<3>(0.0f)};
+            E[1] = {f.y, dconst<3>(0.0f)};
+            E[2] = {f.z, dconst<3>(0.0f)};
+            last = -1;
+            depth = 0;
+            alive = true;
+        }
+        if (!__any_sync(0xffffffffu, alive)) {
+            if (feed.exhausted) break;
+            continue;
+        }
+        if (alive) {
+            float t;
+            int id = closest_hit<false>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+            if (d.z != 0.0f) {
+                float sc = (p.h - o.z) / d.z;
+                if (sc > 0.0f && (id < 0 || sc < t)) {
+                    float fx = (o.x + sc * d.x - p.x0) * p.inv_cell;
+                    float fy = (o.y + sc * d.y - p.y0) * p.inv_cell;
+                    int ix = (int)floorf(fx), iy = (int)floorf(fy);
+                    if (fx >= 0.0f && fy >= 0.0f && ix < p.nx && iy < p.ny) {
+                        const size_t cell = ((size_t)tx * p.ny + iy) * p.nx + ix;
+                        const float g = q.grad_gain[cell];
+                        if (g != 0.0f) {
+                            V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
+                            D3 re = E[0].re * F.x + E[1].re * F.y + E[2].re * F.z;
+                            D3 im = E[0].im * F.x + E[1].im * F.y + E[2].im * F.z;
+                            const float sw = g * p.wscale / fabsf(d.z);
+                            for (int k = 0; k < 3; k++)
+                                acc[k] += sw * 2.0f * (re.v * re.d[k] + im.v * im.d[k]);
+                        }
+                    }
+                }
+            }
+            if (id < 0 || depth >= p.D) {
+                alive = false;
+            } else {
+                float4 pl = __ldg(p.c.s.planes + id);
+                int m = __ldg(p.c.s.mat + id);
+                float2 mp = __ldg(p.c.s.mats + m);
+                f3 n = xyz(pl);
+                f3 r = reflect(d, n);
+                reflect_field<D3>(E, v_const<D3>(d), v_const<D3>(r), n, dconst<3>(mp.x), dconst<3>(mp.y), p.inv_we0);
+                o = o + d * t;
+                d = r;
+                last = id;
+                depth++;
+            }
+        }
+    }
+    flush_ypr(q.grad_ypr, tx, acc);
+}
+
 __global__ void k_dirs(long long N, long long first, long long n, float* __restrict__ out) {
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -403,6 +522,45 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     prof_begin(ctx, "k_coverage");
     kern<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+// VJP of the coverage map w.r.t. the transmitters' (yaw, pitch, roll):
+// grad_ypr [n_tx*3] is overwritten.
+int launch_coverage_vjp(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int tx_port, const float* grad_gain,
+                        float* grad_ypr) {
+    int e = ensure_perm(ctx, N);
+    if (e) return e;
+    CovVjpParams q;
+    CovParams& p = q.p;
+    p.c = make_common(ctx, N, 0, N);
+    p.D = D;
+    p.txa = ctx->tx_ant;
+    p.rxa = ctx->rx_ant;
+    p.tx_port = tx_port;
+    p.inv_we0 = (float)(1.0 / (2.0 * RT_PI_D * ctx->fc * RT_EPS0_D));
+    p.x0 = g->x0;
+    p.y0 = g->y0;
+    p.inv_cell = 1.0f / g->cell;
+    p.h = g->height;
+    p.nx = g->nx;
+    p.ny = g->ny;
+    double lam = RT_C0_D / ctx->fc;
+    p.wscale = (float)(lam * lam / (4.0 * RT_PI_D * (double)g->cell * g->cell * (double)N));
+    p.gain = nullptr;
+    p.hits = nullptr;
+    q.grad_gain = grad_gain;
+    q.grad_ypr = grad_ypr;
+    RT_TRY(cudaMemsetAsync(grad_ypr, 0, sizeof(float) * 3 * (size_t)ctx->n_tx, ctx->stream));
+    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
+    RT_TRY(ensure_smem_attr((const void*)k_coverage_vjp, smem));
+    RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
+    int grid = trace_grid(ctx, (const void*)k_coverage_vjp, smem);
+    p.c.chunk = pick_chunk(ctx, p.c.total, grid);
+    prof_begin(ctx, "k_coverage_vjp");
+    k_coverage_vjp<<<grid, ctx->trace_block, smem, ctx->stream>>>(q);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;

@@ -86,3 +86,29 @@ def orient_transmitter(tracer: rt.Tracer, pair_of_path, yaw0: float, pitch0: flo
         opt.step()
         hist.append(float(obj.item()))
     return float(ang[0, 0].item()), float(ang[0, 1].item()), hist
+
+
+def orient_for_region(tracer: rt.Tracer, grid: dict, max_depth: int, num_rays: int, region, yaw0: float,
+                      pitch0: float, iters: int = 60, lr: float = 0.05, tx_port: int = 0):
+    """Sec. III-B: gradient ascent of the mean received power (in dB) over the
+    cells of `region` ([ny, nx] weights) of the coverage map, over the first
+    transmitter's yaw and pitch, through rt_coverage_map_backward. Returns
+    (yaw, pitch, objective history in dB)."""
+    dev = tracer.device
+    reg = torch.as_tensor(region, dtype=torch.float32, device=dev)
+    reg = reg / reg.sum()
+    ang = torch.tensor([yaw0, pitch0], dtype=torch.float32, device=dev, requires_grad=True)
+    base = tracer._tx_ypr.clone()
+    opt = torch.optim.Adam([ang], lr=lr)
+    hist = []
+    for _ in range(iters):
+        opt.zero_grad()
+        ypr = torch.cat([ang[None], base[:1, 2:3]], 1)
+        if base.shape[0] > 1:
+            ypr = torch.cat([ypr, base[1:]], 0)
+        gain = rt.CoverageMap.apply(tracer, ypr, grid, max_depth, num_rays, tx_port)
+        obj = 10.0 * torch.log10((gain[0] * reg).sum())
+        (-obj).backward()
+        opt.step()
+        hist.append(float(obj.item()))
+    return float(ang[0].item()), float(ang[1].item()), hist

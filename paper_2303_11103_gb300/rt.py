@@ -80,6 +80,7 @@ def lib():
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
             "rt_coverage_map_noalloc": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
+            "rt_coverage_map_backward": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
             "rt_pair_gain": [vp, vp, ctypes.c_float, vp],
@@ -490,6 +491,17 @@ class Tracer:
         a_raw = torch.view_as_real(a.contiguous()) if a.is_complex() else a
         return torch.view_as_complex(self.freq_response_raw(a_raw.contiguous(), tau, freqs))
 
+    def coverage_map_backward(self, grid: dict, max_depth: int, num_rays: int, grad_gain, tx_port: int = 0):
+        """d(sum grad_gain * gain)/d(tx yaw, pitch, roll) [n_tx, 3] (Sec. III-B)."""
+        self.sync_stream()
+        g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
+                    int(grid["nx"]), int(grid["ny"]))
+        gg = self._t(grad_gain, torch.float32).contiguous()
+        out = torch.empty((self.n_tx, 3), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_coverage_map_backward(self.ctx, ctypes.byref(g), int(max_depth), int(num_rays),
+                                                        int(tx_port), _ptr(gg), _ptr(out)))
+        return out
+
     def coverage_map(self, grid: dict, max_depth: int, num_rays: int, tx_port: int = 0):
         self.sync_stream()
         g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
@@ -562,6 +574,23 @@ class CIR(torch.autograd.Function):
             grad_a = torch.zeros((tr.n_paths, tr.nrp, tr.ntp), dtype=torch.complex64, device=tr.device)
         ge, gs, gp, gy = tr.cir_backward(grad_a, grad_tau)
         return None, ge, gs, gp, gy
+
+
+class CoverageMap(torch.autograd.Function):
+    """tx_ypr [n_tx, 3] -> gain map [n_tx, ny, nx]; backward through
+    rt_coverage_map_backward (gradients with respect to the orientation)."""
+
+    @staticmethod
+    def forward(ctx, tracer, tx_ypr, grid, max_depth, num_rays, tx_port=0):
+        tracer.set_tx(tracer._tx_pos, tx_ypr.detach().float(), tracer.tx_antenna)
+        g, _ = tracer.coverage_map(grid, max_depth, num_rays, tx_port)
+        ctx.args = (tracer, grid, max_depth, num_rays, tx_port)
+        return g
+
+    @staticmethod
+    def backward(ctx, grad_gain):
+        tracer, grid, max_depth, num_rays, tx_port = ctx.args
+        return None, tracer.coverage_map_backward(grid, max_depth, num_rays, grad_gain, tx_port), None, None, None, None
 
 
 class FreqResponse(torch.autograd.Function):
