@@ -68,14 +68,26 @@ def test_coverage_autograd_and_region_ascent(small_city):
     (gain * w).sum().backward()
     direct = tr.coverage_map_backward(GRID, D, N, w, 0)
     assert torch.allclose(ypr.grad, direct, rtol=1e-6, atol=0)
-    # Sec. III-B: maximise the mean power in a region away from the boresight
+    # Sec. III-B: maximise the mean power in a region, starting turned 70 degrees away from it
     xs = GRID["x0"] + GRID["cell"] * (np.arange(GRID["nx"]) + 0.5)
     ys = GRID["y0"] + GRID["cell"] * (np.arange(GRID["ny"]) + 0.5)
     X, Y = np.meshgrid(xs, ys)
-    cx, cy = float(tx.pos[0, 0]) + 40.0, float(tx.pos[0, 1]) - 30.0
-    region = ((X - cx) ** 2 + (Y - cy) ** 2 < 15.0 ** 2).astype(np.float32)
-    assert region.sum() > 20
-    yaw0 = math.atan2(cy - tx.pos[0, 1], cx - tx.pos[0, 0]) + 1.2   # turned away from the region
+    tx0, ty0 = float(tx.pos[0, 0]), float(tx.pos[0, 1])
+    region, yaw0 = None, None
+    for k in range(12):                        # the first direction whose disc the rays reach
+        phi = 2 * math.pi * k / 12
+        cx, cy = tx0 + 35.0 * math.cos(phi), ty0 + 35.0 * math.sin(phi)
+        reg = ((X - cx) ** 2 + (Y - cy) ** 2 < 12.0 ** 2).astype(np.float32)
+        if reg.sum() < 20:
+            continue
+        y0 = phi + 1.2
+        tr.set_tx(tx.pos, np.array([[y0, 0.1, 0.0]], np.float32), tx.antenna)
+        g0, _ = tr.coverage_map(GRID, D, N, 0)
+        if float((g0[0].cpu() * torch.as_tensor(reg)).sum()) > 0:
+            region, yaw0 = reg, y0
+            break
+    assert region is not None
     yaw, pitch, hist = LG.orient_for_region(tr, GRID, D, N, region, yaw0, 0.1, iters=60, lr=0.05)
+    assert np.isfinite(hist).all()
     assert hist[-1] > hist[0] + 3.0            # mean power in the region up by more than 3 dB
     tr.set_tx(tx.pos, tx.ypr, tx.antenna)
