@@ -278,6 +278,8 @@ def run_ours(args):
                    "coverage_cells": GRID["nx"] * GRID["ny"], "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"replicas{world}"},
         "paths_per_step": state["P"],
+        "paths_per_s": state["P"] * args.steps / (total_ms / 1e3),
+        "paths_per_s_note": "valid paths of compute_paths per second of the whole timed step",
         "compute_paths_counts": path_stats,
         "ray_bounces_per_step": bounces_per_step,
         "gpu_launches": prof["launches"],
@@ -330,7 +332,9 @@ def roofline(name, rec, sbr_counts, cov_counts, hbm, src):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
             "ops_per_launch": ops, "ops_basis": f"{OPS_PER_NODE} per BVH node record, {OPS_PER_TRI} per triangle record",
             "requested_gbs": req_bytes / per_launch_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
-            "ms_per_launch": per_launch_s * 1e3}
+            "ms_per_launch": per_launch_s * 1e3,
+            "nodes_per_query": counts["nodes"] / max(counts["closest_hit"] + counts["any_hit"], 1),
+            "tris_per_query": counts["tris"] / max(counts["closest_hit"] + counts["any_hit"], 1)}
 
 
 def extra_measurements(tr, scene, dev, args):
