@@ -4,8 +4,9 @@
 //
 // The field of one path is written once over a scalar type (rt_field.cuh).
 // The VJP kernel replays the stored path (no re-trace): for each group of
-// four of the path's local parameters it runs the field with Dual<4>
-// tangents and contracts the Jacobian with the upstream gradient. A path
+// two of the path's local parameters (one group per grid row, so a path's
+// groups run in parallel) it runs the field with Dual<2> tangents and
+// contracts the Jacobian with the upstream gradient. A path
 // depends on at most 6 + 2*depth parameters (tx xyz, yaw/pitch/roll, eps_r
 // and sigma of the materials it reflects on), so per-path forward tangents
 // are cheaper than a taped reverse pass.
@@ -141,7 +142,7 @@ __global__ void k_cir(CirParams c, float2* __restrict__ a_out, float* __restrict
 }
 
 // ----------------------------------------------------------------- VJP of cir
-constexpr int NT = 4;
+constexpr int NT = 2;
 
 __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const float* __restrict__ gtau,
                           float* g_eps, float* g_sig, float* g_pos, float* g_ypr) {
@@ -321,61 +322,51 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
         }
 }
 
-// VJP of H: grad_a_i = sum_k gH_k conj(w_ik); grad_tau_i = sum_k Re(conj(gH_k) a_i (-j 2 pi f_k) w_ik)
+// VJP of H: grad_a_i = sum_k gH_k conj(w_ik); grad_tau_i = sum_k Re(conj(gH_k) a_i (-j 2 pi f_k) w_ik).
+// One block per pair, one warp per path (the pair's paths in parallel, 4 at
+// a time), lanes over the subcarriers, warp-shuffle reductions.
 template <int NP>
 __global__ void __launch_bounds__(128) k_freq_vjp(const int64_t* __restrict__ off, const float2* __restrict__ a,
                                                   const float* __restrict__ tau, const double* __restrict__ freqs,
                                                   int K, const float2* __restrict__ gH, float2* __restrict__ ga,
                                                   float* __restrict__ gt) {
-    __shared__ float red[NP * 2 + 1][4];
     const int64_t pair = blockIdx.x;
     const int64_t b = off[pair], e = off[pair + 1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int64_t i = b; i < e; i++) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t i = b + w; i < e; i += nw) {
         const float t = tau[i];
         float2 av[NP];
         for (int q = 0; q < NP; q++) av[q] = a[i * NP + q];
         float sr[NP], si[NP], sg = 0.0f;
         for (int q = 0; q < NP; q++) { sr[q] = 0.0f; si[q] = 0.0f; }
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        for (int k = lane; k < K; k += 32) {
             float f = (float)freqs[k];
             float cyc = f * t;
             cyc -= rintf(cyc);
             float wi, wr;
             __sincosf(-2.0f * RT_PI_F * cyc, &wi, &wr);
+            const float c = 2.0f * RT_PI_F * f;
             for (int q = 0; q < NP; q++) {
                 float2 g = gH[(pair * NP + q) * K + k];
                 // g * conj(w)
                 sr[q] += g.x * wr + g.y * wi;
                 si[q] += g.y * wr - g.x * wi;
-                // Re(conj(g) * a * (-j 2 pi f) * w)
+                // Re(conj(g) * a * (-j 2 pi f) * w): (-j c)(awr + j awi) = c awi - j c awr
                 float awr = av[q].x * wr - av[q].y * wi, awi = av[q].x * wi + av[q].y * wr;
-                // (-j c)(awr + j awi) = c awi - j c awr, with c = 2 pi f
-                float c = 2.0f * RT_PI_F * f;
-                float zr = c * awi, zi = -c * awr;
-                sg += g.x * zr + g.y * zi;
+                sg += g.x * (c * awi) + g.y * (-c * awr);
             }
         }
-        float v[NP * 2 + 1];
-        for (int q = 0; q < NP; q++) { v[2 * q] = sr[q]; v[2 * q + 1] = si[q]; }
-        v[NP * 2] = sg;
-        for (int j = 0; j < NP * 2 + 1; j++) {
-            float x = v[j];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) red[j][w] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
             for (int q = 0; q < NP; q++) {
-                float xr = 0.0f, xi = 0.0f;
-                for (int ww = 0; ww < 4; ww++) { xr += red[2 * q][ww]; xi += red[2 * q + 1][ww]; }
-                ga[i * NP + q] = make_float2(xr, xi);
+                sr[q] += __shfl_xor_sync(0xffffffffu, sr[q], o);
+                si[q] += __shfl_xor_sync(0xffffffffu, si[q], o);
             }
-            float s = 0.0f;
-            for (int ww = 0; ww < 4; ww++) s += red[NP * 2][ww];
-            gt[i] = s;
+            sg += __shfl_xor_sync(0xffffffffu, sg, o);
         }
-        __syncthreads();
+        if (lane == 0) {
+            for (int q = 0; q < NP; q++) ga[i * NP + q] = make_float2(sr[q], si[q]);
+            gt[i] = sg;
+        }
     }
 }
 
