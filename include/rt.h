@@ -102,6 +102,20 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
 #define RT_BVH_PLOC 1
 int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder);
 
+/*
+ * Duplicate removal of the SBR candidate keys in rt_compute_paths (Sec. II-B:
+ * every distinct interaction sequence is refined once): RT_DEDUP_HASH
+ * (default) = open-addressing hash table of the keys, then a sort of the
+ * distinct keys only; RT_DEDUP_SORT = sort of all keys, then removal of
+ * equal neighbours. Both give the same candidates in the same (key) order
+ * with the same witness rays (the smallest producing ray). Keys that
+ * fill all 64 bits always take RT_DEDUP_SORT. Errors: RT_ERR_INVALID_ARG for
+ * another value.
+ */
+#define RT_DEDUP_HASH 0
+#define RT_DEDUP_SORT 1
+int rt_set_dedup(rt_ctx* ctx, int32_t mode);
+
 /* Replace the material table (same n_mat as the scene). */
 int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat);
 
@@ -158,8 +172,9 @@ int rt_get_paths(rt_ctx* ctx, int64_t* offsets, int32_t* seq, float* points, int
 /*
  * Debug / parity: the de-duplicated candidate list of the last
  * rt_compute_paths. n_out (HOST) = count U (always written); tx [U],
- * depth [U], seq [U*max_depth], witness_ray [U] (the lattice index of a ray
- * that produced the candidate, -1 for LOS). Any device pointer may be NULL.
+ * depth [U], seq [U*max_depth], witness_ray [U] (the smallest lattice index
+ * of the rays that produced the candidate, -1 for LOS). Any device pointer
+ * may be NULL.
  */
 int rt_get_candidates(rt_ctx* ctx, int64_t* n_out, int32_t* tx, int32_t* depth, int32_t* seq,
                       int64_t* witness_ray);
@@ -214,6 +229,39 @@ int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t nu
 int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
                                int64_t first_ray, int64_t ray_count, int32_t tx_port, float* gain,
                                uint32_t* hits);
+
+/*
+ * Coverage map computed concurrently with the calls that follow it (not in
+ * the paper). Same inputs, outputs and result as rt_coverage_map (up to
+ * float summation order), but the map is traced on a second stream of the
+ * context, with its own work counter and status word, beside later calls
+ * that leave the scene, materials, frequency, transmitters, receivers and
+ * ray order unchanged (rt_compute_paths with the same num_rays, rt_cir,
+ * rt_freq_response and their backward calls): their small kernels and host
+ * round trips then fill the GPU while the map traces.
+ *   flags 0: the map starts after all work queued so far on the context's
+ *     stream.
+ *   flags RT_ASYNC_AFTER_TRACE: the map starts after the ray trace of the
+ *     next rt_compute_paths, beside its candidate refinement and the calls
+ *     after it, instead of competing with the trace for the SMs; a call
+ *     that needs the map earlier starts it at that point.
+ *   blocks_per_sm caps the map's resident blocks per SM (0 = as many as
+ *     fit), leaving room for the other stream's kernels.
+ * rt_join(ctx) orders the context's stream after the map; read gain and hits
+ * only after it, and keep them allocated until then. The calls that change
+ * what the map reads (rt_load_scene, rt_set_materials, rt_set_frequency,
+ * rt_set_tx, rt_set_rx, rt_set_tuning, another coverage map, rt_autotune, a
+ * rt_compute_paths with another num_rays) join first by themselves, and so
+ * does rt_set_stream to another stream. Not allowed while capturing a graph
+ * (RT_ERR_NOT_READY). Errors: as rt_coverage_map, and RT_ERR_INVALID_ARG
+ * for blocks_per_sm < 0 or an unknown flag.
+ */
+#define RT_ASYNC_AFTER_TRACE 1u
+int rt_coverage_map_async(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
+                          uint32_t flags, int32_t blocks_per_sm, float* gain, uint32_t* hits);
+/* Orders the context's stream after the map of rt_coverage_map_async
+ * (starting it first if it is still waiting for a path trace). */
+int rt_join(rt_ctx* ctx);
 
 /*
  * Allocation-free coverage map. The paper has no counterpart; it exists for

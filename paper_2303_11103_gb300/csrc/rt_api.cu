@@ -140,6 +140,40 @@ static bool valid_antenna(const rt_antenna* a) {
     return a && a->kind >= RT_ANT_ISO && a->kind <= RT_ANT_TR38901 && (a->n_ports == 1 || a->n_ports == 2);
 }
 
+int side_launch(rt_ctx* ctx) {
+    if (!ctx->side_deferred) return RT_OK;
+    ctx->side_deferred = false;
+    const rt_ctx::SideReq r = ctx->side_req;
+    RT_TRY(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    RT_TRY(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    // the launch code uses the context's stream, counter and status word:
+    // point them at the second stream's for this one launch
+    std::swap(ctx->stream, ctx->side);
+    std::swap(ctx->counters, ctx->side_counters);
+    std::swap(ctx->status, ctx->side_status);
+    const int cap = ctx->grid_cap;
+    ctx->grid_cap = r.blocks_per_sm;
+    cudaError_t me = cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream);
+    int e = me != cudaSuccess ? set_cuda(ctx, me, "cudaMemsetAsync")
+                              : launch_coverage(ctx, &r.g, r.D, r.N, 0, r.N, true, r.tx_port, r.gain, r.hits);
+    ctx->grid_cap = cap;
+    std::swap(ctx->stream, ctx->side);
+    std::swap(ctx->counters, ctx->side_counters);
+    std::swap(ctx->status, ctx->side_status);
+    // whatever was queued, later calls that need it wait for its end
+    RT_TRY(cudaEventRecord(ctx->ev_side, ctx->side));
+    ctx->side_pending = true;
+    return e;
+}
+
+int side_join(rt_ctx* ctx) {
+    int e = side_launch(ctx);
+    if (!ctx->side_pending) return e;
+    ctx->side_pending = false;
+    RT_TRY(cudaStreamWaitEvent(ctx->stream, ctx->ev_side, 0));
+    return e;
+}
+
 extern "C" {
 
 int rt_create(rt_ctx** out, int device, void* stream) {
@@ -175,11 +209,21 @@ int rt_create(rt_ctx** out, int device, void* stream) {
 int rt_destroy(rt_ctx* ctx) {
     if (!ctx) return RT_OK;
     cudaSetDevice(ctx->device);
+    if (ctx->side_deferred) side_launch(ctx);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+        cudaEventDestroy(ctx->ev_fork);
+        cudaEventDestroy(ctx->ev_side);
+        buf_free(ctx->side_counters);
+        buf_free(ctx->side_status);
+    }
     for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->mat, &ctx->mats, &ctx->tx_pos,
                       &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->keys, &ctx->keys_alt,
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
-                      &ctx->cand_img, &ctx->path_key, &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
+                      &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->path_key,
+                      &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
                       &ctx->b_lbox, &ctx->b_cent, &ctx->b_info, &ctx->b_keys, &ctx->b_keys2, &ctx->b_vals,
@@ -196,8 +240,14 @@ int rt_destroy(rt_ctx* ctx) {
 
 int rt_set_stream(rt_ctx* ctx, void* stream) {
     CHECK_CTX(ctx);
+    if ((cudaStream_t)stream == ctx->stream) return RT_OK;
     ctx->stream = (cudaStream_t)stream;
-    return RT_OK;
+    return side_join(ctx);   // a map still running on the second stream comes before the new stream's work
+}
+
+int rt_join(rt_ctx* ctx) {
+    CHECK_CTX(ctx);
+    return side_join(ctx);
 }
 
 int rt_last_error(const rt_ctx* ctx, char* buf, size_t len) {
@@ -211,6 +261,10 @@ int rt_last_error(const rt_ctx* ctx, char* buf, size_t len) {
 int rt_set_frequency(rt_ctx* ctx, double fc) {
     CHECK_CTX(ctx);
     if (!(fc > 0.0)) return set_err(ctx, RT_ERR_INVALID_ARG, "frequency must be positive");
+    {
+        int ej = side_join(ctx);   // a deferred map is traced at the frequency it was requested at
+        if (ej) return ej;
+    }
     ctx->fc = fc;
     return RT_OK;
 }
@@ -219,6 +273,10 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
                   int32_t n_mat) {
     CHECK_CTX(ctx);
     NO_CAPTURE(ctx, "load_scene");
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (n_tris < 0 || n_tris >= (1ll << 30) || n_mat <= 0 || !mat_params || (n_tris > 0 && (!verts || !mat_id)))
         return set_err(ctx, RT_ERR_INVALID_ARG, "load_scene: bad arguments");
     ctx->has_scene = false;
@@ -244,8 +302,19 @@ int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder) {
     return RT_OK;
 }
 
+int rt_set_dedup(rt_ctx* ctx, int32_t mode) {
+    CHECK_CTX(ctx);
+    if (mode != RT_DEDUP_HASH && mode != RT_DEDUP_SORT) return set_err(ctx, RT_ERR_INVALID_ARG, "unknown dedup mode");
+    ctx->dedup = mode;
+    return RT_OK;
+}
+
 int rt_set_materials(rt_ctx* ctx, const float* mat_params, int32_t n_mat) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (!ctx->has_scene || n_mat != ctx->n_mat || !mat_params)
         return set_err(ctx, RT_ERR_INVALID_ARG, "set_materials: material count differs from the scene's");
     RT_TRY(cudaMemcpyAsync(ctx->mats.p, mat_params, sizeof(float) * 2 * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -267,6 +336,10 @@ static int set_devices(rt_ctx* ctx, DevBuf& pos, DevBuf& ypr, const float* p, co
 
 int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const rt_antenna* pat) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (n < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_tx: bad arguments");
     // Same count and ports: a pose update. The stored paths (triangle
     // sequences) and receiver sets stay; rt_cir re-evaluates the paths at
@@ -286,6 +359,10 @@ int rt_set_tx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t n, const 
 int rt_set_rx(rt_ctx* ctx, const float* pos, const float* ypr, int32_t m, const rt_antenna* pat,
               const int32_t* off_host) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (m < 1 || !pos || !valid_antenna(pat)) return set_err(ctx, RT_ERR_INVALID_ARG, "set_rx: bad arguments");
     if (off_host) {
         NO_CAPTURE(ctx, "set_rx with receiver sets");
@@ -387,6 +464,10 @@ int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double
 int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
                     float* gain, uint32_t* hits) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (!g || !gain || !hits || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 || num_rays < 1 ||
         tx_port < 0 || tx_port >= ctx->tx_ant.n_ports)
         return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map: bad arguments");
@@ -399,6 +480,10 @@ int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t nu
 int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays,
                                int64_t first_ray, int64_t ray_count, int32_t tx_port, float* gain, uint32_t* hits) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (!g || !gain || !hits || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 || num_rays < 1 ||
         first_ray < 0 || ray_count < 0 || first_ray + ray_count > num_rays || tx_port < 0 ||
         tx_port >= ctx->tx_ant.n_ports)
@@ -408,9 +493,40 @@ int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth,
     return launch_coverage(ctx, g, max_depth, num_rays, first_ray, ray_count, false, tx_port, gain, hits);
 }
 
+int rt_coverage_map_async(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
+                          uint32_t flags, int32_t blocks_per_sm, float* gain, uint32_t* hits) {
+    CHECK_CTX(ctx);
+    if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "coverage_map_async while capturing a graph");
+    if (!g || !gain || !hits || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 || num_rays < 1 ||
+        tx_port < 0 || tx_port >= ctx->tx_ant.n_ports || blocks_per_sm < 0 || (flags & ~RT_ASYNC_AFTER_TRACE))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_async: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_async: scene, transmitters and receivers must be set");
+    int e = side_join(ctx);   // one map at a time
+    if (e) return e;
+    if (!ctx->side) {
+        int least = 0, greatest = 0;
+        RT_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        RT_TRY(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least));
+        RT_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        RT_TRY(cudaEventCreateWithFlags(&ctx->ev_side, cudaEventDisableTiming));
+    }
+    RT_TRY(buf_reserve(ctx->side_counters, 64));
+    RT_TRY(buf_reserve(ctx->side_status, 64));
+    e = ensure_perm(ctx, num_rays);   // the ray order is built on the context stream
+    if (e) return e;
+    ctx->side_req = {*g, max_depth, tx_port, blocks_per_sm, num_rays, gain, hits};
+    ctx->side_deferred = true;
+    return (flags & RT_ASYNC_AFTER_TRACE) ? RT_OK : side_launch(ctx);
+}
+
 int rt_coverage_map_backward(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,
                              const float* grad_gain, float* grad_ypr) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     NO_CAPTURE(ctx, "coverage_map_backward");
     if (!g || !grad_gain || !grad_ypr || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || max_depth < 0 ||
         num_rays < 1 || tx_port < 0 || tx_port >= ctx->tx_ant.n_ports)
@@ -455,6 +571,14 @@ int rt_graph_begin(rt_ctx* ctx) {
     if (!ctx->cap_stream) RT_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     // the capture starts after everything already queued on the user's stream
     RT_TRY(cudaStreamSynchronize(ctx->stream));
+    {
+        int ej = side_launch(ctx);
+        if (ej) return ej;
+    }
+    if (ctx->side_pending) {
+        RT_TRY(cudaStreamSynchronize(ctx->side));
+        ctx->side_pending = false;
+    }
     ctx->user_stream = ctx->stream;
     ctx->stream = ctx->cap_stream;
     RT_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -504,6 +628,10 @@ int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes)
         (size_t)smem_nodes * 64 > 200 * 1024)
         return set_err(ctx, RT_ERR_INVALID_ARG,
                        "set_tuning: block 128|256, chunk 0 (auto) or >= 32, staged nodes <= 3200");
+    {
+        int ej = side_join(ctx);   // a deferred map is launched with the tuning it was requested with
+        if (ej) return ej;
+    }
     ctx->trace_block = block;
     ctx->warp_chunk = chunk;
     ctx->n_smem_nodes = smem_nodes;
@@ -513,6 +641,10 @@ int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes)
 int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, float* gain, uint32_t* hits,
                 const char* cache_path) {
     CHECK_CTX(ctx);
+    {
+        int ej = side_join(ctx);   // the map on the second stream reads what this call changes
+        if (ej) return ej;
+    }
     if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "autotune while capturing a graph");
     char key[160];
     snprintf(key, sizeof(key), "tris=%d tx=%d rays=%lld depth=%d cells=%dx%d", ctx->n_tris, ctx->n_tx,

@@ -61,6 +61,7 @@ struct rt_ctx {
     DevBuf keys, keys_alt, vals, vals_alt;       // SBR keys + positions
     DevBuf ray_hits;
     DevBuf cand_key, cand_wit, cand_off, cand_img; // candidates
+    DevBuf htab_key, htab_wit, htab_cnt;           // duplicate-removal hash table
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
     int64_t path_cap = 0;
@@ -71,6 +72,22 @@ struct rt_ctx {
 
     // scratch
     DevBuf sort_hist, scan_buf, counters, status;
+    // second stream for rt_coverage_map_async: its own work counter and
+    // status word; ev_side marks the end of the last map queued there
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_side = nullptr;
+    bool side_pending = false;
+    DevBuf side_counters, side_status;
+    // a map requested with RT_ASYNC_AFTER_TRACE, not launched yet
+    bool side_deferred = false;
+    struct SideReq {
+        rt_grid g;
+        int32_t D, tx_port, blocks_per_sm;
+        int64_t N;
+        float* gain;
+        uint32_t* hits;
+    } side_req{};
+    int grid_cap = 0;     // resident blocks per SM of a traversal launch (0 = occupancy limit)
     uint64_t* host_rb = nullptr;  // pinned host words for device -> host reads (RB_WORDS)
     DevBuf perm;          // direction-coherent ray order
     int64_t perm_n = -1;
@@ -78,6 +95,7 @@ struct rt_ctx {
     // tuning
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
     int bvh_builder = RT_BVH_PLOC;  // hierarchy over the Morton order: RT_BVH_KARRAS or RT_BVH_PLOC
+    int dedup = RT_DEDUP_HASH;      // candidate duplicate removal: RT_DEDUP_HASH or RT_DEDUP_SORT
     int trace_block = 256;
     int warp_chunk = 0;       // rays a warp takes per refill (0 = automatic: 32)
 
@@ -129,3 +147,8 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris);
 
 // ray order (direction-coherent permutation of [0, N))
 int ensure_perm(rt_ctx* ctx, int64_t N);
+// orders the context stream after the map of rt_coverage_map_async
+// (launching it first if it was deferred)
+int side_join(rt_ctx* ctx);
+// launches a deferred map on the second stream, after the work queued so far
+int side_launch(rt_ctx* ctx);

@@ -98,6 +98,23 @@ __global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, int n_tx
     }
 }
 
+// witness of every distinct key = the smallest position among its copies
+// (the sorted runs keep the append order, which the warps' atomics decide)
+__global__ void k_dedup_minwit(const uint64_t* __restrict__ k, const uint32_t* __restrict__ v, int64_t n,
+                               const uint64_t* __restrict__ ck, const uint32_t* __restrict__ Up,
+                               unsigned* __restrict__ cw) {
+    const int64_t U = *Up;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = k[i];
+        int64_t lo = 0, hi = U;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (ck[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        if (lo < U) atomicMin(&cw[lo], v[i]);
+    }
+}
+
 // per-tx candidate ranges: off[t] = first candidate with tx >= t
 __global__ void k_cand_off(const uint64_t* __restrict__ ck, const uint32_t* __restrict__ Up, int n_tx, KeyFmt f,
                            int64_t* __restrict__ off) {
@@ -109,6 +126,67 @@ __global__ void k_cand_off(const uint64_t* __restrict__ ck, const uint32_t* __re
         if (f.tx(ck[mid]) < t) lo = mid + 1; else hi = mid;
     }
     off[t] = lo;
+}
+
+// ---------------------------------------------------- hash duplicate removal
+// Candidate keys into an open-addressing table (linear probing, size a
+// power of two at least twice the key count, empty slots all ones, which no
+// key equals since keys are narrower than 64 bits); a slot's witness is the
+// smallest producing position (deterministic). The occupied slots are then
+// compacted and sorted, so the candidate order is the key order. The slot
+// hash is MurmurHash3's 64-bit finaliser (Appleby).
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+__global__ void k_hash_insert(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+                              unsigned long long* __restrict__ tab, unsigned* __restrict__ wit, uint64_t mask) {
+    // rays of one warp are coherent, so equal keys are merged in the warp first
+    // (one table access and one atomicMin per distinct key of the warp)
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool ok = i < n;
+        const unsigned long long k = ok ? keys[i] : ~0ull;
+        const unsigned v = ok ? vals[i] : 0xFFFFFFFFu;
+        const unsigned grp = __match_any_sync(0xffffffffu, k);
+        const unsigned vmin = __reduce_min_sync(grp, v);
+        if (!ok || lane != __ffs(grp) - 1) continue;
+        uint64_t h = mix64(k) & mask;
+        for (uint64_t probe = 0; probe <= mask; probe++) {   // the table is at most half full
+            unsigned long long cur = tab[h];
+            if (cur == ~0ull) cur = atomicCAS(&tab[h], ~0ull, k);
+            if (cur == ~0ull || cur == k) {
+                atomicMin(&wit[h], vmin);
+                break;
+            }
+            h = (h + 1) & mask;
+        }
+    }
+}
+
+__global__ void k_hash_compact(const unsigned long long* __restrict__ tab, const unsigned* __restrict__ wit,
+                               int64_t S, uint64_t* __restrict__ ck, uint32_t* __restrict__ cw,
+                               unsigned* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool occ = i < S && tab[i] != ~0ull;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned b0 = 0;
+    if (lane == leader) b0 = atomicAdd(count, (unsigned)__popc(m));
+    b0 = __shfl_sync(0xffffffffu, b0, leader);
+    if (occ) {
+        const unsigned pos = b0 + __popc(m & lanemask_lt());
+        ck[pos] = tab[i];
+        cw[pos] = wit[i];
+    }
 }
 
 // images I_k of the transmitter through the candidate's planes (FP32)
@@ -548,6 +626,10 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         }
         e = launch_sbr(ctx, N, f.D, keys, vals, hits);
         if (e) return e;
+        // a coverage map requested with RT_ASYNC_AFTER_TRACE starts here, so
+        // that it shares the GPU with the refinement below, not with the trace
+        e = side_launch(ctx);
+        if (e) return e;
         RT_TRY(cudaMemcpyAsync(ctx->host_rb, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS,
                                sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         RT_TRY(cudaStreamSynchronize(st));
@@ -560,36 +642,76 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
-    RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
-                        ctx->key_bits));
-    // duplicate removal
-    const uint64_t sentinel_from = ctx->key_bits >= 64 ? ~0ull : ((1ull << ctx->key_bits) - 1ull);
-    int nb = (int)std::max<int64_t>((nkeys + DD_TILE - 1) / DD_TILE, 1);
-    DevBuf& cnt = ctx->sort_hist;
-    RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * (nb + 1)));
-    uint32_t* cntp = bp<uint32_t>(cnt);
-    RT_TRY(cudaMemsetAsync(cntp, 0, sizeof(uint32_t) * (nb + 1), st));
-    if (nkeys > 0) {
-        prof_begin(ctx, "k_dedup_count");
-        k_dedup_count<<<nb, DD_THREADS, 0, st>>>(keys, nkeys, sentinel_from, cntp);
-        prof_end(ctx);
-        RT_TRY(cudaGetLastError());
-    }
-    RT_TRY(exclusive_scan_u32(ctx, cntp, nb + 1));
-    // From here the candidate count U = cntp[nb] stays on the device until
-    // the path count is read: buffers are sized for U <= nkeys.
-    const uint32_t* Ud = cntp + nb;
     const int64_t Ucap = std::max<int64_t>(nkeys, 1);
     RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * Ucap));
     RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * Ucap));
     RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
     RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * Ucap));
+    const uint32_t* Ud = nullptr;   // device candidate count
+    if (ctx->key_bits < 64 && ctx->dedup == RT_DEDUP_HASH) {
+        DevBuf& cnt = ctx->htab_cnt;
+        // duplicate removal by hashing, then a sort of the distinct keys only
+        int64_t S = 1024;
+        while (S < 2 * nkeys) S <<= 1;
+        RT_TRY(buf_reserve(ctx->htab_key, sizeof(uint64_t) * S));
+        RT_TRY(buf_reserve(ctx->htab_wit, sizeof(uint32_t) * S));
+        RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * 4));
+        RT_TRY(cudaMemsetAsync(ctx->htab_key.p, 0xFF, sizeof(uint64_t) * S, st));
+        RT_TRY(cudaMemsetAsync(ctx->htab_wit.p, 0xFF, sizeof(uint32_t) * S, st));
+        RT_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * 4, st));
+        uint32_t* cntp = bp<uint32_t>(cnt);
+        if (nkeys > 0) {
+            prof_begin(ctx, "k_hash_insert");
+            k_hash_insert<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
+                keys, vals, nkeys, bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit),
+                (uint64_t)(S - 1));
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+            prof_begin(ctx, "k_hash_compact");
+            k_hash_compact<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
+                bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit), S, bp<uint64_t>(ctx->cand_key),
+                bp<uint32_t>(ctx->cand_wit), cntp);
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+        }
+        RT_TRY(cudaMemcpyAsync(ctx->host_rb, cntp, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaStreamSynchronize(st));
+        const int64_t U = *reinterpret_cast<uint32_t*>(ctx->host_rb);
+        RT_TRY(radix_sort64(ctx, bp<uint64_t>(ctx->cand_key), bp<uint64_t>(ctx->keys_alt), bp<uint32_t>(ctx->cand_wit),
+                            bp<uint32_t>(ctx->vals_alt), U, ctx->key_bits));
+        Ud = cntp;
+    } else {
+        RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
+                            ctx->key_bits));
+        // duplicate removal of the sorted keys
+        DevBuf& cnt = ctx->sort_hist;
+        const uint64_t sentinel_from = ~0ull;
+        int nb = (int)std::max<int64_t>((nkeys + DD_TILE - 1) / DD_TILE, 1);
+        RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * (nb + 1)));
+        uint32_t* cntp = bp<uint32_t>(cnt);
+        RT_TRY(cudaMemsetAsync(cntp, 0, sizeof(uint32_t) * (nb + 1), st));
+        if (nkeys > 0) {
+            prof_begin(ctx, "k_dedup_count");
+            k_dedup_count<<<nb, DD_THREADS, 0, st>>>(keys, nkeys, sentinel_from, cntp);
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+        }
+        RT_TRY(exclusive_scan_u32(ctx, cntp, nb + 1));
+        Ud = cntp + nb;
+        if (nkeys > 0) {
+            prof_begin(ctx, "k_dedup_write");
+            k_dedup_write<<<nb, DD_THREADS, 0, st>>>(keys, vals, nkeys, sentinel_from, cntp,
+                                                     bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit));
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+            prof_begin(ctx, "k_dedup_minwit");
+            k_dedup_minwit<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
+                keys, vals, nkeys, bp<uint64_t>(ctx->cand_key), Ud, bp<unsigned>(ctx->cand_wit));
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+        }
+    }
     if (nkeys > 0) {
-        prof_begin(ctx, "k_dedup_write");
-        k_dedup_write<<<nb, DD_THREADS, 0, st>>>(keys, vals, nkeys, sentinel_from, cntp,
-                                                 bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit));
-        prof_end(ctx);
-        RT_TRY(cudaGetLastError());
         prof_begin(ctx, "k_cand_img");
         k_cand_img<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
             bp<uint64_t>(ctx->cand_key), Ud, f, bp<float>(ctx->tx_pos), bp<float4>(ctx->planes),

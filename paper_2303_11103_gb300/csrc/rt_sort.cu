@@ -1,14 +1,17 @@
-// rt_sort.cu -- LSD radix sort of 64-bit keys (optional 32-bit payload),
-// 8-bit digits. Used for Morton codes, BVH level order, candidate keys
-// (duplicate removal) and path keys. Three forms:
-//   - up to SS_MAX keys: one block, all passes in shared memory;
+// rt_sort.cu -- stable sort of 64-bit keys (optional 32-bit payload) by
+// their low end_bit bits (rounded up to whole bytes). Used for Morton codes,
+// BVH level order, candidate keys (duplicate removal) and path keys. Three
+// forms:
+//   - up to 8192 keys: a stable rank sort (each key's position is the count
+//     of smaller keys, ties by index), one launch, no digit passes;
 //   - up to 2^30 keys: one histogram kernel for every digit position, then
 //     one kernel per pass whose tiles find their global offsets by
 //     decoupled look-back over the preceding tiles (Merrill & Garland's
 //     single-pass prefix scan, as used by Adinets & Merrill's Onesweep);
 //   - larger: per pass a histogram kernel, a multi-block scan over
 //     (digit, tile) and a scatter kernel.
-// Every form ranks keys stably with warp match/ballot.
+// The digit passes (LSD radix, 8-bit digits) rank keys stably with warp
+// match/ballot.
 #include <algorithm>
 
 #include "rt_internal.h"
@@ -299,94 +302,87 @@ __global__ void __launch_bounds__(RS_THREADS) os_scatter(const uint64_t* __restr
     }
 }
 
-// Small inputs (<= SS_MAX keys): one block sorts in shared memory, all
-// passes in one launch. Each warp owns a contiguous chunk of the keys. Per
-// pass: the warps count their chunk's digits (warp match, one shared update
-// per distinct digit), one exclusive scan over (digit, warp) gives every
-// warp its first slot per digit, then the warps walk their chunks again in
-// order and scatter (stable: warp order, then step order, then lane order).
-constexpr int SS_THREADS = 1024, SS_WARPS = SS_THREADS / 32, SS_MAX = 6144;
+constexpr int RK_MAX = 256;   // up to this many keys: one-block rank sort
 
+// Tiny inputs (<= RK_MAX keys, one per thread): every key's output position
+// is the number of keys that are smaller, or equal with a smaller index
+// (stable); one shared-memory pass, no digit passes. Only the low end_bit
+// bits of the keys take part, as in the radix passes.
 template <bool VALS>
-__global__ void __launch_bounds__(SS_THREADS) k_sort_small(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                         int n, int passes) {
-    extern __shared__ __align__(16) unsigned char ss_raw[];
-    uint64_t* ka = reinterpret_cast<uint64_t*>(ss_raw);
-    uint64_t* kb = ka + SS_MAX;
-    uint32_t* cnt = reinterpret_cast<uint32_t*>(kb + SS_MAX);   // [SS_WARPS][256]
-    uint32_t* base = cnt + SS_WARPS * 256;                        // [256]
-    uint32_t* va = base + 256;
-    uint32_t* vb = va + SS_MAX;
+__global__ void __launch_bounds__(RK_MAX) k_sort_rank(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int n,
+                                                     uint64_t mask) {
+    __shared__ uint64_t sk[RK_MAX];
+    const int i = threadIdx.x;
+    uint64_t k = 0;
+    uint32_t v = 0;
+    if (i < n) {
+        k = keys[i];
+        if (VALS) v = vals[i];
+        sk[i] = k & mask;
+    }
+    __syncthreads();
+    int r = 0;
+    if (i < n) {
+        const uint64_t km = k & mask;
+        for (int j = 0; j < n; j++) {
+            const uint64_t o = sk[j];
+            r += (o < km) | ((o == km) & (j < i));
+        }
+    }
+    __syncthreads();   // every key has been read before the in-place writes
+    if (i < n) {
+        keys[r] = k;
+        if (VALS) vals[r] = v;
+    }
+}
+
+// Small inputs (RK_MAX < n <= RK_MULTI_MAX): the same stable rank sort
+// spread over the GPU. Every block stages all n (masked) keys in shared
+// memory and ranks 32 of them (one per lane); its 32 warps count the smaller
+// keys in 32 segments of the input (all lanes read the same key at a time:
+// broadcast), and the segment counts are summed in shared memory. When the
+// masked keys leave 13 bits free, a key's index is appended below it, which
+// makes all keys distinct and the stable rank one comparison per pair.
+// O(n^2) comparisons, but one launch and no digit passes.
+constexpr int RK_MULTI_MAX = 8192;   // index fits in 13 bits
+constexpr int RK_IDX_BITS = 13;
+
+template <bool VALS, bool COMP>
+__global__ void __launch_bounds__(1024) k_sort_rank_multi(const uint64_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ vals,
+                                                          uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                          int n, uint64_t mask) {
+    extern __shared__ uint64_t sk[];   // [n]
+    __shared__ int part[32][33];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const uint64_t o = __ldg(keys + j) & mask;
+        sk[j] = COMP ? ((o << RK_IDX_BITS) | (uint64_t)j) : o;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-    const int chunk = (n + SS_WARPS - 1) / SS_WARPS;
-    const int c0 = min(w * chunk, n), c1 = min(c0 + chunk, n);
-    for (int i = threadIdx.x; i < n; i += SS_THREADS) {
-        ka[i] = keys[i];
-        if (VALS) va[i] = vals[i];
+    const int i = blockIdx.x * 32 + lane;
+    const uint64_t km = sk[min(i, n - 1)];
+    const int seg = (n + 31) / 32;
+    const int j0 = min(w * seg, n), j1 = min(j0 + seg, n);
+    int r = 0;
+    if (COMP) {
+#pragma unroll 8
+        for (int j = j0; j < j1; j++) r += sk[j] < km;
+    } else {
+#pragma unroll 4
+        for (int j = j0; j < j1; j++) {
+            const uint64_t o = sk[j];
+            r += (o < km) | ((o == km) & (j < i));
+        }
     }
-    for (int p = 0; p < passes; p++) {
-        const int shift = 8 * p;
-        uint32_t* row = cnt + w * 256;
-        for (int q = lane; q < 256; q += 32) row[q] = 0;
-        __syncthreads();   // also orders the previous pass's scatter before these reads
-        for (int t = c0; t < c1; t += 32) {
-            int i = t + lane;
-            bool ok = i < c1;
-            unsigned act = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                unsigned dg = (unsigned)(ka[i] >> shift) & 255u;
-                unsigned peers = __match_any_sync(act, dg);
-                if ((peers & lt) == 0) row[dg] += __popc(peers);
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        uint32_t run = 0;
-        if (threadIdx.x < 256) {   // per digit: exclusive over warps, total to base
-            for (int ww = 0; ww < SS_WARPS; ww++) {
-                uint32_t c = cnt[ww * 256 + threadIdx.x];
-                cnt[ww * 256 + threadIdx.x] = run;
-                run += c;
-            }
-            base[threadIdx.x] = run;
-        }
-        __syncthreads();
-        if (w == 0) {   // exclusive scan of the 256 digit totals, 8 per lane
-            uint32_t v[8], sum = 0;
-            for (int q = 0; q < 8; q++) { v[q] = base[lane * 8 + q]; sum += v[q]; }
-            uint32_t x = sum;
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            uint32_t r = x - sum;
-            for (int q = 0; q < 8; q++) { base[lane * 8 + q] = r; r += v[q]; }
-        }
-        __syncthreads();
-        for (int t = c0; t < c1; t += 32) {
-            int i = t + lane;
-            bool ok = i < c1;
-            unsigned act = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                uint64_t k = ka[i];
-                unsigned dg = (unsigned)(k >> shift) & 255u;
-                unsigned peers = __match_any_sync(act, dg);
-                uint32_t pos = base[dg] + row[dg] + __popc(peers & lt);
-                kb[pos] = k;
-                if (VALS) vb[pos] = va[i];
-                __syncwarp(act);
-                if ((peers & lt) == 0) row[dg] += __popc(peers);
-            }
-            __syncwarp();
-        }
-        __syncthreads();
-        uint64_t* tk = ka; ka = kb; kb = tk;
-        uint32_t* tv = va; va = vb; vb = tv;
-    }
-    for (int i = threadIdx.x; i < n; i += SS_THREADS) {
-        keys[i] = ka[i];
-        if (VALS) vals[i] = va[i];
+    part[w][lane] = r;
+    __syncthreads();
+    if (w == 0 && i < n) {
+        int rr = 0;
+#pragma unroll
+        for (int q = 0; q < 32; q++) rr += part[q][lane];
+        kout[rr] = keys[i];
+        if (VALS) vout[rr] = vals[i];
     }
 }
 
@@ -396,22 +392,44 @@ cudaError_t radix_sort64(rt_ctx* ctx, uint64_t* keys, uint64_t* keys_alt, uint32
                          uint32_t* vals_alt, int64_t n, int end_bit) {
     if (n <= 1 || end_bit <= 0) return cudaSuccess;
     if (n > (int64_t)0xFFFFFFFFll) return cudaErrorInvalidValue;
-    if (n <= SS_MAX) {
-        const size_t smem = sizeof(uint64_t) * 2 * SS_MAX + sizeof(uint32_t) * (SS_WARPS * 256 + 256) +
-                            (vals ? sizeof(uint32_t) * 2 * SS_MAX : 0);
-        cudaError_t e;
-        prof_begin(ctx, "k_sort_small");
-        if (vals) {
-            e = ensure_smem_attr((const void*)k_sort_small<true>, smem);
-            if (e == cudaSuccess)
-                k_sort_small<true><<<1, SS_THREADS, smem, ctx->stream>>>(keys, vals, (int)n, (end_bit + 7) / 8);
-        } else {
-            e = ensure_smem_attr((const void*)k_sort_small<false>, smem);
-            if (e == cudaSuccess)
-                k_sort_small<false><<<1, SS_THREADS, smem, ctx->stream>>>(keys, nullptr, (int)n, (end_bit + 7) / 8);
-        }
+    if (n <= RK_MAX) {
+        const int bits = 8 * ((end_bit + 7) / 8);   // the bits the digit passes would order by
+        const uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
+        const int threads = 32 * (int)((n + 31) / 32);
+        prof_begin(ctx, "k_sort_rank");
+        if (vals)
+            k_sort_rank<true><<<1, threads, 0, ctx->stream>>>(keys, vals, (int)n, mask);
+        else
+            k_sort_rank<false><<<1, threads, 0, ctx->stream>>>(keys, nullptr, (int)n, mask);
         prof_end(ctx);
-        return e != cudaSuccess ? e : cudaGetLastError();
+        return cudaGetLastError();
+    }
+    if (n <= RK_MULTI_MAX) {
+        const int bits = 8 * ((end_bit + 7) / 8);
+        const uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
+        const bool comp = bits + RK_IDX_BITS <= 64;
+        const unsigned blocks = (unsigned)((n + 31) / 32);
+        const size_t smem = sizeof(uint64_t) * (size_t)n;
+        const void* fn = comp ? (vals ? (const void*)k_sort_rank_multi<true, true> : (const void*)k_sort_rank_multi<false, true>)
+                              : (vals ? (const void*)k_sort_rank_multi<true, false> : (const void*)k_sort_rank_multi<false, false>);
+        cudaError_t e = ensure_smem_attr(fn, smem);
+        if (e != cudaSuccess) return e;
+        prof_begin(ctx, "k_sort_rank_multi");
+        if (comp && vals)
+            k_sort_rank_multi<true, true><<<blocks, 1024, smem, ctx->stream>>>(keys, vals, keys_alt, vals_alt, (int)n, mask);
+        else if (comp)
+            k_sort_rank_multi<false, true><<<blocks, 1024, smem, ctx->stream>>>(keys, nullptr, keys_alt, nullptr, (int)n, mask);
+        else if (vals)
+            k_sort_rank_multi<true, false><<<blocks, 1024, smem, ctx->stream>>>(keys, vals, keys_alt, vals_alt, (int)n, mask);
+        else
+            k_sort_rank_multi<false, false><<<blocks, 1024, smem, ctx->stream>>>(keys, nullptr, keys_alt, nullptr, (int)n, mask);
+        prof_end(ctx);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(keys, keys_alt, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess && vals)
+            e = cudaMemcpyAsync(vals, vals_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, ctx->stream);
+        return e;
     }
     int nb = (int)((n + RS_TILE - 1) / RS_TILE);
     const int passes_all = (end_bit + 7) / 8;

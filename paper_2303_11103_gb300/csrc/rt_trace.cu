@@ -148,13 +148,19 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
             }
         }
         // append this bounce's candidate keys: equal keys within the warp
-        // are appended once (the lowest lane is the witness), one atomic per
-        // warp, ballot ranks
+        // are appended once, by the lowest lane, with the smallest position
+        // of the group (so the smallest over all appends is the smallest
+        // producing ray, whichever rays the warps held together); one atomic
+        // per warp, ballot ranks
         const unsigned em = __ballot_sync(0xffffffffu, emit);
         if (em) {
             const int lane = threadIdx.x & 31;
             bool keep = false;
-            if (emit) keep = (__match_any_sync(em, (unsigned long long)ekey) & lanemask_lt()) == 0;
+            if (emit) {
+                const unsigned grp = __match_any_sync(em, (unsigned long long)ekey);
+                epos = __reduce_min_sync(grp, epos);
+                keep = (grp & lanemask_lt()) == 0;
+            }
             const unsigned km = __ballot_sync(0xffffffffu, keep);
             const int leader = __ffs(km) - 1;
             unsigned long long b0 = 0;
@@ -387,6 +393,7 @@ __global__ void k_dirs(long long N, long long first, long long n, float* __restr
 int trace_grid(rt_ctx* ctx, const void* kernel, size_t smem) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ctx->trace_block, smem);
+    if (ctx->grid_cap > 0) per_sm = std::min(per_sm, ctx->grid_cap);
     if (per_sm < 1) per_sm = 1;
     return per_sm * ctx->num_sms;
 }
@@ -414,6 +421,8 @@ int launch_dirs(rt_ctx* ctx, int64_t N, int64_t first, int64_t n, float* out) {
 
 int ensure_perm(rt_ctx* ctx, int64_t N) {
     if (ctx->perm_n == N) return RT_OK;
+    int ej = side_join(ctx);   // a map on the second stream may still read the old order
+    if (ej) return ej;
     if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "first trace at a new num_rays while capturing a graph");
     if (N > 0xFFFFFFFFll) return set_err(ctx, RT_ERR_INVALID_ARG, "num_rays above 2^32");
     DevBuf k1, k2, v2;

@@ -67,6 +67,7 @@ def lib():
             "rt_load_scene": [vp, vp, i64, vp, vp, i32],
             "rt_set_materials": [vp, vp, i32],
             "rt_set_bvh_builder": [vp, i32],
+            "rt_set_dedup": [vp, i32],
             "rt_set_tx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna)],
             "rt_set_rx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna), vp],
             "rt_compute_paths": [vp, i32, i64, u32, ctypes.POINTER(i64)],
@@ -80,6 +81,8 @@ def lib():
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
             "rt_coverage_map_noalloc": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
+            "rt_coverage_map_async": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, u32, i32, vp, vp],
+            "rt_join": [vp],
             "rt_coverage_map_backward": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_cir_backward": [vp, u32, vp, vp, vp, vp, vp, vp],
             "rt_freq_response_backward": [vp, vp, vp, vp, i32, vp, vp, vp],
@@ -188,6 +191,13 @@ def rt_set_bvh_builder(ctx, builder):
     _check(ctx, lib().rt_set_bvh_builder(ctx, int(builder)))
 
 
+DEDUP_HASH, DEDUP_SORT = 0, 1
+
+
+def rt_set_dedup(ctx, mode):
+    _check(ctx, lib().rt_set_dedup(ctx, int(mode)))
+
+
 def rt_set_tx(ctx, pos, ypr, antenna):
     a = _antenna(antenna)
     _check(ctx, lib().rt_set_tx(ctx, _ptr(pos), _ptr(ypr), int(pos.shape[0]), ctypes.byref(a)))
@@ -254,6 +264,19 @@ def rt_coverage_map_accumulate(ctx, grid: rt_grid, max_depth, num_rays, first_ra
     _check(ctx, lib().rt_coverage_map_accumulate(ctx, ctypes.byref(grid), int(max_depth), int(num_rays),
                                                  int(first_ray), int(ray_count), int(tx_port), _ptr(gain),
                                                  _ptr(hits)))
+
+
+ASYNC_AFTER_TRACE = 1
+
+
+def rt_coverage_map_async(ctx, grid: rt_grid, max_depth, num_rays, tx_port, gain, hits, flags=0, blocks_per_sm=0):
+    """rt_coverage_map on the context's second stream, beside the calls that follow; rt_join before reading."""
+    _check(ctx, lib().rt_coverage_map_async(ctx, ctypes.byref(grid), int(max_depth), int(num_rays), int(tx_port),
+                                            int(flags), int(blocks_per_sm), _ptr(gain), _ptr(hits)))
+
+
+def rt_join(ctx):
+    _check(ctx, lib().rt_join(ctx))
 
 
 def rt_coverage_map_noalloc(ctx, grid: rt_grid, max_depth, num_rays, tx_port, gain, hits):
@@ -379,6 +402,10 @@ class Tracer:
     def set_bvh_builder(self, builder):
         """Hierarchy for the next load_scene: BVH_KARRAS or BVH_PLOC."""
         rt_set_bvh_builder(self.ctx, builder)
+
+    def set_dedup(self, mode):
+        """Candidate duplicate removal of compute_paths: DEDUP_HASH or DEDUP_SORT."""
+        rt_set_dedup(self.ctx, mode)
 
     def set_materials(self, mats):
         self.sync_stream()
@@ -510,6 +537,26 @@ class Tracer:
         hits = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.int32, device=self.device)
         rt_coverage_map(self.ctx, g, max_depth, num_rays, tx_port, gain, hits)
         return gain, hits
+
+    def coverage_map_async(self, grid: dict, max_depth: int, num_rays: int, tx_port: int = 0,
+                           after_trace: bool = False, blocks_per_sm: int = 0):
+        """coverage_map traced beside the calls that follow (after_trace: from the
+        next compute_paths' ray trace on); call join() before reading the tensors."""
+        self.sync_stream()
+        g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
+                    int(grid["nx"]), int(grid["ny"]))
+        gain = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.float32, device=self.device)
+        hits = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.int32, device=self.device)
+        rt_coverage_map_async(self.ctx, g, max_depth, num_rays, tx_port, gain, hits,
+                              ASYNC_AFTER_TRACE if after_trace else 0, blocks_per_sm)
+        self._async_out = (gain, hits)   # kept alive while the second stream may write them
+        return gain, hits
+
+    def join(self):
+        """Order the current stream after the last coverage_map_async."""
+        self.sync_stream()
+        rt_join(self.ctx)
+        self._async_out = None
 
     def coverage_map_ranges(self, grid: dict, max_depth: int, num_rays: int, ranges, tx_port: int = 0):
         """Coverage map accumulated over lattice ray ranges [(first, count), ...]."""

@@ -125,3 +125,36 @@ def test_builders_give_identical_hits(tracer, n_side):
 def test_unknown_builder_rejected(tracer):
     with pytest.raises(rt.RtError):
         tracer.set_bvh_builder(7)
+
+
+@pytest.mark.parametrize("n_tx", [1, 24])
+def test_dedup_modes_identical(tracer, n_tx):
+    """Hash and sort duplicate removal give the same candidates (sequences,
+    order and witness rays) and the same paths. With 24 rooftop transmitters
+    over the 4802-triangle city the distinct candidates outnumber the
+    8192-key one-launch sort, so the large-sort branch runs as well."""
+    sc = S.city_scene(n_side=20, size=500.0, seed=1)
+    _, rx = S.city_devices(sc, n_rx=16, half=240.0)
+    tx = S.rooftop_transmitters(sc, n_tx=n_tx)
+    N, D = 200003, 3
+    cands, sets, arrays = [], [], []
+    try:
+        for mode in (rt.DEDUP_HASH, rt.DEDUP_SORT):
+            tracer.set_dedup(mode)
+            setup(tracer, sc, tx, rx)
+            tracer.compute_paths(D, N)
+            cands.append([x.cpu().numpy().copy() for x in tracer.candidates()])
+            s, p = gpu_paths(tracer)
+            sets.append(s)
+            arrays.append({k: v.cpu().numpy().copy() for k, v in p.items() if torch.is_tensor(v)})
+    finally:
+        tracer.set_dedup(rt.DEDUP_HASH)
+    for a, b in zip(cands[0], cands[1]):
+        assert np.array_equal(a, b)
+    assert sets[0] == sets[1]
+    for k in arrays[0]:
+        assert np.array_equal(arrays[0][k], arrays[1][k]), k
+    if n_tx > 1:
+        assert len(cands[0][0]) > 8192
+    with pytest.raises(rt.RtError):
+        tracer.set_dedup(5)
