@@ -504,7 +504,8 @@ def run_reference(args):
 
 def run_kernel_case(args):
     """One kernel of the step on its own (for ncu captures):
-    `--only coverage|paths|freq|mlp_infer|mlp_train`."""
+    `--only coverage|paths|freq|tail|mlp_infer|mlp_train`; tail = compute_paths,
+    cir, H(f) and both VJPs (the calls after the ray trace)."""
     import torch
     from paper_2303_11103_gb300 import rt
     from paper_2303_11103_gb300 import scenes as S
@@ -530,7 +531,7 @@ def run_kernel_case(args):
     tr = rt.Tracer(0, FC)
     tr.load_scene(scene)
     tr.set_devices(tx, rx)
-    if args.only == "freq":
+    if args.only in ("freq", "tail"):
         tr.compute_paths(MAX_DEPTH, args.rays)
         a, tau = tr.cir_raw()
         freqs = (np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING
@@ -539,6 +540,12 @@ def run_kernel_case(args):
             g, h = tr.coverage_map(GRID, MAX_DEPTH, args.rays, 0)
         elif args.only == "freq":
             tr.freq_response_raw(a, tau, freqs)
+        elif args.only == "tail":
+            tr.compute_paths(MAX_DEPTH, args.rays)
+            ac, tauc = tr.cir()
+            Hc = tr.freq_response(ac, tauc, freqs)
+            ga, gt = tr.freq_response_backward(ac, tauc, freqs, Hc)
+            tr.cir_backward(ga, gt)
         else:
             tr.compute_paths(MAX_DEPTH, args.rays)
     torch.cuda.synchronize()
@@ -547,7 +554,7 @@ def run_kernel_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["coverage", "paths", "freq", "mlp_infer", "mlp_train"], default=None,
+    ap.add_argument("--only", choices=["coverage", "paths", "freq", "tail", "mlp_infer", "mlp_train"], default=None,
                     help="run one kernel case of the step (profiling)")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate queries (--only mlp_*)")

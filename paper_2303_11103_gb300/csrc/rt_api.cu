@@ -63,6 +63,7 @@ DevScene dev_scene(rt_ctx* ctx) {
     s.tris = bp<float4>(ctx->tris);
     s.tris_o = bp<float4>(ctx->tris_o);
     s.planes = bp<float4>(ctx->planes);
+    s.pl64 = bp<double2>(ctx->planes64);
     s.mat = bp<int32_t>(ctx->mat);
     s.mats = bp<float2>(ctx->mats);
     s.big = bp<float4>(ctx->tris) + 3 * (size_t)ctx->n_bvh;
@@ -219,7 +220,7 @@ int rt_destroy(rt_ctx* ctx) {
         buf_free(ctx->side_counters);
         buf_free(ctx->side_status);
     }
-    for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->mat, &ctx->mats, &ctx->tx_pos,
+    for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->planes64, &ctx->mat, &ctx->mats, &ctx->tx_pos,
                       &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->keys, &ctx->keys_alt,
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
                       &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->path_key,

@@ -40,6 +40,19 @@ __device__ __forceinline__ float unord(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+// FP64 planes of the triangles (for path lengths): one warp per block, so
+// that the few FP64 units of many SMs share the work.
+__global__ void k_planes64(const float4* __restrict__ tris_o, int T, double2* __restrict__ pl64) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    const float4 r0 = tris_o[3 * (size_t)i], r1 = tris_o[3 * (size_t)i + 1], r2 = tris_o[3 * (size_t)i + 2];
+    double n[3];
+    plane64(r1, r2, n);
+    pl64[3 * (size_t)i] = make_double2(n[0], n[1]);
+    pl64[3 * (size_t)i + 1] = make_double2(n[2], (double)r0.x);
+    pl64[3 * (size_t)i + 2] = make_double2((double)r0.y, (double)r0.z);
+}
+
 // bounds layout (ordered uints): [0..2] vmin, [3..5] vmax, [6..8] cmin, [9..11] cmax
 __global__ void k_prep(const float* __restrict__ v, const int32_t* __restrict__ mat, int T,
                        float4* __restrict__ tris_o, float4* __restrict__ planes,
@@ -486,6 +499,7 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     RT_TRY(buf_reserve(ctx->tris_o, sizeof(float4) * 3 * (size_t)T));
     RT_TRY(buf_reserve(ctx->tris, sizeof(float4) * 3 * (size_t)T));
     RT_TRY(buf_reserve(ctx->planes, sizeof(float4) * (size_t)T));
+    RT_TRY(buf_reserve(ctx->planes64, sizeof(double2) * 3 * (size_t)std::max(T, 1)));
     int m = std::max(T - 1, 1);
     RT_TRY(buf_reserve(ctx->nodes, sizeof(float4) * 4 * (size_t)m));
     // build scratch, kept in the context between builds
@@ -509,6 +523,12 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
                              lbox, bp<float>(ctx->b_cent), info);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
+    if (T > 0) {
+        prof_begin(ctx, "k_planes64");
+        k_planes64<<<(T + 31) / 32, 32, 0, st>>>(bp<float4>(ctx->tris_o), T, bp<double2>(ctx->planes64));
+        prof_end(ctx);
+        RT_TRY(cudaGetLastError());
+    }
     prof_begin(ctx, "k_morton");
     k_morton<<<gT, B, 0, st>>>(bp<float>(ctx->b_cent), lbox, T, info, keys, vals, info + 12);
     prof_end(ctx);

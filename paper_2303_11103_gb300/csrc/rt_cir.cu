@@ -323,37 +323,53 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
 }
 
 // VJP of H: grad_a_i = sum_k gH_k conj(w_ik); grad_tau_i = sum_k Re(conj(gH_k) a_i (-j 2 pi f_k) w_ik).
-// One block per pair, one warp per path (the pair's paths in parallel, 4 at
-// a time), lanes over the subcarriers, warp-shuffle reductions.
+// One warp per path (all paths in parallel, whatever their pairs), lanes
+// over the subcarriers, warp-shuffle reductions; the path's pair is the high
+// half of its sorted path key.
 template <int NP>
-__global__ void __launch_bounds__(128) k_freq_vjp(const int64_t* __restrict__ off, const float2* __restrict__ a,
-                                                  const float* __restrict__ tau, const double* __restrict__ freqs,
-                                                  int K, const float2* __restrict__ gH, float2* __restrict__ ga,
+__global__ void __launch_bounds__(128) k_freq_vjp(const uint64_t* __restrict__ pkey, int64_t P,
+                                                  const float2* __restrict__ a, const float* __restrict__ tau,
+                                                  const double* __restrict__ freqs, int K,
+                                                  const float2* __restrict__ gH, float2* __restrict__ ga,
                                                   float* __restrict__ gt) {
-    const int64_t pair = blockIdx.x;
-    const int64_t b = off[pair], e = off[pair + 1];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t i = b + w; i < e; i += nw) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i < P) {
+        const int64_t pair = (int64_t)(pkey[i] >> 32);
         const float t = tau[i];
         float2 av[NP];
         for (int q = 0; q < NP; q++) av[q] = a[i * NP + q];
         float sr[NP], si[NP], sg = 0.0f;
         for (int q = 0; q < NP; q++) { sr[q] = 0.0f; si[q] = 0.0f; }
-        for (int k = lane; k < K; k += 32) {
-            float f = (float)freqs[k];
-            float cyc = f * t;
-            cyc -= rintf(cyc);
-            float wi, wr;
-            __sincosf(-2.0f * RT_PI_F * cyc, &wi, &wr);
-            const float c = 2.0f * RT_PI_F * f;
-            for (int q = 0; q < NP; q++) {
-                float2 g = gH[(pair * NP + q) * K + k];
-                // g * conj(w)
-                sr[q] += g.x * wr + g.y * wi;
-                si[q] += g.y * wr - g.x * wi;
-                // Re(conj(g) * a * (-j 2 pi f) * w): (-j c)(awr + j awi) = c awi - j c awr
-                float awr = av[q].x * wr - av[q].y * wi, awi = av[q].x * wi + av[q].y * wr;
-                sg += g.x * (c * awi) + g.y * (-c * awr);
+        // FV subcarriers per lane and step, their loads issued together
+        constexpr int FV = 4;
+        for (int k0 = lane; k0 < K; k0 += 32 * FV) {
+            float fv[FV];
+            float2 gv[FV][NP];
+#pragma unroll
+            for (int u = 0; u < FV; u++) {
+                const int k = k0 + 32 * u;
+                fv[u] = k < K ? (float)freqs[k] : 0.0f;
+#pragma unroll
+                for (int q = 0; q < NP; q++) gv[u][q] = k < K ? gH[(pair * NP + q) * K + k] : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < FV; u++) {
+                const float f = fv[u];
+                float cyc = f * t;
+                cyc -= rintf(cyc);
+                float wi, wr;
+                __sincosf(-2.0f * RT_PI_F * cyc, &wi, &wr);
+                const float c = 2.0f * RT_PI_F * f;
+                for (int q = 0; q < NP; q++) {
+                    float2 g = gv[u][q];
+                    // g * conj(w)
+                    sr[q] += g.x * wr + g.y * wi;
+                    si[q] += g.y * wr - g.x * wi;
+                    // Re(conj(g) * a * (-j 2 pi f) * w): (-j c)(awr + j awi) = c awi - j c awr
+                    float awr = av[q].x * wr - av[q].y * wi, awi = av[q].x * wi + av[q].y * wr;
+                    sg += g.x * (c * awi) + g.y * (-c * awr);
+                }
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -404,9 +420,13 @@ void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* fr
 template <int NP>
 void launch_freq_vjp(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K,
                      const float* gH, float* ga, float* gt, int64_t n_pairs) {
+    (void)n_pairs;
+    const int64_t P = ctx->n_paths;
+    if (P <= 0) return;
     prof_begin(ctx, "k_freq_vjp");
-    k_freq_vjp<NP><<<(unsigned)n_pairs, 128, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau,
-                                                               freqs, K, (const float2*)gH, (float2*)ga, gt);
+    k_freq_vjp<NP><<<(unsigned)((P + 3) / 4), 128, 0, ctx->stream>>>(bp<uint64_t>(ctx->path_key), P, (const float2*)a,
+                                                                     tau, freqs, K, (const float2*)gH, (float2*)ga,
+                                                                     gt);
     prof_end(ctx);
 }
 

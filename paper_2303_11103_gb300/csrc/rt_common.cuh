@@ -48,6 +48,7 @@ struct DevScene {
     const float4* __restrict__ big;     // [n_big*3] large triangles, tested by every query
     const float4* __restrict__ tris_o;  // [T*3] original order (same record layout)
     const float4* __restrict__ planes;  // [T] original order: n, n.v0
+    const double2* __restrict__ pl64;   // [T*3] original order: (n.x, n.y), (n.z, v0.x), (v0.y, v0.z) in FP64
     const int32_t* __restrict__ mat;    // [T] original order
     const float2* __restrict__ mats;    // [M] eps_r, sigma
     int n_tris, n_nodes, n_mat, n_big;
@@ -315,17 +316,28 @@ __device__ __forceinline__ f3 fib_dir(long long N, long long i) {
 // Length of the specular path tx -> triangles ids[0..K-1] -> rx, in FP64:
 // for a specular path it equals |rx - I_K|, I_K the last image of tx, with
 // the planes' normals taken in FP64 from the stored FP32 triangle edges.
+// FP64 unit normal of a triangle from its FP32 edge vectors (computed once
+// per triangle at scene load; path lengths reuse it).
+__device__ __forceinline__ void plane64(float4 r1, float4 r2, double n[3]) {
+    double e1[3] = {r1.x, r1.y, r1.z}, e2[3] = {r2.x, r2.y, r2.z};
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double inl = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    n[0] *= inl;
+    n[1] *= inl;
+    n[2] *= inl;
+}
+
+// Length of the specular path tx -> triangles ids[0..K) -> rx in FP64: the
+// distance from rx to the last image of tx (images through the triangles'
+// FP64 planes).
 __device__ __forceinline__ double path_length64(const DevScene& s, const int32_t* ids, int K, f3 tx, f3 rx) {
     double I[3] = {(double)tx.x, (double)tx.y, (double)tx.z};
     for (int k = 0; k < K; k++) {
-        const float4* tp = s.tris_o + 3 * (size_t)ids[k];
-        float4 r0 = tp[0], r1 = tp[1], r2 = tp[2];
-        double e1[3] = {r1.x, r1.y, r1.z}, e2[3] = {r2.x, r2.y, r2.z}, v0[3] = {r0.x, r0.y, r0.z};
-        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-        double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        n[0] /= nl;
-        n[1] /= nl;
-        n[2] /= nl;
+        const double2* pp = s.pl64 + 3 * (size_t)ids[k];
+        const double2 p0 = pp[0], p1 = pp[1], p2 = pp[2];
+        const double n[3] = {p0.x, p0.y, p1.x}, v0[3] = {p1.y, p2.x, p2.y};
         double sd = (I[0] - v0[0]) * n[0] + (I[1] - v0[1]) * n[1] + (I[2] - v0[2]) * n[2];
         for (int q = 0; q < 3; q++) I[q] -= 2.0 * sd * n[q];
     }

@@ -43,6 +43,7 @@ struct rt_ctx {
     int n_bvh = 0, n_big = 0;  // triangles in the hierarchy / tested directly (large)
     float tmin = 0.0f, extent = 1.0f;
     DevBuf nodes, tris, tris_o, planes, mat, mats;
+    DevBuf planes64;   // [T*3] double2: FP64 unit normal and first vertex per triangle (original order)
 
     // devices
     int n_tx = 0, n_rx = 0;
