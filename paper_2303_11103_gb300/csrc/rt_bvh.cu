@@ -208,6 +208,7 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int n, int2* __restrict
 // (leaf boxes padded as in the refit), so no refit pass is needed.
 constexpr int PLOC_C = 1024;
 constexpr int PLOC_R = 16;
+constexpr int PLOC_W = PLOC_C / 32;   // warps of a chunk block (at most 32)
 
 __device__ __forceinline__ float half_area(float lx, float ly, float lz, float hx, float hy, float hz) {
     float dx = hx - lx, dy = hy - ly, dz = hz - lz;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* _
     float* sb = ploc_sm;                                          // [2][6][PLOC_C]
     int* sid = reinterpret_cast<int*>(ploc_sm + 12 * PLOC_C);    // [2][PLOC_C]
     int* snn = sid + 2 * PLOC_C;                                  // [PLOC_C]
-    __shared__ unsigned wk[PLOC_C / 32], wm[PLOC_C / 32];
+    __shared__ unsigned wk[PLOC_W], wm[PLOC_W];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int c0 = blockIdx.x * PLOC_C;
     const int L = min(PLOC_C, count - c0);
@@ -288,17 +289,19 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* _
         if (lane == 0) { wk[w] = __popc(bk); wm[w] = __popc(bm); }
         __syncthreads();
         if (w == 0) {
-            unsigned a = wk[lane], b = wm[lane];
+            unsigned a = lane < PLOC_W ? wk[lane] : 0u, b = lane < PLOC_W ? wm[lane] : 0u;
             for (int o = 1; o < 32; o <<= 1) {
                 unsigned ya = __shfl_up_sync(0xffffffffu, a, o), yb = __shfl_up_sync(0xffffffffu, b, o);
                 if (lane >= o) { a += ya; b += yb; }
             }
-            wk[lane] = a;   // inclusive
-            wm[lane] = b;
+            if (lane < PLOC_W) {
+                wk[lane] = a;   // inclusive
+                wm[lane] = b;
+            }
         }
         __syncthreads();
         const unsigned lt = lanemask_lt();
-        const int K = (int)wk[31], M = (int)wm[31];
+        const int K = (int)wk[PLOC_W - 1], M = (int)wm[PLOC_W - 1];
         if (keep) {
             const int kpos = (w > 0 ? (int)wk[w - 1] : 0) + __popc(bk & lt);
             if (merge) {

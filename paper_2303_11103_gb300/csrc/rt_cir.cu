@@ -218,7 +218,8 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
 // Twiddles: with uniform spacing one range-reduced sincos for the first
 // subcarrier and one for the 128-subcarrier step per (path, thread), then a
 // complex-rotation recurrence; otherwise a sincos per (path, subcarrier).
-// Pairs without paths write zeros.
+// H is cleared by a memset first, so the blocks of pairs without paths
+// return at once.
 constexpr int HF_RUN = 8;
 constexpr int HF_TILE = 64;
 constexpr int HF_THREADS = 128;
@@ -232,16 +233,7 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
     const int64_t pair = blockIdx.x;
     const int64_t b = off[pair], e = off[pair + 1];
     const int kb = blockIdx.y * HF_THREADS * HF_RUN + threadIdx.x;
-    if (b == e) {
-#pragma unroll
-        for (int q = 0; q < NP; q++)
-#pragma unroll
-            for (int s = 0; s < HF_RUN; s++) {
-                const int k = kb + s * HF_THREADS;
-                if (k < K) H[(pair * NP + q) * K + k] = make_float2(0.0f, 0.0f);
-            }
-        return;
-    }
+    if (b == e) return;   // H was cleared before the launch
     float2 acc[HF_RUN][NP];
 #pragma unroll
     for (int s = 0; s < HF_RUN; s++)
@@ -408,13 +400,16 @@ CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
 }
 
 template <int NP>
-void launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
-                 int64_t n_pairs) {
+cudaError_t launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
+                        int64_t n_pairs) {
     dim3 grid((unsigned)n_pairs, (unsigned)((K + HF_THREADS * HF_RUN - 1) / (HF_THREADS * HF_RUN)));
+    cudaError_t e = cudaMemsetAsync(H, 0, sizeof(float2) * NP * (size_t)K * (size_t)n_pairs, ctx->stream);
+    if (e != cudaSuccess) return e;
     prof_begin(ctx, "k_freq");
     k_freq<NP><<<grid, HF_THREADS, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
                                               (float2*)H);
     prof_end(ctx);
+    return cudaGetLastError();
 }
 
 template <int NP>
@@ -459,9 +454,9 @@ int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs
     if (K <= 0 || n_pairs <= 0) return RT_OK;
     const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
     switch (np) {
-        case 1: launch_freq<1>(ctx, a, tau, freqs, K, H, n_pairs); break;
-        case 2: launch_freq<2>(ctx, a, tau, freqs, K, H, n_pairs); break;
-        default: launch_freq<4>(ctx, a, tau, freqs, K, H, n_pairs); break;
+        case 1: RT_TRY(launch_freq<1>(ctx, a, tau, freqs, K, H, n_pairs)); break;
+        case 2: RT_TRY(launch_freq<2>(ctx, a, tau, freqs, K, H, n_pairs)); break;
+        default: RT_TRY(launch_freq<4>(ctx, a, tau, freqs, K, H, n_pairs)); break;
     }
     RT_TRY(cudaGetLastError());
     return RT_OK;
