@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -89,6 +90,24 @@ cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) cur = bytes;
     return e;
+}
+
+int blocks_per_sm(const void* kernel, int block, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(dev, kernel, block, smem);
+    auto it = done.find(key);
+    if (it != done.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    done[key] = n;
+    return n;
 }
 
 void prof_begin(rt_ctx* ctx, const char* name) {

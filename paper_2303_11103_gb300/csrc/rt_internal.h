@@ -122,6 +122,8 @@ struct rt_ctx {
 // least `bytes` (the attribute call is made once per kernel, device and size
 // increase; thread-safe).
 cudaError_t ensure_smem_attr(const void* kernel, size_t bytes);
+// resident blocks per SM of kernel at (block, dynamic shared memory), cached per device
+int blocks_per_sm(const void* kernel, int block, size_t smem);
 
 void prof_begin(rt_ctx* ctx, const char* name);
 void prof_end(rt_ctx* ctx);

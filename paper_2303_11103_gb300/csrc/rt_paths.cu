@@ -760,8 +760,7 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm + val_warp_bytes(f.D) * 8;
             auto kern = ctx->count_work ? k_validate<true> : k_validate<false>;
             RT_TRY(ensure_smem_attr((const void*)kern, smem));
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+            const int per_sm = blocks_per_sm((const void*)kern, 256, smem);
             // persistent grid: the work total is read on the device
             const int64_t units = nkeys * std::max<int64_t>((n_pairs / std::max(ctx->n_tx, 1) + 31) / 32, 1);
             const int64_t need = (units + 7) / 8;   // 8 warps per block

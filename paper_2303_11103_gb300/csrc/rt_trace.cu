@@ -391,8 +391,7 @@ __global__ void k_dirs(long long N, long long first, long long n, float* __restr
 }
 
 int trace_grid(rt_ctx* ctx, const void* kernel, size_t smem) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ctx->trace_block, smem);
+    int per_sm = blocks_per_sm(kernel, ctx->trace_block, smem);
     if (ctx->grid_cap > 0) per_sm = std::min(per_sm, ctx->grid_cap);
     if (per_sm < 1) per_sm = 1;
     return per_sm * ctx->num_sms;
