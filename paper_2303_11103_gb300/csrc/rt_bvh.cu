@@ -263,17 +263,38 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* _
         if (t < cur) {
             lx = rb[t]; ly = rb[PLOC_C + t]; lz = rb[2 * PLOC_C + t];
             hx = rb[3 * PLOC_C + t]; hy = rb[4 * PLOC_C + t]; hz = rb[5 * PLOC_C + t];
+        }
+        {
+            // nearest neighbour of every cluster: G lanes per cluster (as many
+            // as the block has to spare, at most 32), each scanning an equal
+            // share of the +-PLOC_R window in increasing position order; the
+            // shares are combined by (area, position), which keeps the
+            // sequential scan's choice (the lowest position of the smallest
+            // area), so the tree does not depend on G
+            int G = 1;
+            while (G < 32 && 2 * G * cur <= PLOC_C) G *= 2;
+            const int ci = t / G, part = t - ci * G;
             float best = __int_as_float(0x7f800000);
-            int bj = t > 0 ? t - 1 : 1;
-            const int j0 = max(0, t - PLOC_R), j1 = min(cur - 1, t + PLOC_R);
-            for (int j = j0; j <= j1; j++) {
-                if (j == t) continue;
-                float c = half_area(fminf(lx, rb[j]), fminf(ly, rb[PLOC_C + j]), fminf(lz, rb[2 * PLOC_C + j]),
-                                    fmaxf(hx, rb[3 * PLOC_C + j]), fmaxf(hy, rb[4 * PLOC_C + j]),
-                                    fmaxf(hz, rb[5 * PLOC_C + j]));
-                if (c < best) { best = c; bj = j; }
+            int bj = 0x7fffffff;
+            if (ci < cur) {
+                const float bx0 = rb[ci], by0 = rb[PLOC_C + ci], bz0 = rb[2 * PLOC_C + ci];
+                const float bx1 = rb[3 * PLOC_C + ci], by1 = rb[4 * PLOC_C + ci], bz1 = rb[5 * PLOC_C + ci];
+                const int per = (2 * PLOC_R) / G;   // window offsets -R..-1, 1..R in order, `per` per lane
+                for (int q = part * per; q < (part + 1) * per; q++) {
+                    const int j = ci + (q < PLOC_R ? q - PLOC_R : q - PLOC_R + 1);
+                    if (j < 0 || j >= cur) continue;
+                    float c = half_area(fminf(bx0, rb[j]), fminf(by0, rb[PLOC_C + j]), fminf(bz0, rb[2 * PLOC_C + j]),
+                                        fmaxf(bx1, rb[3 * PLOC_C + j]), fmaxf(by1, rb[4 * PLOC_C + j]),
+                                        fmaxf(bz1, rb[5 * PLOC_C + j]));
+                    if (c < best) { best = c; bj = j; }
+                }
             }
-            snn[t] = bj;
+            for (int o = G >> 1; o > 0; o >>= 1) {   // G is the same for the whole block
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+            }
+            if (ci < cur && part == 0) snn[ci] = bj != 0x7fffffff ? bj : (ci > 0 ? ci - 1 : 1);
         }
         __syncthreads();
         int j = -1;

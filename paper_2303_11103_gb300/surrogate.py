@@ -156,10 +156,12 @@ def time_inference(sur: rt.Surrogate, n: int, lo, hi, reps: int = 3, seed: int =
     return n / (best / 1e3), best
 
 
-def time_tracer_queries(tracer: rt.Tracer, tx_pos, rx_pos, num_rays: int, max_depth: int):
-    """Tracer (tx, rx) queries per second: compute_paths + cir + pair gain."""
+def time_tracer_queries(tracer: rt.Tracer, tx_pos, rx_pos, num_rays: int, max_depth: int, n_rx=None):
+    """Tracer (tx, rx) queries per second: compute_paths + cir + pair gain for
+    the first transmitter and its first n_rx receivers (all when None) in one
+    call, so the ray trace is shared by those receivers."""
     txd = S.Devices(tx_pos[:1], np.zeros((1, 3), np.float32), S.V_ISO)
-    rxs = rx_pos[0]
+    rxs = rx_pos[0] if n_rx is None else rx_pos[0][:n_rx]
     tracer.set_tx(txd.pos, txd.ypr, txd.antenna)
     tracer.set_rx(rxs, np.zeros_like(rxs), S.V_ISO)
     for _ in range(2):
