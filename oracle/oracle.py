@@ -309,6 +309,40 @@ def path_field(osc: OScene, fc: float, txdev, rxdev, tx_index: int, paths, grad:
     return a, tau, da, dtau[:P, :ng]
 
 
+def doppler(a: np.ndarray, paths, tx, rxs, fc: float, fs: float, n_steps: int, v_tx, v_rx=None) -> np.ndarray:
+    """Time evolution of the channel coefficients from the devices' motion
+    (Sec. II-A, Listing 3: apply_doppler with a sampling frequency, a number
+    of time steps and velocity vectors of the transmitters and receivers).
+
+    Path i leaves the transmitter in the unit direction k_t (towards its
+    first reflection point, or the receiver) and reaches the receiver in the
+    unit direction k_r (from its last reflection point, or the transmitter).
+    Its Doppler shift is f_D = (v_tx . k_t - v_rx . k_r) / lambda, the rate of
+    change of -(path length) / lambda when the devices move, and
+    a_i(t_n) = a_i exp(j 2 pi f_D t_n) at t_n = n / fs, n = 0..n_steps-1. The
+    delays are kept.
+
+    a [P, ...] complex, paths with .points [K, 3] and .rx, tx [3], rxs [R, 3],
+    v_tx [3], v_rx [R, 3] or None -> [P, ..., n_steps] complex128.
+    """
+    lam = C0 / fc
+    t = np.arange(n_steps, dtype=np.float64) / fs
+    out = np.zeros(np.shape(a) + (n_steps,), np.complex128)
+    txp = np.asarray(tx, np.float64)
+    vt = np.asarray(v_tx, np.float64)
+    for i, p in enumerate(paths):
+        rxp = np.asarray(rxs[p.rx], np.float64)
+        pts = [txp] + [np.asarray(q, np.float64) for q in p.points] + [rxp]
+        kt = (pts[1] - pts[0]) / np.linalg.norm(pts[1] - pts[0])
+        kr = (pts[-1] - pts[-2]) / np.linalg.norm(pts[-1] - pts[-2])
+        fd = np.dot(vt, kt)
+        if v_rx is not None:
+            fd -= np.dot(np.asarray(v_rx[p.rx], np.float64), kr)
+        fd /= lam
+        out[i] = np.asarray(a[i])[..., None] * np.exp(2j * np.pi * fd * t)
+    return out
+
+
 def subcarrier_freqs(K: int, spacing: float) -> np.ndarray:
     """Baseband subcarrier offsets f_k = (k - K/2) * spacing (k = 0..K-1)."""
     return (np.arange(K, dtype=np.float64) - K // 2) * spacing

@@ -455,3 +455,68 @@ def test_coverage_two_ray_incoherent():
     rel = np.abs(g - want) / want
     assert np.all(rel < 0.05)
     assert np.median(rel) < 0.02
+
+
+# ---------------------------------------------------------------- Doppler
+def test_doppler_los_closed_forms():
+    """LOS: a transmitter closing in on the receiver at v shifts by +v/lambda,
+    one moving across the line of sight by 0, a receiver moving away by -v/lambda."""
+    osc = O.make_scene(_single_far_triangle_scene())
+    tx = np.array([0.0, 0.0, 10.0])
+    rx = np.array([[120.0, 0.0, 10.0]])
+    paths, _ = O.compute_paths(osc, tx, rx.astype(np.float32), D=1, N=100)
+    a = np.array([[[0.3 - 0.4j]]])
+    fs, n = 1e6, 14
+    t = np.arange(n) / fs
+    for vt, vr, fd in [([5.0, 0, 0], None, 5.0 / LAM), ([0, 7.0, 0], None, 0.0),
+                       ([0, 0, 0], [[4.0, 0, 0]], -4.0 / LAM), ([3.0, 0, 0], [[3.0, 0, 0]], 0.0)]:
+        out = O.doppler(a, paths, tx, rx, FC, fs, n, vt, None if vr is None else np.array(vr))
+        assert np.allclose(out[0, 0, 0], a[0, 0, 0] * np.exp(2j * np.pi * fd * t), rtol=1e-12, atol=0)
+
+
+def test_doppler_ground_reflection_closed_form():
+    """Two-ray geometry: the ground path leaves the transmitter at the angle
+    theta below the horizon with tan(theta) = (h1 + h2) / d, so a horizontal
+    transmitter velocity v towards the receiver shifts it by v cos(theta) / lambda."""
+    osc = O.make_scene(S.ground_only_scene(2000.0))
+    h1, h2, d = 25.0, 1.5, 230.0
+    tx = np.array([0.0, 0.0, h1])
+    rx = np.array([[d, 0.0, h2]])
+    paths, _ = O.compute_paths(osc, tx, rx.astype(np.float32), D=1, N=20000)
+    paths = [p for p in paths if p.valid]
+    assert sorted(len(p.seq) for p in paths) == [0, 1]
+    a = np.ones((len(paths), 1, 1), complex)
+    v = 3.0
+    out = O.doppler(a, paths, tx, rx, FC, 1e6, 2, [v, 0.0, 0.0])
+    for i, p in enumerate(paths):
+        cos_t = d / np.hypot(d, (h1 + h2) if p.seq else (h1 - h2))
+        fd = np.angle(out[i, 0, 0, 1]) * 1e6 / (2 * np.pi)
+        assert abs(fd - v * cos_t / LAM) < 1e-9 * v / LAM
+
+
+def test_doppler_is_the_path_length_rate():
+    """On a small city the Doppler shift of every valid path equals the rate of
+    change of -(path length)/lambda when the devices move (central finite
+    difference of the image-method lengths), Fermat's principle for the
+    reflection points."""
+    tris = np.concatenate([S.ground_triangles(60.0), S.box_triangles(-5, 5, 8, 20, 0, 12),
+                           S.box_triangles(10, 18, -15, -4, 0, 20)])
+    sc = S.Scene(tris.astype(np.float32), (np.arange(len(tris)) % 2).astype(np.int32),
+                 np.array([S.CONCRETE, S.GLASS], np.float32))
+    osc = O.make_scene(sc)
+    tx = np.array([0.0, 0.0, 9.0])
+    rxs = np.array([[8.0, -8.0, 1.5], [-12.0, 3.0, 1.5]])
+    paths = [p for p in O.compute_paths(osc, tx, rxs.astype(np.float32), 2, 40000)[0]
+             if p.valid and p.margin > osc.eps]
+    assert len(paths) >= 5
+    vt = np.array([2.0, -1.5, 0.5])
+    vr = np.array([[-1.0, 0.7, 0.0], [0.4, 2.0, -0.3]])
+    out = O.doppler(np.ones((len(paths), 1, 1), complex), paths, tx, rxs, FC, 1e6, 2, vt, vr)
+    h = 1e-3
+    for i, p in enumerate(paths):
+        ok1, _, l1, _ = O.image_path(osc, tx + h * vt, rxs[p.rx] + h * vr[p.rx], p.seq)
+        ok0, _, l0, _ = O.image_path(osc, tx - h * vt, rxs[p.rx] - h * vr[p.rx], p.seq)
+        assert ok1 and ok0
+        fd_fd = -(l1 - l0) / (2 * h) / LAM
+        fd = np.angle(out[i, 0, 0, 1]) * 1e6 / (2 * np.pi)
+        assert abs(fd - fd_fd) < 1e-6 * (np.linalg.norm(vt) + 3.0) / LAM, (p.seq, fd, fd_fd)
