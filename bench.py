@@ -143,11 +143,12 @@ def run_ours(args):
     g_ypr = torch.zeros((1, 3), device=dev)
     state = {}
 
-    def step(inp, concurrent=True):
+    def step(inp, concurrent=True, after_freq=None):
         """One pass of the hot path. concurrent: the coverage map is traced on
         the context's second stream from the end of the path trace on, beside
         the candidate refinement, CIR, H(f) and their VJPs (rt_coverage_map_async);
-        otherwise every call runs in order on one stream."""
+        otherwise every call runs in order on one stream. after_freq: called
+        once H is final (the end-to-end leg starts its read-back there)."""
         rt.rt_set_stream(ctx)
         # the devices do not depend on the scene: set them first, so their host
         # work is not a gap after the scene load's readback
@@ -161,6 +162,8 @@ def run_ours(args):
         tau = torch.empty(max(P, 1), dtype=torch.float32, device=dev)
         rt.rt_cir(ctx, rt.RT_LOS | rt.RT_REFLECTION, a, tau)
         rt.rt_freq_response(ctx, a, tau, inp["freqs"], H)
+        if after_freq is not None:
+            after_freq()
         if not concurrent:
             rt.rt_coverage_map(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits)
         # VJP of L = 0.5 ||H||^2: grad_H = H
@@ -249,17 +252,28 @@ def run_ours(args):
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     out_h = {"H": torch.empty(H.shape, dtype=H.dtype).pin_memory(),
              "gain": torch.empty(gain.shape, dtype=gain.dtype).pin_memory()}
+    copy_stream = torch.cuda.Stream(device=dev)
+
+    def read_H():
+        # the 16 MB H(f) goes back on a copy stream while the VJPs and the
+        # coverage map still run
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        copy_stream.wait_event(ev)
+        with torch.cuda.stream(copy_stream):
+            out_h["H"].copy_(H, non_blocking=True)
+
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         inp = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
-        step(inp)
-        out_h["H"].copy_(H, non_blocking=True)
+        step(inp, after_freq=read_H)
         out_h["gain"].copy_(gain, non_blocking=True)
         a_h = state["a"].to("cpu", non_blocking=True)
         tau_h = state["tau"].to("cpu", non_blocking=True)
+        stream.wait_stream(copy_stream)
         e1.record(stream)
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
@@ -408,11 +422,45 @@ def extra_measurements(tr, scene, dev, args):
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts)
     rt.rt_set_tuning(ctx, *tuning_default)
-    return {"coverage_map_ms": ms,
+    dop = doppler_measurement(tr, scene, dev)
+    return {"doppler": dop, "coverage_map_ms": ms,
             "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch "
                                    "in a captured CUDA graph, median of 10 replays",
             "coverage_map_tuning": {"block": tuning[0], "chunk": tuning[1], "smem_nodes": tuning[2]},
             "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
+
+
+def doppler_measurement(tr, scene, dev, T=14, fs=1e6):
+    """Time evolution of the city workload's CIR (Sec. II-A Listing 3 settings:
+    1 MHz sampling, 14 steps, Tx at [3, 0, 0] m/s; receivers at 1.5 m/s in
+    seeded directions): rt_apply_doppler, median of 20 CUDA-event timings."""
+    import torch
+    from paper_2303_11103_gb300 import scenes as S
+    tx, rx = S.city_devices(scene, n_rx=N_RX)
+    tr.load_scene(scene)
+    tr.set_devices(tx, rx)
+    tr.compute_paths(MAX_DEPTH, N_RAYS)
+    a, _ = tr.cir()
+    rng = np.random.default_rng(5)
+    vr = rng.normal(size=(N_RX, 3))
+    vr[:, 2] = 0.0
+    vr = (1.5 * vr / np.linalg.norm(vr, axis=1, keepdims=True)).astype(np.float32)
+    for _ in range(3):
+        at = tr.apply_doppler(a, fs, T, [3.0, 0.0, 0.0], vr)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        at = tr.apply_doppler(a, fs, T, [3.0, 0.0, 0.0], vr)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"paths": int(a.shape[0]), "time_steps": T, "outputs": int(at.numel()), "ms": ms,
+            "config": "city workload paths (1 Tx, 1000 Rx, 1e6 rays, depth 3), fs 1 MHz, Tx [3,0,0] m/s, "
+                      "Rx 1.5 m/s horizontal in seeded directions; includes the Python binding's tensor set-up"}
 
 
 def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,

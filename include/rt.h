@@ -199,6 +199,21 @@ int rt_cir(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
  */
 int rt_pair_gain(rt_ctx* ctx, const float* a, float floor_db, float* out);
 /*
+ * Sec. II-A (Listing 3, paths.apply_doppler): time evolution of the channel
+ * coefficients of the stored paths from the velocities of the transmitters
+ * and receivers. Path i leaves its transmitter in the unit direction k_t and
+ * reaches its receiver in the unit direction k_r (image method at the
+ * current positions); its Doppler shift is f_D = (v_tx . k_t - v_rx . k_r) /
+ * lambda, and a_t[i][p][q][n] = a[i][p][q] exp(j 2 pi f_D n / fs) for
+ * n = 0..n_steps-1. The delays do not change.
+ * a [P*nrp*ntp] complex (float re, im; as from rt_cir), tx_vel [n_tx*3]
+ * m/s, rx_vel [n_rx*3] m/s or NULL (receivers at rest), a_t
+ * [P*nrp*ntp*n_steps] complex out; all device pointers. Errors:
+ * RT_ERR_INVALID_ARG for n_steps < 1, fs <= 0 or a null pointer.
+ */
+int rt_apply_doppler(rt_ctx* ctx, const float* a, const float* tx_vel, const float* rx_vel, double fs,
+                     int32_t n_steps, float* a_t);
+/*
  * Sec. III-A: H [n_pairs*nrp*ntp*K] complex, H = sum_i a_i exp(-j 2 pi f_k tau_i)
  * over the pair's paths, from a [P*nrp*ntp] and tau [P] as returned by
  * rt_cir; freqs [K] float64 baseband offsets (Hz).

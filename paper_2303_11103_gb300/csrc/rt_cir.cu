@@ -378,6 +378,66 @@ __global__ void __launch_bounds__(128) k_freq_vjp(const uint64_t* __restrict__ p
     }
 }
 
+// Sec. II-A (Listing 3, apply_doppler): time evolution from the devices'
+// motion. Per path, the unit direction k_t in which it leaves the
+// transmitter and k_r in which it reaches the receiver, from the image
+// method at the current positions (the same construction as path_field);
+// f_D = (v_tx . k_t - v_rx . k_r) / lambda (the rate of change of -length /
+// lambda), stored as cycles per time step f_D / fs.
+__global__ void k_doppler_shift(CirParams c, const float* __restrict__ vtx, const float* __restrict__ vrx,
+                                double inv_lambda_fs, float* __restrict__ cyc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.P) return;
+    const int t = c.pair_tx[2 * i], r = c.pair_tx[2 * i + 1];
+    const f3 tx = mk(c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]);
+    const f3 rx = mk(c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]);
+    const int K = c.depth[i];
+    const int32_t* ids = c.seq + i * c.D;
+    f3 first = rx, last = tx;   // neighbours of the transmitter and the receiver along the path
+    if (K > 0) {
+        f3 I[RT_MAX_DEPTH + 1];
+        I[0] = tx;
+        for (int k = 1; k <= K; k++) {
+            const float4 pl = __ldg(c.s.planes + ids[k - 1]);
+            const f3 n = xyz(pl);
+            I[k] = I[k - 1] - n * (2.0f * (dot(I[k - 1], n) - pl.w));
+        }
+        f3 q = rx;   // reflection points from the last one back
+        for (int k = K; k >= 1; k--) {
+            const float4 pl = __ldg(c.s.planes + ids[k - 1]);
+            const f3 n = xyz(pl);
+            const f3 dir = I[k] - q;
+            q = q + dir * ((pl.w - dot(q, n)) / dot(dir, n));
+            if (k == K) last = q;
+            if (k == 1) first = q;
+        }
+    }
+    f3 kt = first - tx, kr = rx - last;
+    kt = kt * (1.0f / sqrtf(dot(kt, kt)));
+    kr = kr * (1.0f / sqrtf(dot(kr, kr)));
+    double fd = (double)vtx[3 * t] * kt.x + (double)vtx[3 * t + 1] * kt.y + (double)vtx[3 * t + 2] * kt.z;
+    if (vrx) fd -= (double)vrx[3 * r] * kr.x + (double)vrx[3 * r + 1] * kr.y + (double)vrx[3 * r + 2] * kr.z;
+    cyc[i] = (float)(fd * inv_lambda_fs);
+}
+
+// a_t[i][q][n] = a[i][q] exp(j 2 pi n cyc_i): one thread per output value,
+// consecutive threads on consecutive time steps (coalesced stores)
+__global__ void k_doppler_apply(const float2* __restrict__ a, const float* __restrict__ cyc, int64_t P, int np,
+                                int T, float2* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = P * np * (int64_t)T;
+    if (e >= total) return;
+    const int64_t iq = e / T;
+    const int n = (int)(e - iq * T);
+    const int64_t i = iq / np;
+    float x = cyc[i] * (float)n;
+    x -= rintf(x);   // whole cycles dropped
+    float sn, cs;
+    sincospif(2.0f * x, &sn, &cs);
+    const float2 v = a[iq];
+    out[e] = make_float2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+}
+
 CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
     CirParams c;
     c.s = dev_scene(ctx);
@@ -432,6 +492,26 @@ int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau) {
     CirParams c = make_cir(ctx, flags);
     prof_begin(ctx, "k_cir");
     k_cir<<<(unsigned)((c.P + 127) / 128), 128, 0, ctx->stream>>>(c, (float2*)a, tau);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int doppler_impl(rt_ctx* ctx, const float* a, const float* vtx, const float* vrx, double fs, int T, float* a_t) {
+    const int64_t P = ctx->n_paths;
+    if (P == 0) return RT_OK;
+    CirParams c = make_cir(ctx, RT_LOS | RT_REFLECTION);
+    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
+    RT_TRY(buf_reserve(ctx->dop_cyc, sizeof(float) * (size_t)P));
+    prof_begin(ctx, "k_doppler_shift");
+    k_doppler_shift<<<(unsigned)((P + 127) / 128), 128, 0, ctx->stream>>>(c, vtx, vrx, 1.0 / (c.lambda * fs),
+                                                                          bp<float>(ctx->dop_cyc));
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    const int64_t total = P * np * (int64_t)T;
+    prof_begin(ctx, "k_doppler_apply");
+    k_doppler_apply<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(
+        (const float2*)a, bp<float>(ctx->dop_cyc), P, np, T, (float2*)a_t);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;

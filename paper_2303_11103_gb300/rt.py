@@ -77,6 +77,7 @@ def lib():
             "rt_get_candidates": [vp, ctypes.POINTER(i64), vp, vp, vp, vp],
             "rt_get_ray_hits": [vp, vp],
             "rt_cir": [vp, u32, vp, vp],
+            "rt_apply_doppler": [vp, vp, vp, vp, dbl, i32, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -244,6 +245,11 @@ def rt_get_ray_hits(ctx, hits):
 
 def rt_cir(ctx, flags, a, tau):
     _check(ctx, lib().rt_cir(ctx, int(flags), _ptr(a), _ptr(tau)))
+
+
+def rt_apply_doppler(ctx, a, tx_vel, rx_vel, fs, n_steps, a_t):
+    _check(ctx, lib().rt_apply_doppler(ctx, _ptr(a), _ptr(tx_vel), _ptr(rx_vel) if rx_vel is not None else None,
+                                       float(fs), int(n_steps), _ptr(a_t)))
 
 
 def rt_freq_response(ctx, a, tau, freqs, H):
@@ -495,6 +501,30 @@ class Tracer:
     def cir(self, los=True, reflection=True):
         a, tau = self.cir_raw(los, reflection)
         return torch.view_as_complex(a), tau
+
+    def apply_doppler(self, a, fs, n_steps, tx_velocities, rx_velocities=None):
+        """Sec. II-A (Listing 3): a [P, nrp, ntp] complex -> [P, nrp, ntp, n_steps]
+        with a_i(t_n) = a_i exp(j 2 pi f_D,i n / fs) from the devices' velocities
+        (tx [n_tx, 3] or [3], rx [n_rx, 3] or None; m/s)."""
+        self.sync_stream()
+        dev = self.device
+        vt = self._t(tx_velocities, torch.float32).reshape(-1, 3)
+        if vt.shape[0] == 1 and self.n_tx > 1:
+            vt = vt.expand(self.n_tx, 3)
+        vt = vt.contiguous()
+        vr = None
+        if rx_velocities is not None:
+            vr = self._t(rx_velocities, torch.float32).reshape(-1, 3)
+            if vr.shape[0] == 1 and self.n_rx > 1:
+                vr = vr.expand(self.n_rx, 3)
+            vr = vr.contiguous()
+        a_raw = torch.view_as_real(a.to(torch.complex64).contiguous()).contiguous()
+        P = a_raw.shape[0]
+        out = torch.empty((max(P, 1),) + tuple(a_raw.shape[1:-1]) + (int(n_steps), 2), dtype=torch.float32,
+                          device=dev)
+        if self.n_paths:
+            rt_apply_doppler(self.ctx, a_raw, vt, vr, fs, n_steps, out)
+        return torch.view_as_complex(out[:P])
 
     def pair_gain(self, a_raw, floor_db=-400.0):
         """[pairs, 2] = (has path, incoherent path gain dB) from cir_raw's a."""
