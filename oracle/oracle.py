@@ -343,6 +343,54 @@ def doppler(a: np.ndarray, paths, tx, rxs, fc: float, fs: float, n_steps: int, v
     return out
 
 
+def rotation_ypr(ypr) -> np.ndarray:
+    """Device rotation R = Rz(yaw) Ry(pitch) Rx(roll) (3GPP TR 38.901 Sec. 7.1):
+    the columns are the device's x, y, z axes in the global frame."""
+    a, b, g = (float(v) for v in ypr)
+    Rz = np.array([[np.cos(a), -np.sin(a), 0.0], [np.sin(a), np.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    Ry = np.array([[np.cos(b), 0.0, np.sin(b)], [0.0, 1.0, 0.0], [-np.sin(b), 0.0, np.cos(b)]])
+    Rx = np.array([[1.0, 0.0, 0.0], [0.0, np.cos(g), -np.sin(g)], [0.0, np.sin(g), np.cos(g)]])
+    return Rz @ Ry @ Rx
+
+
+def array_response(a: np.ndarray, paths, tx, tx_ypr, rxs, rx_ypr, fc: float, tx_el, rx_el) -> np.ndarray:
+    """Synthetic antenna arrays (Sec. II: arrays modelled after the ray
+    tracing with a plane-wave assumption across the array).
+
+    The paths are traced between the array centres. Element m of the
+    transmit array sits at R_tx r_m from the centre (r_m in the device frame),
+    element n of the receive array at R_rx s_n. Under the plane-wave
+    assumption the path from element m to element n is shorter by
+    k_t . R_tx r_m - k_r . R_rx s_n (k_t, k_r: unit departure and arrival
+    directions of the path), so its coefficient is
+    a[i][p][q] exp(j 2 pi (k_t . R_tx r_m - k_r . R_rx s_n) / lambda).
+
+    a [P, nrp, ntp] complex, tx_el [Mt, 3], rx_el [Mr, 3] (metres, device
+    frame), rx_ypr [R, 3] -> [P, Mr*nrp, Mt*ntp] with element-major, port-minor
+    indices (n*nrp + p, m*ntp + q).
+    """
+    lam = C0 / fc
+    a = np.asarray(a)
+    P, nrp, ntp = a.shape
+    tx_el = np.asarray(tx_el, np.float64).reshape(-1, 3)
+    rx_el = np.asarray(rx_el, np.float64).reshape(-1, 3)
+    Mt, Mr = len(tx_el), len(rx_el)
+    out = np.zeros((P, Mr * nrp, Mt * ntp), np.complex128)
+    txp = np.asarray(tx, np.float64)
+    Rt = rotation_ypr(tx_ypr)
+    for i, p in enumerate(paths):
+        rxp = np.asarray(rxs[p.rx], np.float64)
+        pts = [txp] + [np.asarray(q, np.float64) for q in p.points] + [rxp]
+        kt = (pts[1] - pts[0]) / np.linalg.norm(pts[1] - pts[0])
+        kr = (pts[-1] - pts[-2]) / np.linalg.norm(pts[-1] - pts[-2])
+        Rr = rotation_ypr(rx_ypr[p.rx])
+        ph_t = (tx_el @ Rt.T) @ kt / lam       # [Mt] cycles
+        ph_r = -(rx_el @ Rr.T) @ kr / lam      # [Mr] cycles
+        w = np.exp(2j * np.pi * (ph_r[:, None] + ph_t[None, :]))    # [Mr, Mt]
+        out[i] = np.einsum("nm,pq->npmq", w, a[i]).reshape(Mr * nrp, Mt * ntp)
+    return out
+
+
 def subcarrier_freqs(K: int, spacing: float) -> np.ndarray:
     """Baseband subcarrier offsets f_k = (k - K/2) * spacing (k = 0..K-1)."""
     return (np.arange(K, dtype=np.float64) - K // 2) * spacing

@@ -520,3 +520,77 @@ def test_doppler_is_the_path_length_rate():
         fd_fd = -(l1 - l0) / (2 * h) / LAM
         fd = np.angle(out[i, 0, 0, 1]) * 1e6 / (2 * np.pi)
         assert abs(fd - fd_fd) < 1e-6 * (np.linalg.norm(vt) + 3.0) / LAM, (p.seq, fd, fd_fd)
+
+
+# ---------------------------------------------------------------- antenna arrays
+def _los_paths(tx, rxs):
+    osc = O.make_scene(_single_far_triangle_scene())
+    paths, _ = O.compute_paths(osc, np.asarray(tx, np.float32), np.asarray(rxs, np.float32), D=1, N=100)
+    return paths
+
+
+def test_array_rotation_is_tr38901():
+    """R = Rz(yaw) Ry(pitch) Rx(roll): yaw turns the device x axis towards y,
+    positive pitch tilts it downwards (towards -z), and R is orthonormal."""
+    R = O.rotation_ypr([np.pi / 2, 0.0, 0.0])
+    assert np.allclose(R @ [1, 0, 0], [0, 1, 0], atol=1e-15)
+    R = O.rotation_ypr([0.0, np.pi / 6, 0.0])
+    assert np.allclose(R @ [1, 0, 0], [np.cos(np.pi / 6), 0, -np.sin(np.pi / 6)], atol=1e-15)
+    R = O.rotation_ypr([0.3, -0.7, 1.1])
+    assert np.allclose(R.T @ R, np.eye(3), atol=1e-14) and abs(np.linalg.det(R) - 1.0) < 1e-14
+
+
+def test_array_broadside_and_endfire():
+    """A linear transmit array along the device y axis: a receiver on the
+    boresight (x axis) sees all elements in phase; one along +y sees a phase
+    advance of 2 pi d / lambda per element at y = d (that element is closer)."""
+    tx = np.array([0.0, 0.0, 10.0])
+    rxs = np.array([[300.0, 0.0, 10.0], [0.0, 300.0, 10.0]])
+    paths = _los_paths(tx, rxs)
+    d = 0.5 * LAM
+    tx_el = np.array([[0.0, k * d, 0.0] for k in range(4)])
+    a = np.ones((len(paths), 1, 1), complex)
+    out = O.array_response(a, paths, tx, [0, 0, 0], rxs, np.zeros((2, 3)), FC, tx_el, np.zeros((1, 3)))
+    for i, p in enumerate(paths):
+        want = np.ones(4) if p.rx == 0 else np.exp(2j * np.pi * np.arange(4) * d / LAM)
+        assert np.allclose(out[i, 0, :], want, atol=1e-12)
+    # rotating the device by 90 degrees of yaw swaps the two cases
+    out = O.array_response(a, paths, tx, [np.pi / 2, 0, 0], rxs, np.zeros((2, 3)), FC, tx_el, np.zeros((1, 3)))
+    for i, p in enumerate(paths):
+        want = np.exp(-2j * np.pi * np.arange(4) * d / LAM) if p.rx == 0 else np.ones(4)
+        assert np.allclose(out[i, 0, :], want, atol=1e-12)
+
+
+def test_array_matches_explicit_elements():
+    """Against explicit modelling on a small city (Sec. II: paths traced for
+    every element): the exact image-method length from each displaced element
+    pair gives exp(-j 2 pi (L_mn - L_00) / lambda), which the plane-wave phase
+    matches to within the curvature error pi (|r| + |s|)^2 / (lambda L)."""
+    tris = np.concatenate([S.ground_triangles(60.0), S.box_triangles(-5, 5, 8, 20, 0, 12),
+                           S.box_triangles(10, 18, -15, -4, 0, 20)])
+    sc = S.Scene(tris.astype(np.float32), (np.arange(len(tris)) % 2).astype(np.int32),
+                 np.array([S.CONCRETE, S.GLASS], np.float32))
+    osc = O.make_scene(sc)
+    tx = np.array([0.0, 0.0, 9.0])
+    rxs = np.array([[8.0, -8.0, 1.5], [-12.0, 3.0, 1.5]])
+    txy, rxy = np.array([0.4, 0.1, 0.2]), np.array([[-1.0, 0.0, 0.3], [2.0, 0.05, -0.1]])
+    paths = [p for p in O.compute_paths(osc, tx, rxs.astype(np.float32), 2, 40000)[0]
+             if p.valid and p.margin > osc.eps]
+    assert len(paths) >= 5
+    d = 0.5 * LAM
+    tx_el = np.array([[0.0, c * d, r * 0.7 * LAM] for r in (-0.5, 0.5) for c in (-0.5, 0.5)])
+    rx_el = np.array([[0.0, c * d, 0.0] for c in (-0.5, 0.5)])
+    a = np.ones((len(paths), 1, 1), complex)
+    out = O.array_response(a, paths, tx, txy, rxs, rxy, FC, tx_el, rx_el)
+    Rt = O.rotation_ypr(txy)
+    for i, p in enumerate(paths):
+        Rr = O.rotation_ypr(rxy[p.rx])
+        ok, _, L0, _ = O.image_path(osc, tx, rxs[p.rx], p.seq)
+        assert ok
+        bound = 2 * np.pi * (np.linalg.norm(tx_el, axis=1).max() + np.linalg.norm(rx_el, axis=1).max()) ** 2 / (LAM * L0)
+        for n in range(len(rx_el)):
+            for m in range(len(tx_el)):
+                ok, _, L, _ = O.image_path(osc, tx + Rt @ tx_el[m], rxs[p.rx] + Rr @ rx_el[n], p.seq)
+                assert ok
+                exact = np.exp(-2j * np.pi * (L - L0) / LAM)
+                assert abs(np.angle(out[i, n, m] / exact)) < bound, (p.seq, n, m)
