@@ -422,18 +422,20 @@ def extra_measurements(tr, scene, dev, args):
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts)
     rt.rt_set_tuning(ctx, *tuning_default)
-    dop = doppler_measurement(tr, scene, dev)
-    return {"doppler": dop, "coverage_map_ms": ms,
+    ext = cir_extensions_measurement(tr, scene, dev)
+    return {**ext, "coverage_map_ms": ms,
             "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch "
                                    "in a captured CUDA graph, median of 10 replays",
             "coverage_map_tuning": {"block": tuning[0], "chunk": tuning[1], "smem_nodes": tuning[2]},
             "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
 
 
-def doppler_measurement(tr, scene, dev, T=14, fs=1e6):
-    """Time evolution of the city workload's CIR (Sec. II-A Listing 3 settings:
-    1 MHz sampling, 14 steps, Tx at [3, 0, 0] m/s; receivers at 1.5 m/s in
-    seeded directions): rt_apply_doppler, median of 20 CUDA-event timings."""
+def cir_extensions_measurement(tr, scene, dev, T=14, fs=1e6):
+    """On the city workload's paths: the CIR's time evolution (Sec. II-A
+    Listing 3 settings: 1 MHz sampling, 14 steps, Tx at [3, 0, 0] m/s;
+    receivers at 1.5 m/s in seeded directions; rt_apply_doppler) and the
+    synthetic transmit array of Listing 2 (rt_apply_array); medians of 20
+    CUDA-event timings."""
     import torch
     from paper_2303_11103_gb300 import scenes as S
     tx, rx = S.city_devices(scene, n_rx=N_RX)
@@ -458,9 +460,27 @@ def doppler_measurement(tr, scene, dev, T=14, fs=1e6):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     ms = statistics.median(ts)
-    return {"paths": int(a.shape[0]), "time_steps": T, "outputs": int(at.numel()), "ms": ms,
-            "config": "city workload paths (1 Tx, 1000 Rx, 1e6 rays, depth 3), fs 1 MHz, Tx [3,0,0] m/s, "
-                      "Rx 1.5 m/s horizontal in seeded directions; includes the Python binding's tensor set-up"}
+    # synthetic arrays: the paper's transmit array (8 x 2, spacings 0.7 / 0.5 wavelengths) on the same paths
+    from paper_2303_11103_gb300 import rt
+    tx_el = rt.planar_array(8, 2, 0.7, 0.5, 299792458.0 / FC)
+    for _ in range(3):
+        ael = tr.apply_array(a, tx_el)
+    ts = []
+    for _ in range(20):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ael = tr.apply_array(a, tx_el)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return {"doppler": {"paths": int(a.shape[0]), "time_steps": T, "outputs": int(at.numel()), "ms": ms,
+                        "config": "city workload paths (1 Tx, 1000 Rx, 1e6 rays, depth 3), fs 1 MHz, Tx [3,0,0] m/s, "
+                                  "Rx 1.5 m/s horizontal in seeded directions; includes the Python binding's "
+                                  "tensor set-up"},
+            "synthetic_array": {"paths": int(a.shape[0]), "outputs": int(ael.numel()), "ms": statistics.median(ts),
+                                "config": "the same paths, Tx planar array 8 x 2 (0.7 / 0.5 wavelengths), "
+                                          "dual-polarized TR 38.901 elements, single-element Rx"}}
 
 
 def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,

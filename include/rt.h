@@ -214,6 +214,22 @@ int rt_pair_gain(rt_ctx* ctx, const float* a, float floor_db, float* out);
 int rt_apply_doppler(rt_ctx* ctx, const float* a, const float* tx_vel, const float* rx_vel, double fs,
                      int32_t n_steps, float* a_t);
 /*
+ * Sec. II (antenna arrays modelled synthetically after the ray tracing):
+ * the paths are traced between the array centres, and every element pair
+ * gets the plane-wave phase of its offsets. Element m of the transmit array
+ * sits at r_m, element n of the receive array at s_n, in the devices' own
+ * frames (metres; rotated by the devices' yaw/pitch/roll as the patterns
+ * are). With k_t / k_r the unit departure / arrival directions of path i,
+ * a_el[i][n*nrp + p][m*ntp + q] = a[i][p][q] exp(j 2 pi (k_t . R_tx r_m -
+ * k_r . R_rx s_n) / lambda): element-major, port-minor indices.
+ * a [P*nrp*ntp] complex (as from rt_cir), tx_elements [n_tx_el*3],
+ * rx_elements [n_rx_el*3] (n = 0 with NULL: one element at the centre),
+ * a_el [P*n_rx_el*nrp*n_tx_el*ntp] complex out; device pointers. Errors:
+ * RT_ERR_INVALID_ARG for a negative count or a null pointer.
+ */
+int rt_apply_array(rt_ctx* ctx, const float* a, const float* tx_elements, int32_t n_tx_el, const float* rx_elements,
+                   int32_t n_rx_el, float* a_el);
+/*
  * Sec. III-A: H [n_pairs*nrp*ntp*K] complex, H = sum_i a_i exp(-j 2 pi f_k tau_i)
  * over the pair's paths, from a [P*nrp*ntp] and tau [P] as returned by
  * rt_cir; freqs [K] float64 baseband offsets (Hz).

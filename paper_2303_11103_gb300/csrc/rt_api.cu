@@ -14,6 +14,7 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
 int export_candidates(rt_ctx* ctx, int32_t* tx, int32_t* depth, int32_t* seq, int64_t* wit);
 int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
 int doppler_impl(rt_ctx* ctx, const float* a, const float* vtx, const float* vrx, double fs, int T, float* a_t);
+int array_impl(rt_ctx* ctx, const float* a, const float* tel, int Mt, const float* rel, int Mr, float* a_el);
 int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
@@ -243,7 +244,7 @@ int rt_destroy(rt_ctx* ctx) {
     for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->planes64, &ctx->mat, &ctx->mats, &ctx->tx_pos,
                       &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->keys, &ctx->keys_alt,
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
-                      &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->path_key,
+                      &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
@@ -479,6 +480,17 @@ int rt_apply_doppler(rt_ctx* ctx, const float* a, const float* tx_vel, const flo
     if (n_steps < 1 || !(fs > 0.0) || !tx_vel || ((!a || !a_t) && ctx->n_paths > 0))
         return set_err(ctx, RT_ERR_INVALID_ARG, "apply_doppler: bad arguments");
     return doppler_impl(ctx, a, tx_vel, rx_vel, fs, n_steps, a_t);
+}
+
+int rt_apply_array(rt_ctx* ctx, const float* a, const float* tx_elements, int32_t n_tx_el, const float* rx_elements,
+                   int32_t n_rx_el, float* a_el) {
+    CHECK_CTX(ctx);
+    if (n_tx_el < 0 || n_rx_el < 0 || (n_tx_el > 0 && !tx_elements) || (n_rx_el > 0 && !rx_elements) ||
+        ((!a || !a_el) && ctx->n_paths > 0))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "apply_array: bad arguments");
+    // no element list: one element at the centre
+    return array_impl(ctx, a, n_tx_el > 0 ? tx_elements : nullptr, std::max(n_tx_el, 1),
+                      n_rx_el > 0 ? rx_elements : nullptr, std::max(n_rx_el, 1), a_el);
 }
 
 int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int32_t K, float* H) {

@@ -384,11 +384,12 @@ __global__ void __launch_bounds__(128) k_freq_vjp(const uint64_t* __restrict__ p
 // method at the current positions (the same construction as path_field);
 // f_D = (v_tx . k_t - v_rx . k_r) / lambda (the rate of change of -length /
 // lambda), stored as cycles per time step f_D / fs.
-__global__ void k_doppler_shift(CirParams c, const float* __restrict__ vtx, const float* __restrict__ vrx,
-                                double inv_lambda_fs, float* __restrict__ cyc) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.P) return;
-    const int t = c.pair_tx[2 * i], r = c.pair_tx[2 * i + 1];
+// Unit directions in which path i leaves its transmitter (kt) and reaches
+// its receiver (kr), from the image method at the current positions (the
+// same construction as path_field); t, r: the path's devices.
+__device__ __forceinline__ void path_end_dirs(const CirParams& c, int64_t i, f3& kt, f3& kr, int& t, int& r) {
+    t = c.pair_tx[2 * i];
+    r = c.pair_tx[2 * i + 1];
     const f3 tx = mk(c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]);
     const f3 rx = mk(c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]);
     const int K = c.depth[i];
@@ -412,12 +413,64 @@ __global__ void k_doppler_shift(CirParams c, const float* __restrict__ vtx, cons
             if (k == 1) first = q;
         }
     }
-    f3 kt = first - tx, kr = rx - last;
+    kt = first - tx;
+    kr = rx - last;
     kt = kt * (1.0f / sqrtf(dot(kt, kt)));
     kr = kr * (1.0f / sqrtf(dot(kr, kr)));
+}
+
+__global__ void k_doppler_shift(CirParams c, const float* __restrict__ vtx, const float* __restrict__ vrx,
+                                double inv_lambda_fs, float* __restrict__ cyc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.P) return;
+    f3 kt, kr;
+    int t, r;
+    path_end_dirs(c, i, kt, kr, t, r);
     double fd = (double)vtx[3 * t] * kt.x + (double)vtx[3 * t + 1] * kt.y + (double)vtx[3 * t + 2] * kt.z;
     if (vrx) fd -= (double)vrx[3 * r] * kr.x + (double)vrx[3 * r + 1] * kr.y + (double)vrx[3 * r + 2] * kr.z;
     cyc[i] = (float)(fd * inv_lambda_fs);
+}
+
+// Sec. II (synthetic arrays): the path directions in the devices' own frames,
+// kt_l = R_tx^T kt and kr_l = R_rx^T kr, scaled by 1/lambda, so that an
+// element at r (device frame) adds kt_l . r cycles (transmitter) or
+// -kr_l . s cycles (receiver).
+__global__ void k_array_dirs(CirParams c, float inv_lambda, float* __restrict__ dirs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.P) return;
+    f3 kt, kr;
+    int t, r;
+    path_end_dirs(c, i, kt, kr, t, r);
+    const Rot<float> Rt = rot_ypr(c.tx_ypr[3 * t], c.tx_ypr[3 * t + 1], c.tx_ypr[3 * t + 2]);
+    const Rot<float> Rr = rot_ypr(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
+    float* o = dirs + 6 * i;
+    for (int k = 0; k < 3; k++) {
+        o[k] = (Rt.m[0][k] * kt.x + Rt.m[1][k] * kt.y + Rt.m[2][k] * kt.z) * inv_lambda;
+        o[3 + k] = (Rr.m[0][k] * kr.x + Rr.m[1][k] * kr.y + Rr.m[2][k] * kr.z) * inv_lambda;
+    }
+}
+
+// a_el[i][n*nrp + p][m*ntp + q] = a[i][p][q] exp(j 2 pi (kt_l . r_m - kr_l . s_n)):
+// one thread per output value, the transmit element and port fastest
+__global__ void k_array_apply(const float2* __restrict__ a, const float* __restrict__ dirs, int64_t P, int nrp,
+                              int ntp, const float* __restrict__ tel, int Mt, const float* __restrict__ rel, int Mr,
+                              float2* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cols = (int64_t)Mt * ntp, rows = (int64_t)Mr * nrp;
+    if (e >= P * rows * cols) return;
+    const int64_t i = e / (rows * cols);
+    const int64_t rc = e - i * rows * cols;
+    const int row = (int)(rc / cols), col = (int)(rc - (int64_t)row * cols);
+    const int n = row / nrp, p = row - n * nrp, m = col / ntp, q = col - m * ntp;
+    const float* d = dirs + 6 * i;
+    float x = 0.0f;
+    if (tel) x += d[0] * __ldg(tel + 3 * m) + d[1] * __ldg(tel + 3 * m + 1) + d[2] * __ldg(tel + 3 * m + 2);
+    if (rel) x -= d[3] * __ldg(rel + 3 * n) + d[4] * __ldg(rel + 3 * n + 1) + d[5] * __ldg(rel + 3 * n + 2);
+    x -= rintf(x);   // whole cycles dropped
+    float sn, cs;
+    sincospif(2.0f * x, &sn, &cs);
+    const float2 v = a[(i * nrp + p) * ntp + q];
+    out[e] = make_float2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
 }
 
 // a_t[i][q][n] = a[i][q] exp(j 2 pi n cyc_i): one thread per output value,
@@ -512,6 +565,26 @@ int doppler_impl(rt_ctx* ctx, const float* a, const float* vtx, const float* vrx
     prof_begin(ctx, "k_doppler_apply");
     k_doppler_apply<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(
         (const float2*)a, bp<float>(ctx->dop_cyc), P, np, T, (float2*)a_t);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}
+
+int array_impl(rt_ctx* ctx, const float* a, const float* tel, int Mt, const float* rel, int Mr, float* a_el) {
+    const int64_t P = ctx->n_paths;
+    if (P == 0) return RT_OK;
+    CirParams c = make_cir(ctx, RT_LOS | RT_REFLECTION);
+    RT_TRY(buf_reserve(ctx->arr_dirs, sizeof(float) * 6 * (size_t)P));
+    prof_begin(ctx, "k_array_dirs");
+    k_array_dirs<<<(unsigned)((P + 127) / 128), 128, 0, ctx->stream>>>(c, (float)(1.0 / c.lambda),
+                                                                       bp<float>(ctx->arr_dirs));
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    const int nrp = ctx->rx_ant.n_ports, ntp = ctx->tx_ant.n_ports;
+    const int64_t total = P * (int64_t)Mr * nrp * (int64_t)Mt * ntp;
+    prof_begin(ctx, "k_array_apply");
+    k_array_apply<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(
+        (const float2*)a, bp<float>(ctx->arr_dirs), P, nrp, ntp, tel, Mt, rel, Mr, (float2*)a_el);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;

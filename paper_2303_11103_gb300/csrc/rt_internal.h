@@ -64,6 +64,7 @@ struct rt_ctx {
     DevBuf cand_key, cand_wit, cand_off, cand_img; // candidates
     DevBuf htab_key, htab_wit, htab_cnt;           // duplicate-removal hash table
     DevBuf dop_cyc;                                // Doppler cycles per time step, per path
+    DevBuf arr_dirs;                               // per path: R_tx^T kt / lambda, R_rx^T kr / lambda
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
     int64_t path_cap = 0;

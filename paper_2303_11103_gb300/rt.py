@@ -15,6 +15,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -78,6 +79,7 @@ def lib():
             "rt_get_ray_hits": [vp, vp],
             "rt_cir": [vp, u32, vp, vp],
             "rt_apply_doppler": [vp, vp, vp, vp, dbl, i32, vp],
+            "rt_apply_array": [vp, vp, vp, i32, vp, i32, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -250,6 +252,24 @@ def rt_cir(ctx, flags, a, tau):
 def rt_apply_doppler(ctx, a, tx_vel, rx_vel, fs, n_steps, a_t):
     _check(ctx, lib().rt_apply_doppler(ctx, _ptr(a), _ptr(tx_vel), _ptr(rx_vel) if rx_vel is not None else None,
                                        float(fs), int(n_steps), _ptr(a_t)))
+
+
+def rt_apply_array(ctx, a, tx_el, rx_el, a_el):
+    _check(ctx, lib().rt_apply_array(ctx, _ptr(a), _ptr(tx_el) if tx_el is not None else None,
+                                     int(tx_el.shape[0]) if tx_el is not None else 0,
+                                     _ptr(rx_el) if rx_el is not None else None,
+                                     int(rx_el.shape[0]) if rx_el is not None else 0, _ptr(a_el)))
+
+
+def planar_array(num_rows: int, num_cols: int, vertical_spacing: float, horizontal_spacing: float,
+                 wavelength: float) -> np.ndarray:
+    """Element positions [num_rows*num_cols, 3] (metres, device frame) of a
+    planar array in the device's y-z plane, centred on the device: columns
+    along y, rows along z, spacings in wavelengths; element r*num_cols + c."""
+    r, c = np.meshgrid(np.arange(num_rows), np.arange(num_cols), indexing="ij")
+    y = (c.ravel() - (num_cols - 1) / 2) * horizontal_spacing * wavelength
+    z = (r.ravel() - (num_rows - 1) / 2) * vertical_spacing * wavelength
+    return np.stack([np.zeros_like(y), y, z], 1).astype(np.float32)
 
 
 def rt_freq_response(ctx, a, tau, freqs, H):
@@ -524,6 +544,22 @@ class Tracer:
                           device=dev)
         if self.n_paths:
             rt_apply_doppler(self.ctx, a_raw, vt, vr, fs, n_steps, out)
+        return torch.view_as_complex(out[:P])
+
+    def apply_array(self, a, tx_elements=None, rx_elements=None):
+        """Sec. II, synthetic arrays: a [P, nrp, ntp] complex -> [P, Mr*nrp, Mt*ntp]
+        with every element pair's plane-wave phase (element positions [M, 3] in
+        metres in the devices' frames; None: one element at the centre)."""
+        self.sync_stream()
+        te = self._t(tx_elements, torch.float32).reshape(-1, 3) if tx_elements is not None else None
+        re = self._t(rx_elements, torch.float32).reshape(-1, 3) if rx_elements is not None else None
+        Mt = te.shape[0] if te is not None else 1
+        Mr = re.shape[0] if re is not None else 1
+        a_raw = torch.view_as_real(a.to(torch.complex64).contiguous()).contiguous()
+        P, nrp, ntp = a_raw.shape[0], a_raw.shape[1], a_raw.shape[2]
+        out = torch.empty((max(P, 1), Mr * nrp, Mt * ntp, 2), dtype=torch.float32, device=self.device)
+        if self.n_paths:
+            rt_apply_array(self.ctx, a_raw, te, re, out)
         return torch.view_as_complex(out[:P])
 
     def pair_gain(self, a_raw, floor_db=-400.0):
