@@ -109,8 +109,8 @@ int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder);
  * distinct keys only; RT_DEDUP_SORT = sort of all keys, then removal of
  * equal neighbours. Both give the same candidates in the same (key) order
  * with the same witness rays (the smallest producing ray). Keys that
- * fill all 64 bits always take RT_DEDUP_SORT. Errors: RT_ERR_INVALID_ARG for
- * another value.
+ * fill all 64 bits, and more than 2^28 appended keys (a table above 6 GB),
+ * always take RT_DEDUP_SORT. Errors: RT_ERR_INVALID_ARG for another value.
  */
 #define RT_DEDUP_HASH 0
 #define RT_DEDUP_SORT 1

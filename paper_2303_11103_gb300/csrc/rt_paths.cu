@@ -648,11 +648,12 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
     RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * Ucap));
     const uint32_t* Ud = nullptr;   // device candidate count
-    if (ctx->key_bits < 64 && ctx->dedup == RT_DEDUP_HASH) {
+    int64_t S = 1024;   // hash table slots: a power of two, at least twice the keys
+    while (S < 2 * nkeys) S <<= 1;
+    // beyond 2^29 slots (6 GB) the table would outgrow the sort's scratch: sort instead
+    if (ctx->key_bits < 64 && ctx->dedup == RT_DEDUP_HASH && S <= (1ll << 29)) {
         DevBuf& cnt = ctx->htab_cnt;
         // duplicate removal by hashing, then a sort of the distinct keys only
-        int64_t S = 1024;
-        while (S < 2 * nkeys) S <<= 1;
         RT_TRY(buf_reserve(ctx->htab_key, sizeof(uint64_t) * S));
         RT_TRY(buf_reserve(ctx->htab_wit, sizeof(uint32_t) * S));
         RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * 4));
