@@ -1,0 +1,219 @@
+"""FP64 oracle of first-order edge diffraction (Sec. II-B names first-order
+diffraction among the features; the paper leaves its equations to the
+documentation, so this follows the uniform geometrical theory of
+diffraction (UTD) of Kouyoumjian and Pathak for a perfectly conducting
+wedge, as stated below).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, never by the product path. It
+shares no code with the CUDA library; occlusion uses the oracle's own
+brute-force closest hit.
+
+Wedges: scene edges shared by exactly two triangles whose planes differ.
+The solid is taken to be the smaller of the two sectors the faces bound
+(convex edges, as the boxes of the synthetic cities have), so the open
+exterior angle is n pi with n = 2 - alpha / pi, alpha the angle between the
+faces. Face 0 is the triangle with the lower id; angles around the edge are
+measured from face 0 through the exterior.
+
+A diffracted path tx -> D -> rx touches the edge at the point D where the
+incidence and diffraction angles with the edge agree (Keller's law), which
+on the edge line is the point that minimises |tx - D| + |D - rx|. It is
+valid when D lies strictly inside the edge, both devices are in the
+exterior (0 < phi < n pi), and both segments are free of occluders.
+
+Field of a diffracted path (spherical incidence, ray-fixed coordinates):
+  a = lambda/(4 pi) exp(-j k (s' + s)) / sqrt(s s' (s' + s))
+      F_rx(-k_d) . [ -D_s b0 b0'^T - D_h p p'^T ] . F_tx(k_i)
+with s' = |D - tx|, s = |rx - D|, k_i, k_d the unit incident and diffracted
+directions, p' = -(e x k_i)/|.|, b0' = p' x k_i, p = (e x k_d)/|.|,
+b0 = p x k_d, and the UTD coefficients
+  D_{s,h} = -exp(-j pi/4) / (2 n sqrt(2 pi k) sin b) *
+            { cot((pi + (phi - phi'))/(2n)) F(k L a+(phi - phi'))
+            + cot((pi - (phi - phi'))/(2n)) F(k L a-(phi - phi'))
+            -/+ [ cot((pi + (phi + phi'))/(2n)) F(k L a+(phi + phi'))
+                + cot((pi - (phi + phi'))/(2n)) F(k L a-(phi + phi')) ] }
+(minus for soft, plus for hard), L = s s' sin^2 b / (s + s'),
+a+-(x) = 2 cos^2((2 pi n N+- - x)/2) with N+- the integers nearest to
+(x +- pi)/(2 pi n), and the transition function
+F(x) = 2 j sqrt(x) exp(j x) int_{sqrt(x)}^inf exp(-j t^2) dt.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+from scipy.special import fresnel as _fresnel
+
+from . import oracle as O
+
+
+@dataclass
+class Wedge:
+    A: np.ndarray       # edge start [3]
+    e: np.ndarray       # unit edge direction [3]
+    length: float
+    f0: int             # face 0 (lower triangle id)
+    f1: int
+    t0: np.ndarray      # unit vector in face 0, normal to the edge, into the face
+    n0: np.ndarray      # unit normal of face 0 on the exterior side
+    n: float            # exterior angle / pi
+
+
+def _inward(A, e, third):
+    v = third - A
+    v = v - np.dot(v, e) * e
+    return v / np.linalg.norm(v)
+
+
+def wedges(verts: np.ndarray, flat_tol: float = 1e-6) -> list:
+    """Wedges of a triangle soup (float32 [T, 9]); edges are matched on the
+    exact float32 coordinates of their end points."""
+    V = np.asarray(verts, np.float32).reshape(-1, 3, 3)
+    table = {}
+    for t in range(V.shape[0]):
+        for k in range(3):
+            p, q = V[t, k], V[t, (k + 1) % 3]
+            key = tuple(sorted((tuple(p.tolist()), tuple(q.tolist()))))
+            table.setdefault(key, []).append((t, (k + 2) % 3))
+    out = []
+    for key, faces in table.items():
+        if len(faces) != 2:
+            continue
+        (ta, ka), (tb, kb) = sorted(faces)
+        A = np.array(key[0], np.float64)
+        B = np.array(key[1], np.float64)
+        L = float(np.linalg.norm(B - A))
+        if L <= 0.0:
+            continue
+        e = (B - A) / L
+        t0 = _inward(A, e, V[ta, ka].astype(np.float64))
+        t1 = _inward(A, e, V[tb, kb].astype(np.float64))
+        alpha = float(np.arccos(np.clip(np.dot(t0, t1), -1.0, 1.0)))
+        if alpha > np.pi - flat_tol:
+            continue   # coplanar faces: no edge
+        n0 = np.cross(e, t0)
+        if np.dot(n0, t1) > 0.0:
+            n0 = -n0
+        out.append(Wedge(A, e, L, ta, tb, t0, n0, 2.0 - alpha / np.pi))
+    return out
+
+
+def diffraction_point(w: Wedge, tx, rx):
+    """Edge parameter and point of Keller's law on the edge line."""
+    tx = np.asarray(tx, np.float64)
+    rx = np.asarray(rx, np.float64)
+    ts = np.dot(tx - w.A, w.e)
+    tr = np.dot(rx - w.A, w.e)
+    rs = np.linalg.norm(tx - w.A - ts * w.e)
+    rr = np.linalg.norm(rx - w.A - tr * w.e)
+    t = ts + (tr - ts) * rs / (rs + rr)
+    return t, w.A + t * w.e
+
+
+def angle(w: Wedge, D, X) -> float:
+    """Angle of X around the edge at D, from face 0 through the exterior, in [0, 2 pi)."""
+    v = np.asarray(X, np.float64) - D
+    return float(np.mod(np.arctan2(np.dot(v, w.n0), np.dot(v, w.t0)), 2.0 * np.pi))
+
+
+def transition(x: float) -> complex:
+    """F(x) = 2 j sqrt(x) exp(j x) int_{sqrt(x)}^inf exp(-j t^2) dt, x >= 0,
+    through the normalised Fresnel integrals S, C (scipy)."""
+    if x <= 0.0:
+        return 0.0 + 0.0j
+    u = np.sqrt(x)
+    z = u * np.sqrt(2.0 / np.pi)
+    S, C = _fresnel(z)
+    tail = np.sqrt(np.pi / 2.0) * ((0.5 - C) - 1j * (0.5 - S))
+    return 2j * u * np.exp(1j * x) * tail
+
+
+def _a(x: float, n: float, sign: int) -> float:
+    N = np.round((x + sign * np.pi) / (2.0 * np.pi * n))
+    return 2.0 * np.cos((2.0 * np.pi * n * N - x) / 2.0) ** 2
+
+
+def utd_coefficients(n: float, phi: float, phip: float, sin_b: float, s: float, sp: float, k: float):
+    """(D_s, D_h) of a perfectly conducting wedge of exterior angle n pi."""
+    Lp = s * sp * sin_b ** 2 / (s + sp)
+    pre = -np.exp(-1j * np.pi / 4.0) / (2.0 * n * np.sqrt(2.0 * np.pi * k) * sin_b)
+
+    def term(beta, sign):
+        c = 1.0 / np.tan((np.pi + sign * beta) / (2.0 * n))
+        return c * transition(k * Lp * _a(beta, n, sign))
+
+    d1 = term(phi - phip, +1) + term(phi - phip, -1)
+    d2 = term(phi + phip, +1) + term(phi + phip, -1)
+    return pre * (d1 - d2), pre * (d1 + d2)
+
+
+def _occluded(osc, o, p, exclude):
+    d = p - o
+    L = np.linalg.norm(d)
+    i, t, _ = O.closest_hit(osc, o, d / L, exclude)
+    return i >= 0 and t < L - osc.tmin
+
+
+@dataclass
+class DPath:
+    rx: int
+    wedge: int
+    point: np.ndarray
+    length: float
+
+
+def diffracted_paths(osc, scene_verts, tx, rxs, ws=None) -> list:
+    """All valid first-order diffracted paths from tx to every receiver."""
+    ws = wedges(scene_verts) if ws is None else ws
+    tx = np.asarray(tx, np.float64)
+    out = []
+    for r, rx in enumerate(np.asarray(rxs, np.float64)):
+        for wi, w in enumerate(ws):
+            t, D = diffraction_point(w, tx, rx)
+            if not (0.0 < t < w.length):
+                continue
+            pt, pr = angle(w, D, tx), angle(w, D, rx)
+            if not (0.0 < pt < w.n * np.pi and 0.0 < pr < w.n * np.pi):
+                continue
+            if _occluded(osc, tx, D, w.f0) or _occluded(osc, D, rx, w.f0) or \
+               _occluded(osc, tx, D, w.f1) or _occluded(osc, D, rx, w.f1):
+                continue
+            out.append(DPath(r, wi, D, float(np.linalg.norm(D - tx) + np.linalg.norm(rx - D))))
+    return out
+
+
+def diffracted_field(ws, paths, fc, txdev, rxdev, tx_index: int = 0):
+    """a [P, nrp, ntp] complex128 and tau [P] of diffracted paths."""
+    lam = O.C0 / fc
+    k = 2.0 * np.pi / lam
+    tx = np.asarray(txdev.pos[tx_index], np.float64)
+    txa, rxa = txdev.antenna, rxdev.antenna
+    a = np.zeros((len(paths), len(rxa.slants), len(txa.slants)), np.complex128)
+    tau = np.zeros(len(paths))
+    for i, p in enumerate(paths):
+        w = ws[p.wedge]
+        rx = np.asarray(rxdev.pos[p.rx], np.float64)
+        D = p.point
+        ki = D - tx
+        sp = np.linalg.norm(ki)
+        ki /= sp
+        kd = rx - D
+        s = np.linalg.norm(kd)
+        kd /= s
+        sin_b = np.linalg.norm(np.cross(w.e, ki))
+        pp = -np.cross(w.e, ki)
+        pp /= np.linalg.norm(pp)
+        bp = np.cross(pp, ki)
+        ph = np.cross(w.e, kd)
+        ph /= np.linalg.norm(ph)
+        bd = np.cross(ph, kd)
+        Ds, Dh = utd_coefficients(w.n, angle(w, D, rx), angle(w, D, tx), sin_b, s, sp, k)
+        dyad = -Ds * np.outer(bd, bp) - Dh * np.outer(ph, pp)
+        amp = lam / (4.0 * np.pi) * np.exp(-1j * k * (s + sp)) / np.sqrt(s * sp * (s + sp))
+        for q, zt in enumerate(txa.slants):
+            ft = O.antenna(txa.kind, zt, txdev.ypr[tx_index], ki)
+            for pr_, zr in enumerate(rxa.slants):
+                fr = O.antenna(rxa.kind, zr, rxdev.ypr[p.rx], -kd)
+                a[i, pr_, q] = amp * (fr @ dyad @ ft)
+        tau[i] = (s + sp) / O.C0
+    return a, tau
