@@ -478,9 +478,35 @@ def cir_extensions_measurement(tr, scene, dev, T=14, fs=1e6):
     return {"doppler": {"paths": int(a.shape[0]), "time_steps": T, "outputs": int(at.numel()), "ms": ms,
                         "config": "city workload paths (1 Tx, 1000 Rx, 1e6 rays, depth 3), fs 1 MHz, Tx [3,0,0] m/s, "
                                   "Rx 1.5 m/s horizontal in seeded directions; velocities resident on the GPU"},
+            "diffraction": diffraction_measurement(tr),
             "synthetic_array": {"paths": int(a.shape[0]), "outputs": int(ael.numel()), "ms": statistics.median(ts),
                                 "config": "the same paths, Tx planar array 8 x 2 (0.7 / 0.5 wavelengths), "
                                           "dual-polarized TR 38.901 elements, single-element Rx"}}
+
+
+def diffraction_measurement(tr):
+    """First-order diffraction on the city workload as loaded (1 Tx, 1000 Rx):
+    rt_compute_diffraction (all pairs x all wedges) and rt_diffraction_cir,
+    medians of 10 host-timed calls (the search reads its path count back)."""
+    import torch
+    tr.compute_diffraction()
+    tr.diffraction_cir()
+    torch.cuda.synchronize()
+    t_find, t_cir = [], []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        P = tr.compute_diffraction()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        a, _ = tr.diffraction_cir()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        t_find.append((t1 - t0) * 1e3)
+        t_cir.append((t2 - t1) * 1e3)
+    faces, _ = tr.wedges()
+    return {"wedges": int(faces.shape[0]), "pairs": int(tr.n_pairs), "diffracted_paths": int(P),
+            "find_ms": statistics.median(t_find), "cir_ms": statistics.median(t_cir),
+            "candidates_per_s": int(faces.shape[0]) * int(tr.n_pairs) / (statistics.median(t_find) / 1e3)}
 
 
 def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,

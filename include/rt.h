@@ -230,6 +230,39 @@ int rt_apply_doppler(rt_ctx* ctx, const float* a, const float* tx_vel, const flo
 int rt_apply_array(rt_ctx* ctx, const float* a, const float* tx_elements, int32_t n_tx_el, const float* rx_elements,
                    int32_t n_rx_el, float* a_el);
 /*
+ * Sec. II-B (first-order diffraction; the equations are a reading, the paper
+ * leaves them to the documentation): diffracted paths tx -> edge -> rx of
+ * every (tx, rx) pair of the context, kept beside the specular paths.
+ * Wedges are the scene edges shared by two triangles whose planes differ,
+ * matched on the exact input vertex coordinates; the solid is the smaller
+ * sector between the faces (convex edges). A path touches its edge where
+ * the incidence and diffraction angles with the edge agree (Keller's law),
+ * strictly inside the edge, with both devices outside the solid and both
+ * segments free of occluders. num_paths (HOST) receives their count.
+ * Errors: RT_ERR_INVALID_ARG without scene or devices, RT_ERR_NOT_READY
+ * while capturing a graph.
+ */
+int rt_compute_diffraction(rt_ctx* ctx, int64_t* num_paths);
+/* The diffracted paths, ordered by (pair, wedge): offsets [n_pairs+1] int64
+ * (CSR over pairs), wedge [P] int32 (index into rt_get_wedges), points
+ * [P*3] float32 diffraction points; device pointers, any may be NULL. */
+int rt_get_diffraction(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points);
+/*
+ * Channel coefficients of the diffracted paths by the uniform theory of
+ * diffraction for perfectly conducting wedges (Kouyoumjian-Pathak):
+ * a = lambda/(4 pi) exp(-j k (s' + s)) / sqrt(s s' (s' + s))
+ *     F_rx(-k_d) . [-D_s b0 b0' - D_h p p'] . F_tx(k_i),
+ * with the soft / hard coefficients D_s, D_h, the incident and diffracted
+ * ray-fixed bases (b0', p') and (b0, p), and the transition function
+ * evaluated in FP64; path length and carrier phase in FP64. a [P*nrp*ntp]
+ * complex (float re, im), tau [P] seconds; device pointers.
+ */
+int rt_diffraction_cir(rt_ctx* ctx, float* a, float* tau);
+/* Wedges of the current scene: n_out (HOST) = count; faces [n*2] int32 the
+ * two triangles (original ids, lower first), n_ext [n] exterior angle / pi;
+ * device pointers, either may be NULL. Reads back (not while capturing). */
+int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
+/*
  * Sec. III-A: H [n_pairs*nrp*ntp*K] complex, H = sum_i a_i exp(-j 2 pi f_k tau_i)
  * over the pair's paths, from a [P*nrp*ntp] and tau [P] as returned by
  * rt_cir; freqs [K] float64 baseband offsets (Hz).

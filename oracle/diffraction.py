@@ -147,19 +147,41 @@ def utd_coefficients(n: float, phi: float, phip: float, sin_b: float, s: float, 
     return pre * (d1 - d2), pre * (d1 + d2)
 
 
-def _occluded(osc, o, p, exclude):
-    d = p - o
-    L = np.linalg.norm(d)
-    i, t, _ = O.closest_hit(osc, o, d / L, exclude)
-    return i >= 0 and t < L - osc.tmin
-
-
 @dataclass
 class DPath:
     rx: int
     wedge: int
     point: np.ndarray
     length: float
+    margin: float
+
+
+def evaluate(osc, w: Wedge, tx, rx):
+    """(valid, diffraction point, margin) of the candidate tx -> edge -> rx.
+    margin: metres by which a device or the point would have to move to
+    change the decision (edge ends, face planes, occluders)."""
+    tx = np.asarray(tx, np.float64)
+    rx = np.asarray(rx, np.float64)
+    t, D = diffraction_point(w, tx, rx)
+    m = min(abs(t), abs(w.length - t))
+    if not (0.0 < t < w.length):
+        return False, D, m
+    valid = True
+    for X in (tx, rx):
+        v = X - D
+        r = np.linalg.norm(v - np.dot(v, w.e) * w.e)
+        ph = angle(w, D, X)
+        m = min(m, r * abs(np.sin(min(ph, abs(w.n * np.pi - ph), np.pi / 2))))
+        if not (0.0 < ph < w.n * np.pi):
+            valid = False
+    if not valid:
+        return False, D, m
+    for p, q in ((tx, D), (D, rx)):
+        clear, mc = O.segment_clear(osc, p, q, w.f0, w.f1)
+        m = min(m, mc)
+        if not clear:
+            valid = False
+    return valid, D, m
 
 
 def diffracted_paths(osc, scene_verts, tx, rxs, ws=None) -> list:
@@ -169,16 +191,9 @@ def diffracted_paths(osc, scene_verts, tx, rxs, ws=None) -> list:
     out = []
     for r, rx in enumerate(np.asarray(rxs, np.float64)):
         for wi, w in enumerate(ws):
-            t, D = diffraction_point(w, tx, rx)
-            if not (0.0 < t < w.length):
-                continue
-            pt, pr = angle(w, D, tx), angle(w, D, rx)
-            if not (0.0 < pt < w.n * np.pi and 0.0 < pr < w.n * np.pi):
-                continue
-            if _occluded(osc, tx, D, w.f0) or _occluded(osc, D, rx, w.f0) or \
-               _occluded(osc, tx, D, w.f1) or _occluded(osc, D, rx, w.f1):
-                continue
-            out.append(DPath(r, wi, D, float(np.linalg.norm(D - tx) + np.linalg.norm(rx - D))))
+            ok, D, m = evaluate(osc, w, tx, rx)
+            if ok:
+                out.append(DPath(r, wi, D, float(np.linalg.norm(D - tx) + np.linalg.norm(rx - D)), m))
     return out
 
 

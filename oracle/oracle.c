@@ -795,6 +795,12 @@ int ora_closest_hit(int T, const double* V, const double* o, const double* d, in
     return closest_hit(V, T, o, d, exclude, tmin, eps, t, margin);
 }
 
+/* Segment occlusion test (exposed for the diffraction oracle). */
+int ora_segment_clear(int T, const double* V, const double* p, const double* q, int ex0, int ex1, double tmin,
+                      double eps, double* margin) {
+    return segment_clear(V, T, p, q, ex0, ex1, tmin, eps, margin);
+}
+
 /* Fresnel coefficients (exposed for the closed-form pins). */
 void ora_fresnel(double eps_r, double sigma, double fc, double cos1, double* rperp, double* rpar) {
     double omega = 2.0 * ORA_PI * fc;

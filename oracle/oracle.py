@@ -117,6 +117,14 @@ def closest_hit(osc: OScene, o, d, exclude=-1):
     return i, t.value, m.value
 
 
+def segment_clear(osc: OScene, p, q, ex0=-1, ex1=-1):
+    """Is the segment p -> q free of occluders other than ex0 / ex1? (clear, margin)."""
+    m = ctypes.c_double()
+    c = lib().ora_segment_clear(osc.T, _p(osc.V), _p(_f64(p)), _p(_f64(q)), ex0, ex1, ctypes.c_double(osc.tmin),
+                                ctypes.c_double(osc.eps), ctypes.byref(m))
+    return bool(c), m.value
+
+
 def trace_sbr(osc: OScene, tx, N: int, D: int, ray_ids=None):
     """Per-ray hit lists [n, D] (int32, -1 after a miss) and prefix margins [n, D]."""
     ray_ids = np.arange(N, dtype=np.int64) if ray_ids is None else _i64(ray_ids)

@@ -15,6 +15,10 @@ int export_candidates(rt_ctx* ctx, int32_t* tx, int32_t* depth, int32_t* seq, in
 int cir_impl(rt_ctx* ctx, uint32_t flags, float* a, float* tau);
 int doppler_impl(rt_ctx* ctx, const float* a, const float* vtx, const float* vrx, double fs, int T, float* a_t);
 int array_impl(rt_ctx* ctx, const float* a, const float* tel, int Mt, const float* rel, int Mr, float* a_el);
+int diffraction_impl(rt_ctx* ctx, int64_t* n_out);
+int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau);
+int diffraction_get_impl(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points);
+int wedges_impl(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
 int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
@@ -244,7 +248,9 @@ int rt_destroy(rt_ctx* ctx) {
     for (DevBuf* b : {&ctx->nodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->planes64, &ctx->mat, &ctx->mats, &ctx->tx_pos,
                       &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->keys, &ctx->keys_alt,
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
-                      &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs, &ctx->path_key,
+                      &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs,
+                      &ctx->verts_in, &ctx->wedges, &ctx->dpath_raw_key, &ctx->dpath_raw_pt, &ctx->dpath_key,
+                      &ctx->dpath_key_alt, &ctx->dpath_idx, &ctx->dpath_idx_alt, &ctx->dpath_pt, &ctx->dpath_off, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
@@ -304,7 +310,13 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
     ctx->has_scene = false;
     ctx->n_paths = 0;
     ctx->n_cand = 0;
+    ctx->n_dpaths = 0;
+    ctx->scene_gen++;
     ctx->n_mat = n_mat;
+    RT_TRY(buf_reserve(ctx->verts_in, sizeof(float) * 9 * std::max<int64_t>(n_tris, 1)));
+    if (n_tris > 0)
+        RT_TRY(cudaMemcpyAsync(ctx->verts_in.p, verts, sizeof(float) * 9 * n_tris, cudaMemcpyDeviceToDevice,
+                               ctx->stream));
     RT_TRY(buf_reserve(ctx->mats, sizeof(float) * 2 * n_mat));
     RT_TRY(cudaMemcpyAsync(ctx->mats.p, mat_params, sizeof(float) * 2 * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
     RT_TRY(buf_reserve(ctx->mat, sizeof(int32_t) * std::max<int64_t>(n_tris, 1)));
@@ -491,6 +503,34 @@ int rt_apply_array(rt_ctx* ctx, const float* a, const float* tx_elements, int32_
     // no element list: one element at the centre
     return array_impl(ctx, a, n_tx_el > 0 ? tx_elements : nullptr, std::max(n_tx_el, 1),
                       n_rx_el > 0 ? rx_elements : nullptr, std::max(n_rx_el, 1), a_el);
+}
+
+int rt_compute_diffraction(rt_ctx* ctx, int64_t* num_paths) {
+    CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "compute_diffraction");
+    if (!num_paths) return set_err(ctx, RT_ERR_INVALID_ARG, "compute_diffraction: null count");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "compute_diffraction: scene, transmitters and receivers must be set");
+    return diffraction_impl(ctx, num_paths);
+}
+
+int rt_get_diffraction(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points) {
+    CHECK_CTX(ctx);
+    return diffraction_get_impl(ctx, offsets, wedge, points);
+}
+
+int rt_diffraction_cir(rt_ctx* ctx, float* a, float* tau) {
+    CHECK_CTX(ctx);
+    if ((!a || !tau) && ctx->n_dpaths > 0) return set_err(ctx, RT_ERR_INVALID_ARG, "diffraction_cir: null output");
+    return diffraction_cir_impl(ctx, a, tau);
+}
+
+int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext) {
+    CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "get_wedges");
+    if (!n_out) return set_err(ctx, RT_ERR_INVALID_ARG, "get_wedges: null count");
+    if (!ctx->has_scene) return set_err(ctx, RT_ERR_INVALID_ARG, "get_wedges: no scene");
+    return wedges_impl(ctx, n_out, faces, n_ext);
 }
 
 int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int32_t K, float* H) {

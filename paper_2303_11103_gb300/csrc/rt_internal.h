@@ -65,6 +65,13 @@ struct rt_ctx {
     DevBuf htab_key, htab_wit, htab_cnt;           // duplicate-removal hash table
     DevBuf dop_cyc;                                // Doppler cycles per time step, per path
     DevBuf arr_dirs;                               // per path: R_tx^T kt / lambda, R_rx^T kr / lambda
+    // first-order diffraction: input vertices (kept for the edge search),
+    // wedges of the scene, diffracted paths sorted by (pair, wedge)
+    DevBuf verts_in, wedges;
+    int64_t scene_gen = 0, wedge_gen = -1;
+    int n_wedges = 0;
+    int64_t n_dpaths = 0, dpath_cap = 0;
+    DevBuf dpath_raw_key, dpath_raw_pt, dpath_key, dpath_key_alt, dpath_idx, dpath_idx_alt, dpath_pt, dpath_off;
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
     int64_t path_cap = 0;

@@ -80,6 +80,10 @@ def lib():
             "rt_cir": [vp, u32, vp, vp],
             "rt_apply_doppler": [vp, vp, vp, vp, dbl, i32, vp],
             "rt_apply_array": [vp, vp, vp, i32, vp, i32, vp],
+            "rt_compute_diffraction": [vp, ctypes.POINTER(i64)],
+            "rt_get_diffraction": [vp, vp, vp, vp],
+            "rt_diffraction_cir": [vp, vp, vp],
+            "rt_get_wedges": [vp, ctypes.POINTER(i64), vp, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -392,6 +396,7 @@ class Tracer:
         self.ntp = self.nrp = 1
         self.max_depth = 0
         self.n_paths = 0
+        self.n_dpaths = 0
         self.n_mat = 0
 
     def close(self):
@@ -419,6 +424,7 @@ class Tracer:
 
     def load_scene(self, scene):
         self.sync_stream()
+        self.n_dpaths = 0
         self._verts = self._t(scene.verts, torch.float32).reshape(-1, 9)
         self._mat = self._t(scene.mat_id, torch.int32)
         self._mats = self._t(scene.materials, torch.float32).reshape(-1, 2)
@@ -440,6 +446,7 @@ class Tracer:
 
     def set_tx(self, pos, ypr, antenna):
         self.sync_stream()
+        self.n_dpaths = 0
         pos = self._t(pos, torch.float32).reshape(-1, 3)
         ypr = self._t(ypr, torch.float32).reshape(-1, 3)
         rt_set_tx(self.ctx, pos, ypr, antenna)
@@ -448,6 +455,7 @@ class Tracer:
 
     def set_rx(self, pos, ypr, antenna, rx_set_offsets=None):
         self.sync_stream()
+        self.n_dpaths = 0
         pos = self._t(pos, torch.float32).reshape(-1, 3)
         ypr = self._t(ypr, torch.float32).reshape(-1, 3)
         rt_set_rx(self.ctx, pos, ypr, antenna, rx_set_offsets)
@@ -561,6 +569,43 @@ class Tracer:
         if self.n_paths:
             rt_apply_array(self.ctx, a_raw, te, re, out)
         return torch.view_as_complex(out[:P])
+
+    def compute_diffraction(self) -> int:
+        """Sec. II-B: first-order diffracted paths of every (tx, rx) pair; returns their count."""
+        self.sync_stream()
+        n = ctypes.c_int64()
+        _check(self.ctx, lib().rt_compute_diffraction(self.ctx, ctypes.byref(n)))
+        self.n_dpaths = int(n.value)
+        return self.n_dpaths
+
+    def diffraction(self):
+        """offsets [n_pairs+1], wedge [P], points [P, 3] of the diffracted paths."""
+        self.sync_stream()
+        P = self.n_dpaths
+        off = torch.empty(self.n_pairs + 1, dtype=torch.int64, device=self.device)
+        wedge = torch.empty(max(P, 1), dtype=torch.int32, device=self.device)
+        pts = torch.empty((max(P, 1), 3), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_get_diffraction(self.ctx, _ptr(off), _ptr(wedge), _ptr(pts)))
+        return {"offsets": off, "wedge": wedge[:P], "points": pts[:P]}
+
+    def wedges(self):
+        """faces [n, 2] (original triangle ids) and exterior angle / pi [n] of the scene's wedges."""
+        self.sync_stream()
+        n = ctypes.c_int64()
+        _check(self.ctx, lib().rt_get_wedges(self.ctx, ctypes.byref(n), None, None))
+        faces = torch.empty((max(n.value, 1), 2), dtype=torch.int32, device=self.device)
+        ne = torch.empty(max(n.value, 1), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_get_wedges(self.ctx, ctypes.byref(n), _ptr(faces), _ptr(ne)))
+        return faces[:n.value], ne[:n.value]
+
+    def diffraction_cir(self):
+        """a [P, nrp, ntp] complex64 and tau [P] of the diffracted paths (UTD)."""
+        self.sync_stream()
+        P = self.n_dpaths
+        a = torch.empty((max(P, 1), self.nrp, self.ntp, 2), dtype=torch.float32, device=self.device)
+        tau = torch.empty(max(P, 1), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_diffraction_cir(self.ctx, _ptr(a), _ptr(tau)))
+        return torch.view_as_complex(a[:P]), tau[:P]
 
     def pair_gain(self, a_raw, floor_db=-400.0):
         """[pairs, 2] = (has path, incoherent path gain dB) from cir_raw's a."""
