@@ -73,12 +73,6 @@ __device__ __forceinline__ void pair_devices(const int32_t* rx_off, int n_tx, in
     }
 }
 
-__device__ __forceinline__ float edge_angle(const WedgeDev& w, f3 D, f3 X) {
-    const f3 v = X - D;
-    float ph = atan2f(dot(v, xyz(w.n0)), dot(v, xyz(w.t0)));
-    return ph < 0.0f ? ph + 2.0f * RT_PI_F : ph;
-}
-
 // One thread per (pair, wedge): Keller point, exterior test, two segment
 // occlusion tests; valid paths are appended (order fixed afterwards by a sort).
 __global__ void __launch_bounds__(256) k_diff_find(DiffFind p) {
@@ -101,9 +95,15 @@ __global__ void __launch_bounds__(256) k_diff_find(DiffFind p) {
         const float tpar = ts + (tr - ts) * (rs / (rs + rr));
         if (!(tpar > 0.0f && tpar < w.a.w)) continue;
         const f3 D = A + e * tpar;
-        const float lim = w.e.w * RT_PI_F;
-        const float pht = edge_angle(w, D, tx), phr = edge_angle(w, D, rx);
-        if (!(pht > 0.0f && pht < lim && phr > 0.0f && phr < lim)) continue;
+        // outside the solid: on the exterior side of face 0 (v . n0 > 0) or of
+        // face 1, whose exterior normal is sin(n pi) t0 - cos(n pi) n0
+        float sn, cn;
+        sincospif(w.e.w, &sn, &cn);
+        const f3 vt = tx - D, vr = rx - D;
+        const float yt = dot(vt, xyz(w.n0)), yr = dot(vr, xyz(w.n0));
+        const bool out_t = yt > 0.0f || sn * dot(vt, xyz(w.t0)) - cn * yt > 0.0f;
+        const bool out_r = yr > 0.0f || sn * dot(vr, xyz(w.t0)) - cn * yr > 0.0f;
+        if (!(out_t && out_r)) continue;
         const int f0 = __float_as_int(w.t0.w), f1 = __float_as_int(w.n0.w);
         f3 d = D - tx;
         float L = sqrtf(dot(d, d));
@@ -224,9 +224,14 @@ struct DiffField {
     double lambda;
 };
 
-__global__ void k_diff_field(DiffField c, float2* __restrict__ a_out, float* __restrict__ tau) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.P) return;
+// Four lanes per path: lane j evaluates one of the four cot * F terms (the
+// FP64 transition function is the long part), a shuffle sums them, lane 0
+// finishes the path.
+__global__ void __launch_bounds__(64) k_diff_field(DiffField c, float2* __restrict__ a_out, float* __restrict__ tau) {
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+    const int sub = threadIdx.x & 3;
+    const bool live = i0 < c.P;
+    const int64_t i = live ? i0 : c.P - 1;   // lanes past the end repeat the last path and write nothing
     const uint64_t key = c.keys[i];
     const int64_t pair = (int64_t)(key >> 32);
     const WedgeDev w = c.w[key & 0xFFFFFFFFull];
@@ -266,8 +271,13 @@ __global__ void k_diff_field(DiffField c, float2* __restrict__ a_out, float* __r
     const double phi = angle(rx), phip = angle(tx), n = w.e.w;
     const double k = 2.0 * RT_PI_D / c.lambda;
     const double kL = k * s * sp * sin_b * sin_b / (s + sp);
-    const C64 d1 = cadd(utd_term(phi - phip, n, +1, kL), utd_term(phi - phip, n, -1, kL));
-    const C64 d2 = cadd(utd_term(phi + phip, n, +1, kL), utd_term(phi + phip, n, -1, kL));
+    // terms: 0: (phi - phi', +), 1: (phi - phi', -), 2: (phi + phi', +), 3: (phi + phi', -)
+    const C64 term = utd_term(sub < 2 ? phi - phip : phi + phip, n, (sub & 1) ? -1 : +1, kL);
+    const unsigned full = 0xffffffffu;
+    C64 pair_sum = {term.re + __shfl_xor_sync(full, term.re, 1), term.im + __shfl_xor_sync(full, term.im, 1)};
+    const C64 other = {__shfl_xor_sync(full, pair_sum.re, 2), __shfl_xor_sync(full, pair_sum.im, 2)};
+    if (!live || sub != 0) return;
+    const C64 d1 = pair_sum, d2 = other;   // lane 0 holds terms 0 + 1, lane 2 terms 2 + 3
     // pre = -exp(-j pi/4) / (2 n sqrt(2 pi k) sin b)
     const double m = 1.0 / (2.0 * n * sqrt(2.0 * RT_PI_D * k) * sin_b);
     const C64 pre = {-m * 0.70710678118654752, m * 0.70710678118654752};
@@ -479,7 +489,7 @@ int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau) {
     c.rxa = ctx->rx_ant;
     c.lambda = RT_C0_D / ctx->fc;
     prof_begin(ctx, "k_diff_field");
-    k_diff_field<<<(unsigned)((P + 63) / 64), 64, 0, ctx->stream>>>(c, (float2*)a, tau);
+    k_diff_field<<<(unsigned)((4 * P + 63) / 64), 64, 0, ctx->stream>>>(c, (float2*)a, tau);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
