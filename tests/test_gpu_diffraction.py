@@ -95,3 +95,34 @@ def test_diffraction_empty_and_rescene(tracer):
     setup(tracer, sc2, tx2, rx2)
     assert tracer.wedges()[0].shape[0] == 12
     assert tracer.compute_diffraction() > 0
+
+
+def test_diffraction_uneven_receiver_sets(tracer):
+    """Several transmitters with uneven receiver sets (one empty): every
+    pair's diffracted paths equal the oracle's for that transmitter."""
+    sc = S.city_scene(n_side=6, size=150.0, seed=5)
+    tx, rx = S.city_devices(sc, n_rx=12, half=70.0)
+    tx3 = S.Devices(np.concatenate([tx.pos, tx.pos + np.float32([[-5.0, 3.0, 2.0]]), tx.pos + np.float32([[4.0, 4.0, 0.0]])]),
+                    np.zeros((3, 3), np.float32), tx.antenna)
+    off = [0, 5, 5, 12]
+    setup(tracer, sc, tx3, rx, off)
+    tracer.compute_diffraction()
+    faces = [tuple(f) for f in tracer.wedges()[0].cpu().numpy()]
+    d = tracer.diffraction()
+    doff, wed = d["offsets"].cpu().numpy(), d["wedge"].cpu().numpy()
+    ws = DF.wedges(sc.verts)
+    osc = O.make_scene(sc)
+    n = 0
+    for t in range(3):
+        for r in range(off[t], off[t + 1]):
+            got = sorted(faces[k] for k in wed[doff[r]:doff[r + 1]])
+            want, edge = [], []
+            for w in ws:
+                ok, _, m = DF.evaluate(osc, w, tx3.pos[t], rx.pos[r])
+                if m < max(osc.eps, 1e-3):
+                    edge.append((w.f0, w.f1))
+                elif ok:
+                    want.append((w.f0, w.f1))
+            assert set(want) <= set(got) and set(got) - set(want) <= set(edge), (t, r)
+            n += len(got)
+    assert n > 0

@@ -85,3 +85,41 @@ def test_doppler_arguments(tracer):
     # devices at rest: every time step is the CIR
     at = tracer.apply_doppler(a, 1e6, 5, [0.0, 0.0, 0.0]).cpu().numpy()
     assert np.array_equal(at, np.repeat(a.cpu().numpy()[..., None], 5, axis=-1))
+
+
+def test_doppler_and_array_per_transmitter(tracer):
+    """Two transmitters with their own velocities and orientations: each path
+    takes its own transmitter's (Doppler against the oracle, array phases
+    against the oracle on the GPU's own coefficients)."""
+    sc = S.tiny_scene()
+    _, rx = S.tiny_devices(visible=True)
+    tx = S.Devices(np.array([[-60.0, 0.0, 25.0], [-50.0, 30.0, 20.0]], np.float32),
+                   np.array([[0.3, 0.0, 0.0], [-1.2, 0.1, 0.2]], np.float32), S.TR38901_VH)
+    setup(tracer, sc, tx, rx)
+    tracer.compute_paths(2, 20000)
+    gsets, p = gpu_paths(tracer)
+    a, _ = tracer.cir()
+    vt = np.array([[3.0, 0.0, 0.0], [0.0, -2.0, 1.0]], np.float32)
+    at = tracer.apply_doppler(a, 1e6, 6, vt).cpu().numpy()
+    el = rt.planar_array(2, 2, 0.5, 0.5, O.C0 / FC)
+    ael = tracer.apply_array(a, el).cpu().numpy()
+    a = a.cpu().numpy()
+    off = p["offsets"].cpu().numpy()
+    osc = O.make_scene(sc)
+    n = 0
+    for t in range(2):
+        ora, _ = O.compute_paths(osc, tx.pos[t], rx.pos, 2, 20000)
+        byseq = {q.seq: q for q in ora if q.valid}
+        for k, s in enumerate(gsets[t]):   # pair t: transmitter t, receiver 0
+            if s not in byseq:
+                continue
+            i = off[t] + k
+            q = byseq[s]
+            q0 = O.OPath(0, q.seq, q.valid, q.margin, q.points, q.length)
+            ref = O.doppler(a[i:i + 1].astype(np.complex128), [q0], tx.pos[t], rx.pos, FC, 1e6, 6, vt[t])[0]
+            assert np.all(np.abs(at[i] - ref) <= 2e-5 * np.abs(a[i])[..., None] + 1e-30)
+            refa = O.array_response(a[i:i + 1].astype(np.complex128), [q0], tx.pos[t], tx.ypr[t], rx.pos, rx.ypr,
+                                    FC, el, np.zeros((1, 3)))[0]
+            assert np.all(np.abs(ael[i] - refa) <= 3e-5 * np.abs(refa) + 1e-12)
+            n += 1
+    assert n >= 4
