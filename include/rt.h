@@ -258,6 +258,19 @@ int rt_get_diffraction(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* poi
  * complex (float re, im), tau [P] seconds; device pointers.
  */
 int rt_diffraction_cir(rt_ctx* ctx, float* a, float* tau);
+/*
+ * Sec. II-A (Listing 2: coverage_map(..., diffraction=True)): the
+ * first-order diffracted part of a coverage map. For every transmitter and
+ * every cell, the diffracted paths to the cell centre at g->height (found
+ * and weighted as in rt_compute_diffraction / rt_diffraction_cir, receiver
+ * antenna port 0 unrotated, transmit port tx_port) and the incoherent sum
+ * of their |a|^2, the path gain the specular map estimates per cell.
+ * gain [n_tx*ny*nx] float32 (device) is overwritten; add it to the
+ * rt_coverage_map gain for the map with diffraction. Errors:
+ * RT_ERR_INVALID_ARG for a bad grid or port or without scene and devices,
+ * RT_ERR_NOT_READY while capturing a graph.
+ */
+int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, float* gain);
 /* Wedges of the current scene: n_out (HOST) = count; faces [n*2] int32 the
  * two triangles (original ids, lower first), n_ext [n] exterior angle / pi;
  * device pointers, either may be NULL. Reads back (not while capturing). */

@@ -32,7 +32,9 @@ b0 = p x k_d, and the UTD coefficients
             + cot((pi - (phi - phi'))/(2n)) F(k L a-(phi - phi'))
             -/+ [ cot((pi + (phi + phi'))/(2n)) F(k L a+(phi + phi'))
                 + cot((pi - (phi + phi'))/(2n)) F(k L a-(phi + phi')) ] }
-(minus for soft, plus for hard), L = s s' sin^2 b / (s + s'),
+(minus for soft, plus for hard; a term whose cotangent is singular, exactly
+on a shadow or reflection boundary, takes the mean of its two one-sided
+limits, zero), L = s s' sin^2 b / (s + s'),
 a+-(x) = 2 cos^2((2 pi n N+- - x)/2) with N+- the integers nearest to
 (x +- pi)/(2 pi n), and the transition function
 F(x) = 2 j sqrt(x) exp(j x) int_{sqrt(x)}^inf exp(-j t^2) dt.
@@ -139,8 +141,13 @@ def utd_coefficients(n: float, phi: float, phip: float, sin_b: float, s: float, 
     pre = -np.exp(-1j * np.pi / 4.0) / (2.0 * n * np.sqrt(2.0 * np.pi * k) * sin_b)
 
     def term(beta, sign):
-        c = 1.0 / np.tan((np.pi + sign * beta) / (2.0 * n))
-        return c * transition(k * Lp * _a(beta, n, sign))
+        arg = (np.pi + sign * beta) / (2.0 * n)
+        if abs(np.sin(arg)) < 1e-12:
+            # exactly on a shadow or reflection boundary (a set of measure
+            # zero): the term's two one-sided limits are +-n sqrt(2 pi k L)
+            # exp(j pi/4); their mean, zero, is taken
+            return 0.0
+        return transition(k * Lp * _a(beta, n, sign)) / np.tan(arg)
 
     d1 = term(phi - phip, +1) + term(phi - phip, -1)
     d2 = term(phi + phip, +1) + term(phi + phip, -1)
@@ -181,6 +188,13 @@ def evaluate(osc, w: Wedge, tx, rx):
         m = min(m, mc)
         if not clear:
             valid = False
+    # distance from the shadow and reflection boundaries, where one UTD term
+    # changes sign (metres at the nearer device)
+    pt, pr = angle(w, D, tx), angle(w, D, rx)
+    near = min(np.linalg.norm(tx - D), np.linalg.norm(rx - D))
+    for beta in (pr - pt, pr + pt):
+        for sg in (1.0, -1.0):
+            m = min(m, near * 2.0 * w.n * abs(np.sin((np.pi + sg * beta) / (2.0 * w.n))))
     return valid, D, m
 
 
@@ -232,3 +246,33 @@ def diffracted_field(ws, paths, fc, txdev, rxdev, tx_index: int = 0):
                 a[i, pr_, q] = amp * (fr @ dyad @ ft)
         tau[i] = (s + sp) / O.C0
     return a, tau
+
+
+def diffraction_map(osc, scene_verts, txdev, grid, tx_port: int, rx_antenna, fc: float, ws=None):
+    """Diffracted part of a coverage map: per transmitter and cell, the sum of
+    |a|^2 (receiver port 0, unrotated, transmit port tx_port) over the
+    first-order diffracted paths to the cell centre at grid['h'].
+    Returns (gain [n_tx, ny, nx], margin [n_tx, ny, nx]: the smallest decision
+    margin of the cell's candidates)."""
+    from paper_2303_11103_gb300 import scenes as S   # device records only
+    ws = wedges(scene_verts) if ws is None else ws
+    nx, ny = int(grid["nx"]), int(grid["ny"])
+    gain = np.zeros((len(txdev.pos), ny, nx))
+    marg = np.full((len(txdev.pos), ny, nx), np.inf)
+    for t in range(len(txdev.pos)):
+        tx = S.Devices(txdev.pos[t:t + 1], txdev.ypr[t:t + 1], txdev.antenna)
+        for iy in range(ny):
+            for ix in range(nx):
+                c = np.array([grid["x0"] + (ix + 0.5) * grid["cell"], grid["y0"] + (iy + 0.5) * grid["cell"],
+                              grid["h"]], np.float64)
+                paths = []
+                for wi, w in enumerate(ws):
+                    ok, D, m = evaluate(osc, w, tx.pos[0], c)
+                    marg[t, iy, ix] = min(marg[t, iy, ix], m)
+                    if ok:
+                        paths.append(DPath(0, wi, D, 0.0, m))
+                if paths:
+                    rx = S.Devices(c[None].astype(np.float32), np.zeros((1, 3), np.float32), rx_antenna)
+                    a, _ = diffracted_field(ws, paths, fc, tx, rx)
+                    gain[t, iy, ix] = float((np.abs(a[:, 0, tx_port]) ** 2).sum())
+    return gain, marg

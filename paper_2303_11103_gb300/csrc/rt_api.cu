@@ -19,6 +19,7 @@ int diffraction_impl(rt_ctx* ctx, int64_t* n_out);
 int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau);
 int diffraction_get_impl(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points);
 int wedges_impl(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
+int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain);
 int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
@@ -250,7 +251,8 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->vals, &ctx->vals_alt, &ctx->ray_hits, &ctx->cand_key, &ctx->cand_wit, &ctx->cand_off,
                       &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs,
                       &ctx->verts_in, &ctx->wedges, &ctx->dpath_raw_key, &ctx->dpath_raw_pt, &ctx->dpath_key,
-                      &ctx->dpath_key_alt, &ctx->dpath_idx, &ctx->dpath_idx_alt, &ctx->dpath_pt, &ctx->dpath_off, &ctx->path_key,
+                      &ctx->dpath_key_alt, &ctx->dpath_idx, &ctx->dpath_idx_alt, &ctx->dpath_pt, &ctx->dpath_off,
+                      &ctx->dmap_key, &ctx->dmap_pt, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
@@ -523,6 +525,17 @@ int rt_diffraction_cir(rt_ctx* ctx, float* a, float* tau) {
     CHECK_CTX(ctx);
     if ((!a || !tau) && ctx->n_dpaths > 0) return set_err(ctx, RT_ERR_INVALID_ARG, "diffraction_cir: null output");
     return diffraction_cir_impl(ctx, a, tau);
+}
+
+int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, float* gain) {
+    CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "coverage_map_diffraction");
+    if (!g || !gain || g->nx < 1 || g->ny < 1 || !(g->cell > 0.0f) || tx_port < 0 || tx_port >= ctx->tx_ant.n_ports ||
+        (int64_t)g->nx * g->ny * ctx->n_tx >= (1ll << 32))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_diffraction: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_diffraction: scene, transmitters and receivers must be set");
+    return diffraction_map_impl(ctx, g, tx_port, gain);
 }
 
 int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext) {

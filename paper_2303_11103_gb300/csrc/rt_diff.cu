@@ -42,6 +42,17 @@ struct WedgeDev {
     float4 a, e, t0, n0;
 };
 
+// Receivers at the centres of a coverage-map grid (nx = 0: the context's receivers)
+struct CellGrid {
+    float x0, y0, cell, h;
+    int nx, ny;
+};
+
+__device__ __forceinline__ f3 cell_centre(const CellGrid& g, int64_t r) {
+    const int64_t iy = r / g.nx, ix = r - iy * g.nx;
+    return mk(g.x0 + ((float)ix + 0.5f) * g.cell, g.y0 + ((float)iy + 0.5f) * g.cell, g.h);
+}
+
 struct DiffFind {
     DevScene s;
     const WedgeDev* w;
@@ -51,6 +62,7 @@ struct DiffFind {
     const int32_t* rx_off;   // [n_tx+1] or null
     int n_tx, n_rx;
     int64_t total;           // pairs * wedges
+    CellGrid grid;           // receivers at cell centres when grid.nx > 0
     unsigned long long* count;
     unsigned long long cap;
     uint64_t* keys;          // pair << 32 | wedge
@@ -87,7 +99,8 @@ __global__ void __launch_bounds__(256) k_diff_find(DiffFind p) {
         const WedgeDev w = p.w[wi];
         const f3 A = xyz(w.a), e = xyz(w.e);
         const f3 tx = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
-        const f3 rx = mk(p.rx_pos[3 * r], p.rx_pos[3 * r + 1], p.rx_pos[3 * r + 2]);
+        const f3 rx = p.grid.nx > 0 ? cell_centre(p.grid, r)
+                                    : mk(p.rx_pos[3 * r], p.rx_pos[3 * r + 1], p.rx_pos[3 * r + 2]);
         const float ts = dot(tx - A, e), tr = dot(rx - A, e);
         const f3 ps = tx - A - e * ts, pr = rx - A - e * tr;
         const float rs = sqrtf(dot(ps, ps)), rr = sqrtf(dot(pr, pr));
@@ -222,6 +235,9 @@ struct DiffField {
     int n_tx, n_rx;
     DevAntenna txa, rxa;
     double lambda;
+    CellGrid grid;   // map mode when grid.nx > 0: receiver port 0, unrotated, at the cell centres
+    int tx_port;     // map mode: the transmit port
+    float* map;      // map mode: [n_tx][ny][nx] sum of |a|^2
 };
 
 // Four lanes per path: lane j evaluates one of the four cot * F terms (the
@@ -241,7 +257,9 @@ __global__ void __launch_bounds__(64) k_diff_field(DiffField c, float2* __restri
     const float4 Dp = c.pts[i];
     const double D[3] = {Dp.x, Dp.y, Dp.z};
     const double tx[3] = {c.tx_pos[3 * t], c.tx_pos[3 * t + 1], c.tx_pos[3 * t + 2]};
-    const double rx[3] = {c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]};
+    const bool map = c.grid.nx > 0;
+    f3 rxf = map ? cell_centre(c.grid, r) : mk(c.rx_pos[3 * r], c.rx_pos[3 * r + 1], c.rx_pos[3 * r + 2]);
+    const double rx[3] = {rxf.x, rxf.y, rxf.z};
     double ki[3], kd[3];
     for (int q = 0; q < 3; q++) { ki[q] = D[q] - tx[q]; kd[q] = rx[q] - D[q]; }
     const double sp = sqrt(ki[0] * ki[0] + ki[1] * ki[1] + ki[2] * ki[2]);
@@ -291,11 +309,11 @@ __global__ void __launch_bounds__(64) k_diff_field(DiffField c, float2* __restri
     const double amp = c.lambda / (4.0 * RT_PI_D) / sqrt(s * sp * len);
     const C64 ea = {amp * cph, amp * sph};
     const Rot<float> Rt = rot_ypr(c.tx_ypr[3 * t], c.tx_ypr[3 * t + 1], c.tx_ypr[3 * t + 2]);
-    const Rot<float> Rr = rot_ypr(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
+    const Rot<float> Rr = map ? rot_ypr(0.0f, 0.0f, 0.0f) : rot_ypr(c.rx_ypr[3 * r], c.rx_ypr[3 * r + 1], c.rx_ypr[3 * r + 2]);
     const V3<float> ui = {(float)ki[0], (float)ki[1], (float)ki[2]};
     const V3<float> ud = {(float)-kd[0], (float)-kd[1], (float)-kd[2]};
-    const int ntp = c.txa.n_ports, nrp = c.rxa.n_ports;
-    for (int q = 0; q < ntp; q++) {
+    const int ntp = c.txa.n_ports, nrp = map ? 1 : c.rxa.n_ports;
+    for (int q = map ? c.tx_port : 0; q < (map ? c.tx_port + 1 : ntp); q++) {
         const V3<float> ft = antenna_vec<float>(c.txa.kind, c.txa.slant[q], Rt, ui);
         // projections of the transmit pattern on the incident basis
         const double fbp = ft.x * bp[0] + ft.y * bp[1] + ft.z * bp[2];
@@ -307,10 +325,13 @@ __global__ void __launch_bounds__(64) k_diff_field(DiffField c, float2* __restri
             // F_rx . (-Ds bd bp^T - Dh ph pp^T) . F_tx
             const C64 v = cadd(cscale(Ds, -rbd * fbp), cscale(Dh, -rph * fpp));
             const C64 av = cmul(ea, v);
-            a_out[(i * nrp + pq) * ntp + q] = make_float2((float)av.re, (float)av.im);
+            if (map)
+                atomicAdd(c.map + (size_t)t * c.grid.nx * c.grid.ny + r, (float)(av.re * av.re + av.im * av.im));
+            else
+                a_out[(i * nrp + pq) * ntp + q] = make_float2((float)av.re, (float)av.im);
         }
     }
-    tau[i] = (float)(len / RT_C0_D);
+    if (!map) tau[i] = (float)(len / RT_C0_D);
 }
 
 }  // namespace
@@ -415,6 +436,7 @@ int diffraction_impl(rt_ctx* ctx, int64_t* n_out) {
     p.n_tx = ctx->n_tx;
     p.n_rx = ctx->n_rx;
     p.total = total;
+    p.grid = CellGrid{0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
     unsigned long long cap = std::max<unsigned long long>(1ull << 14, (unsigned long long)ctx->dpath_cap);
     unsigned long long found = 0;
     for (int attempt = 0; attempt < 2; attempt++) {
@@ -488,6 +510,9 @@ int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau) {
     c.txa = ctx->tx_ant;
     c.rxa = ctx->rx_ant;
     c.lambda = RT_C0_D / ctx->fc;
+    c.grid = CellGrid{0.0f, 0.0f, 0.0f, 0.0f, 0, 0};
+    c.tx_port = 0;
+    c.map = nullptr;
     prof_begin(ctx, "k_diff_field");
     k_diff_field<<<(unsigned)((4 * P + 63) / 64), 64, 0, ctx->stream>>>(c, (float2*)a, tau);
     prof_end(ctx);
@@ -534,5 +559,79 @@ int wedges_impl(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext) {
     if (n_ext)
         RT_TRY(cudaMemcpyAsync(n_ext, n.data(), sizeof(float) * n.size(), cudaMemcpyHostToDevice, ctx->stream));
     RT_TRY(cudaStreamSynchronize(ctx->stream));
+    return RT_OK;
+}
+
+// Diffracted coverage map: every transmitter against every cell centre
+// (receiver port 0, unrotated, as the specular map), the incoherent sum of
+// |a|^2 of its first-order diffracted paths; gain [n_tx*ny*nx] overwritten.
+int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain) {
+    {
+        const int eb = build_wedges(ctx);
+        if (eb) return eb;
+    }
+    cudaStream_t st = ctx->stream;
+    const int64_t cells = (int64_t)g->nx * g->ny;
+    RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * cells * ctx->n_tx, st));
+    const int64_t n_pairs = cells * ctx->n_tx;
+    const int64_t total = n_pairs * ctx->n_wedges;
+    if (total == 0) return RT_OK;
+    const CellGrid grid{g->x0, g->y0, g->cell, g->height, g->nx, g->ny};
+    DiffFind p;
+    p.s = dev_scene(ctx);
+    p.w = bp<WedgeDev>(ctx->wedges);
+    p.n_w = ctx->n_wedges;
+    p.tx_pos = bp<float>(ctx->tx_pos);
+    p.rx_pos = nullptr;
+    p.rx_off = nullptr;
+    p.n_tx = ctx->n_tx;
+    p.n_rx = (int)cells;
+    p.total = total;
+    p.grid = grid;
+    unsigned long long cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)ctx->dmap_cap);
+    unsigned long long found = 0;
+    for (int attempt = 0; attempt < 2; attempt++) {
+        RT_TRY(buf_reserve(ctx->dmap_key, sizeof(uint64_t) * cap));
+        RT_TRY(buf_reserve(ctx->dmap_pt, sizeof(float4) * cap));
+        RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), st));
+        p.count = bp<unsigned long long>(ctx->counters);
+        p.cap = cap;
+        p.keys = bp<uint64_t>(ctx->dmap_key);
+        p.pts = bp<float4>(ctx->dmap_pt);
+        const int64_t blocks = std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->num_sms);
+        prof_begin(ctx, "k_diff_find");
+        k_diff_find<<<(unsigned)blocks, 256, 0, st>>>(p);
+        prof_end(ctx);
+        RT_TRY(cudaGetLastError());
+        RT_TRY(cudaMemcpyAsync(ctx->host_rb, ctx->counters.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        RT_TRY(cudaStreamSynchronize(st));
+        found = ctx->host_rb[0];
+        if (found <= cap) break;
+        cap = found;
+    }
+    ctx->dmap_cap = (int64_t)cap;
+    if (found == 0) return RT_OK;
+    DiffField c;
+    c.w = bp<WedgeDev>(ctx->wedges);
+    c.keys = bp<uint64_t>(ctx->dmap_key);
+    c.pts = bp<float4>(ctx->dmap_pt);
+    c.P = (int64_t)found;
+    c.tx_pos = bp<float>(ctx->tx_pos);
+    c.tx_ypr = bp<float>(ctx->tx_ypr);
+    c.rx_pos = nullptr;
+    c.rx_ypr = nullptr;
+    c.rx_off = nullptr;
+    c.n_tx = ctx->n_tx;
+    c.n_rx = (int)cells;
+    c.txa = ctx->tx_ant;
+    c.rxa = ctx->rx_ant;
+    c.lambda = RT_C0_D / ctx->fc;
+    c.grid = grid;
+    c.tx_port = tx_port;
+    c.map = gain;
+    prof_begin(ctx, "k_diff_field");
+    k_diff_field<<<(unsigned)((4 * c.P + 63) / 64), 64, 0, st>>>(c, nullptr, nullptr);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
     return RT_OK;
 }

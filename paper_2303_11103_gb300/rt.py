@@ -84,6 +84,7 @@ def lib():
             "rt_get_diffraction": [vp, vp, vp, vp],
             "rt_diffraction_cir": [vp, vp, vp],
             "rt_get_wedges": [vp, ctypes.POINTER(i64), vp, vp],
+            "rt_coverage_map_diffraction": [vp, ctypes.POINTER(rt_grid), i32, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -597,6 +598,16 @@ class Tracer:
         ne = torch.empty(max(n.value, 1), dtype=torch.float32, device=self.device)
         _check(self.ctx, lib().rt_get_wedges(self.ctx, ctypes.byref(n), _ptr(faces), _ptr(ne)))
         return faces[:n.value], ne[:n.value]
+
+    def coverage_map_diffraction(self, grid: dict, tx_port: int = 0):
+        """First-order diffracted part of the coverage map [n_tx, ny, nx]: the
+        incoherent path gain of the diffracted paths to every cell centre."""
+        self.sync_stream()
+        g = rt_grid(float(grid["x0"]), float(grid["y0"]), float(grid["cell"]), float(grid["h"]),
+                    int(grid["nx"]), int(grid["ny"]))
+        gain = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_coverage_map_diffraction(self.ctx, ctypes.byref(g), int(tx_port), _ptr(gain)))
+        return gain
 
     def diffraction_cir(self):
         """a [P, nrp, ntp] complex64 and tau [P] of the diffracted paths (UTD)."""

@@ -126,3 +126,22 @@ def test_diffraction_uneven_receiver_sets(tracer):
             assert set(want) <= set(got) and set(got) - set(want) <= set(edge), (t, r)
             n += len(got)
     assert n > 0
+
+
+def test_diffraction_coverage_map_matches_oracle(tracer):
+    """The diffracted part of a coverage map (Listing 2's coverage map with
+    diffraction) around the tiny scene's box, per cell against the oracle's
+    sum over the diffracted paths to the cell centre."""
+    sc = S.tiny_scene()
+    tx = S.Devices(np.array([[-60.0, 0.0, 25.0]], np.float32), np.array([[0.2, 0.05, 0.0]], np.float32),
+                   S.TR38901_VH)
+    rx = S.Devices(np.zeros((1, 3), np.float32), np.zeros((1, 3), np.float32), S.V_ISO)
+    setup(tracer, sc, tx, rx)
+    grid = dict(x0=-64.0, y0=-64.0, cell=8.0, nx=16, ny=16, h=1.5)
+    for port in (0, 1):
+        g = tracer.coverage_map_diffraction(grid, port).cpu().numpy()
+        og, om = DF.diffraction_map(O.make_scene(sc), sc.verts, tx, grid, port, rx.antenna, FC)
+        sure = om > 1e-3
+        assert np.count_nonzero(og[sure] > 0) >= 20
+        bad = sure & ~(np.abs(g - og) <= 2e-3 * og + 1e-12 * og.max())
+        assert not bad.any(), [(tuple(ix), g[tuple(ix)], og[tuple(ix)], om[tuple(ix)]) for ix in np.argwhere(bad)[:8]]
