@@ -504,9 +504,19 @@ def diffraction_measurement(tr):
         t_find.append((t1 - t0) * 1e3)
         t_cir.append((t2 - t1) * 1e3)
     faces, _ = tr.wedges()
+    # the diffracted part of the step's 500 x 500 coverage map (every cell centre against every wedge)
+    tr.coverage_map_diffraction(GRID, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    gd = tr.coverage_map_diffraction(GRID, 0)
+    torch.cuda.synchronize()
+    t_map = (time.perf_counter() - t0) * 1e3
+    cells = GRID["nx"] * GRID["ny"]
     return {"wedges": int(faces.shape[0]), "pairs": int(tr.n_pairs), "diffracted_paths": int(P),
             "find_ms": statistics.median(t_find), "cir_ms": statistics.median(t_cir),
-            "candidates_per_s": int(faces.shape[0]) * int(tr.n_pairs) / (statistics.median(t_find) / 1e3)}
+            "candidates_per_s": int(faces.shape[0]) * int(tr.n_pairs) / (statistics.median(t_find) / 1e3),
+            "map_ms": t_map, "map_cells": cells, "map_cells_with_diffraction": int((gd > 0).sum().item()),
+            "map_candidates_per_s": int(faces.shape[0]) * cells / (t_map / 1e3)}
 
 
 def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,

@@ -80,6 +80,8 @@ def test_diffraction_matches_oracle(tracer, case):
         for j in js:
             i = osel[j][0]
             assert abs(tau[i] - otau[j]) <= TAU_REL * otau[j]
+            if osel[j][1].margin < 1e-3:
+                continue   # on a shadow or reflection boundary: one term's sign is a rounding decision
             err = np.abs(a[i] - oa[j])
             assert np.all(err <= A_REL * np.abs(oa[j]) + A_ABS * amax), (r, osel[j][1].wedge, a[i], oa[j])
 
