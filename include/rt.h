@@ -325,7 +325,8 @@ int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth,
  *   blocks_per_sm caps the map's resident blocks per SM (0 = as many as
  *     fit), leaving room for the other stream's kernels.
  * rt_join(ctx) orders the context's stream after the map; read gain and hits
- * only after it, and keep them allocated until then. The calls that change
+ * only after it, and keep them allocated until then. rt_destroy waits for a
+ * started map and drops one still waiting for a path trace. The calls that change
  * what the map reads (rt_load_scene, rt_set_materials, rt_set_frequency,
  * rt_set_tx, rt_set_rx, rt_set_tuning, another coverage map, rt_autotune, a
  * rt_compute_paths with another num_rays) join first by themselves, and so

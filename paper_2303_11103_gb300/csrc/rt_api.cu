@@ -236,7 +236,7 @@ int rt_create(rt_ctx** out, int device, void* stream) {
 int rt_destroy(rt_ctx* ctx) {
     if (!ctx) return RT_OK;
     cudaSetDevice(ctx->device);
-    if (ctx->side_deferred) side_launch(ctx);
+    ctx->side_deferred = false;   // a map still waiting for a path trace is dropped, not started
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->side) {
         cudaStreamSynchronize(ctx->side);

@@ -158,3 +158,22 @@ def test_dedup_modes_identical(tracer, n_tx):
         assert len(cands[0][0]) > 8192
     with pytest.raises(rt.RtError):
         tracer.set_dedup(5)
+
+
+def test_extensions_with_no_paths(tracer):
+    """Doppler, arrays and diffraction on a context without paths: empty
+    outputs, no error; a ground-only scene has no wedges."""
+    sc = S.ground_only_scene(100.0)
+    tx, rx = _devices(3)
+    setup(tracer, sc, tx, rx)
+    tracer.compute_paths(0, 0, los=False)
+    assert tracer.n_paths == 0
+    a = torch.zeros((0, 1, 1), dtype=torch.complex64, device="cuda")
+    assert tracer.apply_doppler(a, 1e6, 4, [1.0, 0.0, 0.0]).shape == (0, 1, 1, 4)
+    assert tracer.apply_array(a, np.zeros((2, 3))).shape == (0, 1, 2)
+    assert tracer.compute_diffraction() == 0
+    ad, td = tracer.diffraction_cir()
+    assert ad.shape[0] == 0 and td.shape[0] == 0
+    assert tracer.diffraction()["offsets"].cpu().numpy().tolist() == [0, 0, 0, 0]
+    g = tracer.coverage_map_diffraction(dict(x0=-50.0, y0=-50.0, cell=10.0, nx=10, ny=10, h=1.5))
+    assert float(g.abs().sum()) == 0.0
