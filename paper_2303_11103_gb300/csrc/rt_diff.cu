@@ -459,6 +459,7 @@ int diffraction_impl(rt_ctx* ctx, int64_t* n_out) {
         cap = found;   // grow and trace again
     }
     ctx->dpath_cap = (int64_t)cap;
+    if (found > cap) return set_err(ctx, RT_ERR_CUDA, "compute_diffraction: path count changed between passes");
     const int64_t P = (int64_t)found;
     if (P == 0) return RT_OK;
     // order: (pair, wedge); positions carried along and gathered
@@ -610,6 +611,7 @@ int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain
         cap = found;
     }
     ctx->dmap_cap = (int64_t)cap;
+    if (found > cap) return set_err(ctx, RT_ERR_CUDA, "coverage_map_diffraction: path count changed between passes");
     if (found == 0) return RT_OK;
     DiffField c;
     c.w = bp<WedgeDev>(ctx->wedges);
