@@ -253,6 +253,8 @@ def run_ours(args):
     out_h = {"H": torch.empty(H.shape, dtype=H.dtype).pin_memory(),
              "gain": torch.empty(gain.shape, dtype=gain.dtype).pin_memory()}
     copy_stream = torch.cuda.Stream(device=dev)
+    pin = {"a": torch.empty(1 << 16, dtype=torch.float32).pin_memory(),
+           "tau": torch.empty(1 << 14, dtype=torch.float32).pin_memory()}
 
     def read_H():
         # the 16 MB H(f) goes back on a copy stream while the VJPs and the
@@ -271,8 +273,14 @@ def run_ours(args):
         inp = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
         step(inp, after_freq=read_H)
         out_h["gain"].copy_(gain, non_blocking=True)
-        a_h = state["a"].to("cpu", non_blocking=True)
-        tau_h = state["tau"].to("cpu", non_blocking=True)
+        # a and tau into pinned host buffers (grown when a step has more paths)
+        na, nt = state["a"].numel(), state["tau"].numel()
+        if pin["a"].numel() < na:
+            pin["a"] = torch.empty(2 * na, dtype=torch.float32).pin_memory()
+        if pin["tau"].numel() < nt:
+            pin["tau"] = torch.empty(2 * nt, dtype=torch.float32).pin_memory()
+        pin["a"][:na].copy_(state["a"].reshape(-1), non_blocking=True)
+        pin["tau"][:nt].copy_(state["tau"].reshape(-1), non_blocking=True)
         stream.wait_stream(copy_stream)
         e1.record(stream)
         e1.synchronize()
