@@ -1,0 +1,73 @@
+"""FP64 oracle of first-order diffuse scattering (Sec. II-B lists diffuse
+reflections, i.e. scattering, among the features and leaves the model to
+the documentation; the reading here is the effective-roughness model with a
+Lambertian pattern).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, never by the product path. It
+shares no code with the CUDA library; hits and occlusion use the oracle's
+brute-force closest hit and segment test.
+
+Each of the N Fibonacci-lattice rays of a transmitter carries the fraction
+|F_tx,q(d)|^2 / N of the transmitted power (its solid angle 4 pi / N). Where
+it first hits a surface of scattering coefficient S, the fraction S^2 of
+that power is re-radiated with the Lambertian intensity pattern
+cos(theta_s) / pi on the side the ray came from. A receiver at distance r
+from the hit point in that half-space, with the segment to it unoccluded,
+collects with the effective aperture lambda^2 / (4 pi) |F_rx,p|^2, and the
+scattered wave is taken as depolarised, so a single-polarised port
+receives half of it:
+  g[p][q] += S^2 (|F_tx,q(d)|^2 / N) (cos theta_s / pi)
+             (lambda^2 / (4 pi r^2)) |F_rx,p(-k_s)|^2 / 2.
+The result is the incoherent scattered path gain of every (tx, rx) pair and
+port pair. The specular coefficients are left as they are.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as O
+
+
+def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=None, tx_index: int = 0):
+    """g [R, nrp, ntp]: incoherent first-order scattered gain from transmitter
+    tx_index to every receiver, over the lattice rays ray_ids (all N when None;
+    each ray keeps the weight 1/N). scene_mat: int [T] material ids; S [M]."""
+    lam = O.C0 / fc
+    tx = np.asarray(txdev.pos[tx_index], np.float64)
+    txa, rxa = txdev.antenna, rxdev.antenna
+    R = len(rxdev.pos)
+    g = np.zeros((R, len(rxa.slants), len(txa.slants)))
+    ids = np.arange(N) if ray_ids is None else np.asarray(ray_ids)
+    dirs = O.fibonacci(N)
+    for i in ids:
+        d = dirs[i]
+        j, t, _ = O.closest_hit(osc, tx, d, -1)
+        if j < 0:
+            continue
+        s = float(S[int(scene_mat[j])])
+        if s <= 0.0:
+            continue
+        V = osc.V[j].reshape(3, 3)
+        n = np.cross(V[1] - V[0], V[2] - V[0])
+        n /= np.linalg.norm(n)
+        if np.dot(d, n) > 0.0:
+            n = -n          # the side the ray came from
+        P = tx + t * d
+        ptx = np.array([np.dot(O.antenna(txa.kind, z, txdev.ypr[tx_index], d),
+                               O.antenna(txa.kind, z, txdev.ypr[tx_index], d)) for z in txa.slants])
+        for r in range(R):
+            rx = np.asarray(rxdev.pos[r], np.float64)
+            v = rx - P
+            dist = np.linalg.norm(v)
+            cs = np.dot(v, n) / dist
+            if cs <= 0.0:
+                continue
+            clear, _ = O.segment_clear(osc, P, rx, j, -1)
+            if not clear:
+                continue
+            ks = v / dist
+            prx = np.array([np.dot(O.antenna(rxa.kind, z, rxdev.ypr[r], -ks),
+                                   O.antenna(rxa.kind, z, rxdev.ypr[r], -ks)) for z in rxa.slants])
+            w = s * s / N * cs / np.pi * lam ** 2 / (4.0 * np.pi * dist ** 2) * 0.5
+            g[r] += w * np.outer(prx, ptx)
+    return g
