@@ -271,6 +271,26 @@ int rt_diffraction_cir(rt_ctx* ctx, float* a, float* tau);
  * RT_ERR_NOT_READY while capturing a graph.
  */
 int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, float* gain);
+/*
+ * Sec. II-B (diffuse reflections, i.e. scattering; the model is a reading,
+ * the paper leaves it to the documentation): scattering coefficients S
+ * [n_mat] float32 (device, 0..1) of the scene's materials; all zero (no
+ * scattering) until set, and reset by rt_load_scene. Errors:
+ * RT_ERR_INVALID_ARG for another material count.
+ */
+int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat);
+/*
+ * First-order diffuse scattering by the effective-roughness model with a
+ * Lambertian pattern: each of the num_rays Fibonacci rays of a transmitter
+ * carries |F_tx,q(d)|^2 / num_rays of its power; at its first hit the
+ * fraction S^2 is re-radiated with the intensity cos(theta_s)/pi towards
+ * the side the ray came from, and a receiver there with an unoccluded
+ * segment collects lambda^2/(4 pi r^2) |F_rx,p|^2 of it, half per port
+ * (depolarised wave). gain [n_pairs*nrp*ntp] float32 (device, overwritten):
+ * the incoherent scattered path gain of every pair and port pair. The
+ * specular coefficients are not changed. Errors: RT_ERR_INVALID_ARG.
+ */
+int rt_scattering_gain(rt_ctx* ctx, int64_t num_rays, float* gain);
 /* Wedges of the current scene: n_out (HOST) = count; faces [n*2] int32 the
  * two triangles (original ids, lower first), n_ext [n] exterior angle / pi;
  * device pointers, either may be NULL. Reads back (not while capturing). */

@@ -20,6 +20,7 @@ int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau);
 int diffraction_get_impl(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points);
 int wedges_impl(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
 int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain);
+int scattering_impl(rt_ctx* ctx, int64_t N, float* gain);
 int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
@@ -252,7 +253,7 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs,
                       &ctx->verts_in, &ctx->wedges, &ctx->dpath_raw_key, &ctx->dpath_raw_pt, &ctx->dpath_key,
                       &ctx->dpath_key_alt, &ctx->dpath_idx, &ctx->dpath_idx_alt, &ctx->dpath_pt, &ctx->dpath_off,
-                      &ctx->dmap_key, &ctx->dmap_pt, &ctx->path_key,
+                      &ctx->dmap_key, &ctx->dmap_pt, &ctx->scat, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
@@ -313,6 +314,7 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
     ctx->n_paths = 0;
     ctx->n_cand = 0;
     ctx->n_dpaths = 0;
+    ctx->scat_set = false;
     ctx->scene_gen++;
     ctx->n_mat = n_mat;
     RT_TRY(buf_reserve(ctx->verts_in, sizeof(float) * 9 * std::max<int64_t>(n_tris, 1)));
@@ -536,6 +538,25 @@ int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, 
     if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
         return set_err(ctx, RT_ERR_INVALID_ARG, "coverage_map_diffraction: scene, transmitters and receivers must be set");
     return diffraction_map_impl(ctx, g, tx_port, gain);
+}
+
+int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat) {
+    CHECK_CTX(ctx);
+    if (!ctx->has_scene || n_mat != ctx->n_mat || !coeff)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "set_scattering: material count differs from the scene's");
+    RT_TRY(buf_reserve(ctx->scat, sizeof(float) * n_mat));
+    RT_TRY(cudaMemcpyAsync(ctx->scat.p, coeff, sizeof(float) * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->scat_set = true;
+    return RT_OK;
+}
+
+int rt_scattering_gain(rt_ctx* ctx, int64_t num_rays, float* gain) {
+    CHECK_CTX(ctx);
+    if (num_rays < 0 || num_rays >= (1ll << 40) || !gain)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain: scene, transmitters and receivers must be set");
+    return scattering_impl(ctx, num_rays, gain);
 }
 
 int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext) {

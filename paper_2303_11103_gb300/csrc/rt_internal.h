@@ -73,6 +73,8 @@ struct rt_ctx {
     int64_t n_dpaths = 0, dpath_cap = 0;
     DevBuf dpath_raw_key, dpath_raw_pt, dpath_key, dpath_key_alt, dpath_idx, dpath_idx_alt, dpath_pt, dpath_off;
     DevBuf dmap_key, dmap_pt;   // diffracted coverage map: found (tx, cell, wedge) entries
+    DevBuf scat;                // [n_mat] scattering coefficients (rt_set_scattering)
+    bool scat_set = false;
     int64_t dmap_cap = 0;
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;

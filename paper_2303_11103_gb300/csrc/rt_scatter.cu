@@ -1,0 +1,147 @@
+// rt_scatter.cu -- first-order diffuse scattering (Sec. II-B lists diffuse
+// reflections, i.e. scattering, among the features and leaves the model to
+// the documentation). Reading used here: the effective-roughness model with
+// a Lambertian pattern, the scattered wave depolarised.
+//
+// Each of the N Fibonacci-lattice rays of a transmitter carries the fraction
+// |F_tx,q(d)|^2 / N of the transmitted power. Where it first hits a surface
+// of scattering coefficient S, the fraction S^2 is re-radiated with the
+// intensity pattern cos(theta_s)/pi on the side the ray came from; a
+// receiver there, with the segment to it unoccluded, collects with the
+// effective aperture lambda^2/(4 pi) |F_rx,p|^2, half of the depolarised
+// wave per port:
+//   g[pair][p][q] += S^2 (|F_tx,q(d)|^2/N) (cos theta_s/pi) (lambda^2/(4 pi r^2)) |F_rx,p(-k_s)|^2 / 2.
+// The result is the incoherent scattered gain of every pair and port pair.
+#include "rt_field.cuh"
+#include "rt_internal.h"
+
+namespace {
+
+struct ScatParams {
+    DevScene s;
+    const float* tx_pos;
+    const float* tx_ypr;
+    const float* rx_pos;
+    const float* rx_ypr;
+    const int32_t* rx_off;   // [n_tx+1] or null
+    const float* scat;       // [n_mat] scattering coefficients
+    int n_tx, n_rx;
+    long long N;
+    DevAntenna txa, rxa;
+    float w0;                // lambda^2 / (4 pi) / (2 pi N)
+    float* gain;             // [n_pairs][nrp][ntp]
+};
+
+// One thread per (transmitter, lattice ray): first hit, then every receiver
+// of that transmitter in order (the warp's lanes visit the same receiver
+// together and add their contributions with one atomic when they share the
+// transmitter).
+__global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
+    const unsigned full = 0xffffffffu;
+    const long long total = (long long)p.n_tx * p.N;
+    const long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long b = base; b < total; b += (long long)gridDim.x * blockDim.x) {
+        const long long slot = b + (threadIdx.x & 31);
+        const bool has = slot < total;
+        const int t = has ? (int)(slot / p.N) : p.n_tx - 1;
+        const long long i = has ? slot - (long long)t * p.N : 0;
+        const int t0 = __shfl_sync(full, t, 0);
+        const bool uniform = __all_sync(full, t == t0);
+        float s2 = 0.0f;
+        f3 P = mk(0, 0, 0), n = mk(0, 0, 1);
+        int hit = -1;
+        float ptx[2] = {0.0f, 0.0f};
+        if (has) {
+            const f3 o = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
+            const f3 d = fib_dir(p.N, i);
+            TravCount cnt;
+            float th;
+            hit = closest_hit<false>(p.s, nullptr, 0, o, d, -1, th, cnt);
+            if (hit >= 0) {
+                const float sc = __ldg(p.scat + __ldg(p.s.mat + hit));
+                s2 = sc * sc;
+                n = xyz(__ldg(p.s.planes + hit));
+                if (dot(d, n) > 0.0f) n = n * -1.0f;   // the side the ray came from
+                P = o + d * th;
+                const Rot<float> Rt = rot_ypr(p.tx_ypr[3 * t], p.tx_ypr[3 * t + 1], p.tx_ypr[3 * t + 2]);
+                for (int q = 0; q < p.txa.n_ports; q++) {
+                    const V3<float> f = antenna_vec<float>(p.txa.kind, p.txa.slant[q], Rt, V3<float>{d.x, d.y, d.z});
+                    ptx[q] = f.x * f.x + f.y * f.y + f.z * f.z;
+                }
+            }
+        }
+        const bool live = __any_sync(full, s2 > 0.0f);
+        if (!live) continue;
+        // receivers of this lane's transmitter
+        const int rb = p.rx_off ? p.rx_off[t] : 0, re = p.rx_off ? p.rx_off[t + 1] : p.n_rx;
+        const int nr = re - rb;
+        const int nr_max = __reduce_max_sync(full, (unsigned)nr);
+        for (int k = 0; k < nr_max; k++) {
+            float w = 0.0f, prx[2] = {0.0f, 0.0f};
+            const int r = rb + k;
+            if (s2 > 0.0f && k < nr) {
+                const f3 rx = mk(p.rx_pos[3 * r], p.rx_pos[3 * r + 1], p.rx_pos[3 * r + 2]);
+                const f3 v = rx - P;
+                const float dist = sqrtf(dot(v, v));
+                const float cs = dot(v, n) / dist;
+                if (cs > 0.0f) {
+                    const f3 ks = v * (1.0f / dist);
+                    TravCount cnt;
+                    if (!any_hit<false>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
+                        w = s2 * cs * p.w0 / (dist * dist);
+                        const Rot<float> Rr = rot_ypr(p.rx_ypr[3 * r], p.rx_ypr[3 * r + 1], p.rx_ypr[3 * r + 2]);
+                        for (int pp = 0; pp < p.rxa.n_ports; pp++) {
+                            const V3<float> f = antenna_vec<float>(p.rxa.kind, p.rxa.slant[pp], Rr,
+                                                                   V3<float>{-ks.x, -ks.y, -ks.z});
+                            prx[pp] = f.x * f.x + f.y * f.y + f.z * f.z;
+                        }
+                    }
+                }
+            }
+            const long long pair = p.rx_off ? (long long)r : (long long)t * p.n_rx + r;
+            for (int pp = 0; pp < p.rxa.n_ports; pp++)
+                for (int q = 0; q < p.txa.n_ports; q++) {
+                    float c = w * prx[pp] * ptx[q];
+                    if (uniform) {   // same transmitter and receiver in every lane: one atomic per warp
+                        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(full, c, o);
+                        if ((threadIdx.x & 31) == 0 && c != 0.0f && k < nr)
+                            atomicAdd(p.gain + (pair * p.rxa.n_ports + pp) * p.txa.n_ports + q, c);
+                    } else if (c != 0.0f) {
+                        atomicAdd(p.gain + (pair * p.rxa.n_ports + pp) * p.txa.n_ports + q, c);
+                    }
+                }
+        }
+    }
+}
+
+}  // namespace
+
+int scattering_impl(rt_ctx* ctx, int64_t N, float* gain) {
+    const int64_t n_pairs = ctx->rx_sets ? (int64_t)ctx->rx_off[ctx->n_tx] : (int64_t)ctx->n_tx * ctx->n_rx;
+    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
+    RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * (size_t)n_pairs * np, ctx->stream));
+    if (N == 0 || ctx->n_tris == 0 || !ctx->scat_set) return RT_OK;
+    ScatParams p;
+    p.s = dev_scene(ctx);
+    p.tx_pos = bp<float>(ctx->tx_pos);
+    p.tx_ypr = bp<float>(ctx->tx_ypr);
+    p.rx_pos = bp<float>(ctx->rx_pos);
+    p.rx_ypr = bp<float>(ctx->rx_ypr);
+    p.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
+    p.scat = bp<float>(ctx->scat);
+    p.n_tx = ctx->n_tx;
+    p.n_rx = ctx->n_rx;
+    p.N = N;
+    p.txa = ctx->tx_ant;
+    p.rxa = ctx->rx_ant;
+    const double lam = RT_C0_D / ctx->fc;
+    p.w0 = (float)(lam * lam / (4.0 * RT_PI_D) / (2.0 * RT_PI_D * (double)N));
+    p.gain = gain;
+    const long long total = (long long)ctx->n_tx * N;
+    const long long blocks = std::min<long long>((total + 127) / 128, 16ll * ctx->num_sms);
+    prof_begin(ctx, "k_scatter");
+    k_scatter<<<(unsigned)blocks, 128, 0, ctx->stream>>>(p);
+    prof_end(ctx);
+    RT_TRY(cudaGetLastError());
+    return RT_OK;
+}

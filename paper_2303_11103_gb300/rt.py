@@ -85,6 +85,8 @@ def lib():
             "rt_diffraction_cir": [vp, vp, vp],
             "rt_get_wedges": [vp, ctypes.POINTER(i64), vp, vp],
             "rt_coverage_map_diffraction": [vp, ctypes.POINTER(rt_grid), i32, vp],
+            "rt_set_scattering": [vp, vp, i32],
+            "rt_scattering_gain": [vp, i64, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -608,6 +610,20 @@ class Tracer:
         gain = torch.empty((self.n_tx, g.ny, g.nx), dtype=torch.float32, device=self.device)
         _check(self.ctx, lib().rt_coverage_map_diffraction(self.ctx, ctypes.byref(g), int(tx_port), _ptr(gain)))
         return gain
+
+    def set_scattering(self, coeff):
+        """Scattering coefficients S [n_mat] of the scene's materials (0..1)."""
+        self.sync_stream()
+        c = self._t(coeff, torch.float32).reshape(-1)
+        _check(self.ctx, lib().rt_set_scattering(self.ctx, _ptr(c), int(c.shape[0])))
+        torch.cuda.current_stream().synchronize()
+
+    def scattering_gain(self, num_rays: int):
+        """Incoherent first-order diffuse-scattering gain [n_pairs, nrp, ntp]."""
+        self.sync_stream()
+        g = torch.empty((self.n_pairs, self.nrp, self.ntp), dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_scattering_gain(self.ctx, int(num_rays), _ptr(g)))
+        return g
 
     def diffraction_cir(self):
         """a [P, nrp, ntp] complex64 and tau [P] of the diffracted paths (UTD)."""

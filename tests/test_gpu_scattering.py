@@ -1,0 +1,42 @@
+"""First-order diffuse scattering (rt_set_scattering, rt_scattering_gain;
+Sec. II-B) against the FP64 oracle over the same lattice rays."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle import scattering as SC
+from paper_2303_11103_gb300 import rt
+from paper_2303_11103_gb300 import scenes as S
+
+from gpu_helpers import FC, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tracer():
+    tr = rt.Tracer(0, FC)
+    yield tr
+    tr.close()
+
+
+def test_scattering_matches_oracle(tracer):
+    sc = S.tiny_scene()
+    tx = S.Devices(np.array([[-60.0, 0.0, 25.0]], np.float32), np.array([[0.2, 0.05, 0.0]], np.float32),
+                   S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [60.0, 10.0, 1.5], [30.0, 25.0, 1.5], [-20.0, -40.0, 6.0]],
+                            np.float32), np.array([[0.5, 0.0, 0.0]] * 4, np.float32),
+                   S.Antenna(S.ANT_DIPOLE, (np.pi / 4, -np.pi / 4)))
+    setup(tracer, sc, tx, rx)
+    N = 20000
+    assert float(tracer.scattering_gain(N).abs().sum()) == 0.0      # no coefficients set: no scattering
+    S_m = np.array([0.5], np.float32)
+    tracer.set_scattering(S_m)
+    g = tracer.scattering_gain(N).cpu().numpy()
+    og = SC.scattering_gain(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N)
+    assert g.shape == og.shape == (4, 2, 2)
+    assert (og > 0).sum() >= 8
+    # a lattice ray whose decision is near-degenerate may land on either side: 1e-3 of the total
+    assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
+    with pytest.raises(rt.RtError):
+        tracer.set_scattering(np.zeros(3, np.float32))
