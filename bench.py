@@ -487,6 +487,7 @@ def cir_extensions_measurement(tr, scene, dev, T=14, fs=1e6):
                         "config": "city workload paths (1 Tx, 1000 Rx, 1e6 rays, depth 3), fs 1 MHz, Tx [3,0,0] m/s, "
                                   "Rx 1.5 m/s horizontal in seeded directions; velocities resident on the GPU"},
             "diffraction": diffraction_measurement(tr),
+            "scattering": scattering_measurement(tr, scene),
             "synthetic_array": {"paths": int(a.shape[0]), "outputs": int(ael.numel()), "ms": statistics.median(ts),
                                 "config": "the same paths, Tx planar array 8 x 2 (0.7 / 0.5 wavelengths), "
                                           "dual-polarized TR 38.901 elements, single-element Rx"}}
@@ -525,6 +526,30 @@ def diffraction_measurement(tr):
             "candidates_per_s": int(faces.shape[0]) * int(tr.n_pairs) / (statistics.median(t_find) / 1e3),
             "map_ms": t_map, "map_cells": cells, "map_cells_with_diffraction": int((gd > 0).sum().item()),
             "map_candidates_per_s": int(faces.shape[0]) * cells / (t_map / 1e3)}
+
+
+def scattering_measurement(tr, scene, n_rays=100_000, S_m=0.3):
+    """First-order diffuse scattering on the city workload as loaded (1 Tx,
+    1000 Rx, every material S = 0.3): rt_scattering_gain over n_rays lattice
+    rays, every ray's hit against every receiver; median of 5 CUDA-event
+    timings."""
+    import torch
+    tr.set_scattering(np.full(len(scene.materials), S_m, np.float32))
+    g = tr.scattering_gain(n_rays)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = tr.scattering_gain(n_rays)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    return {"rays": n_rays, "receivers": int(tr.n_pairs), "ms": ms,
+            "ray_receiver_pairs_per_s": n_rays * int(tr.n_pairs) / (ms / 1e3),
+            "links_with_scattering": int((g.sum(dim=(1, 2)) > 0).sum().item())}
 
 
 def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,
