@@ -40,3 +40,36 @@ def test_scattering_matches_oracle(tracer):
     assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
     with pytest.raises(rt.RtError):
         tracer.set_scattering(np.zeros(3, np.float32))
+
+
+@pytest.mark.parametrize("uneven", [False, True])
+def test_scattering_several_transmitters(tracer, uneven):
+    """Three transmitters, a ray count that is no multiple of the warp width
+    (warps straddle two transmitters), all pairs or uneven receiver sets
+    (one empty): every pair's gain equals the oracle's for its transmitter."""
+    sc = S.tiny_scene()
+    tx = S.Devices(np.array([[-60.0, 0.0, 25.0], [0.0, 50.0, 10.0], [45.0, -30.0, 3.0]], np.float32),
+                   np.array([[0.2, 0.05, 0.0], [1.5, 0.0, 0.1], [-2.0, 0.0, 0.0]], np.float32), S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [60.0, 10.0, 1.5], [30.0, 25.0, 1.5], [-20.0, -40.0, 6.0],
+                             [10.0, 70.0, 2.0], [-40.0, 30.0, 1.5]], np.float32),
+                   np.array([[0.5, 0.0, 0.0]] * 6, np.float32), S.Antenna(S.ANT_DIPOLE, (0.0,)))
+    off = [0, 4, 4, 6] if uneven else None
+    setup(tracer, sc, tx, rx, off)
+    N = 4999
+    S_m = np.array([0.7], np.float32)
+    tracer.set_scattering(S_m)
+    g = tracer.scattering_gain(N).cpu().numpy()
+    osc = O.make_scene(sc)
+    n_pairs = 6 if uneven else 18
+    assert g.shape == (n_pairs, 1, 2)
+    live = 0
+    for t in range(3):
+        rs = range(off[t], off[t + 1]) if uneven else range(6)
+        if len(rs) == 0:
+            continue
+        sub = S.Devices(rx.pos[list(rs)], rx.ypr[list(rs)], rx.antenna)
+        og = SC.scattering_gain(osc, sc.mat_id, S_m.astype(np.float64), FC, tx, sub, N, tx_index=t)
+        got = g[list(rs)] if uneven else g[t * 6:(t + 1) * 6]
+        assert np.all(np.abs(got - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (t, got, og)
+        live += int((og > 0).any(axis=(1, 2)).sum())
+    assert live >= 4
