@@ -291,6 +291,16 @@ int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat);
  * specular coefficients are not changed. Errors: RT_ERR_INVALID_ARG.
  */
 int rt_scattering_gain(rt_ctx* ctx, int64_t num_rays, float* gain);
+/*
+ * Sec. II (gradients with respect to the parameters of the scattering
+ * functions): vector-Jacobian product of rt_scattering_gain with respect to
+ * the coefficients S. grad_gain [n_pairs*nrp*ntp] float32 (device) is
+ * dL/dgain; grad_coeff [n_mat] float32 (device, overwritten) receives dL/dS.
+ * The gain is quadratic in S: dL/dS_m = (2/S_m) * the sum of dL/dgain times
+ * the gain carried by the rays that first hit material m (0 where S_m = 0).
+ * Errors: RT_ERR_INVALID_ARG.
+ */
+int rt_scattering_gain_vjp(rt_ctx* ctx, int64_t num_rays, const float* grad_gain, float* grad_coeff);
 /* Wedges of the current scene: n_out (HOST) = count; faces [n*2] int32 the
  * two triangles (original ids, lower first), n_ext [n] exterior angle / pi;
  * device pointers, either may be NULL. Reads back (not while capturing). */

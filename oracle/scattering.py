@@ -20,6 +20,11 @@ receives half of it:
              (lambda^2 / (4 pi r^2)) |F_rx,p(-k_s)|^2 / 2.
 The result is the incoherent scattered path gain of every (tx, rx) pair and
 port pair. The specular coefficients are left as they are.
+
+Gradients with respect to the scattering coefficients (Sec. II names the
+parameters of the scattering functions among the differentiable inputs):
+the gain is S_m^2 times the gain the rays hitting material m would carry at
+S_m = 1, so dL/dS_m = 2 S_m sum(dL/dg * g_m(S_m = 1)).
 """
 from __future__ import annotations
 
@@ -71,3 +76,18 @@ def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=
             w = s * s / N * cs / np.pi * lam ** 2 / (4.0 * np.pi * dist ** 2) * 0.5
             g[r] += w * np.outer(prx, ptx)
     return g
+
+
+def scattering_gain_vjp(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, up, tx_index: int = 0):
+    """dL/dS [M] from the upstream gradient up [R, nrp, ntp] of scattering_gain,
+    by the derivative of the definition: one unit-coefficient run per material."""
+    S = np.asarray(S, np.float64)
+    grad = np.zeros(len(S))
+    for m in range(len(S)):
+        if S[m] == 0.0:
+            continue
+        one = np.zeros(len(S))
+        one[m] = 1.0
+        gm = scattering_gain(osc, scene_mat, one, fc, txdev, rxdev, N, tx_index=tx_index)
+        grad[m] = 2.0 * S[m] * float(np.sum(np.asarray(up) * gm))
+    return grad

@@ -20,7 +20,7 @@ int diffraction_cir_impl(rt_ctx* ctx, float* a, float* tau);
 int diffraction_get_impl(rt_ctx* ctx, int64_t* offsets, int32_t* wedge, float* points);
 int wedges_impl(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
 int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain);
-int scattering_impl(rt_ctx* ctx, int64_t N, float* gain);
+int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float* grad);
 int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau, float* g_eps, float* g_sig,
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
@@ -556,7 +556,16 @@ int rt_scattering_gain(rt_ctx* ctx, int64_t num_rays, float* gain) {
         return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain: bad arguments");
     if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
         return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain: scene, transmitters and receivers must be set");
-    return scattering_impl(ctx, num_rays, gain);
+    return scattering_impl(ctx, num_rays, gain, nullptr, nullptr);
+}
+
+int rt_scattering_gain_vjp(rt_ctx* ctx, int64_t num_rays, const float* grad_gain, float* grad_coeff) {
+    CHECK_CTX(ctx);
+    if (num_rays < 0 || num_rays >= (1ll << 40) || !grad_gain || !grad_coeff)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain_vjp: bad arguments");
+    if (!ctx->has_scene || ctx->n_tx < 1 || ctx->n_rx < 1)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "scattering_gain_vjp: scene, transmitters and receivers must be set");
+    return scattering_impl(ctx, num_rays, nullptr, grad_gain, grad_coeff);
 }
 
 int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext) {

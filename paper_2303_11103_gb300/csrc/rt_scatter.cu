@@ -12,6 +12,12 @@
 // wave per port:
 //   g[pair][p][q] += S^2 (|F_tx,q(d)|^2/N) (cos theta_s/pi) (lambda^2/(4 pi r^2)) |F_rx,p(-k_s)|^2 / 2.
 // The result is the incoherent scattered gain of every pair and port pair.
+//
+// The gain is quadratic in S, so its vector-Jacobian product with respect to
+// the coefficients (Sec. II: gradients with respect to the parameters of the
+// scattering functions) is, for material m,
+//   dL/dS_m = 2 S_m sum over rays hitting m, receivers and ports of dL/dg * g / S_m^2,
+// accumulated by the same kernel in its VJP mode.
 #include "rt_field.cuh"
 #include "rt_internal.h"
 
@@ -25,6 +31,10 @@ struct ScatParams {
     const float* rx_ypr;
     const int32_t* rx_off;   // [n_tx+1] or null
     const float* scat;       // [n_mat] scattering coefficients
+    const float* up;         // VJP: upstream dL/dgain [n_pairs][nrp][ntp]
+    float* grad;             // VJP: dL/dS [n_mat]
+    int n_mat;
+    bool grad_smem;          // VJP: per-block partial sums in shared memory
     int n_tx, n_rx;
     long long N;
     DevAntenna txa, rxa;
@@ -35,9 +45,16 @@ struct ScatParams {
 // One thread per (transmitter, lattice ray): first hit, then every receiver
 // of that transmitter in order (the warp's lanes visit the same receiver
 // together and add their contributions with one atomic when they share the
-// transmitter).
+// transmitter). VJP: each ray's sum of dL/dg * g / S^2 is added, times
+// 2 S, to its material's gradient (per block in shared memory first).
+template <bool VJP>
 __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
+    extern __shared__ float sgrad[];
     const unsigned full = 0xffffffffu;
+    if (VJP && p.grad_smem) {
+        for (int i = threadIdx.x; i < p.n_mat; i += blockDim.x) sgrad[i] = 0.0f;
+        __syncthreads();
+    }
     const long long total = (long long)p.n_tx * p.N;
     const long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     for (long long b = base; b < total; b += (long long)gridDim.x * blockDim.x) {
@@ -47,9 +64,9 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
         const long long i = has ? slot - (long long)t * p.N : 0;
         const int t0 = __shfl_sync(full, t, 0);
         const bool uniform = __all_sync(full, t == t0);
-        float s2 = 0.0f;
+        float s2 = 0.0f, sc = 0.0f, acc = 0.0f;
         f3 P = mk(0, 0, 0), n = mk(0, 0, 1);
-        int hit = -1;
+        int hit = -1, m = 0;
         float ptx[2] = {0.0f, 0.0f};
         if (has) {
             const f3 o = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
@@ -58,7 +75,8 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
             float th;
             hit = closest_hit<false>(p.s, nullptr, 0, o, d, -1, th, cnt);
             if (hit >= 0) {
-                const float sc = __ldg(p.scat + __ldg(p.s.mat + hit));
+                m = __ldg(p.s.mat + hit);
+                sc = __ldg(p.scat + m);
                 s2 = sc * sc;
                 n = xyz(__ldg(p.s.planes + hit));
                 if (dot(d, n) > 0.0f) n = n * -1.0f;   // the side the ray came from
@@ -88,7 +106,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                     const f3 ks = v * (1.0f / dist);
                     TravCount cnt;
                     if (!any_hit<false>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
-                        w = s2 * cs * p.w0 / (dist * dist);
+                        w = (VJP ? 1.0f : s2) * cs * p.w0 / (dist * dist);
                         const Rot<float> Rr = rot_ypr(p.rx_ypr[3 * r], p.rx_ypr[3 * r + 1], p.rx_ypr[3 * r + 2]);
                         for (int pp = 0; pp < p.rxa.n_ports; pp++) {
                             const V3<float> f = antenna_vec<float>(p.rxa.kind, p.rxa.slant[pp], Rr,
@@ -99,6 +117,13 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                 }
             }
             const long long pair = p.rx_off ? (long long)r : (long long)t * p.n_rx + r;
+            if (VJP) {   // w is g / S^2 here
+                if (w != 0.0f)
+                    for (int pp = 0; pp < p.rxa.n_ports; pp++)
+                        for (int q = 0; q < p.txa.n_ports; q++)
+                            acc += __ldg(p.up + (pair * p.rxa.n_ports + pp) * p.txa.n_ports + q) * w * prx[pp] * ptx[q];
+                continue;
+            }
             for (int pp = 0; pp < p.rxa.n_ports; pp++)
                 for (int q = 0; q < p.txa.n_ports; q++) {
                     float c = w * prx[pp] * ptx[q];
@@ -111,15 +136,24 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                     }
                 }
         }
+        if (VJP && acc != 0.0f) atomicAdd((p.grad_smem ? sgrad : p.grad) + m, 2.0f * sc * acc);
+    }
+    if (VJP && p.grad_smem) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.n_mat; i += blockDim.x)
+            if (sgrad[i] != 0.0f) atomicAdd(p.grad + i, sgrad[i]);
     }
 }
 
 }  // namespace
 
-int scattering_impl(rt_ctx* ctx, int64_t N, float* gain) {
+// gain != null: forward; else up / grad: the VJP with respect to S.
+int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float* grad) {
     const int64_t n_pairs = ctx->rx_sets ? (int64_t)ctx->rx_off[ctx->n_tx] : (int64_t)ctx->n_tx * ctx->n_rx;
     const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
-    RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * (size_t)n_pairs * np, ctx->stream));
+    const bool vjp = gain == nullptr;
+    if (vjp) RT_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)ctx->n_mat, ctx->stream));
+    else RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * (size_t)n_pairs * np, ctx->stream));
     if (N == 0 || ctx->n_tris == 0 || !ctx->scat_set) return RT_OK;
     ScatParams p;
     p.s = dev_scene(ctx);
@@ -129,6 +163,10 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain) {
     p.rx_ypr = bp<float>(ctx->rx_ypr);
     p.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
     p.scat = bp<float>(ctx->scat);
+    p.up = up;
+    p.grad = grad;
+    p.n_mat = ctx->n_mat;
+    p.grad_smem = vjp && ctx->n_mat <= 4096;
     p.n_tx = ctx->n_tx;
     p.n_rx = ctx->n_rx;
     p.N = N;
@@ -139,8 +177,13 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain) {
     p.gain = gain;
     const long long total = (long long)ctx->n_tx * N;
     const long long blocks = std::min<long long>((total + 127) / 128, 16ll * ctx->num_sms);
-    prof_begin(ctx, "k_scatter");
-    k_scatter<<<(unsigned)blocks, 128, 0, ctx->stream>>>(p);
+    if (vjp) {
+        prof_begin(ctx, "k_scatter_vjp");
+        k_scatter<true><<<(unsigned)blocks, 128, p.grad_smem ? sizeof(float) * ctx->n_mat : 0, ctx->stream>>>(p);
+    } else {
+        prof_begin(ctx, "k_scatter");
+        k_scatter<false><<<(unsigned)blocks, 128, 0, ctx->stream>>>(p);
+    }
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;

@@ -87,6 +87,7 @@ def lib():
             "rt_coverage_map_diffraction": [vp, ctypes.POINTER(rt_grid), i32, vp],
             "rt_set_scattering": [vp, vp, i32],
             "rt_scattering_gain": [vp, i64, vp],
+            "rt_scattering_gain_vjp": [vp, i64, vp, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
@@ -624,6 +625,16 @@ class Tracer:
         g = torch.empty((self.n_pairs, self.nrp, self.ntp), dtype=torch.float32, device=self.device)
         _check(self.ctx, lib().rt_scattering_gain(self.ctx, int(num_rays), _ptr(g)))
         return g
+
+    def scattering_gain_vjp(self, num_rays: int, grad_gain):
+        """dL/dS [n_mat] from dL/dgain [n_pairs, nrp, ntp] of scattering_gain."""
+        self.sync_stream()
+        up = self._t(grad_gain, torch.float32).contiguous()
+        if up.numel() != self.n_pairs * self.nrp * self.ntp:
+            raise RtError(-1, "scattering_gain_vjp: grad_gain must have n_pairs * nrp * ntp elements")
+        gs = torch.empty(self.n_mat, dtype=torch.float32, device=self.device)
+        _check(self.ctx, lib().rt_scattering_gain_vjp(self.ctx, int(num_rays), _ptr(up), _ptr(gs)))
+        return gs
 
     def diffraction_cir(self):
         """a [P, nrp, ntp] complex64 and tau [P] of the diffracted paths (UTD)."""

@@ -93,6 +93,17 @@ def tiny_scene() -> Scene:
                  np.array([[-10, 10, -10, 10, 30.0]]))
 
 
+def tiny_scene_3mat() -> Scene:
+    """The tiny scene with three materials: the ground and the box's floor
+    (0), the box's two x-facing walls (1), its other walls and roof (2)."""
+    sc = tiny_scene()
+    v = sc.verts.reshape(-1, 3, 3)
+    x_wall = np.all(v[:, :, 0] == v[:, :1, 0], axis=1)
+    on_ground = np.all(v[:, :, 2] == 0.0, axis=1)
+    mat = np.where(on_ground, 0, np.where(x_wall, 1, 2)).astype(np.int32)
+    return Scene(sc.verts, mat, np.array([CONCRETE, GLASS, CONCRETE], np.float32), "tiny3", sc.footprints)
+
+
 def tiny_devices(visible: bool = False):
     """Tx (-60,0,25), Rx (60,10,1.5); the 'visible' variant moves Rx to (-75,0,1.5)."""
     tx = Devices(np.array([[-60.0, 0.0, 25.0]], np.float32), np.zeros((1, 3), np.float32), V_ISO)

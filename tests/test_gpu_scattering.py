@@ -73,3 +73,23 @@ def test_scattering_several_transmitters(tracer, uneven):
         assert np.all(np.abs(got - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (t, got, og)
         live += int((og > 0).any(axis=(1, 2)).sum())
     assert live >= 4
+
+
+def test_scattering_vjp_matches_oracle(tracer):
+    """dL/dS of the scattered gain (three materials, random upstream
+    gradient) against the oracle's derivative of the definition."""
+    sc = S.tiny_scene_3mat()
+    tx = S.Devices(np.array([[-50.0, -50.0, 20.0]], np.float32), np.zeros((1, 3), np.float32), S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [60.0, 10.0, 1.5], [30.0, 25.0, 1.5], [-20.0, -40.0, 6.0]],
+                            np.float32), np.zeros((4, 3), np.float32), S.Antenna(S.ANT_DIPOLE, (0.0,)))
+    setup(tracer, sc, tx, rx)
+    S_m = np.array([0.4, 0.7, 0.0], np.float32)
+    tracer.set_scattering(S_m)
+    N = 10000
+    up = np.random.default_rng(1).normal(size=(4, 1, 2)).astype(np.float32)
+    gs = tracer.scattering_gain_vjp(N, up).cpu().numpy()
+    og = SC.scattering_gain_vjp(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N, up)
+    assert gs.shape == (3,) and gs[2] == 0.0 and np.abs(og[:2]).min() > 0
+    assert np.allclose(gs, og, rtol=3e-3, atol=2e-3 * np.abs(og).max()), (gs, og)
+    with pytest.raises(rt.RtError):
+        tracer.scattering_gain_vjp(N, np.zeros(5, np.float32))

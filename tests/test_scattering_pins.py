@@ -71,3 +71,29 @@ def test_cosine_law_and_zero_cases():
     osc2 = O.make_scene(sc2)
     rxw = S.Devices(np.array([[100.0, 0.0, 5.0]], np.float32), np.zeros((1, 3), np.float32), S.V_ISO)
     assert SC.scattering_gain(osc2, sc2.mat_id, np.array([1.0]), FC, _tx(), rxw, 3000)[0, 0, 0] == 0.0
+
+
+def test_vjp_matches_central_differences():
+    """The gain is quadratic in every S_m, so central differences of the
+    forward oracle are exact up to rounding: they pin the VJP's factor 2 S_m
+    and its split over materials (the tiny scene with three materials)."""
+    sc = S.tiny_scene_3mat()
+    osc = O.make_scene(sc)
+    tx = S.Devices(np.array([[-50.0, -50.0, 20.0]], np.float32), np.zeros((1, 3), np.float32), S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [60.0, 10.0, 1.5], [30.0, 25.0, 1.5], [-20.0, -40.0, 6.0]],
+                            np.float32), np.zeros((4, 3), np.float32), S.Antenna(S.ANT_DIPOLE, (0.0,)))
+    Sm = np.array([0.4, 0.7, 0.25])
+    N = 1500
+    up = np.random.default_rng(0).normal(size=(4, 1, 2))
+    grad = SC.scattering_gain_vjp(osc, sc.mat_id, Sm, FC, tx, rx, N, up)
+    h = 1e-3
+    fd = np.zeros(3)
+    for m in range(3):
+        e = np.zeros(3)
+        e[m] = h
+        gp = SC.scattering_gain(osc, sc.mat_id, Sm + e, FC, tx, rx, N)
+        gm = SC.scattering_gain(osc, sc.mat_id, Sm - e, FC, tx, rx, N)
+        fd[m] = np.sum(up * (gp - gm)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0 and (np.abs(grad) > 1e-3 * scale).sum() == 3
+    assert np.allclose(grad, fd, rtol=1e-8, atol=1e-9 * scale), (grad, fd)
