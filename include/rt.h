@@ -280,8 +280,20 @@ int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, 
  */
 int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat);
 /*
- * First-order diffuse scattering by the effective-roughness model with a
- * Lambertian pattern: each of the num_rays Fibonacci rays of a transmitter
+ * Sec. II (the radio materials carry a scattering pattern): pattern of each
+ * material for rt_scattering_gain. alpha_r [n_mat] int32 (HOST, read during
+ * the call): -1 the Lambertian pattern cos(theta_s)/pi (the default until
+ * set, and after rt_load_scene); 0..RT_MAX_ALPHA_R the directive pattern of
+ * the effective-roughness model, a lobe ((1 + k_r . k_s)/2)^alpha_r around
+ * the specular direction k_r, normalised over the hemisphere on the
+ * incident side so that it re-radiates the same power S^2. Errors:
+ * RT_ERR_INVALID_ARG for another material count or an exponent out of range.
+ */
+#define RT_MAX_ALPHA_R 64
+int rt_set_scattering_pattern(rt_ctx* ctx, const int32_t* alpha_r, int32_t n_mat);
+/*
+ * First-order diffuse scattering by the effective-roughness model with the
+ * materials' patterns (rt_set_scattering_pattern; Lambertian below): each of the num_rays Fibonacci rays of a transmitter
  * carries |F_tx,q(d)|^2 / num_rays of its power; at its first hit the
  * fraction S^2 is re-radiated with the intensity cos(theta_s)/pi towards
  * the side the ray came from, and a receiver there with an unoccluded

@@ -21,6 +21,15 @@ receives half of it:
 The result is the incoherent scattered path gain of every (tx, rx) pair and
 port pair. The specular coefficients are left as they are.
 
+Scattering pattern per material: alpha < 0 takes the Lambertian pattern
+above; alpha >= 0 the directive pattern of the effective-roughness model, a
+lobe around the specular direction k_r:
+  intensity(k_s) = ((1 + k_r . k_s) / 2)^alpha / F_alpha,
+with F_alpha the integral of the lobe over the hemisphere on the incident
+side (here by Gauss-Legendre quadrature in cos(theta_s) and the trapezoidal
+rule in azimuth, both exact for this polynomial integrand), so that the
+pattern re-radiates exactly the fraction S^2 like the Lambertian one.
+
 Gradients with respect to the scattering coefficients (Sec. II names the
 parameters of the scattering functions among the differentiable inputs):
 the gain is S_m^2 times the gain the rays hitting material m would carry at
@@ -33,10 +42,31 @@ import numpy as np
 from . import oracle as O
 
 
-def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=None, tx_index: int = 0):
+def directive_norm(alpha: int, kr, n, n_mu: int = 40) -> float:
+    """F_alpha: integral of ((1 + kr . k_s)/2)^alpha over the unit vectors k_s
+    with k_s . n > 0 (cos(theta_s) by Gauss-Legendre, azimuth by the
+    trapezoidal rule; the integrand is a polynomial of degree alpha)."""
+    n = np.asarray(n, np.float64)
+    e1 = np.cross(n, [1.0, 0.0, 0.0] if abs(n[0]) < 0.9 else [0.0, 1.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    x, wx = np.polynomial.legendre.leggauss(n_mu)
+    mu, wmu = 0.5 * (x + 1.0), 0.5 * wx
+    n_phi = 2 * n_mu
+    phi = 2.0 * np.pi * np.arange(n_phi) / n_phi
+    st = np.sqrt(1.0 - mu ** 2)
+    ks = (st[:, None, None] * (np.cos(phi)[None, :, None] * e1 + np.sin(phi)[None, :, None] * e2)
+          + mu[:, None, None] * n)
+    f = ((1.0 + ks @ np.asarray(kr, np.float64)) / 2.0) ** alpha
+    return float((f * wmu[:, None]).sum() * (2.0 * np.pi / n_phi))
+
+
+def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=None, tx_index: int = 0,
+                    alpha=None):
     """g [R, nrp, ntp]: incoherent first-order scattered gain from transmitter
     tx_index to every receiver, over the lattice rays ray_ids (all N when None;
-    each ray keeps the weight 1/N). scene_mat: int [T] material ids; S [M]."""
+    each ray keeps the weight 1/N). scene_mat: int [T] material ids; S [M];
+    alpha [M] pattern per material (None: all Lambertian)."""
     lam = O.C0 / fc
     tx = np.asarray(txdev.pos[tx_index], np.float64)
     txa, rxa = txdev.antenna, rxdev.antenna
@@ -58,6 +88,10 @@ def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=
         if np.dot(d, n) > 0.0:
             n = -n          # the side the ray came from
         P = tx + t * d
+        a_m = -1 if alpha is None else int(alpha[int(scene_mat[j])])
+        if a_m >= 0:
+            kr = d - 2.0 * np.dot(d, n) * n          # specular direction
+            F = directive_norm(a_m, kr, n)
         ptx = np.array([np.dot(O.antenna(txa.kind, z, txdev.ypr[tx_index], d),
                                O.antenna(txa.kind, z, txdev.ypr[tx_index], d)) for z in txa.slants])
         for r in range(R):
@@ -73,12 +107,13 @@ def scattering_gain(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, ray_ids=
             ks = v / dist
             prx = np.array([np.dot(O.antenna(rxa.kind, z, rxdev.ypr[r], -ks),
                                    O.antenna(rxa.kind, z, rxdev.ypr[r], -ks)) for z in rxa.slants])
-            w = s * s / N * cs / np.pi * lam ** 2 / (4.0 * np.pi * dist ** 2) * 0.5
+            pattern = cs / np.pi if a_m < 0 else ((1.0 + np.dot(kr, ks)) / 2.0) ** a_m / F
+            w = s * s / N * pattern * lam ** 2 / (4.0 * np.pi * dist ** 2) * 0.5
             g[r] += w * np.outer(prx, ptx)
     return g
 
 
-def scattering_gain_vjp(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, up, tx_index: int = 0):
+def scattering_gain_vjp(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, up, tx_index: int = 0, alpha=None):
     """dL/dS [M] from the upstream gradient up [R, nrp, ntp] of scattering_gain,
     by the derivative of the definition: one unit-coefficient run per material."""
     S = np.asarray(S, np.float64)
@@ -88,6 +123,6 @@ def scattering_gain_vjp(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, up, 
             continue
         one = np.zeros(len(S))
         one[m] = 1.0
-        gm = scattering_gain(osc, scene_mat, one, fc, txdev, rxdev, N, tx_index=tx_index)
+        gm = scattering_gain(osc, scene_mat, one, fc, txdev, rxdev, N, tx_index=tx_index, alpha=alpha)
         grad[m] = 2.0 * S[m] * float(np.sum(np.asarray(up) * gm))
     return grad

@@ -253,7 +253,7 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->cand_img, &ctx->htab_key, &ctx->htab_wit, &ctx->htab_cnt, &ctx->dop_cyc, &ctx->arr_dirs,
                       &ctx->verts_in, &ctx->wedges, &ctx->dpath_raw_key, &ctx->dpath_raw_pt, &ctx->dpath_key,
                       &ctx->dpath_key_alt, &ctx->dpath_idx, &ctx->dpath_idx_alt, &ctx->dpath_pt, &ctx->dpath_off,
-                      &ctx->dmap_key, &ctx->dmap_pt, &ctx->scat, &ctx->path_key,
+                      &ctx->dmap_key, &ctx->dmap_pt, &ctx->scat, &ctx->scat_alpha, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
@@ -315,6 +315,7 @@ int rt_load_scene(rt_ctx* ctx, const float* verts, int64_t n_tris, const int32_t
     ctx->n_cand = 0;
     ctx->n_dpaths = 0;
     ctx->scat_set = false;
+    ctx->scat_alpha_set = false;
     ctx->scene_gen++;
     ctx->n_mat = n_mat;
     RT_TRY(buf_reserve(ctx->verts_in, sizeof(float) * 9 * std::max<int64_t>(n_tris, 1)));
@@ -547,6 +548,20 @@ int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat) {
     RT_TRY(buf_reserve(ctx->scat, sizeof(float) * n_mat));
     RT_TRY(cudaMemcpyAsync(ctx->scat.p, coeff, sizeof(float) * n_mat, cudaMemcpyDeviceToDevice, ctx->stream));
     ctx->scat_set = true;
+    return RT_OK;
+}
+
+int rt_set_scattering_pattern(rt_ctx* ctx, const int32_t* alpha_r, int32_t n_mat) {
+    CHECK_CTX(ctx);
+    if (!ctx->has_scene || n_mat != ctx->n_mat || !alpha_r)
+        return set_err(ctx, RT_ERR_INVALID_ARG, "set_scattering_pattern: material count differs from the scene's");
+    for (int i = 0; i < n_mat; i++)
+        if (alpha_r[i] < -1 || alpha_r[i] > RT_MAX_ALPHA_R)
+            return set_err(ctx, RT_ERR_INVALID_ARG, "set_scattering_pattern: alpha_r must be -1 or 0..64");
+    RT_TRY(buf_reserve(ctx->scat_alpha, sizeof(int32_t) * n_mat));
+    RT_TRY(cudaMemcpyAsync(ctx->scat_alpha.p, alpha_r, sizeof(int32_t) * n_mat, cudaMemcpyHostToDevice, ctx->stream));
+    RT_TRY(cudaStreamSynchronize(ctx->stream));   // the host array may go away after the call
+    ctx->scat_alpha_set = true;
     return RT_OK;
 }
 

@@ -75,6 +75,8 @@ struct rt_ctx {
     DevBuf dmap_key, dmap_pt;   // diffracted coverage map: found (tx, cell, wedge) entries
     DevBuf scat;                // [n_mat] scattering coefficients (rt_set_scattering)
     bool scat_set = false;
+    DevBuf scat_alpha;          // [n_mat] int32 pattern exponent, -1 Lambertian (rt_set_scattering_pattern)
+    bool scat_alpha_set = false;
     int64_t dmap_cap = 0;
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;

@@ -12,6 +12,9 @@
 // wave per port:
 //   g[pair][p][q] += S^2 (|F_tx,q(d)|^2/N) (cos theta_s/pi) (lambda^2/(4 pi r^2)) |F_rx,p(-k_s)|^2 / 2.
 // The result is the incoherent scattered gain of every pair and port pair.
+// A material with a directive pattern (exponent alpha >= 0) replaces
+// cos(theta_s)/pi by ((1 + k_r . k_s)/2)^alpha / F_alpha, k_r the specular
+// direction and F_alpha the lobe's integral over the hemisphere.
 //
 // The gain is quadratic in S, so its vector-Jacobian product with respect to
 // the coefficients (Sec. II: gradients with respect to the parameters of the
@@ -31,6 +34,7 @@ struct ScatParams {
     const float* rx_ypr;
     const int32_t* rx_off;   // [n_tx+1] or null
     const float* scat;       // [n_mat] scattering coefficients
+    const int32_t* alpha;    // [n_mat] pattern exponent, -1 Lambertian; null: all Lambertian
     const float* up;         // VJP: upstream dL/dgain [n_pairs][nrp][ntp]
     float* grad;             // VJP: dL/dS [n_mat]
     int n_mat;
@@ -41,6 +45,31 @@ struct ScatParams {
     float w0;                // lambda^2 / (4 pi) / (2 pi N)
     float* gain;             // [n_pairs][nrp][ntp]
 };
+
+// F_alpha: the integral of ((1 + k_r . k_s)/2)^alpha over the hemisphere
+// k_s . n > 0, with cos(theta_i) = k_r . n = ci. Binomial expansion in
+// x = k_r . k_s; the hemisphere integral of x^j is 2 pi/(j+1) for even j
+// (half the sphere's) and, for odd j = 2w+1,
+//   2 pi/(j+1) ci sum_{u=0..w} C(2u, u) (sin^2(theta_i)/4)^u.
+__device__ float directive_norm(int alpha, float ci) {
+    const float q = 0.25f * fmaxf(0.0f, 1.0f - ci * ci);
+    float tot = 0.0f, binom = 1.0f, part = 0.0f, term = 1.0f;
+    int u = 0;
+    for (int j = 0; j <= alpha; j++) {
+        float I;
+        if ((j & 1) == 0) {
+            I = 2.0f * RT_PI_F / (float)(j + 1);
+        } else {
+            part += term;                                   // adds C(2u, u) q^u
+            term *= q * 2.0f * (float)(2 * u + 1) / (float)(u + 1);
+            u++;
+            I = 2.0f * RT_PI_F / (float)(j + 1) * ci * part;
+        }
+        tot += binom * I;
+        binom *= (float)(alpha - j) / (float)(j + 1);
+    }
+    return ldexpf(tot, -alpha);
+}
 
 // One thread per (transmitter, lattice ray): first hit, then every receiver
 // of that transmitter in order (the warp's lanes visit the same receiver
@@ -66,7 +95,9 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
         const bool uniform = __all_sync(full, t == t0);
         float s2 = 0.0f, sc = 0.0f, acc = 0.0f;
         f3 P = mk(0, 0, 0), n = mk(0, 0, 1);
-        int hit = -1, m = 0;
+        int hit = -1, m = 0, am = -1;
+        f3 kr = mk(0, 0, 1);
+        float fa = 1.0f;
         float ptx[2] = {0.0f, 0.0f};
         if (has) {
             const f3 o = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
@@ -81,6 +112,12 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                 n = xyz(__ldg(p.s.planes + hit));
                 if (dot(d, n) > 0.0f) n = n * -1.0f;   // the side the ray came from
                 P = o + d * th;
+                am = p.alpha ? __ldg(p.alpha + m) : -1;
+                if (am >= 0) {
+                    const float dn = dot(d, n);                 // < 0: n faces the incoming ray
+                    kr = d - n * (2.0f * dn);
+                    fa = directive_norm(am, -dn) / RT_PI_F;     // pi / F_alpha replaces 1/pi in w0
+                }
                 const Rot<float> Rt = rot_ypr(p.tx_ypr[3 * t], p.tx_ypr[3 * t + 1], p.tx_ypr[3 * t + 2]);
                 for (int q = 0; q < p.txa.n_ports; q++) {
                     const V3<float> f = antenna_vec<float>(p.txa.kind, p.txa.slant[q], Rt, V3<float>{d.x, d.y, d.z});
@@ -106,7 +143,8 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                     const f3 ks = v * (1.0f / dist);
                     TravCount cnt;
                     if (!any_hit<false>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
-                        w = (VJP ? 1.0f : s2) * cs * p.w0 / (dist * dist);
+                        const float pat = am < 0 ? cs : powf(0.5f * (1.0f + dot(kr, ks)), (float)am) / fa;
+                        w = (VJP ? 1.0f : s2) * pat * p.w0 / (dist * dist);
                         const Rot<float> Rr = rot_ypr(p.rx_ypr[3 * r], p.rx_ypr[3 * r + 1], p.rx_ypr[3 * r + 2]);
                         for (int pp = 0; pp < p.rxa.n_ports; pp++) {
                             const V3<float> f = antenna_vec<float>(p.rxa.kind, p.rxa.slant[pp], Rr,
@@ -163,6 +201,7 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float*
     p.rx_ypr = bp<float>(ctx->rx_ypr);
     p.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
     p.scat = bp<float>(ctx->scat);
+    p.alpha = ctx->scat_alpha_set ? bp<int32_t>(ctx->scat_alpha) : nullptr;
     p.up = up;
     p.grad = grad;
     p.n_mat = ctx->n_mat;

@@ -87,6 +87,7 @@ def lib():
             "rt_coverage_map_diffraction": [vp, ctypes.POINTER(rt_grid), i32, vp],
             "rt_set_scattering": [vp, vp, i32],
             "rt_scattering_gain": [vp, i64, vp],
+            "rt_set_scattering_pattern": [vp, vp, i32],
             "rt_scattering_gain_vjp": [vp, i64, vp, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
@@ -618,6 +619,12 @@ class Tracer:
         c = self._t(coeff, torch.float32).reshape(-1)
         _check(self.ctx, lib().rt_set_scattering(self.ctx, _ptr(c), int(c.shape[0])))
         torch.cuda.current_stream().synchronize()
+
+    def set_scattering_pattern(self, alpha_r):
+        """Pattern per material: -1 Lambertian, 0..64 directive lobe exponent alpha_R."""
+        self.sync_stream()
+        a = np.ascontiguousarray(np.asarray(alpha_r, dtype=np.int32).reshape(-1))
+        _check(self.ctx, lib().rt_set_scattering_pattern(self.ctx, a.ctypes.data, int(a.shape[0])))
 
     def scattering_gain(self, num_rays: int):
         """Incoherent first-order diffuse-scattering gain [n_pairs, nrp, ntp]."""

@@ -93,3 +93,31 @@ def test_scattering_vjp_matches_oracle(tracer):
     assert np.allclose(gs, og, rtol=3e-3, atol=2e-3 * np.abs(og).max()), (gs, og)
     with pytest.raises(rt.RtError):
         tracer.scattering_gain_vjp(N, np.zeros(5, np.float32))
+
+
+def test_directive_pattern_matches_oracle(tracer):
+    """Per-material patterns (Lambertian, directive alpha_R = 3 and 8) for
+    the gain and its VJP; exponents out of range are rejected."""
+    sc = S.tiny_scene_3mat()
+    tx = S.Devices(np.array([[-50.0, -50.0, 20.0]], np.float32), np.array([[0.3, 0.1, 0.0]], np.float32),
+                   S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [60.0, 10.0, 1.5], [30.0, 25.0, 1.5], [-20.0, -40.0, 6.0]],
+                            np.float32), np.zeros((4, 3), np.float32), S.Antenna(S.ANT_DIPOLE, (0.0, np.pi / 2)))
+    setup(tracer, sc, tx, rx)
+    S_m = np.array([0.5, 0.6, 0.7], np.float32)
+    alpha = np.array([-1, 3, 8], np.int32)
+    tracer.set_scattering(S_m)
+    tracer.set_scattering_pattern(alpha)
+    N = 20000
+    osc = O.make_scene(sc)
+    g = tracer.scattering_gain(N).cpu().numpy()
+    og = SC.scattering_gain(osc, sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N, alpha=alpha)
+    assert (og > 0).sum() >= 12
+    assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
+    up = np.random.default_rng(2).normal(size=(4, 2, 2)).astype(np.float32)
+    gs = tracer.scattering_gain_vjp(N, up).cpu().numpy()
+    ogs = SC.scattering_gain_vjp(osc, sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N, up, alpha=alpha)
+    assert np.allclose(gs, ogs, rtol=3e-3, atol=2e-3 * np.abs(ogs).max()), (gs, ogs)
+    for bad in ([-2, 0, 0], [0, 65, 0], [0, 0]):
+        with pytest.raises(rt.RtError):
+            tracer.set_scattering_pattern(bad)

@@ -97,3 +97,46 @@ def test_vjp_matches_central_differences():
     scale = np.abs(fd).max()
     assert scale > 0 and (np.abs(grad) > 1e-3 * scale).sum() == 3
     assert np.allclose(grad, fd, rtol=1e-8, atol=1e-9 * scale), (grad, fd)
+
+
+def test_directive_pattern_energy_balance_and_lobe():
+    """Directive pattern (alpha_R = 4): over a Fibonacci hemisphere of distant
+    receivers the collected power integrates back to S^2 (hits / N), as for
+    the Lambertian pattern; the lobe peaks at the specular direction; with
+    alpha_R = 0 the intensity is the same in every direction of the
+    hemisphere (1 / (2 pi))."""
+    sc = _patch_scene()
+    osc = O.make_scene(sc)
+    tx = S.Devices(np.array([[-6.0, 0.0, 8.0]], np.float32), np.zeros((1, 3), np.float32), S.V_ISO)
+    N = 20000
+    hits, _ = O.trace_sbr(osc, tx.pos[0], N, 1)
+    n_hit = int((hits[:, 0] >= 0).sum())
+    assert n_hit > 5
+    M, Rr = 4000, 3000.0
+    d = O.fibonacci(2 * M)
+    d = d[d[:, 2] > 0][:M]
+    rx = S.Devices((Rr * d).astype(np.float32), np.zeros((len(d), 3), np.float32), S.V_ISO)
+    for a in (0, 4):
+        g = SC.scattering_gain(osc, sc.mat_id, np.array([1.0]), FC, tx, rx, N, alpha=[a])
+        power = g[:, 0, 0] * 2.0 * 4 * np.pi * Rr ** 2 / LAM ** 2
+        total = power.sum() * (2 * np.pi / len(d))
+        assert abs(total - n_hit / N) < 0.01 * n_hit / N, (a, total, n_hit / N)
+        if a == 0:
+            assert np.allclose(power / (n_hit / N), 1.0 / (2 * np.pi), rtol=1e-3)
+    # the lobe: receivers on an arc in the plane of incidence; incidence at
+    # atan(6/8) from the normal, so the specular direction is 36.87 deg on the +x side
+    ang = np.radians(np.arange(-80.0, 81.0, 1.0))
+    rxa = S.Devices(np.stack([Rr * np.sin(ang), np.zeros_like(ang), Rr * np.cos(ang)], 1).astype(np.float32),
+                    np.zeros((len(ang), 3), np.float32), S.V_ISO)
+    g = SC.scattering_gain(osc, sc.mat_id, np.array([1.0]), FC, tx, rxa, 2000, alpha=[6])[:, 0, 0]
+    assert abs(np.degrees(ang[np.argmax(g)]) - np.degrees(np.arctan2(6.0, 8.0))) <= 1.0
+
+
+def test_directive_norm_closed_cases():
+    """F_0 is the hemisphere's solid angle 2 pi; F_1 = pi (1 + cos(theta_i) / 2):
+    the mean of the integrals of 1 (2 pi) and of k_r . k_s (k_r . pi n)."""
+    n = np.array([0.0, 0.0, 1.0])
+    for ti in (0.0, 0.4, 1.3):
+        kr = np.array([np.sin(ti), 0.0, np.cos(ti)])
+        assert abs(SC.directive_norm(0, kr, n) - 2 * np.pi) < 1e-12
+        assert abs(SC.directive_norm(1, kr, n) - np.pi * (1 + 0.5 * np.cos(ti))) < 1e-12
