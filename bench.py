@@ -650,8 +650,10 @@ def run_reference(args):
 
 def run_kernel_case(args):
     """One kernel of the step on its own (for ncu captures):
-    `--only coverage|paths|freq|tail|mlp_infer|mlp_train`; tail = compute_paths,
-    cir, H(f) and both VJPs (the calls after the ray trace)."""
+    `--only coverage|paths|freq|tail|scatter|mlp_infer|mlp_train`; tail =
+    compute_paths, cir, H(f) and both VJPs (the calls after the ray trace);
+    scatter = first-order diffuse scattering (every material S = 0.3) over
+    --rays lattice rays to the 1000 receivers."""
     import torch
     from paper_2303_11103_gb300 import rt
     from paper_2303_11103_gb300 import scenes as S
@@ -681,6 +683,8 @@ def run_kernel_case(args):
         tr.compute_paths(MAX_DEPTH, args.rays)
         a, tau = tr.cir_raw()
         freqs = (np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING
+    if args.only == "scatter":
+        tr.set_scattering(np.full(len(scene.materials), 0.3, np.float32))
     for _ in range(args.warmup + args.steps):
         if args.only == "coverage":
             g, h = tr.coverage_map(GRID, MAX_DEPTH, args.rays, 0)
@@ -692,6 +696,8 @@ def run_kernel_case(args):
             Hc = tr.freq_response(ac, tauc, freqs)
             ga, gt = tr.freq_response_backward(ac, tauc, freqs, Hc)
             tr.cir_backward(ga, gt)
+        elif args.only == "scatter":
+            tr.scattering_gain(args.rays)
         else:
             tr.compute_paths(MAX_DEPTH, args.rays)
     torch.cuda.synchronize()
@@ -700,7 +706,7 @@ def run_kernel_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["coverage", "paths", "freq", "tail", "mlp_infer", "mlp_train"], default=None,
+    ap.add_argument("--only", choices=["coverage", "paths", "freq", "tail", "scatter", "mlp_infer", "mlp_train"], default=None,
                     help="run one kernel case of the step (profiling)")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate queries (--only mlp_*)")
