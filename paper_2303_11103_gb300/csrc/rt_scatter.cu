@@ -40,6 +40,7 @@ struct ScatParams {
     int n_mat;
     bool grad_smem;          // VJP: per-block partial sums in shared memory
     int n_tx, n_rx;
+    int n_chunks;            // receiver chunks per ray (each (ray, chunk) is one thread)
     long long N;
     DevAntenna txa, rxa;
     float w0;                // lambda^2 / (4 pi) / (2 pi N)
@@ -84,15 +85,18 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
         for (int i = threadIdx.x; i < p.n_mat; i += blockDim.x) sgrad[i] = 0.0f;
         __syncthreads();
     }
-    const long long total = (long long)p.n_tx * p.N;
+    const long long n_slots = (long long)p.n_tx * p.N;
+    const long long total = n_slots * p.n_chunks;
     const long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     for (long long b = base; b < total; b += (long long)gridDim.x * blockDim.x) {
-        const long long slot = b + (threadIdx.x & 31);
-        const bool has = slot < total;
+        const long long vs = b + (threadIdx.x & 31);
+        const bool has = vs < total;
+        const int c = has ? (int)(vs / n_slots) : p.n_chunks - 1;      // receiver chunk
+        const long long slot = has ? vs - (long long)c * n_slots : n_slots - 1;
         const int t = has ? (int)(slot / p.N) : p.n_tx - 1;
         const long long i = has ? slot - (long long)t * p.N : 0;
-        const int t0 = __shfl_sync(full, t, 0);
-        const bool uniform = __all_sync(full, t == t0);
+        const int t0 = __shfl_sync(full, t, 0), c0 = __shfl_sync(full, c, 0);
+        const bool uniform = __all_sync(full, t == t0 && c == c0);
         float s2 = 0.0f, sc = 0.0f, acc = 0.0f;
         f3 P = mk(0, 0, 0), n = mk(0, 0, 1);
         int hit = -1, m = 0, am = -1;
@@ -127,8 +131,10 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
         }
         const bool live = __any_sync(full, s2 > 0.0f);
         if (!live) continue;
-        // receivers of this lane's transmitter
-        const int rb = p.rx_off ? p.rx_off[t] : 0, re = p.rx_off ? p.rx_off[t + 1] : p.n_rx;
+        // this lane's chunk of the receivers of its transmitter
+        const int rb0 = p.rx_off ? p.rx_off[t] : 0, re0 = p.rx_off ? p.rx_off[t + 1] : p.n_rx;
+        const int len = (re0 - rb0 + p.n_chunks - 1) / p.n_chunks;
+        const int rb = min(re0, rb0 + c * len), re = min(re0, rb + len);
         const int nr = re - rb;
         const int nr_max = __reduce_max_sync(full, (unsigned)nr);
         for (int k = 0; k < nr_max; k++) {
@@ -214,7 +220,19 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float*
     const double lam = RT_C0_D / ctx->fc;
     p.w0 = (float)(lam * lam / (4.0 * RT_PI_D) / (2.0 * RT_PI_D * (double)N));
     p.gain = gain;
-    const long long total = (long long)ctx->n_tx * N;
+    // few rays: split every ray's receivers into chunks, one thread each, so
+    // that about 4 x 2048 threads per SM are in flight (the first hit is
+    // traced once per chunk, against hundreds of segment tests per chunk)
+    int nr_max = ctx->n_rx;
+    if (ctx->rx_sets) {
+        nr_max = 0;
+        for (int t = 0; t < ctx->n_tx; t++) nr_max = std::max(nr_max, ctx->rx_off[t + 1] - ctx->rx_off[t]);
+    }
+    const long long slots = (long long)ctx->n_tx * N;
+    const long long want = 4ll * 2048 * ctx->num_sms;
+    const long long by_rx = std::min<long long>(8, (long long)nr_max / 64);
+    p.n_chunks = (int)std::max<long long>(1, std::min<long long>(by_rx, (want + slots - 1) / slots));
+    const long long total = slots * p.n_chunks;
     const long long blocks = std::min<long long>((total + 127) / 128, 16ll * ctx->num_sms);
     if (vjp) {
         prof_begin(ctx, "k_scatter_vjp");

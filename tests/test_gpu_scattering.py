@@ -121,3 +121,27 @@ def test_directive_pattern_matches_oracle(tracer):
     for bad in ([-2, 0, 0], [0, 65, 0], [0, 0]):
         with pytest.raises(rt.RtError):
             tracer.set_scattering_pattern(bad)
+
+
+def test_scattering_many_receivers():
+    """200 receivers: each ray's receivers are split over several threads
+    (three chunks, the last one shorter); the gain equals the oracle's."""
+    tr = rt.Tracer(0, FC)
+    try:
+        sc = S.tiny_scene()
+        tx = S.Devices(np.array([[-60.0, -20.0, 25.0]], np.float32), np.zeros((1, 3), np.float32), S.TR38901_VH)
+        rng = np.random.default_rng(7)
+        xy = rng.uniform(-95.0, 95.0, size=(400, 2))
+        xy = xy[(np.abs(xy[:, 0]) > 12.0) | (np.abs(xy[:, 1]) > 12.0)][:200]
+        rx = S.Devices(np.concatenate([xy, np.full((200, 1), 1.5)], 1).astype(np.float32), np.zeros((200, 3), np.float32),
+                       S.V_ISO)
+        setup(tr, sc, tx, rx)
+        S_m = np.array([0.6], np.float32)
+        tr.set_scattering(S_m)
+        N = 2000
+        g = tr.scattering_gain(N).cpu().numpy()
+        og = SC.scattering_gain(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N)
+        assert (og > 0).sum() > 150
+        assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
+    finally:
+        tr.close()
