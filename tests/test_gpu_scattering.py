@@ -125,7 +125,8 @@ def test_directive_pattern_matches_oracle(tracer):
 
 def test_scattering_many_receivers():
     """200 receivers: each ray's receivers are split over several threads
-    (three chunks, the last one shorter); the gain equals the oracle's."""
+    (three chunks, the last one shorter); the gain and its VJP equal the
+    oracle's."""
     tr = rt.Tracer(0, FC)
     try:
         sc = S.tiny_scene()
@@ -143,5 +144,10 @@ def test_scattering_many_receivers():
         og = SC.scattering_gain(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N)
         assert (og > 0).sum() > 150
         assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
+        up = rng.normal(size=(200, 1, 2)).astype(np.float32)
+        gs = tr.scattering_gain_vjp(N, up).cpu().numpy()
+        ogs = SC.scattering_gain_vjp(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N, up)
+        scale = 2.0 / float(S_m[0]) * float(np.sum(np.abs(up) * og))   # bound of |dL/dS|
+        assert np.allclose(gs, ogs, rtol=3e-3, atol=2e-3 * scale), (gs, ogs, scale)
     finally:
         tr.close()
