@@ -274,8 +274,9 @@ int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, 
 /*
  * Sec. II-B (diffuse reflections, i.e. scattering; the model is a reading,
  * the paper leaves it to the documentation): scattering coefficients S
- * [n_mat] float32 (device, 0..1) of the scene's materials; all zero (no
- * scattering) until set, and reset by rt_load_scene. Errors:
+ * [n_mat] float32 (device, 0..1; a value <= 0 scatters nothing) of the
+ * scene's materials; all zero (no scattering) until set, and reset by
+ * rt_load_scene. Errors:
  * RT_ERR_INVALID_ARG for another material count.
  */
 int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat);

@@ -119,7 +119,7 @@ def scattering_gain_vjp(osc, scene_mat, S, fc: float, txdev, rxdev, N: int, up, 
     S = np.asarray(S, np.float64)
     grad = np.zeros(len(S))
     for m in range(len(S)):
-        if S[m] == 0.0:
+        if S[m] <= 0.0:     # S <= 0 scatters nothing (as in scattering_gain)
             continue
         one = np.zeros(len(S))
         one[m] = 1.0

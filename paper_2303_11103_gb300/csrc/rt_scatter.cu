@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
             if (hit >= 0) {
                 m = __ldg(p.s.mat + hit);
                 sc = __ldg(p.scat + m);
-                s2 = sc * sc;
+                s2 = sc > 0.0f ? sc * sc : 0.0f;   // S <= 0: no scattering
                 n = xyz(__ldg(p.s.planes + hit));
                 if (dot(d, n) > 0.0f) n = n * -1.0f;   // the side the ray came from
                 P = o + d * th;

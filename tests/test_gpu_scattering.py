@@ -151,3 +151,20 @@ def test_scattering_many_receivers():
         assert np.allclose(gs, ogs, rtol=3e-3, atol=2e-3 * scale), (gs, ogs, scale)
     finally:
         tr.close()
+
+
+def test_negative_coefficient_scatters_nothing(tracer):
+    """A coefficient <= 0 scatters nothing, in the gain and in its VJP."""
+    sc = S.tiny_scene_3mat()
+    tx = S.Devices(np.array([[-50.0, -50.0, 20.0]], np.float32), np.zeros((1, 3), np.float32), S.TR38901_VH)
+    rx = S.Devices(np.array([[-75.0, 0.0, 1.5], [-20.0, -40.0, 6.0]], np.float32), np.zeros((2, 3), np.float32),
+                   S.V_ISO)
+    setup(tracer, sc, tx, rx)
+    S_m = np.array([-0.5, 0.6, 0.0], np.float32)
+    tracer.set_scattering(S_m)
+    N = 5000
+    g = tracer.scattering_gain(N).cpu().numpy()
+    og = SC.scattering_gain(O.make_scene(sc), sc.mat_id, S_m.astype(np.float64), FC, tx, rx, N)
+    assert np.all(np.abs(g - og) <= 2e-3 * og + 1e-3 * og.sum(axis=(1, 2), keepdims=True)), (g, og)
+    gs = tracer.scattering_gain_vjp(N, np.ones((2, 1, 2), np.float32)).cpu().numpy()
+    assert gs[0] == 0.0 and gs[2] == 0.0 and gs[1] > 0.0
