@@ -49,22 +49,84 @@ def peaks():
     return 6800.0, "fallback"
 
 
-class Clocks:
-    """Samples nvidia-smi clocks / throttle reasons during the timed region."""
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver)."""
 
-    def __init__(self, index: int):
+    SM = 1
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device_index: int):
+        import ctypes
+        import torch
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        props = torch.cuda.get_device_properties(device_index)
+        ok = False
+        uuid = getattr(props, "uuid", None)
+        if uuid is not None:
+            ok = self.lib.nvmlDeviceGetHandleByUUID(f"GPU-{uuid}".encode(), ctypes.byref(self.h)) == 0
+        if not ok:
+            bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0".encode()
+            ok = self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) == 0
+        if not ok:
+            raise OSError("no NVML handle for the CUDA device")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn if fn is not None else self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def sample(self):
+        v = self.c.c_uint()
+        m = self.c.c_uint()
+        r = self.c.c_ulonglong()
+        if (self.lib.nvmlDeviceGetClockInfo(self.h, self.SM, self.c.byref(v)) or
+                self.lib.nvmlDeviceGetMaxClockInfo(self.h, self.SM, self.c.byref(m)) or
+                self.reasons_fn(self.h, self.c.byref(r))):
+            return None
+        return float(v.value), float(m.value), sorted(n for b, n in self.REASONS.items() if r.value & b)
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons during the timed region: NVML
+    every 2 ms from a thread (nvidia-smi at 10 ms if NVML cannot be loaded)."""
+
+    def __init__(self, index: int, period_s: float = 0.002):
         self.index = index
-        self.samples = []
+        self.period = period_s
+        self.samples = []      # (sm_mhz, max_mhz, [reasons])
         self.proc = None
+        self.stop = threading.Event()
+        self.thread = None
+        self.source = None
 
     def __enter__(self):
+        try:
+            nv = _Nvml(self.index)
+            self.source = "nvml, 2 ms"
+
+            def run():
+                while not self.stop.is_set():
+                    s = nv.sample()
+                    if s is not None:
+                        self.samples.append(s)
+                    time.sleep(self.period)
+            s0 = nv.sample()
+            if s0 is not None:
+                self.samples.append(s0)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return self
+        except (OSError, AttributeError):
+            pass
         q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi, 10 ms"
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -72,28 +134,32 @@ class Clocks:
         return self
 
     def _read(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.proc.stdout:
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) == 6:
-                self.samples.append(parts)
+            if len(parts) == 6 and parts[0].replace(".", "").isdigit() and parts[1].replace(".", "").isdigit():
+                self.samples.append((float(parts[0]), float(parts[1]),
+                                     [names[k] for k in range(4) if parts[2 + k] == "Active"]))
 
     def __exit__(self, *a):
+        self.stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
     def summary(self):
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[2 + k] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "source": self.source}
+        sm = [x[0] for x in self.samples]
+        mx = [x[1] for x in self.samples]
+        reasons = sorted({r for x in self.samples for r in x[2]})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "sm_min_mhz": min(sm),
+                "reasons": reasons, "samples": len(self.samples), "source": self.source}
 
 
 def dist_init():
@@ -292,7 +358,8 @@ def run_ours(args):
     # dominant kernel and its roofline (durations measured in the timed region)
     kern = prof["kernels"]
     hbm, src = peaks()
-    roof = roofline(dom, kern[dom], sbr_counts, cov_counts, hbm, src)
+    probe = traversal_probe(ctx, cov_counts)
+    roof = roofline(dom, kern[dom], sbr_counts, cov_counts, hbm, src, probe)
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = extra_measurements(tr, scene, dev, args)
@@ -350,8 +417,9 @@ def run_ours(args):
 # node record (2 x (6 FMA + 6 per-axis min/max + 4 combining min/max + 1
 # compare) = 34) and one Moller-Trumbore test per triangle record (35).
 OPS_PER_NODE, OPS_PER_TRI = 34, 35
-# FP32/ALU lane-operation peak: 152 SMs x 128 lanes x 2070 MHz (one op per
-# lane per clock, an FMA counted as one operation).
+# Lane-operation count of the SMs: 152 SMs x 128 lanes x 2070 MHz (one op per
+# lane per clock, an FMA counted as one operation); reported beside the
+# measured peak, which is what the fraction uses.
 ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
@@ -359,27 +427,45 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 K_COVERAGE_TRAFFIC = 4.267e6
 
 
-def roofline(name, rec, sbr_counts, cov_counts, hbm, src):
+def traversal_probe(ctx, counts, n_tri=4):
+    """Measured issue peak of the traversal arithmetic (rt_probe_peak): the
+    tracer's own slab and triangle tests on register data, in the mix of
+    slab tests (2 per node record) to triangle tests the counting pass of
+    the coverage kernel measured. Returns (Gop/s, mix)."""
+    from paper_2303_11103_gb300 import rt
+    slabs_per_tri = 2.0 * counts["nodes"] / max(counts["tris"], 1)
+    n_slab = max(8, int(round(slabs_per_tri * n_tri / 8.0)) * 8)
+    gops = rt.rt_probe_peak(ctx, rt.PROBE_TRAVERSAL, n_slab, n_tri) / 1e9
+    return gops, {"slab_tests": n_slab, "triangle_tests": n_tri}
+
+
+def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
     """Roofline of the dominant kernel: algorithmic work per launch / mean duration.
 
     The traversal kernels keep the BVH and triangles in L1/L2 (ncu: 94 % L1
-    hits, 4.3 MB of DRAM traffic per coverage launch), so their bound is ALU
-    issue, not HBM; the node/triangle record bytes they request are reported
-    beside it (`requested_gbs`) for comparison with the HBM peak.
+    hits, 4.3 MB of DRAM traffic per coverage launch), so their bound is
+    instruction issue, not HBM. The peak is measured: rt_probe_peak runs the
+    traversal's own slab and triangle tests on register data in the
+    kernel's measured mix. The node/triangle record bytes requested are
+    reported beside it (`requested_gbs`) for comparison with the HBM peak.
     """
     launches, ms = rec
     per_launch_s = ms / launches / 1e3
     counts = {"k_coverage": cov_counts, "k_sbr": sbr_counts, "k_validate": sbr_counts}.get(name)
+    peak, mix = probe
     if counts is None:
-        return {"kernel": name, "bound": "alu", "achieved": None, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+        return {"kernel": name, "bound": "alu", "achieved": None, "peak": peak, "unit": "Gop/s",
                 "frac": None, "traffic": None, "note": "no algorithmic model for this kernel"}
     ops = counts["nodes"] * OPS_PER_NODE + counts["tris"] * OPS_PER_TRI
     req_bytes = counts["nodes"] * 64 + counts["tris"] * 48
     ach = ops / per_launch_s / 1e9
-    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
-            "frac": ach / ALU_PEAK_GOPS,
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
+            "frac": ach / peak,
             "traffic": K_COVERAGE_TRAFFIC if name == "k_coverage" else None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+            "peak_source": "measured: rt_probe_peak(RT_PROBE_TRAVERSAL), the traversal's slab and "
+                           f"Moller-Trumbore tests on register data, {mix['slab_tests']} slab tests per "
+                           f"{mix['triangle_tests']} triangle tests (the kernel's counted mix), best of 5",
+            "lane_count_gops": ALU_PEAK_GOPS, "frac_of_lane_count": ach / ALU_PEAK_GOPS,
             "ops_per_launch": ops, "ops_basis": f"{OPS_PER_NODE} per BVH node record, {OPS_PER_TRI} per triangle record",
             "requested_gbs": req_bytes / per_launch_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
             "ms_per_launch": per_launch_s * 1e3,
@@ -431,6 +517,8 @@ def extra_measurements(tr, scene, dev, args):
     ms = statistics.median(ts)
     rt.rt_set_tuning(ctx, *tuning_default)
     ext = cir_extensions_measurement(tr, scene, dev)
+    ext["freq_response_dense"] = freq_dense_measurement(tr)
+    ext["differentiation"] = differentiation_measurement()
     return {**ext, "coverage_map_ms": ms,
             "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch "
                                    "in a captured CUDA graph, median of 10 replays",
@@ -491,6 +579,111 @@ def cir_extensions_measurement(tr, scene, dev, T=14, fs=1e6):
             "synthetic_array": {"paths": int(a.shape[0]), "outputs": int(ael.numel()), "ms": statistics.median(ts),
                                 "config": "the same paths, Tx planar array 8 x 2 (0.7 / 0.5 wavelengths), "
                                           "dual-polarized TR 38.901 elements, single-element Rx"}}
+
+
+def _event_ms(fn, reps=20, warm=3):
+    """Median CUDA-event time (ms) of fn() on torch's current stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def freq_dense_measurement(tr, n_pairs=1000, mean_paths=64, K=N_SC):
+    """H(f) where it is compute-bound: a seeded dense path list (Poisson(64)
+    paths per pair, 1000 pairs, 2 x 2 port pairs, 1024 subcarriers of
+    30 kHz) through rt_freq_response_paths; FP32 work = 8 flops per complex
+    MAC per (path, subcarrier, port pair) + 6 per twiddle step per (path,
+    subcarrier), against the measured FP32 FMA peak (rt_probe_peak)."""
+    import torch
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import scenes as S
+    dev = tr.device
+    off, a, tau = S.dense_path_list(n_pairs, mean_paths, 4, seed=10)
+    off_d = torch.as_tensor(off, device=dev)
+    a_d = torch.view_as_real(torch.as_tensor(a, device=dev)).contiguous()
+    tau_d = torch.as_tensor(tau, device=dev)
+    f_d = torch.as_tensor((np.arange(K, dtype=np.float64) - K // 2) * SC_SPACING, device=dev)
+    H = torch.empty((n_pairs, 4, K, 2), dtype=torch.float32, device=dev)
+    rt.rt_set_stream(tr.ctx)
+    ms = _event_ms(lambda: rt.rt_freq_response_paths(tr.ctx, off_d, 4, a_d, tau_d, f_d, H))
+    P = int(off[-1])
+    flops = P * K * (8 * 4 + 6)
+    peak = rt.rt_probe_peak(tr.ctx, rt.PROBE_FFMA) / 1e12
+    tf = flops / (ms / 1e3) / 1e12
+    return {"pairs": n_pairs, "paths": P, "subcarriers": K, "port_pairs": 4, "ms": ms,
+            "path_subcarrier_terms_per_s": P * K * 4 / (ms / 1e3), "tflops": tf,
+            "fp32_peak_tflops": peak, "fp32_frac": tf / peak,
+            "peak_source": "measured: rt_probe_peak(RT_PROBE_FFMA), 8 chains of FP32 FMA per thread, best of 5",
+            "output_bytes": n_pairs * 4 * K * 8,
+            "config": "seeded dense path list (scenes.dense_path_list, seed 10): Poisson(64) paths per pair, "
+                      "tau U(0.2, 3.3) us, 2x2 port pairs; median of 20 CUDA-event timings"}
+
+
+def differentiation_measurement(n_rx=256, n_mat=8):
+    """The differentiation workload: the seeded city with 8 materials, 1 TR
+    38.901 dual-polarized transmitter, 256 receivers, 1e6 rays, max_depth 3.
+    Times the path search once, then (median of 20) the forward CIR and the
+    backward pass of L = sum_rx 10 log10(sum |a|^2) through rt.CIR (the
+    replayed-path VJP kernels), and of the NMSE of H(f) at 128 subcarriers
+    through rt.CIR and rt.FreqResponse (Sec. III-A)."""
+    import torch
+    from paper_2303_11103_gb300 import rt
+    from paper_2303_11103_gb300 import scenes as S
+    scene = S.city_scene(20, n_materials=n_mat)
+    tx, rx = S.city_devices(scene, n_rx=n_rx, tx_antenna=S.TR38901_VH)
+    tr = rt.Tracer(0, FC)
+    dev = tr.device
+    tr.load_scene(scene)
+    tr.set_devices(tx, rx)
+    t_paths = _event_ms(lambda: tr.compute_paths(MAX_DEPTH, N_RAYS), reps=5, warm=1)
+    P = tr.compute_paths(MAX_DEPTH, N_RAYS)
+    freqs = torch.as_tensor((np.arange(128, dtype=np.float64) - 64) * SC_SPACING, device=dev)
+    rx_of = torch.repeat_interleave(torch.arange(n_rx, device=dev),
+                                    torch.diff(tr.paths()["offsets"]).to(dev))
+    eps = torch.tensor(scene.materials[:, 0], device=dev, requires_grad=True)
+    sig = torch.tensor(scene.materials[:, 1], device=dev, requires_grad=True)
+    pos = torch.tensor(tx.pos, device=dev, requires_grad=True)
+    ypr = torch.tensor(tx.ypr, device=dev, requires_grad=True)
+    with torch.no_grad():
+        a0, t0 = rt.CIR.apply(tr, eps, sig, pos, ypr)
+        H_ref = rt.FreqResponse.apply(tr, a0, t0, freqs)
+
+    def power_step():
+        for p in (eps, sig, pos, ypr):
+            p.grad = None
+        a, _ = rt.CIR.apply(tr, eps, sig, pos, ypr)
+        pw = torch.zeros(n_rx, device=dev).index_add(0, rx_of, (a.abs() ** 2).sum(dim=(1, 2)))
+        (10 * torch.log10(pw[pw > 0])).sum().backward()
+
+    def nmse_step():
+        for p in (eps, sig, pos, ypr):
+            p.grad = None
+        a, tau = rt.CIR.apply(tr, eps, sig, pos, ypr)
+        H = rt.FreqResponse.apply(tr, a, tau, freqs)
+        (((H - H_ref).abs() ** 2).sum() / (H_ref.abs() ** 2).sum()).backward()
+
+    t_pw = _event_ms(power_step)
+    t_nm = _event_ms(nmse_step)
+    ga = torch.randn((max(P, 1), tr.nrp, tr.ntp), dtype=torch.complex64, device=dev)
+    t_vjp = _event_ms(lambda: tr.cir_backward(ga))
+    tr.close()
+    return {"paths": P, "receivers": n_rx, "materials": n_mat, "parameters": 2 * n_mat + 6,
+            "compute_paths_ms": t_paths, "power_db_grad_step_ms": t_pw, "nmse_grad_step_ms": t_nm,
+            "cir_vjp_ms": t_vjp,
+            "config": "city 4802 tris, 8 materials (eps_r U(2,8), sigma logU(1e-3,1)), 1 TR 38.901 dual-pol Tx, "
+                      "256 Rx, 1e6 rays, max_depth 3; grad steps = forward CIR (+ H(f) at 128 subcarriers) + "
+                      "loss + backward through the replayed paths; medians of 20 CUDA-event timings"}
 
 
 def diffraction_measurement(tr):
@@ -650,7 +843,8 @@ def run_reference(args):
 
 def run_kernel_case(args):
     """One kernel of the step on its own (for ncu captures):
-    `--only coverage|paths|freq|tail|scatter|mlp_infer|mlp_train`; tail =
+    `--only coverage|paths|freq|freq_dense|tail|scatter|mlp_infer|mlp_train`;
+    freq_dense = H(f) on the seeded dense path list; tail =
     compute_paths, cir, H(f) and both VJPs (the calls after the ray trace);
     scatter = first-order diffuse scattering (every material S = 0.3) over
     --rays lattice rays to the 1000 receivers."""
@@ -673,6 +867,21 @@ def run_kernel_case(args):
                 sur.train_step(x[:8192], t[:8192], 1e-4, acc)
         torch.cuda.synchronize()
         print(json.dumps({"case": args.only, "queries": args.queries, "launches": args.warmup + args.steps}))
+        return
+    if args.only == "freq_dense":
+        # H(f) on the seeded dense path list (64 paths per pair, 1000 pairs, 2 x 2 ports, 1024 subcarriers)
+        tr = rt.Tracer(0, FC)
+        off, a, tau = S.dense_path_list(1000, 64, 4, seed=10)
+        off_d = torch.as_tensor(off, device="cuda")
+        a_d = torch.view_as_real(torch.as_tensor(a, device="cuda")).contiguous()
+        tau_d = torch.as_tensor(tau, device="cuda")
+        f_d = torch.as_tensor((np.arange(N_SC, dtype=np.float64) - N_SC // 2) * SC_SPACING, device="cuda")
+        H = torch.empty((1000, 4, N_SC, 2), dtype=torch.float32, device="cuda")
+        rt.rt_set_stream(tr.ctx)
+        for _ in range(args.warmup + args.steps):
+            rt.rt_freq_response_paths(tr.ctx, off_d, 4, a_d, tau_d, f_d, H)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.only, "paths": int(off[-1]), "launches": args.warmup + args.steps}))
         return
     scene = S.city_scene(20)
     tx, rx = S.city_devices(scene, n_rx=N_RX)
@@ -706,7 +915,8 @@ def run_kernel_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", choices=["coverage", "paths", "freq", "tail", "scatter", "mlp_infer", "mlp_train"], default=None,
+    ap.add_argument("--only", choices=["coverage", "paths", "freq", "freq_dense", "tail", "scatter", "mlp_infer",
+                                       "mlp_train"], default=None,
                     help="run one kernel case of the step (profiling)")
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--queries", type=int, default=1 << 20, help="surrogate queries (--only mlp_*)")

@@ -276,7 +276,11 @@ int rt_coverage_map_diffraction(rt_ctx* ctx, const rt_grid* g, int32_t tx_port, 
  * the paper leaves it to the documentation): scattering coefficients S
  * [n_mat] float32 (device, 0..1; a value <= 0 scatters nothing) of the
  * scene's materials; all zero (no scattering) until set, and reset by
- * rt_load_scene. Errors:
+ * rt_load_scene. The values stay on the device and are not checked: S > 1
+ * re-radiates more power than arrives, which is outside the model, and a
+ * material with S <= 0 gets a zero gradient from rt_scattering_gain_vjp, so
+ * an optimiser stepping S must keep it in (0, 1] itself (clamp it, or
+ * optimise an unconstrained u with S = sigmoid(u)). Errors:
  * RT_ERR_INVALID_ARG for another material count.
  */
 int rt_set_scattering(rt_ctx* ctx, const float* coeff, int32_t n_mat);
@@ -325,6 +329,20 @@ int rt_get_wedges(rt_ctx* ctx, int64_t* n_out, int32_t* faces, float* n_ext);
  */
 int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double* freqs,
                      int32_t K, float* H);
+
+/*
+ * Sec. III-A: rt_freq_response over a path list the caller provides rather
+ * than the context's traced paths (paths from another tracer, a saved CIR,
+ * synthetic channels). offsets [n_pairs+1] int64 (device, CSR: pair r owns
+ * paths offsets[r] .. offsets[r+1]-1, non-decreasing, offsets[0] = 0);
+ * a [P*n_port_pairs] complex64 (device, path-major); tau [P] float32
+ * (device, s); freqs [K] float64 (device, Hz baseband offsets);
+ * H [n_pairs*n_port_pairs*K] complex64 (device, overwritten):
+ * H[r][q][k] = sum_i a[i][q] exp(-j 2 pi f_k tau_i). n_port_pairs is 1, 2
+ * or 4. Needs no scene. Errors: RT_ERR_INVALID_ARG.
+ */
+int rt_freq_response_paths(rt_ctx* ctx, const int64_t* offsets, int64_t n_pairs, int32_t n_port_pairs,
+                           const float* a, const float* tau, const double* freqs, int32_t K, float* H);
 
 /*
  * Sec. II-A Listing 2 / Fig. 2: coverage map of every transmitter, port
@@ -385,6 +403,25 @@ int rt_coverage_map_async(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int6
 int rt_join(rt_ctx* ctx);
 
 /*
+ * Measured issue peaks for the roofline of the tracer's kernels (the paper
+ * has no counterpart; this is measurement support). Runs a register-only
+ * micro-kernel on the context's device and stream, six launches of about
+ * 2 ms (the first is a warm-up), and writes the best rate to *ops_per_s
+ * (HOST):
+ *   RT_PROBE_TRAVERSAL: the traversal's own slab test and Moller-Trumbore
+ *     triangle test, n_slab slab tests (a positive multiple of 8) per n_tri
+ *     triangle tests, as algorithmic operations per second (17 per slab
+ *     test, 35 per triangle test, the counts the bench's roofline uses);
+ *   RT_PROBE_FFMA: FP32 fused multiply-adds, as flops per second (2 per
+ *     FMA); n_slab and n_tri are ignored.
+ * Synchronises the stream. Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_READY
+ * while capturing a graph, RT_ERR_CUDA.
+ */
+#define RT_PROBE_TRAVERSAL 0
+#define RT_PROBE_FFMA 1
+int rt_probe_peak(rt_ctx* ctx, int32_t kind, int32_t n_slab, int32_t n_tri, double* ops_per_s);
+
+/*
  * Allocation-free coverage map. The paper has no counterpart; it exists for
  * callers that must not allocate device memory at call time: hosts whose
  * device memory is owned by another allocator (a framework's caching
@@ -400,9 +437,14 @@ int rt_join(rt_ctx* ctx);
  *     RT_ERR_INVALID_ARG with a message (use rt_coverage_map for more);
  *   - the context must already hold the scene and devices (rt_load_scene,
  *     rt_set_tx, rt_set_rx allocate; call them during set-up);
- *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     during set-up, before any stream capture;
+ *   - every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the context's device current, so the address stays right after
+ *     cudaDeviceReset or under another context of the device; the first
+ *     lookup on a device may load the library's GPU module, so make the
+ *     first call during set-up, before any stream capture;
+ *   - like rt_coverage_map it reports no traversal overflow: every scene
+ *     load checks the hierarchy on the device (a tree, depth below the
+ *     traversal stack), so a query cannot overflow its stack;
  *   - all calls share the one array and each call clears what must start at
  *     zero; calls whose GPU work overlaps (other streams or contexts on the
  *     same device) race on it, so serialise them.
@@ -514,6 +556,22 @@ int rt_mlp_infer_layers(rt_mlp* m, const float* x, int64_t n, float* out);
 int rt_mlp_num_params(const rt_mlp* m, int64_t* n_host);
 int rt_mlp_get_params(rt_mlp* m, float* dst);
 int rt_mlp_set_params(rt_mlp* m, const float* src);
+/*
+ * Save and load a surrogate (configs of the learned part: a model trained
+ * once is reused for inference). rt_mlp_save writes the shape (n_freq,
+ * width, n_hidden), the normalisation box, the free-space baseline, the
+ * output scaling and the parameter vector (rt_mlp_get_params layout), with
+ * a 64-bit FNV-1a hash, into buf (HOST, cap bytes); *size_out (HOST)
+ * receives the byte count, and buf == NULL only queries it. Synchronises
+ * the model's stream. The optimiser state (Adam moments, step) is not
+ * saved: training a loaded model starts it afresh. Errors:
+ * RT_ERR_INVALID_ARG, RT_ERR_CAPACITY if cap is below the size.
+ * rt_mlp_load creates a model on device/cuda_stream from such bytes (buf
+ * HOST, size bytes); outputs equal the saved model's bit for bit. Errors:
+ * RT_ERR_INVALID_ARG for a size, magic or hash mismatch; as rt_mlp_create.
+ */
+int rt_mlp_save(rt_mlp* m, void* buf, int64_t cap, int64_t* size_out);
+int rt_mlp_load(rt_mlp** m, int device, void* cuda_stream, const void* buf, int64_t size);
 /* Gradients of the last training step (before its update), parameter layout. */
 int rt_mlp_get_grads(rt_mlp* m, float* dst);
 /* Error bits of the GEMM kernels (1 = a bounded wait timed out) (HOST out). */

@@ -25,6 +25,8 @@ int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau
                  float* g_pos, float* g_ypr);
 int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
               int64_t n_pairs);
+int freq_csr_impl(rt_ctx* ctx, const int64_t* off, int64_t n_pairs, int np, const float* a, const float* tau,
+                  const double* freqs, int K, float* H);
 int freq_vjp_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, const float* gH,
                   float* ga, float* gt, int64_t n_pairs);
 int launch_coverage_vjp(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int tx_port, const float* grad_gain,
@@ -598,6 +600,16 @@ int rt_freq_response(rt_ctx* ctx, const float* a, const float* tau, const double
     int64_t np = 0;
     rt_num_pairs(ctx, &np);
     return freq_impl(ctx, a, tau, freqs, K, H, np);
+}
+
+int rt_freq_response_paths(rt_ctx* ctx, const int64_t* offsets, int64_t n_pairs, int32_t n_port_pairs,
+                           const float* a, const float* tau, const double* freqs, int32_t K, float* H) {
+    CHECK_CTX(ctx);
+    if (n_pairs < 0 || K < 0 || (n_port_pairs != 1 && n_port_pairs != 2 && n_port_pairs != 4) ||
+        (n_pairs > 0 && K > 0 && (!offsets || !a || !tau || !freqs || !H)))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "freq_response_paths: bad arguments");
+    if (n_pairs > 0x7fffffffll) return set_err(ctx, RT_ERR_INVALID_ARG, "freq_response_paths: n_pairs above 2^31-1");
+    return freq_csr_impl(ctx, offsets, n_pairs, n_port_pairs, a, tau, freqs, K, H);
 }
 
 int rt_coverage_map(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_rays, int32_t tx_port,

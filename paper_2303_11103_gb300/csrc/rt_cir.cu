@@ -513,14 +513,13 @@ CirParams make_cir(rt_ctx* ctx, uint32_t flags) {
 }
 
 template <int NP>
-cudaError_t launch_freq(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
-                        int64_t n_pairs) {
+cudaError_t launch_freq(rt_ctx* ctx, const int64_t* off, const float* a, const float* tau, const double* freqs,
+                        int K, float* H, int64_t n_pairs) {
     dim3 grid((unsigned)n_pairs, (unsigned)((K + HF_THREADS * HF_RUN - 1) / (HF_THREADS * HF_RUN)));
     cudaError_t e = cudaMemsetAsync(H, 0, sizeof(float2) * NP * (size_t)K * (size_t)n_pairs, ctx->stream);
     if (e != cudaSuccess) return e;
     prof_begin(ctx, "k_freq");
-    k_freq<NP><<<grid, HF_THREADS, 0, ctx->stream>>>(bp<int64_t>(ctx->path_off), (const float2*)a, tau, freqs, K,
-                                              (float2*)H);
+    k_freq<NP><<<grid, HF_THREADS, 0, ctx->stream>>>(off, (const float2*)a, tau, freqs, K, (float2*)H);
     prof_end(ctx);
     return cudaGetLastError();
 }
@@ -602,17 +601,24 @@ int cir_vjp_impl(rt_ctx* ctx, uint32_t flags, const float* ga, const float* gtau
     return RT_OK;
 }
 
-int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
-              int64_t n_pairs) {
+// H(f) over the CSR path list off [n_pairs+1] with np port pairs per path
+// (1, 2 or 4): the context's own paths, or a caller's list.
+int freq_csr_impl(rt_ctx* ctx, const int64_t* off, int64_t n_pairs, int np, const float* a, const float* tau,
+                  const double* freqs, int K, float* H) {
     if (K <= 0 || n_pairs <= 0) return RT_OK;
-    const int np = ctx->tx_ant.n_ports * ctx->rx_ant.n_ports;
     switch (np) {
-        case 1: RT_TRY(launch_freq<1>(ctx, a, tau, freqs, K, H, n_pairs)); break;
-        case 2: RT_TRY(launch_freq<2>(ctx, a, tau, freqs, K, H, n_pairs)); break;
-        default: RT_TRY(launch_freq<4>(ctx, a, tau, freqs, K, H, n_pairs)); break;
+        case 1: RT_TRY(launch_freq<1>(ctx, off, a, tau, freqs, K, H, n_pairs)); break;
+        case 2: RT_TRY(launch_freq<2>(ctx, off, a, tau, freqs, K, H, n_pairs)); break;
+        default: RT_TRY(launch_freq<4>(ctx, off, a, tau, freqs, K, H, n_pairs)); break;
     }
     RT_TRY(cudaGetLastError());
     return RT_OK;
+}
+
+int freq_impl(rt_ctx* ctx, const float* a, const float* tau, const double* freqs, int K, float* H,
+              int64_t n_pairs) {
+    return freq_csr_impl(ctx, bp<int64_t>(ctx->path_off), n_pairs, ctx->tx_ant.n_ports * ctx->rx_ant.n_ports, a,
+                         tau, freqs, K, H);
 }
 
 // Per pair: incoherent path gain sum_paths sum_ports |a|^2 in dB, and whether

@@ -997,6 +997,104 @@ static int mlp_params(rt_mlp* m, float* p, int dir) {
 int rt_mlp_get_params(rt_mlp* m, float* dst) { return mlp_params(m, dst, 0); }
 int rt_mlp_set_params(rt_mlp* m, const float* src) { return mlp_params(m, const_cast<float*>(src), 1); }
 
+// Serialised model (rt_mlp_save / rt_mlp_load), little-endian host bytes:
+//   "RTMLP001" | int32 F, W, L, 0 | float lo[6], hi[6], lam, db_scale,
+//   db_offset, 0 | int64 n_params | float params[n_params] (the
+//   rt_mlp_get_params layout) | uint64 FNV-1a hash of everything before it.
+namespace {
+constexpr char MLP_MAGIC[8] = {'R', 'T', 'M', 'L', 'P', '0', '0', '1'};
+constexpr size_t MLP_HDR = 8 + 4 * 4 + 16 * 4 + 8;
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+}  // namespace
+
+int rt_mlp_save(rt_mlp* m, void* buf, int64_t cap, int64_t* size_out) {
+    if (!m || !size_out) return RT_ERR_INVALID_ARG;
+    int64_t np = 0;
+    rt_mlp_num_params(m, &np);
+    const size_t need = MLP_HDR + 4 * (size_t)np + 8;
+    *size_out = (int64_t)need;
+    if (!buf) return RT_OK;
+    if (cap < (int64_t)need) return mlp_err(m, RT_ERR_CAPACITY, "mlp_save: buffer smaller than the size query");
+    if (cudaSetDevice(m->device) != cudaSuccess) return RT_ERR_CUDA;
+    unsigned char* out = (unsigned char*)buf;
+    std::memcpy(out, MLP_MAGIC, 8);
+    const int32_t dims[4] = {m->F, m->W, m->L, 0};
+    std::memcpy(out + 8, dims, sizeof(dims));
+    float box[16] = {0};
+    MT(cudaMemcpyAsync(box, m->lo.p, 24, cudaMemcpyDeviceToHost, m->stream));
+    MT(cudaMemcpyAsync(box + 6, m->hi.p, 24, cudaMemcpyDeviceToHost, m->stream));
+    float* params = (float*)(out + MLP_HDR);
+    int64_t o = 0;
+    for (int l = 0; l <= m->L; l++) {
+        size_t nw = (size_t)m->in_dim(l) * m->out_dim(l), nb = m->out_dim(l);
+        MT(cudaMemcpyAsync(params + o, m->w[l].p, 4 * nw, cudaMemcpyDeviceToHost, m->stream));
+        MT(cudaMemcpyAsync(params + o + nw, m->b[l].p, 4 * nb, cudaMemcpyDeviceToHost, m->stream));
+        o += nw + nb;
+    }
+    MT(cudaMemcpyAsync(params + o, m->Bf.p, 4 * 6 * m->F, cudaMemcpyDeviceToHost, m->stream));
+    MT(cudaStreamSynchronize(m->stream));
+    box[12] = m->lam;
+    box[13] = m->db_scale;
+    box[14] = m->db_offset;
+    std::memcpy(out + 8 + 16, box, sizeof(box));
+    std::memcpy(out + 8 + 16 + 64, &np, 8);
+    const uint64_t h = fnv1a(out, need - 8);
+    std::memcpy(out + need - 8, &h, 8);
+    return RT_OK;
+}
+
+int rt_mlp_load(rt_mlp** out, int device, void* cuda_stream, const void* buf, int64_t size) {
+    if (!out || !buf || size < (int64_t)(MLP_HDR + 8)) return RT_ERR_INVALID_ARG;
+    *out = nullptr;
+    const unsigned char* in = (const unsigned char*)buf;
+    if (std::memcmp(in, MLP_MAGIC, 8) != 0) return RT_ERR_INVALID_ARG;
+    int32_t dims[4];
+    float box[16];
+    int64_t np = 0;
+    std::memcpy(dims, in + 8, sizeof(dims));
+    std::memcpy(box, in + 8 + 16, sizeof(box));
+    std::memcpy(&np, in + 8 + 16 + 64, 8);
+    if (np < 0 || size != (int64_t)(MLP_HDR + 4 * (size_t)np + 8)) return RT_ERR_INVALID_ARG;
+    uint64_t h = 0;
+    std::memcpy(&h, in + size - 8, 8);
+    if (h != fnv1a(in, (size_t)size - 8)) return RT_ERR_INVALID_ARG;
+    rt_mlp* m = nullptr;
+    int rc = rt_mlp_create(&m, device, cuda_stream, dims[0], dims[1], dims[2], 1.0f, 0, box, box + 6);
+    if (rc) return rc;
+    int64_t want = 0;
+    rt_mlp_num_params(m, &want);
+    if (want != np) {
+        rt_mlp_destroy(m);
+        return RT_ERR_INVALID_ARG;
+    }
+    DevBuf tmp;
+    if (buf_reserve(tmp, 4 * (size_t)np) != cudaSuccess) {
+        rt_mlp_destroy(m);
+        return RT_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(tmp.p, in + MLP_HDR, 4 * (size_t)np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) rc = mlp_params(m, bp<float>(tmp), 1);
+    if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(m->stream);
+    buf_free(tmp);
+    if (e != cudaSuccess || rc) {
+        rt_mlp_destroy(m);
+        return rc ? rc : RT_ERR_CUDA;
+    }
+    m->lam = box[12];
+    m->db_scale = box[13];
+    m->db_offset = box[14];
+    *out = m;
+    return RT_OK;
+}
+
 // Gradients of the last rt_mlp_train_step (before its Adam update), same
 // layout as the parameters (Fourier matrix entries are 0: not trained).
 int rt_mlp_get_grads(rt_mlp* m, float* dst) {

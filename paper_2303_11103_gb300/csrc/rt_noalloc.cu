@@ -3,8 +3,6 @@
 // direction-coherent ray order and the counting-sort cells that build it)
 // lives in one file-scope static __device__ array, sized for at most
 // RT_NOALLOC_MAX_RAYS rays per transmitter.
-#include <mutex>
-
 #include "rt_field.cuh"
 #include "rt_internal.h"
 
@@ -22,9 +20,6 @@ constexpr size_t NA_BYTES = NA_OFF_PERM + sizeof(uint32_t) * NA_MAX_RAYS;
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
-
-std::mutex g_na_mutex;
-void* g_na_ptr[128] = {nullptr};
 
 __device__ __forceinline__ int na_cell(f3 d) {
     int zb = (int)((d.z + 1.0f) * 0.5f * NA_ZB);
@@ -69,18 +64,16 @@ __global__ void k_na_scatter(long long N, uint32_t* __restrict__ cells, uint32_t
     if (i < N) perm[atomicAdd(cells + na_cell(fib_dir(N, i)), 1u)] = (uint32_t)i;
 }
 
-// Device address of the scratch array for the current device (looked up once
-// per device, with that device current).
+// Device address of the scratch array in the current context, looked up on
+// every call with the context's device current: a cached address would
+// dangle after cudaDeviceReset or under another context of the same device.
+// The lookup allocates nothing; the first one on a device may load the
+// library's module, which is why the first call belongs before any capture.
 int na_scratch(rt_ctx* ctx, unsigned char** out) {
-    if (ctx->device < 0 || ctx->device >= 128) return set_err(ctx, RT_ERR_INVALID_ARG, "device index");
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[ctx->device]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return set_cuda(ctx, e, "cudaGetSymbolAddress(noalloc scratch)");
-        g_na_ptr[ctx->device] = p;
-    }
-    *out = (unsigned char*)g_na_ptr[ctx->device];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return set_cuda(ctx, e, "cudaGetSymbolAddress(noalloc scratch)");
+    *out = (unsigned char*)p;
     return RT_OK;
 }
 

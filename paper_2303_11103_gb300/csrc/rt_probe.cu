@@ -1,0 +1,135 @@
+// rt_probe.cu -- measured issue peaks for the roofline of the tracer's
+// kernels (rt_probe_peak). The paper has no counterpart.
+//
+// The traversal kernels keep the scene in L1/L2 and are bound by instruction
+// issue, not by HBM. Their algorithmic work is the slab tests of BVH child
+// boxes and the Moller-Trumbore triangle tests; the rate at which an SM can
+// execute exactly that arithmetic depends on how it splits over the FMA and
+// ALU pipes (min/max and compares are ALU work). This probe runs the
+// tracer's own device functions (slab, tri_hit from rt_common.cuh) on
+// register-resident data, in the proportions the caller measured, with no
+// loads, stack or branching around them, so its rate is the ceiling of that
+// arithmetic on this GPU at the clock it runs at.
+//
+// Every test's result feeds the next test of the same box or triangle (the
+// far bound of a slab test, the origin of a triangle test), so nothing can
+// be hoisted out of the loop, merged or dropped as dead, and no operation
+// beyond the tests' own is added except one min per triangle test.
+#include <algorithm>
+
+#include "rt_internal.h"
+
+namespace {
+
+// Traversal arithmetic: n_slab8 x 8 slab tests and n_tri triangle tests per
+// iteration. Every lane holds its own ray, eight boxes and two triangles,
+// arranged so that about half of the box tests and a quarter of the
+// triangle tests are hits (the triangle division is then taken as in a
+// traversal).
+__global__ void __launch_bounds__(256) k_probe_traversal(int iters, int n_slab8, int n_tri, float* out) {
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    const float jx = 0.01f * (float)(t & 15), jy = 0.01f * (float)((t >> 4) & 15);
+    f3 o = mk(-20.0f + jx, -3.0f + jy, 1.5f);
+    const f3 d = unit(mk(1.0f, 0.05f + jy, 0.02f + jx));
+    const f3 inv = safe_inv(d);
+    const f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
+    float bx[8][6], r[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const float y0 = (k & 1) ? -2.0f : 4.0f;   // odd boxes straddle the ray, even ones miss
+        bx[k][0] = -10.0f + 2.5f * k; bx[k][1] = y0 - 3.0f; bx[k][2] = 0.0f;
+        bx[k][3] = -8.0f + 2.5f * k;  bx[k][4] = y0 + 3.0f; bx[k][5] = 3.0f;
+        r[k] = 1e30f;
+    }
+    float4 tr[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        // triangle in the plane x = 5 + k: lanes with bit k of t set are hit
+        const float yc = ((t >> k) & 1u) ? -2.0f : 9.0f;
+        tr[k][0] = make_float4(5.0f + k, yc - 4.0f, -4.0f, __int_as_float(k));
+        tr[k][1] = make_float4(0.0f, 8.0f, 0.0f, 0.0f);
+        tr[k][2] = make_float4(0.0f, 0.0f, 12.0f, 0.0f);
+    }
+    const float tmin = 1e-4f;
+    for (int it = 0; it < iters; it++) {
+        for (int s = 0; s < n_slab8; s++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                r[k] = slab(bx[k][0], bx[k][1], bx[k][2], bx[k][3], bx[k][4], bx[k][5], oi, inv, tmin, r[k]);
+        }
+        for (int q = 0; q < n_tri; q++) {
+            const float th = (q & 1) ? tri_hit(tr[1][0], tr[1][1], tr[1][2], o, d)
+                                     : tri_hit(tr[0][0], tr[0][1], tr[0][2], o, d);
+            o.x = fminf(o.x, th);
+        }
+    }
+    float sum = o.x;
+#pragma unroll
+    for (int k = 0; k < 8; k++) sum += r[k];
+    if (sum == 12345.678f) out[0] = sum;   // keeps every chain live; never true for these inputs
+}
+
+// FP32 FMA: 8 independent chains of 16 FMAs per iteration.
+__global__ void __launch_bounds__(256) k_probe_ffma(int iters, float seed, float* out) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = seed + (float)(threadIdx.x + k);
+    const float m = 0.999f, c = 1e-3f;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+#pragma unroll
+            for (int k = 0; k < 8; k++) a[k] = fmaf(a[k], m, c);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += a[k];
+    if (s == 12345.678f) out[0] = s;   // keeps the chains live; never true for these inputs
+}
+
+}  // namespace
+
+extern "C" int rt_probe_peak(rt_ctx* ctx, int32_t kind, int32_t n_slab, int32_t n_tri, double* ops_per_s) {
+    if (!ctx) return RT_ERR_INVALID_ARG;
+    cudaError_t de = cudaSetDevice(ctx->device);
+    if (de != cudaSuccess) return set_cuda(ctx, de, "cudaSetDevice");
+    if (!ops_per_s || (kind != RT_PROBE_TRAVERSAL && kind != RT_PROBE_FFMA))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "probe_peak: bad arguments");
+    if (kind == RT_PROBE_TRAVERSAL && (n_slab < 8 || n_slab % 8 || n_tri < 0 || n_slab > 4096 || n_tri > 4096))
+        return set_err(ctx, RT_ERR_INVALID_ARG, "probe_peak: n_slab a positive multiple of 8, n_tri >= 0");
+    if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "probe_peak while capturing a graph");
+    const int block = 256;
+    const void* kern = kind == RT_PROBE_TRAVERSAL ? (const void*)k_probe_traversal : (const void*)k_probe_ffma;
+    const int grid = blocks_per_sm(kern, block, 0) * ctx->num_sms;
+    const double threads = (double)grid * block;
+    // algorithmic operations per iteration and thread: 17 per slab test
+    // (6 FMA, 6 per-axis min/max, 4 combining min/max, 1 compare), 35 per
+    // triangle test; 2 flops per FMA
+    const double per_iter = kind == RT_PROBE_TRAVERSAL ? 17.0 * n_slab + 35.0 * n_tri : 2.0 * 16 * 8;
+    // about 2 ms of work at 40e12 operations/s
+    int iters = (int)std::max(8.0, 8e10 / (threads * per_iter));
+    float* sink = bp<float>(ctx->counters);   // never written (see the kernels' last lines)
+    cudaEvent_t e0, e1;
+    RT_TRY(cudaEventCreate(&e0));
+    RT_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 6 && err == cudaSuccess; rep++) {
+        cudaEventRecord(e0, ctx->stream);
+        if (kind == RT_PROBE_TRAVERSAL)
+            k_probe_traversal<<<grid, block, 0, ctx->stream>>>(iters, n_slab / 8, n_tri, sink);
+        else
+            k_probe_ffma<<<grid, block, 0, ctx->stream>>>(iters, 1.0f, sink);
+        ctx->launches++;
+        cudaEventRecord(e1, ctx->stream);
+        err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && rep > 0) best = std::min(best, ms);   // the first launch is a warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return set_cuda(ctx, err, "probe_peak");
+    *ops_per_s = threads * iters * per_iter / (best * 1e-3);
+    return RT_OK;
+}

@@ -90,6 +90,8 @@ def lib():
             "rt_set_scattering_pattern": [vp, vp, i32],
             "rt_scattering_gain_vjp": [vp, i64, vp, vp],
             "rt_freq_response": [vp, vp, vp, vp, i32, vp],
+            "rt_freq_response_paths": [vp, vp, i64, i32, vp, vp, vp, i32, vp],
+            "rt_probe_peak": [vp, i32, i32, i32, ctypes.POINTER(ctypes.c_double)],
             "rt_coverage_map": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
             "rt_coverage_map_accumulate": [vp, ctypes.POINTER(rt_grid), i32, i64, i64, i64, i32, vp, vp],
             "rt_coverage_map_noalloc": [vp, ctypes.POINTER(rt_grid), i32, i64, i32, vp, vp],
@@ -118,6 +120,8 @@ def lib():
             "rt_mlp_get_params": [vp, vp],
             "rt_mlp_set_params": [vp, vp],
             "rt_mlp_get_grads": [vp, vp],
+            "rt_mlp_save": [vp, vp, i64, ctypes.POINTER(i64)],
+            "rt_mlp_load": [ctypes.POINTER(vp), ctypes.c_int, vp, vp, i64],
             "rt_mlp_status": [vp, ctypes.POINTER(u32)],
             "rt_gemm_bf16": [vp, vp, vp, i32, i32, i32, vp, i32, i32, vp, vp],
             "rt_profile": [vp, ctypes.c_int],
@@ -323,6 +327,22 @@ def rt_coverage_map_noalloc(ctx, grid: rt_grid, max_depth, num_rays, tx_port, ga
 def rt_cir_backward(ctx, flags, grad_a, grad_tau, g_eps, g_sigma, g_txpos, g_txypr):
     _check(ctx, lib().rt_cir_backward(ctx, int(flags), _ptr(grad_a), _ptr(grad_tau), _ptr(g_eps), _ptr(g_sigma),
                                       _ptr(g_txpos), _ptr(g_txypr)))
+
+
+def rt_freq_response_paths(ctx, offsets, n_port_pairs, a, tau, freqs, H):
+    """H(f) over a caller's CSR path list (offsets [n_pairs+1] int64)."""
+    _check(ctx, lib().rt_freq_response_paths(ctx, _ptr(offsets), int(offsets.shape[0]) - 1, int(n_port_pairs),
+                                             _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]), _ptr(H)))
+
+
+PROBE_TRAVERSAL, PROBE_FFMA = 0, 1
+
+
+def rt_probe_peak(ctx, kind, n_slab=8, n_tri=0) -> float:
+    """Measured issue peak (operations/s) of the traversal arithmetic or FP32 FMA."""
+    v = ctypes.c_double()
+    _check(ctx, lib().rt_probe_peak(ctx, int(kind), int(n_slab), int(n_tri), ctypes.byref(v)))
+    return float(v.value)
 
 
 def rt_freq_response_backward(ctx, a, tau, freqs, grad_H, grad_a, grad_tau):
@@ -894,6 +914,32 @@ class Surrogate:
     def set_params(self, p):
         self._sync()
         self._check(lib().rt_mlp_set_params(self.h, _ptr(p.to(torch.float32).contiguous())))
+
+    def save(self) -> bytes:
+        """Serialised model (rt_mlp_save): shape, normalisation box, parameters."""
+        self._sync()
+        n = ctypes.c_int64()
+        self._check(lib().rt_mlp_save(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(int(n.value))
+        self._check(lib().rt_mlp_save(self.h, ctypes.cast(buf, ctypes.c_void_p), int(n.value), ctypes.byref(n)))
+        return buf.raw[:int(n.value)]
+
+    @classmethod
+    def load(cls, data: bytes, device: int = 0) -> "Surrogate":
+        """A model from rt_mlp_save's bytes (rt_mlp_load)."""
+        self = cls.__new__(cls)
+        self.device = torch.device("cuda", device)
+        self.h = ctypes.c_void_p()
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        code = lib().rt_mlp_load(ctypes.byref(self.h), device, _stream(), ctypes.cast(buf, ctypes.c_void_p), len(data))
+        if code:
+            self.h = None
+            raise RtError(code, "rt_mlp_load failed")
+        self.F, self.W, self.L = (int(v) for v in np.frombuffer(bytes(data[8:20]), dtype="<i4"))
+        n = ctypes.c_int64()
+        lib().rt_mlp_num_params(self.h, ctypes.byref(n))
+        self.n_params = int(n.value)
+        return self
 
     def grads(self):
         g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)

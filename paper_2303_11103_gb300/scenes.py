@@ -299,3 +299,31 @@ def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
                                   np.full((n_rx_per_tx, 1), 1.5)], 1))
     return np.array(tx, np.float32), np.stack(rx).astype(np.float32)
 
+
+
+def dense_path_list(n_pairs: int = 1000, mean_paths: int = 64, n_port_pairs: int = 4, seed: int = 6,
+                    tau_range=(2e-7, 3.3e-6)):
+    """Seeded synthetic channel path list for the frequency response where it
+    is compute-bound: many paths per (tx, rx) pair.
+
+    Per pair a Poisson(mean_paths) number of paths (ragged), except pair 0
+    with 3 * mean_paths + 5 (several shared-memory tiles) and pair 1 with
+    none. Delays uniform over tau_range (60 m to 1 km of path length);
+    coefficients of independent uniform phase and a magnitude uniform in dB
+    over [-140, -70] dB, per port pair.
+    Returns offsets int64 [n_pairs+1], a complex64 [P, n_port_pairs],
+    tau float32 [P].
+    """
+    rng = np.random.default_rng(seed)
+    cnt = rng.poisson(mean_paths, n_pairs).astype(np.int64)
+    if n_pairs > 0:
+        cnt[0] = 3 * mean_paths + 5
+    if n_pairs > 1:
+        cnt[1] = 0
+    off = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    P = int(off[-1])
+    mag = 10.0 ** (rng.uniform(-140.0, -70.0, (P, n_port_pairs)) / 20.0)
+    ph = rng.uniform(-np.pi, np.pi, (P, n_port_pairs))
+    a = (mag * np.exp(1j * ph)).astype(np.complex64)
+    tau = rng.uniform(tau_range[0], tau_range[1], P).astype(np.float32)
+    return off, a, tau

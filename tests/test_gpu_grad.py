@@ -156,5 +156,5 @@ def test_frequency_response_nmse_gradient(prepared):
     M = osc.M
     for gsl in [slice(0, 3), slice(3, 6), slice(6, 6 + M), slice(6 + M, 6 + 2 * M)]:
         ref = g_ora[gsl]
-        tol = 5 * GRAD_REL * np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max() + 1e-12)
+        tol = GRAD_REL * np.maximum(np.abs(ref), 0.1 * np.abs(ref).max() + 1e-12)
         assert np.all(np.abs(g_gpu[gsl] - ref) <= tol), (gsl, g_gpu[gsl], ref)

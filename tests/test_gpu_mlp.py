@@ -120,3 +120,31 @@ def test_baseline_outputs_match_reference():
     with pytest.raises(rt.RtError):
         S.set_baseline(-1.0)
     S.close()
+
+
+def test_surrogate_save_load_roundtrip():
+    """rt_mlp_save / rt_mlp_load: a trained model, saved and loaded into a
+    new model, answers bit for bit as the original; a corrupted buffer is
+    rejected."""
+    S, lo, hi = _surrogate(seed=5)
+    S.set_baseline(299792458.0 / 3.5e9)
+    x, t = _batch(512, 3)
+    xd, td = torch.as_tensor(x).cuda(), torch.as_tensor(t).cuda()
+    for _ in range(3):
+        S.train_step(xd, td, 1e-3)
+    q, _ = _batch(1000, 4)
+    qd = torch.as_tensor(q).cuda()
+    y0 = S.infer(qd)
+    data = S.save()
+    S2 = rt.Surrogate.load(data)
+    assert (S2.F, S2.W, S2.L, S2.n_params) == (S.F, S.W, S.L, S.n_params)
+    assert torch.equal(S2.params(), S.params())
+    assert torch.equal(S2.infer(qd), y0)
+    assert torch.equal(S2.infer_layers(qd), S.infer_layers(qd))
+    assert S2.save() == data
+    bad = bytearray(data)
+    bad[200] ^= 1
+    with pytest.raises(rt.RtError):
+        rt.Surrogate.load(bytes(bad))
+    S.close()
+    S2.close()

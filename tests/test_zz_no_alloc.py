@@ -47,6 +47,33 @@ def test_noalloc_matches_coverage_map():
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free0 == free1
+    # max_depth 0 (line of sight only) on a stream other than the default one
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        rt.rt_set_stream(tr.ctx)
+        g0, h0 = tr.coverage_map(GRID, 0, n_rays, 0)
+        gain.fill_(123.0)
+        hits.fill_(7)
+        rt.rt_coverage_map_noalloc(tr.ctx, grid, 0, n_rays, 0, gain, hits)
+    side.synchronize()
+    assert int(h0.sum()) > 0 and torch.equal(hits, h0)
+    assert torch.allclose(gain, g0, rtol=1e-5, atol=0)
+    rt.rt_set_stream(tr.ctx)
+    # captured in a CUDA graph after the warm-up calls above, then replayed
+    # twice: every replay reuses the static array and must give the result
+    gain.fill_(123.0)
+    hits.fill_(7)
+    rt.rt_graph_begin(tr.ctx)
+    rt.rt_coverage_map_noalloc(tr.ctx, grid, depth, n_rays, 1, gain, hits)
+    rt.rt_graph_end(tr.ctx)
+    g_ref, h_ref = tr.coverage_map(GRID, depth, n_rays, 1)
+    for replay in range(2):
+        gain.fill_(123.0)
+        hits.fill_(7)
+        rt.rt_graph_launch(tr.ctx)
+        torch.cuda.synchronize()
+        assert torch.equal(hits, h_ref), f"replay {replay}: hit counts differ"
+        assert torch.allclose(gain, g_ref, rtol=1e-5, atol=0), f"replay {replay}"
     # a size beyond the static scratch is rejected with a clear error
     with pytest.raises(rt.RtError) as e:
         rt.rt_coverage_map_noalloc(tr.ctx, grid, depth, (1 << 20) + 1, 0, gain, hits)
