@@ -413,10 +413,15 @@ def run_ours(args):
     print(json.dumps(line))
 
 
-# Algorithmic FP32/ALU operations of the traversal: two slab tests per BVH
-# node record (2 x (6 FMA + 6 per-axis min/max + 4 combining min/max + 1
-# compare) = 34) and one Moller-Trumbore test per triangle record (35).
-OPS_PER_NODE, OPS_PER_TRI = 34, 35
+# Algorithmic FP32/ALU operations of the traversal. The default binary
+# layout: two slab tests per node record (2 x (6 FMA + 6 per-axis min/max +
+# 4 combining min/max + 1 compare) = 34); the 8-wide layout: 8
+# octant-selected box tests per node record (8 x (6 FMA + 4 min/max + 1
+# compare) = 88); one Moller-Trumbore test per triangle record (35).
+BVH_WIDTH = 2
+OPS_PER_NODE = {8: 88, 2: 34}[BVH_WIDTH]
+BYTES_PER_NODE = {8: 240, 2: 64}[BVH_WIDTH]
+OPS_PER_TRI = 35
 # Lane-operation count of the SMs: 152 SMs x 128 lanes x 2070 MHz (one op per
 # lane per clock, an FMA counted as one operation); reported beside the
 # measured peak, which is what the fraction uses.
@@ -424,19 +429,21 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = 4.267e6
+K_COVERAGE_TRAFFIC = None
 
 
 def traversal_probe(ctx, counts, n_tri=4):
     """Measured issue peak of the traversal arithmetic (rt_probe_peak): the
-    tracer's own slab and triangle tests on register data, in the mix of
-    slab tests (2 per node record) to triangle tests the counting pass of
-    the coverage kernel measured. Returns (Gop/s, mix)."""
+    tracer's own box and triangle tests on register data, in the mix of box
+    tests (8 per wide node record, 2 per binary one) to triangle tests the
+    counting pass of the coverage kernel measured. Returns (Gop/s, mix)."""
     from paper_2303_11103_gb300 import rt
-    slabs_per_tri = 2.0 * counts["nodes"] / max(counts["tris"], 1)
-    n_slab = max(8, int(round(slabs_per_tri * n_tri / 8.0)) * 8)
-    gops = rt.rt_probe_peak(ctx, rt.PROBE_TRAVERSAL, n_slab, n_tri) / 1e9
-    return gops, {"slab_tests": n_slab, "triangle_tests": n_tri}
+    per_node = 8 if BVH_WIDTH == 8 else 2
+    boxes_per_tri = per_node * counts["nodes"] / max(counts["tris"], 1)
+    n_box = max(8, int(round(boxes_per_tri * n_tri / 8.0)) * 8)
+    kind = rt.PROBE_TRAVERSAL8 if BVH_WIDTH == 8 else rt.PROBE_TRAVERSAL
+    gops = rt.rt_probe_peak(ctx, kind, n_box, n_tri) / 1e9
+    return gops, {"box_tests": n_box, "triangle_tests": n_tri}
 
 
 def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
@@ -457,16 +464,19 @@ def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
         return {"kernel": name, "bound": "alu", "achieved": None, "peak": peak, "unit": "Gop/s",
                 "frac": None, "traffic": None, "note": "no algorithmic model for this kernel"}
     ops = counts["nodes"] * OPS_PER_NODE + counts["tris"] * OPS_PER_TRI
-    req_bytes = counts["nodes"] * 64 + counts["tris"] * 48
+    req_bytes = counts["nodes"] * BYTES_PER_NODE + counts["tris"] * 48
     ach = ops / per_launch_s / 1e9
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
             "frac": ach / peak,
             "traffic": K_COVERAGE_TRAFFIC if name == "k_coverage" else None,
-            "peak_source": "measured: rt_probe_peak(RT_PROBE_TRAVERSAL), the traversal's slab and "
-                           f"Moller-Trumbore tests on register data, {mix['slab_tests']} slab tests per "
-                           f"{mix['triangle_tests']} triangle tests (the kernel's counted mix), best of 5",
+            "peak_source": f"measured: rt_probe_peak({'RT_PROBE_TRAVERSAL8' if BVH_WIDTH == 8 else 'RT_PROBE_TRAVERSAL'}), "
+                           "the traversal's box and Moller-Trumbore tests on register data, "
+                           f"{mix['box_tests']} box tests per {mix['triangle_tests']} triangle tests "
+                           "(the kernel's counted mix), best of 5",
+            "bvh_width": BVH_WIDTH,
             "lane_count_gops": ALU_PEAK_GOPS, "frac_of_lane_count": ach / ALU_PEAK_GOPS,
-            "ops_per_launch": ops, "ops_basis": f"{OPS_PER_NODE} per BVH node record, {OPS_PER_TRI} per triangle record",
+            "ops_per_launch": ops, "ops_basis": f"{OPS_PER_NODE} per BVH node record ({BVH_WIDTH}-wide), "
+                                                f"{OPS_PER_TRI} per triangle record",
             "requested_gbs": req_bytes / per_launch_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
             "ms_per_launch": per_launch_s * 1e3,
             "nodes_per_query": counts["nodes"] / max(counts["closest_hit"] + counts["any_hit"], 1),

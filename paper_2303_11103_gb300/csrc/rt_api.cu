@@ -71,6 +71,9 @@ int set_cuda(rt_ctx* ctx, cudaError_t e, const char* what) {
 DevScene dev_scene(rt_ctx* ctx) {
     DevScene s;
     s.nodes = bp<float4>(ctx->nodes);
+    s.wnodes = bp<float4>(ctx->wnodes);
+    s.n_wnodes = ctx->n_wnodes;
+    s.wide = wide_layout(ctx) ? 1 : 0;
     s.tris = bp<float4>(ctx->tris);
     s.tris_o = bp<float4>(ctx->tris_o);
     s.planes = bp<float4>(ctx->planes);
@@ -258,10 +261,10 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->dmap_key, &ctx->dmap_pt, &ctx->scat, &ctx->scat_alpha, &ctx->path_key,
                       &ctx->path_key_alt, &ctx->path_cap_dummy, &ctx->path_off,
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
-                      &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm,
+                      &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm, &ctx->dirs,
                       &ctx->b_lbox, &ctx->b_cent, &ctx->b_info, &ctx->b_keys, &ctx->b_keys2, &ctx->b_vals,
                       &ctx->b_vals2, &ctx->b_child, &ctx->b_pint, &ctx->b_pleaf, &ctx->b_ibox, &ctx->b_flag,
-                      &ctx->b_dkeys, &ctx->b_dkeys2, &ctx->b_rank})
+                      &ctx->b_dkeys, &ctx->b_dkeys2, &ctx->b_rank, &ctx->b_wroot, &ctx->wnodes})
         buf_free(*b);
     if (ctx->host_rb) cudaFreeHost(ctx->host_rb);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
@@ -340,6 +343,13 @@ int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder) {
     if (builder != RT_BVH_KARRAS && builder != RT_BVH_PLOC)
         return set_err(ctx, RT_ERR_INVALID_ARG, "unknown BVH builder");
     ctx->bvh_builder = builder;
+    return RT_OK;
+}
+
+int rt_set_bvh_width(rt_ctx* ctx, int32_t width) {
+    CHECK_CTX(ctx);
+    if (width != 2 && width != 8) return set_err(ctx, RT_ERR_INVALID_ARG, "BVH width must be 2 or 8");
+    ctx->bvh_width = width;
     return RT_OK;
 }
 

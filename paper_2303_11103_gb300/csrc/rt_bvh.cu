@@ -106,8 +106,9 @@ __device__ __forceinline__ float bounds_extent(const unsigned* __restrict__ b) {
 
 // Build info words: [0..11] bounds (min words all ones, max words zero),
 // [12] large-triangle count, [13] tree depth, [14] clustering status,
-// [15] tree check.
-constexpr int INFO_WORDS = 16;
+// [15] tree check, [16] 8-wide node count, [17] 8-wide depth, [18] 8-wide
+// tree check.
+constexpr int INFO_WORDS = 20;
 __global__ void k_info_init(unsigned* __restrict__ info) {
     int k = threadIdx.x;
     if (k < INFO_WORDS) info[k] = (k < 12 && (k % 6) < 3) ? 0xffffffffu : 0u;
@@ -497,6 +498,239 @@ __global__ void k_single_leaf(const float* __restrict__ lbox, const uint32_t* __
     nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
 }
 
+// ------------------------------------------------------ 8-wide collapse
+// The binary hierarchy is collapsed top-down into nodes of up to 8
+// children, breadth-first, by one block (a few hundred nodes per level):
+//   - a wide node starts from the two children of its binary node and
+//     repeatedly opens its internal child of largest surface area, until it
+//     has 8 children or only triangles;
+//   - each child goes to the slot of the corner it lies towards from the
+//     children's common centre (bit a of the slot set for the positive side
+//     of axis a), greedily by the largest projection onto the corner's
+//     diagonal, so that slot order XOR a ray's octant runs near to far;
+//   - the new wide nodes of a level are numbered by a block-wide prefix sum
+//     in (parent, child) order, so the layout is deterministic and each
+//     level follows the previous one (the top levels form a prefix, staged
+//     in shared memory by the traversal kernels).
+// The loop is bounded by the binary node count and RT_STACK levels; a
+// malformed input sets info[18] instead of running on.
+constexpr int WC_THREADS = 256;
+
+__device__ __forceinline__ float half_area(const float* b) {
+    const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// child c (0, 1) of binary node r: box (lo xyz, hi xyz) and reference
+__device__ __forceinline__ void binary_child(const float4* __restrict__ nodes, int r, int c, float* box, int& ref) {
+    const float4* p = nodes + 4 * (size_t)r;
+    if (c == 0) {
+        const float4 a = p[0], b = p[1];
+        box[0] = a.x; box[1] = a.y; box[2] = a.z; box[3] = a.w; box[4] = b.x; box[5] = b.y;
+    } else {
+        const float4 b = p[1], c2 = p[2];
+        box[0] = b.z; box[1] = b.w; box[2] = c2.x; box[3] = c2.y; box[4] = c2.z; box[5] = c2.w;
+    }
+    const float4 e = p[3];
+    ref = __float_as_int(c == 0 ? e.x : e.y);
+}
+
+__global__ void __launch_bounds__(WC_THREADS) k_collapse(const float4* __restrict__ nodes, int m,
+                                                         int* __restrict__ wroot, float4* __restrict__ wnodes,
+                                                         unsigned* __restrict__ info) {
+    __shared__ int s_count, s_begin, s_end, s_stop;
+    __shared__ int s_warp[WC_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        wroot[0] = 0;
+        s_count = 1;
+        s_begin = 0;
+        s_end = 1;
+        s_stop = 0;
+    }
+    __syncthreads();
+    int depth = 0;
+    while (true) {
+        const int begin = s_begin, end = s_end;
+        if (begin >= end || s_stop) break;
+        if (++depth > RT_STACK) {
+            if (threadIdx.x == 0) atomicOr(info + 18, 1u);
+            break;
+        }
+        for (int base = begin; base < end; base += WC_THREADS) {
+            const int w = base + threadIdx.x;
+            const bool act = w < end;
+            float box[8][6];
+            int ref[8];
+            int n = 0;
+            bool bad = false;
+            if (act) {
+                const int r0 = wroot[w];
+                if (r0 < 0 || r0 >= m) {
+                    bad = true;
+                } else {
+                    binary_child(nodes, r0, 0, box[0], ref[0]);
+                    binary_child(nodes, r0, 1, box[1], ref[1]);
+                    n = 2;
+                }
+                while (!bad && n < 8) {
+                    int pick = -1;
+                    float best = -1.0f;
+                    for (int k = 0; k < n; k++)
+                        if (ref[k] >= 0) {
+                            const float a = half_area(box[k]);
+                            if (a > best) { best = a; pick = k; }
+                        }
+                    if (pick < 0) break;
+                    const int r = ref[pick];
+                    if (r >= m) { bad = true; break; }
+                    binary_child(nodes, r, 0, box[pick], ref[pick]);
+                    binary_child(nodes, r, 1, box[n], ref[n]);
+                    n++;
+                }
+            }
+            // corner slots: greedy on the projection onto the corner diagonal
+            int slot_of[8];
+            if (act && !bad) {
+                float c[3] = {0.0f, 0.0f, 0.0f}, lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+                for (int k = 0; k < n; k++)
+                    for (int a = 0; a < 3; a++) {
+                        lo[a] = fminf(lo[a], box[k][a]);
+                        hi[a] = fmaxf(hi[a], box[k][3 + a]);
+                    }
+                for (int a = 0; a < 3; a++) c[a] = 0.5f * (lo[a] + hi[a]);
+                unsigned used = 0, done = 0;
+                for (int round = 0; round < n; round++) {
+                    float bs = -3e38f;
+                    int bk = 0, bslot = 0;
+                    for (int k = 0; k < n; k++) {
+                        if (done >> k & 1u) continue;
+                        float dk[3];
+                        for (int a = 0; a < 3; a++) dk[a] = 0.5f * (box[k][a] + box[k][3 + a]) - c[a];
+                        for (int sl = 0; sl < 8; sl++) {
+                            if (used >> sl & 1u) continue;
+                            const float sc = ((sl & 1) ? dk[0] : -dk[0]) + ((sl & 2) ? dk[1] : -dk[1]) +
+                                             ((sl & 4) ? dk[2] : -dk[2]);
+                            if (sc > bs) { bs = sc; bk = k; bslot = sl; }
+                        }
+                    }
+                    slot_of[bk] = bslot;
+                    used |= 1u << bslot;
+                    done |= 1u << bk;
+                }
+            }
+            // number the internal children: block-wide exclusive scan
+            int ni = 0;
+            if (act && !bad)
+                for (int k = 0; k < n; k++) ni += ref[k] >= 0;
+            int incl = ni;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) s_warp[warp] = incl;
+            if (bad) atomicOr(info + 18, 1u);
+            __syncthreads();
+            int wbase = 0, total = 0;
+            for (int q = 0; q < WC_THREADS / 32; q++) {
+                if (q < warp) wbase += s_warp[q];
+                total += s_warp[q];
+            }
+            const int count0 = s_count;
+            const bool room = count0 + total <= m;
+            if (act && !bad && room) {
+                int next = count0 + wbase + incl - ni;
+                float pl[6][8];
+                int rf[8];
+                for (int sl = 0; sl < 8; sl++) {
+                    for (int a = 0; a < 3; a++) {
+                        pl[2 * a][sl] = 1e30f;
+                        pl[2 * a + 1][sl] = -1e30f;
+                    }
+                    rf[sl] = RT_WN_EMPTY;
+                }
+                unsigned imask = 0, tmask = 0;
+                for (int k = 0; k < n; k++) {
+                    const int sl = slot_of[k];
+                    for (int a = 0; a < 3; a++) {
+                        pl[2 * a][sl] = box[k][a];
+                        pl[2 * a + 1][sl] = box[k][3 + a];
+                    }
+                    if (ref[k] >= 0) {
+                        wroot[next] = ref[k];
+                        rf[sl] = next++;
+                        imask |= 1u << sl;
+                    } else {
+                        rf[sl] = ref[k];
+                        tmask |= 1u << sl;
+                    }
+                }
+                float4* wp = wnodes + RT_WN_F4 * (size_t)w;
+                for (int q = 0; q < 6; q++) {
+                    wp[2 * q] = make_float4(pl[q][0], pl[q][1], pl[q][2], pl[q][3]);
+                    wp[2 * q + 1] = make_float4(pl[q][4], pl[q][5], pl[q][6], pl[q][7]);
+                }
+                wp[12] = make_float4(__int_as_float(rf[0]), __int_as_float(rf[1]), __int_as_float(rf[2]),
+                                     __int_as_float(rf[3]));
+                wp[13] = make_float4(__int_as_float(rf[4]), __int_as_float(rf[5]), __int_as_float(rf[6]),
+                                     __int_as_float(rf[7]));
+                wp[14] = make_float4(__uint_as_float(imask | (tmask << 8)), 0.0f, 0.0f, 0.0f);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (room) s_count = count0 + total;
+                else s_stop = 1;
+            }
+            if (!room && threadIdx.x == 0) atomicOr(info + 18, 1u);
+            __syncthreads();
+            if (s_stop) break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_begin = end;
+            s_end = s_count;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        info[16] = (unsigned)s_count;
+        info[17] = (unsigned)depth;
+    }
+}
+
+// Tree check of the 8-wide layout: internal references after their node and
+// in range, triangle references in range, masks disjoint; with
+// k_check_degree, every node but the root and every triangle referenced once.
+__global__ void k_wcheck(const unsigned* __restrict__ info, int n_leaves, const float4* __restrict__ wnodes,
+                         int* __restrict__ indeg, unsigned* __restrict__ bad) {
+    const int W = (int)info[16];
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    const float4* np = wnodes + RT_WN_F4 * (size_t)w;
+    const unsigned masks = __float_as_uint(np[14].x);
+    const unsigned im = masks & 0xffu, tm = (masks >> 8) & 0xffu;
+    if ((im & tm) || (masks >> 16)) atomicOr(bad, 1u);
+    const int* rf = reinterpret_cast<const int*>(np + 12);
+    for (int sl = 0; sl < 8; sl++) {
+        const int r = rf[sl];
+        if (im >> sl & 1u) {
+            if (r <= w || r >= W) atomicOr(bad, 1u);
+            else atomicAdd(&indeg[r], 1);
+        } else if (tm >> sl & 1u) {
+            if (r >= 0 || ~r >= n_leaves) atomicOr(bad, 1u);
+            else atomicAdd(&indeg[W + ~r], 1);
+        }
+    }
+}
+
+__global__ void k_wcheck_degree(const unsigned* __restrict__ info, int n_leaves, const int* __restrict__ indeg,
+                                unsigned* __restrict__ bad) {
+    const int W = (int)info[16];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W + n_leaves) return;
+    if (indeg[i] != (i == 0 ? 0 : 1)) atomicOr(bad, 1u);
+}
+
 float host_unord(unsigned u) {
     unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
     float f;
@@ -579,7 +813,8 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     ctx->n_bvh = n;
     m = std::max(n - 1, 1);
     const uint32_t* leaf_tri = vals;
-    int hd[3] = {0, 0, 0};   // tree depth, clustering status, tree check
+    // tree depth, clustering status, tree check, 8-wide node count, depth, check
+    int hd[6] = {0, 0, 0, 0, 0, 0};
     if (n == 0) {
         ctx->n_nodes = 0;
         ctx->bvh_depth = 0;
@@ -685,24 +920,44 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
         ctx->n_nodes = m;
+        if (ctx->bvh_width == 8) {
+            // wide nodes: at most one per binary node
+            RT_TRY(buf_reserve(ctx->wnodes, sizeof(float4) * RT_WN_F4 * (size_t)m));
+            RT_TRY(buf_reserve(ctx->b_wroot, sizeof(int) * (size_t)m));
+            prof_begin(ctx, "k_collapse");
+            k_collapse<<<1, WC_THREADS, 0, st>>>(bp<float4>(ctx->nodes), m, bp<int>(ctx->b_wroot),
+                                                 bp<float4>(ctx->wnodes), info);
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+            RT_TRY(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)(m + T), st));
+            prof_begin(ctx, "k_wcheck");
+            k_wcheck<<<gm, B, 0, st>>>(info, T, bp<float4>(ctx->wnodes), indeg, info + 18);
+            prof_end(ctx);
+            prof_begin(ctx, "k_wcheck_degree");
+            k_wcheck_degree<<<(m + T + B - 1) / B, B, 0, st>>>(info, T, indeg, info + 18);
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+        }
     }
     // leaf records in sorted order: the hierarchy's leaves, then the large triangles
     prof_begin(ctx, "k_leaf_tris");
     k_leaf_tris<<<gT, B, 0, st>>>(T, leaf_tri, bp<float4>(ctx->tris_o), bp<float4>(ctx->tris));
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
+    ctx->n_wnodes = 0;
     if (n >= 2) {
         RT_TRY(cudaMemcpyAsync(ctx->host_rb, info + 13, sizeof(hd), cudaMemcpyDeviceToHost, st));
         RT_TRY(cudaStreamSynchronize(st));
         memcpy(hd, ctx->host_rb, sizeof(hd));
         if (hd[1] != 0)   // the clustering found no pair to merge: non-finite geometry
             return set_err(ctx, RT_ERR_INVALID_ARG, "BVH build: non-finite triangle boxes");
-        if (hd[2] != 0) {
+        if (hd[2] != 0 || (ctx->bvh_width == 8 && hd[5] != 0)) {
             ctx->n_nodes = 0;
             ctx->n_tris = 0;
             return set_err(ctx, RT_ERR_CUDA, "BVH build: hierarchy failed the tree check");
         }
         ctx->bvh_depth = hd[0] + 1;
+        if (ctx->bvh_width == 8) ctx->n_wnodes = hd[3];
     }
     if (ctx->bvh_depth + 1 >= RT_STACK)
         return set_err(ctx, RT_ERR_CAPACITY, "BVH deeper than the traversal stack");

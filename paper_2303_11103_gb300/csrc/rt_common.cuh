@@ -6,6 +6,8 @@
 //               indices (child < 0 means leaf triangle ~child). Nodes are in
 //               breadth-first order, so the top levels are a prefix that a
 //               block can stage in shared memory.
+//   8-wide node (selectable) = 15 x float4 (240 B), below; collapsed from
+//               the binary hierarchy, breadth-first as well.
 //   triangle  = 3 x float4 (48 B), leaf (Morton) order: v0 | id,
 //               e1 = v1 - v0 | material, e2 = v2 - v0 | 0.
 //   plane     = float4 (n, n . v0) per triangle, original order.
@@ -41,9 +43,24 @@ __host__ __device__ __forceinline__ f3 cross(f3 a, f3 b) {
 __device__ __forceinline__ f3 unit(f3 a) { return a * rsqrtf(dot(a, a)); }
 __device__ __forceinline__ f3 xyz(float4 v) { return {v.x, v.y, v.z}; }
 
+// 8-wide node (rt_set_bvh_width(8)), 15 x float4 = 240 B:
+//   [0..1] lo_x of children 0-3 | 4-7,  [2..3] hi_x,
+//   [4..5] lo_y, [6..7] hi_y, [8..9] lo_z, [10..11] hi_z,
+//   [12..13] child references (int32: >= 0 a wide node, < 0 leaf triangle
+//            ~ref in leaf order; empty slots have the box lo = +1e30,
+//            hi = -1e30, which no ray hits, and are in neither mask),
+//   [14].x   masks: bits 0-7 internal children, bits 8-15 triangle children.
+// Child slot s holds the child lying towards the corner whose axis a is
+// positive when bit a of s is set, so a ray visits slots in the order
+// j XOR octant (j = 0, 1, ...), near to far.
+#define RT_WN_F4 15
+#define RT_WN_EMPTY (-2147483647 - 1)
+
 // Scene as seen by kernels.
 struct DevScene {
     const float4* __restrict__ nodes;   // [n_nodes*4]
+    const float4* __restrict__ wnodes;  // [n_wnodes*RT_WN_F4] 8-wide nodes (layout when wide != 0)
+    int n_wnodes, wide;
     const float4* __restrict__ tris;    // [T*3] leaf order
     const float4* __restrict__ big;     // [n_big*3] large triangles, tested by every query
     const float4* __restrict__ tris_o;  // [T*3] original order (same record layout)
@@ -56,6 +73,10 @@ struct DevScene {
 };
 
 __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
+
+// float4 words per node of the scene's layout, and the node array
+__device__ __forceinline__ int node_f4(const DevScene& s) { return s.wide ? RT_WN_F4 : 4; }
+__device__ __forceinline__ const float4* node_base(const DevScene& s) { return s.wide ? s.wnodes : s.nodes; }
 
 // Fetch one BVH node: from shared memory if staged, else from global.
 __device__ __forceinline__ void fetch_node(const DevScene& s, const float4* sm, int n_sm, int node,
@@ -119,6 +140,98 @@ __device__ __forceinline__ float tri_hit(float4 r0, float4 r1, float4 r2, f3 o, 
     return dot(e2, q) / det;
 }
 
+// Box test with the planes already chosen by the ray's octant: near planes
+// (nx, ny, nz: lo where the direction component is positive, hi where it is
+// negative) and far planes (fx, fy, fz). The entry and exit distances are
+// the same values the slab test computes for that box (the per-axis min/max
+// there picks exactly these planes), without its six min/max. (min and max
+// are exact, so the grouping of the three-way min/max does not matter.)
+__device__ __forceinline__ bool box_oct(float nx, float ny, float nz, float fx, float fy, float fz, f3 oi, f3 inv,
+                                        float tlo, float thi) {
+    const float tn = fmax3(fmaf(nx, inv.x, -oi.x), fmaf(ny, inv.y, -oi.y), fmaxf(fmaf(nz, inv.z, -oi.z), tlo));
+    const float tf = fmin3(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y), fminf(fmaf(fz, inv.z, -oi.z), thi));
+    return tn <= tf;
+}
+
+// Bit j of the result is bit (j XOR oct) of m (8-bit masks): slot order to
+// the ray's visiting order, and back.
+__device__ __forceinline__ unsigned oct_permute(unsigned m, unsigned oct) {
+    if (oct & 1u) m = ((m & 0x55u) << 1) | ((m >> 1) & 0x55u);
+    if (oct & 2u) m = ((m & 0x33u) << 2) | ((m >> 2) & 0x33u);
+    if (oct & 4u) m = ((m & 0x0fu) << 4) | ((m >> 4) & 0x0fu);
+    return m;
+}
+
+// Ray constants of the wide traversal: reciprocal direction, origin times
+// it, octant (bit a set when the direction's component a is negative, by
+// the sign of the reciprocal) and the float4 offsets of the near plane
+// words of each axis in a node (the far words are at offset XOR 2).
+struct WideRay {
+    f3 inv, oi;
+    unsigned oct;
+    int nx, ny, nz;
+};
+__device__ __forceinline__ WideRay wide_ray(f3 o, f3 d) {
+    WideRay r;
+    r.inv = safe_inv(d);
+    r.oi = {o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z};
+    r.oct = (__float_as_uint(r.inv.x) >> 31) | ((__float_as_uint(r.inv.y) >> 31) << 1) |
+            ((__float_as_uint(r.inv.z) >> 31) << 2);
+    r.nx = (r.oct & 1u) ? 2 : 0;
+    r.ny = (r.oct & 2u) ? 6 : 4;
+    r.nz = (r.oct & 4u) ? 10 : 8;
+    return r;
+}
+
+// Hit mask (slot order) of the 8 children of node np against (tlo, thi):
+// per group of 4 children, the entry and exit distances are accumulated one
+// axis at a time (the values of box_oct, in its order of operations).
+__device__ __forceinline__ unsigned wide_children(const float4* np, const WideRay& r, float tlo, float thi) {
+    unsigned hm = 0;
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+        float4 n = np[r.nx + h], f = np[(r.nx ^ 2) + h];
+        float n0 = fmaf(n.x, r.inv.x, -r.oi.x), n1 = fmaf(n.y, r.inv.x, -r.oi.x);
+        float n2 = fmaf(n.z, r.inv.x, -r.oi.x), n3 = fmaf(n.w, r.inv.x, -r.oi.x);
+        float f0 = fmaf(f.x, r.inv.x, -r.oi.x), f1 = fmaf(f.y, r.inv.x, -r.oi.x);
+        float f2 = fmaf(f.z, r.inv.x, -r.oi.x), f3v = fmaf(f.w, r.inv.x, -r.oi.x);
+        n = np[r.ny + h];
+        f = np[(r.ny ^ 2) + h];
+        n0 = fmaxf(n0, fmaf(n.x, r.inv.y, -r.oi.y));
+        n1 = fmaxf(n1, fmaf(n.y, r.inv.y, -r.oi.y));
+        n2 = fmaxf(n2, fmaf(n.z, r.inv.y, -r.oi.y));
+        n3 = fmaxf(n3, fmaf(n.w, r.inv.y, -r.oi.y));
+        f0 = fminf(f0, fmaf(f.x, r.inv.y, -r.oi.y));
+        f1 = fminf(f1, fmaf(f.y, r.inv.y, -r.oi.y));
+        f2 = fminf(f2, fmaf(f.z, r.inv.y, -r.oi.y));
+        f3v = fminf(f3v, fmaf(f.w, r.inv.y, -r.oi.y));
+        n = np[r.nz + h];
+        f = np[(r.nz ^ 2) + h];
+        n0 = fmax3(n0, fmaf(n.x, r.inv.z, -r.oi.z), tlo);
+        n1 = fmax3(n1, fmaf(n.y, r.inv.z, -r.oi.z), tlo);
+        n2 = fmax3(n2, fmaf(n.z, r.inv.z, -r.oi.z), tlo);
+        n3 = fmax3(n3, fmaf(n.w, r.inv.z, -r.oi.z), tlo);
+        f0 = fmin3(f0, fmaf(f.x, r.inv.z, -r.oi.z), thi);
+        f1 = fmin3(f1, fmaf(f.y, r.inv.z, -r.oi.z), thi);
+        f2 = fmin3(f2, fmaf(f.z, r.inv.z, -r.oi.z), thi);
+        f3v = fmin3(f3v, fmaf(f.w, r.inv.z, -r.oi.z), thi);
+        if (n0 <= f0) hm |= 1u << (4 * h);
+        if (n1 <= f1) hm |= 2u << (4 * h);
+        if (n2 <= f2) hm |= 4u << (4 * h);
+        if (n3 <= f3v) hm |= 8u << (4 * h);
+    }
+    return hm;
+}
+
+// Node pointer: the staged copy in shared memory for the first n_sm nodes,
+// else global memory (a generic pointer, so both take the same loads).
+__device__ __forceinline__ const float4* wide_node(const DevScene& s, const float4* sm, int n_sm, int node) {
+    return node < n_sm ? sm + RT_WN_F4 * node : s.wnodes + RT_WN_F4 * (size_t)node;
+}
+__device__ __forceinline__ int wide_ref(const float4* np, int slot) {
+    return reinterpret_cast<const int*>(np + 12)[slot];
+}
+
 // Per-lane traversal counters (BVH node records and triangle records
 // fetched, queries), flushed once per warp at kernel end.
 struct TravCount {
@@ -157,8 +270,8 @@ __device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* c
 // RT_STACK, so the loop visits each node at most once and the stack cannot
 // overflow. C: count node / triangle records and queries in cnt.
 template <bool C>
-__device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                           int exclude, float& t_out, TravCount& cnt) {
+__device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
+                                             int exclude, float& t_out, TravCount& cnt) {
     t_out = __int_as_float(0x7f800000);
     if (C) cnt.queries++;
     if (s.n_tris == 0) return -1;
@@ -234,8 +347,8 @@ __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, 
 // Any occluder on the open segment (tmin, tmax) along o + t d (d unit),
 // skipping original ids ex0 / ex1.
 template <bool C>
-__device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
-                                        float tmax, int ex0, int ex1, TravCount& cnt) {
+__device__ __forceinline__ bool any_hit_b(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
+                                          float tmax, int ex0, int ex1, TravCount& cnt) {
     if (C) cnt.queries++;
     if (s.n_tris == 0) return false;
     f3 inv = safe_inv(d);
@@ -297,6 +410,154 @@ __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int
         }
     }
     return false;
+}
+
+// Closest hit on the 8-wide layout; same contract as closest_hit_b.
+//
+// Each step intersects the 8 children of one node (octant-selected planes),
+// tests the node's hit triangle children at once, then descends into its
+// nearest hit internal child; the other hit internal children stay on the
+// stack as one entry (node << 8 | their visiting-order mask), taken in
+// order when popped. The hierarchy is checked at build time (children after
+// parents, every node and triangle referenced once, depth below RT_STACK),
+// so each node is entered at most once and the stack cannot overflow.
+template <bool C>
+__device__ __forceinline__ int closest_hit_w(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
+                                             int exclude, float& t_out, TravCount& cnt) {
+    t_out = __int_as_float(0x7f800000);
+    if (C) cnt.queries++;
+    if (s.n_tris == 0) return -1;
+    const WideRay r = wide_ray(o, d);
+    float tb = __int_as_float(0x7f800000);
+    int best = -1;
+    const float tmin = s.tmin;
+    for (int k = 0; k < s.n_big; k++) {
+        const float4* tp = s.big + 3 * k;
+        float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+        if (C) cnt.tris++;
+        int id = __float_as_int(r0.w);
+        if (id != exclude) {
+            float t = tri_hit(r0, r1, r2, o, d);
+            if (t > tmin && (t < tb || (t == tb && id < best))) { tb = t; best = id; }
+        }
+    }
+    unsigned stack[RT_STACK];
+    int sp = 0;
+    int node = 0;
+    while (s.n_wnodes > 0) {
+        const float4* np = wide_node(s, sm, n_sm, node);
+        if (C) cnt.nodes++;
+        const unsigned hm = wide_children(np, r, tmin, tb);
+        const unsigned meta = __float_as_uint(np[14].x);
+        unsigned th = hm & (meta >> 8);
+        while (th) {
+            const int slot = __ffs(th) - 1;
+            th &= th - 1;
+            const float4* tp = s.tris + 3 * (size_t)(~wide_ref(np, slot));
+            float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            if (C) cnt.tris++;
+            int id = __float_as_int(r0.w);
+            if (id != exclude) {
+                float t = tri_hit(r0, r1, r2, o, d);
+                if (t > tmin && (t < tb || (t == tb && id < best))) { tb = t; best = id; }
+            }
+        }
+        unsigned v = oct_permute(hm & meta & 0xffu, r.oct);
+        if (v) {
+            const int j = __ffs(v) - 1;
+            v &= v - 1;
+            if (v) stack[sp++] = ((unsigned)node << 8) | v;
+            node = wide_ref(np, j ^ (int)r.oct);
+            continue;
+        }
+        if (sp == 0) break;
+        const unsigned e = stack[sp - 1];
+        unsigned pv = e & 0xffu;
+        const int j = __ffs(pv) - 1;
+        pv &= pv - 1;
+        if (pv) stack[sp - 1] = (e & ~0xffu) | pv;
+        else sp--;
+        node = wide_ref(wide_node(s, sm, n_sm, (int)(e >> 8)), j ^ (int)r.oct);
+    }
+    t_out = tb;
+    return best;
+}
+
+// Any occluder on the 8-wide layout; same contract as any_hit_b.
+template <bool C>
+__device__ __forceinline__ bool any_hit_w(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
+                                          float tmax, int ex0, int ex1, TravCount& cnt) {
+    if (C) cnt.queries++;
+    if (s.n_tris == 0) return false;
+    const WideRay r = wide_ray(o, d);
+    const float tmin = s.tmin;
+    for (int k = 0; k < s.n_big; k++) {
+        const float4* tp = s.big + 3 * k;
+        float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+        if (C) cnt.tris++;
+        int id = __float_as_int(r0.w);
+        if (id != ex0 && id != ex1) {
+            float t = tri_hit(r0, r1, r2, o, d);
+            if (t > tmin && t < tmax) return true;
+        }
+    }
+    unsigned stack[RT_STACK];
+    int sp = 0;
+    int node = 0;
+    while (s.n_wnodes > 0) {
+        const float4* np = wide_node(s, sm, n_sm, node);
+        if (C) cnt.nodes++;
+        const unsigned hm = wide_children(np, r, tmin, tmax);
+        const unsigned meta = __float_as_uint(np[14].x);
+        unsigned th = hm & (meta >> 8);
+        while (th) {
+            const int slot = __ffs(th) - 1;
+            th &= th - 1;
+            const float4* tp = s.tris + 3 * (size_t)(~wide_ref(np, slot));
+            float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);
+            if (C) cnt.tris++;
+            int id = __float_as_int(r0.w);
+            if (id != ex0 && id != ex1) {
+                float t = tri_hit(r0, r1, r2, o, d);
+                if (t > tmin && t < tmax) return true;
+            }
+        }
+        unsigned v = oct_permute(hm & meta & 0xffu, r.oct);
+        if (v) {
+            const int j = __ffs(v) - 1;
+            v &= v - 1;
+            if (v) stack[sp++] = ((unsigned)node << 8) | v;
+            node = wide_ref(np, j ^ (int)r.oct);
+            continue;
+        }
+        if (sp == 0) break;
+        const unsigned e = stack[sp - 1];
+        unsigned pv = e & 0xffu;
+        const int j = __ffs(pv) - 1;
+        pv &= pv - 1;
+        if (pv) stack[sp - 1] = (e & ~0xffu) | pv;
+        else sp--;
+        node = wide_ref(wide_node(s, sm, n_sm, (int)(e >> 8)), j ^ (int)r.oct);
+    }
+    return false;
+}
+
+// Closest hit / any hit on a layout: L = 8 the 8-wide nodes, L = 2 the
+// binary nodes, L = 0 the scene's own (a branch, uniform across a launch).
+// The hot kernels are compiled per layout (L = 2 or 8), so each carries one
+// traversal's registers.
+#define RT_LAYOUT_ANY 0
+template <bool C, int L = RT_LAYOUT_ANY>
+__device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d, int exclude,
+                                           float& t_out, TravCount& cnt) {
+    if (L == 8 || (L == RT_LAYOUT_ANY && s.wide)) return closest_hit_w<C>(s, sm, n_sm, o, d, exclude, t_out, cnt);
+    return closest_hit_b<C>(s, sm, n_sm, o, d, exclude, t_out, cnt);
+}
+template <bool C, int L = RT_LAYOUT_ANY>
+__device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d, float tmax,
+                                        int ex0, int ex1, TravCount& cnt) {
+    if (L == 8 || (L == RT_LAYOUT_ANY && s.wide)) return any_hit_w<C>(s, sm, n_sm, o, d, tmax, ex0, ex1, cnt);
+    return any_hit_b<C>(s, sm, n_sm, o, d, tmax, ex0, ex1, cnt);
 }
 
 // Spherical Fibonacci lattice direction of ray i of N (global frame):

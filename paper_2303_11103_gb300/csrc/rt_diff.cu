@@ -87,6 +87,7 @@ __device__ __forceinline__ void pair_devices(const int32_t* rx_off, int n_tx, in
 
 // One thread per (pair, wedge): Keller point, exterior test, two segment
 // occlusion tests; valid paths are appended (order fixed afterwards by a sort).
+template <int LY>
 __global__ void __launch_bounds__(256) k_diff_find(DiffFind p) {
     TravCount cnt;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < p.total;
@@ -120,10 +121,10 @@ __global__ void __launch_bounds__(256) k_diff_find(DiffFind p) {
         const int f0 = __float_as_int(w.t0.w), f1 = __float_as_int(w.n0.w);
         f3 d = D - tx;
         float L = sqrtf(dot(d, d));
-        if (any_hit<false>(p.s, nullptr, 0, tx, d * (1.0f / L), L - p.s.tmin, f0, f1, cnt)) continue;
+        if (any_hit<false, LY>(p.s, nullptr, 0, tx, d * (1.0f / L), L - p.s.tmin, f0, f1, cnt)) continue;
         d = rx - D;
         L = sqrtf(dot(d, d));
-        if (any_hit<false>(p.s, nullptr, 0, D, d * (1.0f / L), L - p.s.tmin, f0, f1, cnt)) continue;
+        if (any_hit<false, LY>(p.s, nullptr, 0, D, d * (1.0f / L), L - p.s.tmin, f0, f1, cnt)) continue;
         const unsigned long long k = atomicAdd(p.count, 1ull);
         if (k < p.cap) {
             p.keys[k] = ((uint64_t)pair << 32) | (uint64_t)wi;
@@ -449,7 +450,7 @@ int diffraction_impl(rt_ctx* ctx, int64_t* n_out) {
         p.pts = bp<float4>(ctx->dpath_raw_pt);
         const int64_t grid = std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->num_sms);
         prof_begin(ctx, "k_diff_find");
-        k_diff_find<<<(unsigned)grid, 256, 0, st>>>(p);
+        (wide_layout(ctx) ? k_diff_find<8> : k_diff_find<2>)<<<(unsigned)grid, 256, 0, st>>>(p);
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
         RT_TRY(cudaMemcpyAsync(ctx->host_rb, ctx->counters.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -601,7 +602,7 @@ int diffraction_map_impl(rt_ctx* ctx, const rt_grid* g, int tx_port, float* gain
         p.pts = bp<float4>(ctx->dmap_pt);
         const int64_t blocks = std::min<int64_t>((total + 255) / 256, 8 * (int64_t)ctx->num_sms);
         prof_begin(ctx, "k_diff_find");
-        k_diff_find<<<(unsigned)blocks, 256, 0, st>>>(p);
+        (wide_layout(ctx) ? k_diff_find<8> : k_diff_find<2>)<<<(unsigned)blocks, 256, 0, st>>>(p);
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
         RT_TRY(cudaMemcpyAsync(ctx->host_rb, ctx->counters.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

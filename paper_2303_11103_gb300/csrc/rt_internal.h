@@ -43,6 +43,8 @@ struct rt_ctx {
     int n_bvh = 0, n_big = 0;  // triangles in the hierarchy / tested directly (large)
     float tmin = 0.0f, extent = 1.0f;
     DevBuf nodes, tris, tris_o, planes, mat, mats;
+    DevBuf wnodes;        // 8-wide layout [n_wnodes * RT_WN_F4] (when bvh_width == 8)
+    int n_wnodes = 0;
     DevBuf planes64;   // [T*3] double2: FP64 unit normal and first vertex per triangle (original order)
 
     // devices
@@ -84,7 +86,7 @@ struct rt_ctx {
 
     // BVH build scratch (kept between builds: no allocation per rt_load_scene)
     DevBuf b_lbox, b_cent, b_info, b_keys, b_keys2, b_vals, b_vals2, b_child, b_pint, b_pleaf, b_ibox, b_flag,
-        b_dkeys, b_dkeys2, b_rank;
+        b_dkeys, b_dkeys2, b_rank, b_wroot;
 
     // scratch
     DevBuf sort_hist, scan_buf, counters, status;
@@ -107,10 +109,13 @@ struct rt_ctx {
     uint64_t* host_rb = nullptr;  // pinned host words for device -> host reads (RB_WORDS)
     DevBuf perm;          // direction-coherent ray order
     int64_t perm_n = -1;
+    DevBuf dirs;          // float4 [perm_n]: FP32 lattice direction of ray perm[k], perm[k]
+    bool dirs_ok = false;
 
     // tuning
     int n_smem_nodes = 256;   // BVH nodes staged in shared memory
     int bvh_builder = RT_BVH_PLOC;  // hierarchy over the Morton order: RT_BVH_KARRAS or RT_BVH_PLOC
+    int bvh_width = 2;              // traversal layout: 2 (binary nodes) or 8 (wide nodes)
     int dedup = RT_DEDUP_HASH;      // candidate duplicate removal: RT_DEDUP_HASH or RT_DEDUP_SORT
     int trace_block = 256;
     int warp_chunk = 0;       // rays a warp takes per refill (0 = automatic: 32)
@@ -152,6 +157,19 @@ void prof_end(rt_ctx* ctx);
 int set_err(rt_ctx* ctx, int code, const std::string& msg);
 int set_cuda(rt_ctx* ctx, cudaError_t e, const char* what);
 DevScene dev_scene(rt_ctx* ctx);
+
+// The traversal layout of the context's scene, and the nodes the traversal
+// kernels stage in shared memory: n_smem_nodes counts 64-byte binary nodes,
+// so both layouts stage the same bytes (the top of the tree).
+inline bool wide_layout(const rt_ctx* c) { return c->bvh_width == 8 && c->n_wnodes > 0; }
+inline int staged_nodes(const rt_ctx* c) {
+    const int n = wide_layout(c) ? c->n_smem_nodes * 4 / RT_WN_F4 : c->n_smem_nodes;
+    const int have = wide_layout(c) ? c->n_wnodes : c->n_nodes;
+    return n < have ? n : have;
+}
+inline size_t staged_bytes(const rt_ctx* c) {
+    return sizeof(float4) * (wide_layout(c) ? RT_WN_F4 : 4) * (size_t)staged_nodes(c);
+}
 
 // radix sort of 64-bit keys with an optional 32-bit payload, bits [0, end_bit)
 // result in keys/vals (alt buffers used as ping-pong), n may be 0

@@ -328,8 +328,8 @@ struct ValWarpPtrs {
     unsigned char* sq; // [32 (D+1)]
 };
 
-__device__ __forceinline__ ValWarpPtrs val_warp(float4* sm, int n_sm, int D) {
-    uint8_t* b = reinterpret_cast<uint8_t*>(sm + 4 * n_sm) + (threadIdx.x >> 5) * val_warp_bytes(D);
+__device__ __forceinline__ ValWarpPtrs val_warp(float4* sm, int staged_f4, int D) {
+    uint8_t* b = reinterpret_cast<uint8_t*>(sm + staged_f4) + (threadIdx.x >> 5) * val_warp_bytes(D);
     ValWarpPtrs w;
     w.qc = reinterpret_cast<uint32_t*>(b);
     w.qr = w.qc + VQ;
@@ -346,7 +346,7 @@ __device__ __forceinline__ ValWarpPtrs val_warp(float4* sm, int n_sm, int D) {
 // occluder tests of all passing items' segments, queued so that the lanes
 // run them side by side, skipping segments of items already occluded;
 // valid paths are appended. Called by all 32 lanes.
-template <bool C>
+template <bool C, int L>
 __device__ void validate_batch(const ValParams& p, const float4* sm, const ValWarpPtrs& W, int head, int n,
                                TravCount& cnt) {
     const int lane = threadIdx.x & 31, D = p.f.D;
@@ -407,10 +407,10 @@ __device__ void validate_batch(const ValParams& p, const float4* sm, const ValWa
             f3 a = mk(pl[0], pl[1], pl[2]);
             f3 b = mk(pl[3], pl[4], pl[5]);
             f3 seg = b - a;
-            float L = sqrtf(dot(seg, seg));
-            f3 d = seg * (1.0f / L);
+            float Ls = sqrtf(dot(seg, seg));
+            f3 d = seg * (1.0f / Ls);
             int ex0 = j >= 1 ? W.ids[il * D + j - 1] : -1, ex1 = j < Ki ? W.ids[il * D + j] : -1;
-            hit = any_hit<C>(p.s, sm, p.n_sm, a, d, L - p.s.tmin, ex0, ex1, cnt);
+            hit = any_hit<C, L>(p.s, sm, p.n_sm, a, d, Ls - p.s.tmin, ex0, ex1, cnt);
         }
         occluded |= __reduce_or_sync(full, hit ? (1u << il) : 0u);
     }
@@ -436,12 +436,14 @@ __device__ void validate_batch(const ValParams& p, const float4* sm, const ValWa
 // parameter in (0, 1)). Most pairs fail it; the ones that pass go to a
 // per-warp queue, and whenever 32 are queued they are validated in full
 // (validate_batch) with all lanes busy.
-template <bool C>
+template <bool C, int L>
 __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
     extern __shared__ float4 sm[];
-    for (int i = threadIdx.x; i < p.n_sm * 4; i += blockDim.x) sm[i] = p.s.nodes[i];
+    const float4* src = node_base(p.s);
+    const int staged_f4 = p.n_sm * node_f4(p.s);
+    for (int i = threadIdx.x; i < staged_f4; i += blockDim.x) sm[i] = src[i];
     const int D = p.f.D;
-    const ValWarpPtrs W = val_warp(sm, p.n_sm, D);
+    const ValWarpPtrs W = val_warp(sm, staged_f4, D);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
@@ -490,13 +492,13 @@ __global__ void __launch_bounds__(256, 4) k_validate(ValParams p) {
         count += __popc(m);
         __syncwarp();
         if (count >= 32) {
-            validate_batch<C>(p, sm, W, head, 32, cnt);
+            validate_batch<C, L>(p, sm, W, head, 32, cnt);
             head = (head + 32) % VQ;
             count -= 32;
             __syncwarp();
         }
     }
-    if (count > 0) validate_batch<C>(p, sm, W, head, count, cnt);
+    if (count > 0) validate_batch<C, L>(p, sm, W, head, count, cnt);
     if (C) flush_counts(cnt, p.count - RT_CNT_PATHS, RT_CNT_ANY);
 }
 
@@ -756,10 +758,11 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
             vp.out = bp<uint64_t>(ctx->path_key);
             vp.count = bp<unsigned long long>(ctx->counters) + 1;
             vp.cap = ctx->path_cap;
-            vp.n_sm = std::min(ctx->n_smem_nodes, ctx->n_nodes);
+            vp.n_sm = staged_nodes(ctx);
             vp.status = bp<unsigned>(ctx->status);
-            size_t smem = sizeof(float4) * 4 * (size_t)vp.n_sm + val_warp_bytes(f.D) * 8;
-            auto kern = ctx->count_work ? k_validate<true> : k_validate<false>;
+            size_t smem = staged_bytes(ctx) + val_warp_bytes(f.D) * 8;
+            auto kern = wide_layout(ctx) ? (ctx->count_work ? k_validate<true, 8> : k_validate<false, 8>)
+                                         : (ctx->count_work ? k_validate<true, 2> : k_validate<false, 2>);
             RT_TRY(ensure_smem_attr((const void*)kern, smem));
             const int per_sm = blocks_per_sm((const void*)kern, 256, smem);
             // persistent grid: the work total is read on the device

@@ -77,7 +77,7 @@ __device__ float directive_norm(int alpha, float ci) {
 // together and add their contributions with one atomic when they share the
 // transmitter). VJP: each ray's sum of dL/dg * g / S^2 is added, times
 // 2 S, to its material's gradient (per block in shared memory first).
-template <bool VJP>
+template <bool VJP, int L>
 __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
     extern __shared__ float sgrad[];
     const unsigned full = 0xffffffffu;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
             const f3 d = fib_dir(p.N, i);
             TravCount cnt;
             float th;
-            hit = closest_hit<false>(p.s, nullptr, 0, o, d, -1, th, cnt);
+            hit = closest_hit<false, L>(p.s, nullptr, 0, o, d, -1, th, cnt);
             if (hit >= 0) {
                 m = __ldg(p.s.mat + hit);
                 sc = __ldg(p.scat + m);
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                 if (cs > 0.0f) {
                     const f3 ks = v * (1.0f / dist);
                     TravCount cnt;
-                    if (!any_hit<false>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
+                    if (!any_hit<false, L>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
                         const float pat = am < 0 ? cs : powf(0.5f * (1.0f + dot(kr, ks)), (float)am) / fa;
                         w = (VJP ? 1.0f : s2) * pat * p.w0 / (dist * dist);
                         const Rot<float> Rr = rot_ypr(p.rx_ypr[3 * r], p.rx_ypr[3 * r + 1], p.rx_ypr[3 * r + 2]);
@@ -236,10 +236,12 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float*
     const long long blocks = std::min<long long>((total + 127) / 128, 16ll * ctx->num_sms);
     if (vjp) {
         prof_begin(ctx, "k_scatter_vjp");
-        k_scatter<true><<<(unsigned)blocks, 128, p.grad_smem ? sizeof(float) * ctx->n_mat : 0, ctx->stream>>>(p);
+        auto kern = wide_layout(ctx) ? k_scatter<true, 8> : k_scatter<true, 2>;
+        kern<<<(unsigned)blocks, 128, p.grad_smem ? sizeof(float) * ctx->n_mat : 0, ctx->stream>>>(p);
     } else {
         prof_begin(ctx, "k_scatter");
-        k_scatter<false><<<(unsigned)blocks, 128, 0, ctx->stream>>>(p);
+        auto kern = wide_layout(ctx) ? k_scatter<false, 8> : k_scatter<false, 2>;
+        kern<<<(unsigned)blocks, 128, 0, ctx->stream>>>(p);
     }
     prof_end(ctx);
     RT_TRY(cudaGetLastError());

@@ -32,6 +32,15 @@ __global__ void k_perm_keys(long long N, uint64_t* __restrict__ keys, uint32_t* 
     vals[i] = (uint32_t)i;
 }
 
+// Direction table in trace order: (fib_dir(N, perm[k]), perm[k]).
+__global__ void k_dir_table(long long N, const uint32_t* __restrict__ perm, float4* __restrict__ dirs) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const uint32_t i = perm[k];
+    f3 d = fib_dir(N, (long long)i);
+    dirs[k] = make_float4(d.x, d.y, d.z, __uint_as_float(i));
+}
+
 struct TraceCommon {
     DevScene s;
     const float* tx_pos;  // [n_tx*3]
@@ -41,6 +50,7 @@ struct TraceCommon {
     long long count;      // lattice indices traced per transmitter
     long long total;      // n_tx * count
     const uint32_t* perm; // [N] direction-coherent order (full range only) or null
+    const float4* dirs;   // [N] with perm: (direction of lattice ray perm[k], perm[k] as bits), or null
     unsigned long long* counter;
     int chunk;            // rays per warp refill
     int n_sm;             // staged BVH nodes
@@ -48,7 +58,8 @@ struct TraceCommon {
 };
 
 __device__ __forceinline__ void stage_nodes(const TraceCommon& c, float4* sm) {
-    for (int i = threadIdx.x; i < c.n_sm * 4; i += blockDim.x) sm[i] = c.s.nodes[i];
+    const float4* src = node_base(c.s);
+    for (int i = threadIdx.x; i < c.n_sm * node_f4(c.s); i += blockDim.x) sm[i] = src[i];
     __syncthreads();
 }
 
@@ -57,7 +68,8 @@ __device__ __forceinline__ void stage_nodes(const TraceCommon& c, float4* sm) {
 struct WarpFeed {
     long long next = 0, end = 0;
     bool exhausted = false;
-    __device__ __forceinline__ long long refill(const TraceCommon& c, bool alive) {
+    // k_out receives the ray's index in the trace order (its slot in c.dirs).
+    __device__ __forceinline__ long long refill(const TraceCommon& c, bool alive, long long& k_out) {
         const unsigned full = 0xffffffffu;
         unsigned dead = __ballot_sync(full, !alive);
         long long slot = -1;
@@ -81,11 +93,19 @@ struct WarpFeed {
             long long tx = q / c.count, k = q - tx * c.count;
             long long i = c.perm ? (long long)c.perm[k] : c.first + k;
             slot = tx * c.N + i;
+            k_out = k;
         }
         next += take;
         return slot;
     }
 };
+
+// Direction of lattice ray i (trace-order index k): from the context's table
+// when it has one (the FP64 lattice rounded to FP32 once, when the ray order
+// was built), else computed here.
+__device__ __forceinline__ f3 ray_dir(const TraceCommon& c, long long k, long long i) {
+    return c.dirs ? xyz(__ldg(c.dirs + k)) : fib_dir(c.N, i);
+}
 
 // ------------------------------------------------------------ SBR candidates
 struct SbrParams {
@@ -98,7 +118,7 @@ struct SbrParams {
     int32_t* hits;                 // [total*D] or null
 };
 
-template <bool C>
+template <bool C, int L>
 __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
     extern __shared__ float4 sm[];
     stage_nodes(p.c, sm);
@@ -110,12 +130,13 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
     uint64_t key = 0;
     TravCount cnt;
     while (true) {
-        long long s = feed.refill(p.c, alive);
+        long long kd = 0;
+        long long s = feed.refill(p.c, alive, kd);
         if (s >= 0) {
             slot = s;
             long long tx = s / p.c.N, i = s - tx * p.c.N;
             o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
-            d = fib_dir(p.c.N, i);
+            d = ray_dir(p.c, kd, i);
             last = -1;
             depth = 0;
             key = (uint64_t)tx << p.tx_shift;
@@ -130,7 +151,7 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
         uint32_t epos = 0;
         if (alive) {
             float t;
-            int id = closest_hit<C>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+            int id = closest_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
             if (id < 0) {
                 alive = false;
             } else {
@@ -190,7 +211,7 @@ struct CovParams {
     uint32_t* hits;        // [n_tx*ny*nx]
 };
 
-template <bool C>
+template <bool C, int L>
 __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     extern __shared__ float4 sm[];
     stage_nodes(p.c, sm);
@@ -203,12 +224,13 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
     TravCount cnt;
     while (true) {
-        long long s = feed.refill(p.c, alive);
+        long long kd = 0;
+        long long s = feed.refill(p.c, alive, kd);
         if (s >= 0) {
             long long t64 = s / p.c.N, i = s - t64 * p.c.N;
             tx = (int)t64;
             o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
-            d = fib_dir(p.c.N, i);
+            d = ray_dir(p.c, kd, i);
             Rot<float> Rt = rot_ypr(p.c.tx_ypr[3 * tx], p.c.tx_ypr[3 * tx + 1], p.c.tx_ypr[3 * tx + 2]);
             V3<float> f = antenna_vec<float>(p.txa.kind, zeta_t, Rt, V3<float>{d.x, d.y, d.z});
             E[0] = {f.x, 0.0f};
@@ -224,7 +246,7 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
         }
         if (alive) {
             float t;
-            int id = closest_hit<C>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+            int id = closest_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
             if (d.z != 0.0f) {
                 float sc = (p.h - o.z) / d.z;
                 if (sc > 0.0f && (id < 0 || sc < t)) {
@@ -291,6 +313,7 @@ __device__ __forceinline__ void flush_ypr(float* g, int tx, float (&acc)[3]) {
     acc[0] = acc[1] = acc[2] = 0.0f;
 }
 
+template <int L>
 __global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
     extern __shared__ float4 sm[];
     const CovParams& p = q.p;
@@ -306,7 +329,8 @@ __global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
     Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
     TravCount cnt;
     while (true) {
-        long long s = feed.refill(p.c, alive);
+        long long kd = 0;
+        long long s = feed.refill(p.c, alive, kd);
         // a lane moving to another transmitter flushes its accumulators first
         const int next_tx = s >= 0 ? (int)(s / p.c.N) : tx;
         if (__any_sync(0xffffffffu, next_tx != tx && tx >= 0)) {
@@ -320,7 +344,7 @@ __global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
             long long i = s - (long long)next_tx * p.c.N;
             tx = next_tx;
             o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
-            d = fib_dir(p.c.N, i);
+            d = ray_dir(p.c, kd, i);
             D3 yaw = dconst<3>(p.c.tx_ypr[3 * tx]), pitch = dconst<3>(p.c.tx_ypr[3 * tx + 1]),
                roll = dconst<3>(p.c.tx_ypr[3 * tx + 2]);
             yaw.d[0] = 1.0f;
@@ -341,7 +365,7 @@ __global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
         }
         if (alive) {
             float t;
-            int id = closest_hit<false>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+            int id = closest_hit<false, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
             if (d.z != 0.0f) {
                 float sc = (p.h - o.z) / d.z;
                 if (sc > 0.0f && (id < 0 || sc < t)) {
@@ -438,6 +462,19 @@ int ensure_perm(rt_ctx* ctx, int64_t N) {
     }
     if (e == cudaSuccess)
         e = radix_sort64(ctx, bp<uint64_t>(k1), bp<uint64_t>(k2), bp<uint32_t>(ctx->perm), bp<uint32_t>(v2), N, 24);
+    // the directions in that order, computed once per ray count: the tracing
+    // kernels then read them instead of evaluating the FP64 lattice per ray
+    // (GB300's FP64 units are few). Without room for the table they compute
+    // the directions themselves.
+    ctx->dirs_ok = false;
+    if (e == cudaSuccess && buf_reserve(ctx->dirs, sizeof(float4) * (size_t)N) == cudaSuccess) {
+        prof_begin(ctx, "k_dir_table");
+        k_dir_table<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(N, bp<uint32_t>(ctx->perm),
+                                                                        bp<float4>(ctx->dirs));
+        prof_end(ctx);
+        e = cudaGetLastError();
+        ctx->dirs_ok = e == cudaSuccess;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     buf_free(k1);
     buf_free(k2);
@@ -457,9 +494,10 @@ static TraceCommon make_common(rt_ctx* ctx, int64_t N, int64_t first, int64_t co
     c.count = count;
     c.total = (long long)count * ctx->n_tx;
     c.perm = (first == 0 && count == N && ctx->perm_n == N) ? bp<uint32_t>(ctx->perm) : nullptr;
+    c.dirs = (c.perm && ctx->dirs_ok) ? bp<float4>(ctx->dirs) : nullptr;
     c.counter = bp<unsigned long long>(ctx->counters);
     c.chunk = ctx->warp_chunk;
-    c.n_sm = ctx->n_smem_nodes < ctx->n_nodes ? ctx->n_smem_nodes : ctx->n_nodes;
+    c.n_sm = staged_nodes(ctx);
     c.status = bp<unsigned>(ctx->status);
     return c;
 }
@@ -479,8 +517,9 @@ int launch_sbr(rt_ctx* ctx, int64_t N, int D, uint64_t* keys, uint32_t* vals, in
     p.vals = vals;
     p.n_keys = bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS;
     p.hits = hits;
-    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    auto kern = ctx->count_work ? k_sbr<true> : k_sbr<false>;
+    size_t smem = staged_bytes(ctx);
+    auto kern = wide_layout(ctx) ? (ctx->count_work ? k_sbr<true, 8> : k_sbr<false, 8>)
+                                 : (ctx->count_work ? k_sbr<true, 2> : k_sbr<false, 2>);
     RT_TRY(ensure_smem_attr((const void*)kern, smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     RT_TRY(cudaMemsetAsync(p.n_keys, 0, sizeof(unsigned long long), ctx->stream));
@@ -522,8 +561,9 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
         RT_TRY(cudaMemsetAsync(hits, 0, sizeof(uint32_t) * cells, ctx->stream));
     }
     if (count == 0) return RT_OK;
-    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    auto kern = ctx->count_work ? k_coverage<true> : k_coverage<false>;
+    size_t smem = staged_bytes(ctx);
+    auto kern = wide_layout(ctx) ? (ctx->count_work ? k_coverage<true, 8> : k_coverage<false, 8>)
+                                 : (ctx->count_work ? k_coverage<true, 2> : k_coverage<false, 2>);
     RT_TRY(ensure_smem_attr((const void*)kern, smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)kern, smem);
@@ -562,13 +602,14 @@ int launch_coverage_vjp(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int tx_
     q.grad_gain = grad_gain;
     q.grad_ypr = grad_ypr;
     RT_TRY(cudaMemsetAsync(grad_ypr, 0, sizeof(float) * 3 * (size_t)ctx->n_tx, ctx->stream));
-    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    RT_TRY(ensure_smem_attr((const void*)k_coverage_vjp, smem));
+    size_t smem = staged_bytes(ctx);
+    auto kern = wide_layout(ctx) ? k_coverage_vjp<8> : k_coverage_vjp<2>;
+    RT_TRY(ensure_smem_attr((const void*)kern, smem));
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
-    int grid = trace_grid(ctx, (const void*)k_coverage_vjp, smem);
+    int grid = trace_grid(ctx, (const void*)kern, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     prof_begin(ctx, "k_coverage_vjp");
-    k_coverage_vjp<<<grid, ctx->trace_block, smem, ctx->stream>>>(q);
+    kern<<<grid, ctx->trace_block, smem, ctx->stream>>>(q);
     prof_end(ctx);
     RT_TRY(cudaGetLastError());
     return RT_OK;
@@ -585,6 +626,7 @@ int launch_coverage_scratch(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int
     p.c.counter = counters;
     p.c.status = status;
     p.c.perm = perm;
+    p.c.dirs = nullptr;
     p.D = D;
     p.txa = ctx->tx_ant;
     p.rxa = ctx->rx_ant;
@@ -604,12 +646,13 @@ int launch_coverage_scratch(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int
     RT_TRY(cudaMemsetAsync(gain, 0, sizeof(float) * cells, ctx->stream));
     RT_TRY(cudaMemsetAsync(hits, 0, sizeof(uint32_t) * cells, ctx->stream));
     RT_TRY(cudaMemsetAsync(counters, 0, 8 * sizeof(unsigned long long), ctx->stream));
-    size_t smem = sizeof(float4) * 4 * (size_t)p.c.n_sm;
-    RT_TRY(ensure_smem_attr((const void*)k_coverage<false>, smem));
-    int grid = trace_grid(ctx, (const void*)k_coverage<false>, smem);
+    size_t smem = staged_bytes(ctx);
+    auto kern = wide_layout(ctx) ? k_coverage<false, 8> : k_coverage<false, 2>;
+    RT_TRY(ensure_smem_attr((const void*)kern, smem));
+    int grid = trace_grid(ctx, (const void*)kern, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
     ctx->launches++;
-    k_coverage<false><<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
+    kern<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
     RT_TRY(cudaGetLastError());
     return RT_OK;
 }

@@ -68,6 +68,7 @@ def lib():
             "rt_load_scene": [vp, vp, i64, vp, vp, i32],
             "rt_set_materials": [vp, vp, i32],
             "rt_set_bvh_builder": [vp, i32],
+            "rt_set_bvh_width": [vp, i32],
             "rt_set_dedup": [vp, i32],
             "rt_set_tx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna)],
             "rt_set_rx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna), vp],
@@ -207,6 +208,10 @@ def rt_set_bvh_builder(ctx, builder):
     _check(ctx, lib().rt_set_bvh_builder(ctx, int(builder)))
 
 
+def rt_set_bvh_width(ctx, width):
+    _check(ctx, lib().rt_set_bvh_width(ctx, int(width)))
+
+
 DEDUP_HASH, DEDUP_SORT = 0, 1
 
 
@@ -335,7 +340,7 @@ def rt_freq_response_paths(ctx, offsets, n_port_pairs, a, tau, freqs, H):
                                              _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]), _ptr(H)))
 
 
-PROBE_TRAVERSAL, PROBE_FFMA = 0, 1
+PROBE_TRAVERSAL, PROBE_FFMA, PROBE_TRAVERSAL8 = 0, 1, 2
 
 
 def rt_probe_peak(ctx, kind, n_slab=8, n_tri=0) -> float:
@@ -459,6 +464,10 @@ class Tracer:
     def set_bvh_builder(self, builder):
         """Hierarchy for the next load_scene: BVH_KARRAS or BVH_PLOC."""
         rt_set_bvh_builder(self.ctx, builder)
+
+    def set_bvh_width(self, width):
+        """Traversal layout for the next load_scene: 2 (binary, default) or 8 (wide nodes)."""
+        rt_set_bvh_width(self.ctx, width)
 
     def set_dedup(self, mode):
         """Candidate duplicate removal of compute_paths: DEDUP_HASH or DEDUP_SORT."""

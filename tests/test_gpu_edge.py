@@ -98,33 +98,45 @@ def test_argument_errors(tracer):
     assert tracer.compute_paths(2, 10000) == 4
 
 
-@pytest.mark.parametrize("n_side", [6, 20])
+@pytest.mark.parametrize("n_side", [1, 2, 6, 20])
 def test_builders_give_identical_hits(tracer, n_side):
     """The closest hit of every query does not depend on the hierarchy: the
-    radix-tree builder and the clustering builder give the same per-ray hit
-    lists and the same path set (small city, and the full 4802-triangle
-    city), and both keep every triangle reachable."""
-    sc = S.city_scene(n_side=n_side, size=150.0 if n_side == 6 else 500.0, seed=5 if n_side == 6 else 1)
-    tx, rx = S.city_devices(sc, n_rx=16, half=70.0 if n_side == 6 else 240.0)
+    radix-tree builder and the clustering builder, each in the binary and
+    the 8-wide node layout, give the same per-ray hit lists, the same path
+    set and the same coverage map (one box, 2 x 2 boxes, a small city, and
+    the full 4802-triangle city), and all keep every triangle reachable."""
+    big = n_side == 20
+    sc = S.city_scene(n_side=n_side, size=500.0 if big else 150.0, seed=1 if big else 5)
+    tx, rx = S.city_devices(sc, n_rx=16, half=240.0 if big else 70.0)
     N, D = 50021, 3
-    hits, sets = [], []
+    grid = dict(x0=-75.0, y0=-75.0, cell=2.0, nx=75, ny=75, h=1.5)
+    hits, sets, maps = [], [], []
     try:
         for b in (rt.BVH_KARRAS, rt.BVH_PLOC):
-            tracer.set_bvh_builder(b)
-            setup(tracer, sc, tx, rx)
-            tracer.compute_paths(D, N, record_rays=True)
-            hits.append(tracer.ray_hits()[0].cpu().numpy().copy())
-            sets.append(gpu_paths(tracer)[0])
+            for w in (2, 8):
+                tracer.set_bvh_builder(b)
+                tracer.set_bvh_width(w)
+                setup(tracer, sc, tx, rx)
+                tracer.compute_paths(D, N, record_rays=True)
+                hits.append(tracer.ray_hits()[0].cpu().numpy().copy())
+                sets.append(gpu_paths(tracer)[0])
+                maps.append([x.cpu().numpy() for x in tracer.coverage_map(grid, D, N)])
     finally:
         tracer.set_bvh_builder(rt.BVH_PLOC)
-    assert np.array_equal(hits[0], hits[1])
-    assert sets[0] == sets[1]
-    assert (hits[0] >= 0).sum() > N   # many rays bounce
+        tracer.set_bvh_width(2)
+    for k in range(1, 4):
+        assert np.array_equal(hits[0], hits[k]), k
+        assert sets[0] == sets[k], k
+        assert np.array_equal(maps[0][1], maps[k][1]), k
+        assert np.allclose(maps[0][0], maps[k][0], rtol=1e-5, atol=0), k
+    assert (hits[0] >= 0).sum() > (N if n_side >= 6 else N // 20)   # many rays bounce
 
 
 def test_unknown_builder_rejected(tracer):
     with pytest.raises(rt.RtError):
         tracer.set_bvh_builder(7)
+    with pytest.raises(rt.RtError):
+        tracer.set_bvh_width(4)
 
 
 @pytest.mark.parametrize("n_tx", [1, 24])
