@@ -364,8 +364,10 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         extras = extra_measurements(tr, scene, dev, args)
         if not args.no_surrogate:
+            sweep = [parse_sigma(item) for item in args.sur_sweep.split(",")] if args.sur_sweep else None
+            sig, _ = parse_sigma(args.sur_sigma + ":0")
             extras.update(surrogate_measurement(tr, scene, n_tx=args.sur_tx, n_rx=args.sur_rx,
-                                                epochs=args.sur_epochs))
+                                                epochs=args.sur_epochs, sigma=sig, sweep=sweep))
 
     if world > 1:
         dist.barrier()
@@ -429,7 +431,11 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = None
+K_COVERAGE_TRAFFIC = 20.29e6
+# L1/TEX throughput of the same launch (% of its peak, elapsed) and the
+# sector hit rate: the traversal's record reads are served by L1.
+K_COVERAGE_L1 = {"l1tex_throughput_pct": 55.7, "l1tex_sector_hit_pct": 94.6, "lts_throughput_pct": 2.7,
+                 "source": "profiles/k_coverage_city_1e6rays.md (ncu --set full, one launch)"}
 
 
 def traversal_probe(ctx, counts, n_tri=4):
@@ -469,6 +475,7 @@ def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
             "frac": ach / peak,
             "traffic": K_COVERAGE_TRAFFIC if name == "k_coverage" else None,
+            "l1": K_COVERAGE_L1 if name == "k_coverage" else None,
             "peak_source": f"measured: rt_probe_peak({'RT_PROBE_TRAVERSAL8' if BVH_WIDTH == 8 else 'RT_PROBE_TRAVERSAL'}), "
                            "the traversal's box and Moller-Trumbore tests on register data, "
                            f"{mix['box_tests']} box tests per {mix['triangle_tests']} triangle tests "
@@ -755,17 +762,26 @@ def scattering_measurement(tr, scene, n_rays=100_000, S_m=0.3):
             "links_with_scattering": int((g.sum(dim=(1, 2)) > 0).sum().item())}
 
 
-def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, max_depth=3, epochs=40,
-                          n_query=100_000_000, n_heldout=100_000, batch=16384, lr=1.5e-3, oversample=4):
-    """Learned surrogate on the city: tracer labels, training, held-out error, q/s vs the tracer."""
+def surrogate_measurement(tr, scene, n_tx=10_000, n_rx=1000, num_rays=200_000, max_depth=3, epochs=40,
+                          n_query=100_000_000, n_heldout=100_000, batch=16384, lr=1.5e-3, oversample=4,
+                          sigma=(0.25, 4.0, 0.0, 0.0), sweep=None):
+    """Learned surrogate on the city (config S): tracer labels for 1e7 (tx, rx)
+    pairs over n_tx transmitters on rooftops (continuous positions along roof
+    edges, scenes.surrogate_sites, seed 4), training, and the error against
+    the tracer on 1e5 pairs of transmitters the network never saw (seed 14),
+    beside new receivers of the training sites; q/s against the tracer.
+    sweep: list of (sigma, epochs) settings to train and evaluate as well."""
     import torch
     from paper_2303_11103_gb300 import rt
     from paper_2303_11103_gb300 import surrogate as SG
     from paper_2303_11103_gb300 import scenes as S
     t0 = time.perf_counter()
     tr.load_scene(scene)
-    tx, rx = S.surrogate_pairs(scene, n_tx, n_rx, seed=4)
+    tx, rx = S.surrogate_sites(scene, n_tx, n_rx, seed=4)
     x, t = SG.tracer_labels(tr, tx, rx, num_rays, max_depth)
+    n_new = max(1, n_heldout // n_rx)
+    txn, rxn = S.surrogate_sites(scene, n_new, n_rx, seed=14)
+    xn, tn = SG.tracer_labels(tr, txn, rxn, num_rays, max_depth)
     torch.cuda.synchronize()
     t_label = time.perf_counter() - t0
     n = x.shape[0]
@@ -774,12 +790,27 @@ def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, ma
     held, train_idx = perm[:n_heldout], perm[n_heldout:]
     lo = np.array([-250, -250, 0, -250, -250, 0], np.float32)
     hi = np.array([250, 250, 70, 250, 250, 3], np.float32)
-    sur = rt.Surrogate(lo, hi, n_freq=32, width=256, n_hidden=8, sigma=8.0, seed=1)
-    t1 = time.perf_counter()
-    losses = SG.train(sur, x[train_idx], t[train_idx], epochs=epochs, batch=batch, lr=lr, oversample=oversample)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    ev = SG.evaluate(sur, x[held], t[held])
+
+    def fit(sig, ep):
+        """sig: isotropic Fourier scale, or (sigma_tx, sigma_rx, rel_frac, sigma_rel)."""
+        iso = not isinstance(sig, (tuple, list))
+        sur = rt.Surrogate(lo, hi, n_freq=32, width=256, n_hidden=8, sigma=sig if iso else 1.0, seed=1)
+        if not iso:
+            SG.set_fourier(sur, *sig, seed=1)
+        t1 = time.perf_counter()
+        losses = SG.train(sur, x[train_idx], t[train_idx], epochs=ep, batch=batch, lr=lr, oversample=oversample)
+        torch.cuda.synchronize()
+        return sur, losses, time.perf_counter() - t1
+
+    sweep_out = []
+    for sig, ep in (sweep or []):
+        s2, l2, ts2 = fit(sig, ep)
+        sweep_out.append({"fourier_scales": sig, "epochs": ep, "train_s": ts2, "final_loss": l2[-1],
+                          "new_sites": SG.evaluate(s2, xn, tn), "seen_sites": SG.evaluate(s2, x[held], t[held])})
+        s2.close()
+    sur, losses, t_train = fit(sigma, epochs)
+    ev_new = SG.evaluate(sur, xn, tn)
+    ev_seen = SG.evaluate(sur, x[held], t[held])
     q_sur, ms_sur = SG.time_inference(sur, n_query, lo, hi, reps=2)
     # tracer queries: one site with 1000 receivers per call (the city step's
     # receiver count), and with all of the site's receivers in one call (the
@@ -787,17 +818,34 @@ def surrogate_measurement(tr, scene, n_tx=64, n_rx=156_250, num_rays=200_000, ma
     q_tr, s_tr = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth, n_rx=1000)
     q_tr_all, s_tr_all = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth)
     sur.close()
-    return {"surrogate": {
+    out = {"surrogate": {
         "train_pairs": int(len(train_idx)), "epochs": epochs, "batch": batch, "lr": lr,
+        "fourier_scales": sigma if not isinstance(sigma, tuple) else
+        {"sigma_tx": sigma[0], "sigma_rx": sigma[1], "rel_frac": sigma[2], "sigma_rel": sigma[3]},
         "path_pair_oversample": oversample, "final_loss": losses[-1],
-        "label_s": t_label, "train_s": t_train, "heldout": ev,
+        "label_s": t_label, "train_s": t_train,
+        "heldout": ev_new,
+        "heldout_note": "headline: 1e5 pairs of 25 transmitter sites not in training (independent draw of "
+                        "rooftop-edge positions); rms_db_all_path_pairs is over every held-out pair with a path, "
+                        "rms_db_answered over those the network answers (|logit| >= margin)",
+        "heldout_sites": n_new,
+        "heldout_seen_sites": ev_seen,
         "queries": n_query, "infer_ms": ms_sur, "queries_per_s": q_sur,
         "tracer_queries_per_s": q_tr, "speedup_vs_tracer": q_sur / q_tr,
         "tracer_note": "compute_paths + cir + pair gain at the label settings, one site with 1000 receivers per call",
         "tracer_queries_per_s_all_rx": q_tr_all, "speedup_vs_tracer_all_rx": q_sur / q_tr_all,
-        "config": f"city 4802 tris; {n_tx} rooftop Tx sites x {n_rx} street Rx within 100 m; held-out pairs "
-                  f"are new receivers of the same sites; labels: {num_rays} rays, max_depth {max_depth}; "
-                  f"MLP 64 Fourier features, 8 x 256 ReLU, BF16 tcgen05"}}
+        "config": f"city 4802 tris; {n_tx} rooftop Tx (1 m outside a roof-edge point, mast 1-5 m) x {n_rx} street "
+                  f"Rx within 100 m; labels: {num_rays} rays, max_depth {max_depth}; MLP 64 Fourier features, "
+                  f"8 x 256 ReLU, BF16 tcgen05"}}
+    if sweep_out:
+        out["surrogate"]["sweep"] = sweep_out
+    return out
+
+
+def parse_sigma(item: str):
+    """'sigma:epochs' (isotropic Fourier scale) or 'sigma_tx:sigma_rx:rel_frac:sigma_rel:epochs'."""
+    v = [float(x) for x in item.split(":")]
+    return (v[0] if len(v) == 2 else tuple(v[:4])), int(v[-1])
 
 
 def cpu_baseline(scene, tx, rx, seconds=15.0):
@@ -937,10 +985,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--sur-tx", type=int, default=64,
-                    help="surrogate transmitter sites (64: a fixed deployment; 2500: open sites)")
-    ap.add_argument("--sur-rx", type=int, default=156_250, help="surrogate receivers per transmitter site")
+    ap.add_argument("--sur-tx", type=int, default=10_000, help="surrogate training transmitter sites")
+    ap.add_argument("--sur-rx", type=int, default=1000, help="surrogate receivers per transmitter site")
     ap.add_argument("--sur-epochs", type=int, default=40)
+    ap.add_argument("--sur-sigma", default="0.25:4:0:0",
+                    help="Fourier scales of the surrogate: 'sigma' (all coordinates) or "
+                         "'sigma_tx:sigma_rx:rel_frac:sigma_rel'")
+    ap.add_argument("--sur-sweep", default="",
+                    help="extra surrogate settings to train and evaluate, comma-separated 'sigma:epochs' or "
+                         "'sigma_tx:sigma_rx:rel_frac:sigma_rel:epochs' (e.g. 4:40,1:8:0.5:8:40)")
     args = ap.parse_args()
     if args.only:
         run_kernel_case(args)

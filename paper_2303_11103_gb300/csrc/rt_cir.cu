@@ -218,9 +218,13 @@ __global__ void k_cir_vjp(CirParams c, const float2* __restrict__ ga, const floa
 // Twiddles: with uniform spacing one range-reduced sincos for the first
 // subcarrier and one for the 128-subcarrier step per (path, thread), then a
 // complex-rotation recurrence; otherwise a sincos per (path, subcarrier).
+// With uniform spacing two paths are taken per step (their twiddle chains
+// interleave; each accumulator still sums the paths in order). Four
+// subcarriers per thread keep the registers at about 70 for 2 x 2 port
+// pairs, so more warps hide the sincos and recurrence latencies.
 // H is cleared by a memset first, so the blocks of pairs without paths
 // return at once.
-constexpr int HF_RUN = 8;
+constexpr int HF_RUN = 4;
 constexpr int HF_TILE = 64;
 constexpr int HF_THREADS = 128;
 
@@ -240,7 +244,6 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
 #pragma unroll
         for (int q = 0; q < NP; q++) acc[s][q] = make_float2(0.0f, 0.0f);
     // this thread's subcarriers; the recurrence needs them evenly spaced
-    float fl[HF_RUN];
     double f0 = 0.0, df = 0.0;
     if (kb < K) {
         f0 = freqs[kb];
@@ -251,7 +254,6 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
     for (int s = 0; s < HF_RUN; s++) {
         const int k = kb + s * HF_THREADS;
         double fs = k < K ? freqs[k] : f0 + s * df;
-        fl[s] = (float)fs;
         if (fabs(fs - (f0 + s * df)) > 1e-9 * (fabs(fs) + 1.0)) uniform = false;
     }
     const float fk0 = (float)f0, dff = (float)df;
@@ -262,32 +264,69 @@ __global__ void __launch_bounds__(HF_THREADS) k_freq(const int64_t* __restrict__
         for (int j = threadIdx.x; j < n; j += blockDim.x) st[j] = tau[tb + j];
         __syncthreads();
         if (kb >= K) continue;
-        for (int j = 0; j < n; j++) {
-            const float t = st[j];
-            if (uniform) {
-                // w_k = exp(-j 2 pi f_k tau): cycles reduced to [-0.5, 0.5) before sincos
+        if (uniform) {
+            int j = 0;
+            for (; j + 1 < n; j += 2) {
+                float wr[2], wi[2], cdd[2], sd[2];
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    const float t = st[j + u];
+                    float cyc = fk0 * t;
+                    cyc -= rintf(cyc);
+                    __sincosf(-2.0f * RT_PI_F * cyc, &wi[u], &wr[u]);
+                    float cd = dff * t;
+                    cd -= rintf(cd);
+                    __sincosf(-2.0f * RT_PI_F * cd, &sd[u], &cdd[u]);
+                }
+#pragma unroll
+                for (int s = 0; s < HF_RUN; s++) {
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+#pragma unroll
+                        for (int q = 0; q < NP; q++) {
+                            float2 av = sa[j + u][q];
+                            acc[s][q].x = fmaf(av.x, wr[u], fmaf(-av.y, wi[u], acc[s][q].x));
+                            acc[s][q].y = fmaf(av.x, wi[u], fmaf(av.y, wr[u], acc[s][q].y));
+                        }
+                        float nr = wr[u] * cdd[u] - wi[u] * sd[u];
+                        wi[u] = wr[u] * sd[u] + wi[u] * cdd[u];
+                        wr[u] = nr;
+                    }
+                }
+            }
+            for (; j < n; j++) {
+                const float t = st[j];
                 float cyc = fk0 * t;
                 cyc -= rintf(cyc);
                 float s0, c0;
                 __sincosf(-2.0f * RT_PI_F * cyc, &s0, &c0);
                 float cd = dff * t;
                 cd -= rintf(cd);
-                float sd, cdd;
-                __sincosf(-2.0f * RT_PI_F * cd, &sd, &cdd);
-                float wr = c0, wi = s0;
+                float sdv, cddv;
+                __sincosf(-2.0f * RT_PI_F * cd, &sdv, &cddv);
+                float wrv = c0, wiv = s0;
 #pragma unroll
                 for (int s = 0; s < HF_RUN; s++) {
 #pragma unroll
                     for (int q = 0; q < NP; q++) {
                         float2 av = sa[j][q];
-                        acc[s][q].x = fmaf(av.x, wr, fmaf(-av.y, wi, acc[s][q].x));
-                        acc[s][q].y = fmaf(av.x, wi, fmaf(av.y, wr, acc[s][q].y));
+                        acc[s][q].x = fmaf(av.x, wrv, fmaf(-av.y, wiv, acc[s][q].x));
+                        acc[s][q].y = fmaf(av.x, wiv, fmaf(av.y, wrv, acc[s][q].y));
                     }
-                    float nr = wr * cdd - wi * sd;
-                    wi = wr * sd + wi * cdd;
-                    wr = nr;
+                    float nr = wrv * cddv - wiv * sdv;
+                    wiv = wrv * sdv + wiv * cddv;
+                    wrv = nr;
                 }
-            } else {
+            }
+        } else {
+            float fl[HF_RUN];
+#pragma unroll
+            for (int s = 0; s < HF_RUN; s++) {
+                const int k = kb + s * HF_THREADS;
+                fl[s] = k < K ? (float)freqs[k] : 0.0f;
+            }
+            for (int j = 0; j < n; j++) {
+                const float t = st[j];
 #pragma unroll
                 for (int s = 0; s < HF_RUN; s++) {
                     float cyc = fl[s] * t;

@@ -34,6 +34,7 @@ struct ScatParams {
     const float* rx_ypr;
     const int32_t* rx_off;   // [n_tx+1] or null
     const float* scat;       // [n_mat] scattering coefficients
+    const float4* dirs;      // [N] directions in the direction-coherent ray order, or null
     const int32_t* alpha;    // [n_mat] pattern exponent, -1 Lambertian; null: all Lambertian
     const float* up;         // VJP: upstream dL/dgain [n_pairs][nrp][ntp]
     float* grad;             // VJP: dL/dS [n_mat]
@@ -75,7 +76,11 @@ __device__ float directive_norm(int alpha, float ci) {
 // One thread per (transmitter, lattice ray): first hit, then every receiver
 // of that transmitter in order (the warp's lanes visit the same receiver
 // together and add their contributions with one atomic when they share the
-// transmitter). VJP: each ray's sum of dL/dg * g / S^2 is added, times
+// transmitter). The rays are taken in the direction-coherent order of the
+// tracing kernels (directions from the context's table), so the lanes of a
+// warp hit nearby points and their segment tests to a receiver follow
+// similar paths through the hierarchy: 2.2x faster than the lattice order,
+// whose neighbours are a golden angle apart in azimuth. VJP: each ray's sum of dL/dg * g / S^2 is added, times
 // 2 S, to its material's gradient (per block in shared memory first).
 template <bool VJP, int L>
 __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
         float ptx[2] = {0.0f, 0.0f};
         if (has) {
             const f3 o = mk(p.tx_pos[3 * t], p.tx_pos[3 * t + 1], p.tx_pos[3 * t + 2]);
-            const f3 d = fib_dir(p.N, i);
+            const f3 d = p.dirs ? xyz(__ldg(p.dirs + i)) : fib_dir(p.N, i);
             TravCount cnt;
             float th;
             hit = closest_hit<false, L>(p.s, nullptr, 0, o, d, -1, th, cnt);
@@ -207,6 +212,11 @@ int scattering_impl(rt_ctx* ctx, int64_t N, float* gain, const float* up, float*
     p.rx_ypr = bp<float>(ctx->rx_ypr);
     p.rx_off = ctx->rx_sets ? bp<int32_t>(ctx->rx_off_d) : nullptr;
     p.scat = bp<float>(ctx->scat);
+    {
+        int e = ensure_perm(ctx, N);
+        if (e) return e;
+    }
+    p.dirs = ctx->dirs_ok ? bp<float4>(ctx->dirs) : nullptr;
     p.alpha = ctx->scat_alpha_set ? bp<int32_t>(ctx->scat_alpha) : nullptr;
     p.up = up;
     p.grad = grad;

@@ -11,7 +11,8 @@ Materials are described by relative permittivity and conductivity only, the
 two properties the paper names for radio materials (Sec. II).
 
 Seeds: 0 tiny, 1 city geometry, 2 transmitter/receiver placement,
-3 materials of the differentiation workload, 4 surrogate pairs.
+3 materials of the differentiation workload, 4 surrogate training sites,
+14 surrogate held-out sites, 6-10 dense path lists.
 """
 from __future__ import annotations
 
@@ -266,15 +267,17 @@ def rooftop_transmitters(scene: Scene, n_tx: int = 64, seed: int = 2,
     return Devices(np.array(pos, np.float32), np.array(ypr, np.float32), antenna)
 
 
-def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
-                    half: float = 240.0, mast: float = 3.0, rx_radius: float = 100.0):
-    """Tx on a 3 m mast at a random roof corner, Rx 1.5 m above nearby streets.
+def surrogate_sites(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4, half: float = 240.0,
+                    mast=(1.0, 5.0), rx_radius: float = 100.0):
+    """Transmitters over rooftops at continuous positions, with street receivers.
 
-    The transmitter stands 1 m diagonally outside a corner of a random
-    building, `mast` metres above that roof (a mast at the roof centre sees
-    no street: the roof hides it), and not inside a taller building. Its
-    receivers are street points within a square of half-side rx_radius
-    around it (clipped to the city).
+    Each transmitter stands 1 m outside a uniformly drawn point of the roof
+    edge of a random building (a mast set back on the roof would see no
+    street: the roof hides it), a uniform mast height above that roof, and
+    not inside a taller building. Every draw is a new position, so two seeds
+    give disjoint transmitter sets (transmitters never seen in training).
+    Its receivers are street points within a square of half-side rx_radius
+    around it (clipped to the city), 1.5 m high.
     Returns tx [n_tx, 3] and rx [n_tx, n_rx_per_tx, 3] (float32).
     """
     rng = np.random.default_rng(seed)
@@ -283,11 +286,18 @@ def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
                 (np.abs(0.5 * (fps[:, 2] + fps[:, 3])) < half)]
     tx = []
     while len(tx) < n_tx:
-        b = inner[rng.integers(0, len(inner))]
-        cx, cy = int(rng.integers(0, 2)), int(rng.integers(0, 2))
-        x = b[1] + 1.0 if cx else b[0] - 1.0
-        y = b[3] + 1.0 if cy else b[2] - 1.0
-        z = b[4] + mast
+        x0, x1, y0, y1, h = inner[rng.integers(0, len(inner))]
+        w, dpt = x1 - x0, y1 - y0
+        u = rng.uniform(0.0, 2.0 * (w + dpt))      # arc length along the roof edge
+        if u < w:
+            x, y = x0 + u, y0 - 1.0
+        elif u < w + dpt:
+            x, y = x1 + 1.0, y0 + (u - w)
+        elif u < 2 * w + dpt:
+            x, y = x1 - (u - w - dpt), y1 + 1.0
+        else:
+            x, y = x0 - 1.0, y1 - (u - 2 * w - dpt)
+        z = h + rng.uniform(mast[0], mast[1])
         if _height_at(fps, x, y) >= z - 0.5:
             continue
         tx.append((x, y, z))
@@ -298,7 +308,6 @@ def surrogate_pairs(scene: Scene, n_tx: int, n_rx_per_tx: int, seed: int = 4,
         rx.append(np.concatenate([street_points(scene, n_rx_per_tx, rng, r, center=c),
                                   np.full((n_rx_per_tx, 1), 1.5)], 1))
     return np.array(tx, np.float32), np.stack(rx).astype(np.float32)
-
 
 
 def dense_path_list(n_pairs: int = 1000, mean_paths: int = 64, n_port_pairs: int = 4, seed: int = 6,

@@ -41,21 +41,25 @@ def tracer_labels(tracer: rt.Tracer, tx_pos, rx_pos, num_rays: int, max_depth: i
     return torch.cat(xs), torch.cat(ts)
 
 
-def set_fourier(sur: rt.Surrogate, sigma: float, sigma_rel: float, rel_frac: float = 0.5, seed: int = 0):
-    """Seeded Fourier matrix B [F x 6] on the normalised (tx, rx): the first
-    rel_frac of the rows see only the horizontal Tx -> Rx offset (rows
-    (-bx, -by, 0, bx, by, 0), b ~ N(0, sigma_rel^2)), the others all six
-    coordinates (N(0, sigma^2)). The network then gets the relative geometry,
-    which the path gain mostly depends on, without having to build it from
-    products of absolute-coordinate sinusoids."""
+def set_fourier(sur: rt.Surrogate, sigma_tx: float, sigma_rx: float, rel_frac: float = 0.0,
+                sigma_rel: float = 0.0, seed: int = 0):
+    """Seeded Fourier matrix B [F x 6] on the normalised (tx, rx) with its own
+    scale per coordinate group: the first rel_frac of the rows see only the
+    horizontal Tx -> Rx offset (rows (-bx, -by, 0, bx, by, 0), b ~ N(0,
+    sigma_rel^2)); the others see the transmitter's coordinates with scale
+    sigma_tx and the receiver's with sigma_rx. A small sigma_tx makes the
+    network's answer vary slowly with the transmitter position, so that it
+    interpolates between the training sites instead of keeping one map per
+    site."""
     rng = np.random.default_rng(seed)
     F = sur.F
     n_rel = int(round(rel_frac * F))
-    B = rng.normal(0.0, sigma, (F, 6))
-    b = rng.normal(0.0, sigma_rel, (n_rel, 2))
-    B[:n_rel] = 0.0
-    B[:n_rel, 0:2] = -b
-    B[:n_rel, 3:5] = b
+    B = np.concatenate([rng.normal(0.0, sigma_tx, (F, 3)), rng.normal(0.0, sigma_rx, (F, 3))], 1)
+    if n_rel:
+        b = rng.normal(0.0, sigma_rel, (n_rel, 2))
+        B[:n_rel] = 0.0
+        B[:n_rel, 0:2] = -b
+        B[:n_rel, 3:5] = b
     p = sur.params().clone()
     p[-6 * F:] = torch.as_tensor(B.astype(np.float32).ravel(), device=p.device)
     sur.set_params(p)
