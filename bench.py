@@ -415,13 +415,13 @@ def run_ours(args):
     print(json.dumps(line))
 
 
-# Algorithmic FP32/ALU operations of the traversal. The default binary
-# layout: two slab tests per node record (2 x (6 FMA + 6 per-axis min/max +
-# 4 combining min/max + 1 compare) = 34); the 8-wide layout: 8
-# octant-selected box tests per node record (8 x (6 FMA + 4 min/max + 1
-# compare) = 88); one Moller-Trumbore test per triangle record (35).
+# Algorithmic FP32/ALU operations of the traversal: one octant-selected box
+# test per child (6 FMA + 4 min/max + 1 compare = 11), i.e. 22 per node
+# record of the default binary layout (its ray-octant copies), 88 per node
+# record of the 8-wide layout; one Moller-Trumbore test per triangle record
+# (35).
 BVH_WIDTH = 2
-OPS_PER_NODE = {8: 88, 2: 34}[BVH_WIDTH]
+OPS_PER_NODE = {8: 88, 2: 22}[BVH_WIDTH]
 BYTES_PER_NODE = {8: 240, 2: 64}[BVH_WIDTH]
 OPS_PER_TRI = 35
 # Lane-operation count of the SMs: 152 SMs x 128 lanes x 2070 MHz (one op per
@@ -431,11 +431,10 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = 20.29e6
+K_COVERAGE_TRAFFIC = None
 # L1/TEX throughput of the same launch (% of its peak, elapsed) and the
 # sector hit rate: the traversal's record reads are served by L1.
-K_COVERAGE_L1 = {"l1tex_throughput_pct": 55.7, "l1tex_sector_hit_pct": 94.6, "lts_throughput_pct": 2.7,
-                 "source": "profiles/k_coverage_city_1e6rays.md (ncu --set full, one launch)"}
+K_COVERAGE_L1 = None
 
 
 def traversal_probe(ctx, counts, n_tri=4):
@@ -447,8 +446,7 @@ def traversal_probe(ctx, counts, n_tri=4):
     per_node = 8 if BVH_WIDTH == 8 else 2
     boxes_per_tri = per_node * counts["nodes"] / max(counts["tris"], 1)
     n_box = max(8, int(round(boxes_per_tri * n_tri / 8.0)) * 8)
-    kind = rt.PROBE_TRAVERSAL8 if BVH_WIDTH == 8 else rt.PROBE_TRAVERSAL
-    gops = rt.rt_probe_peak(ctx, kind, n_box, n_tri) / 1e9
+    gops = rt.rt_probe_peak(ctx, rt.PROBE_TRAVERSAL, n_box, n_tri) / 1e9
     return gops, {"box_tests": n_box, "triangle_tests": n_tri}
 
 
@@ -476,7 +474,7 @@ def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
             "frac": ach / peak,
             "traffic": K_COVERAGE_TRAFFIC if name == "k_coverage" else None,
             "l1": K_COVERAGE_L1 if name == "k_coverage" else None,
-            "peak_source": f"measured: rt_probe_peak({'RT_PROBE_TRAVERSAL8' if BVH_WIDTH == 8 else 'RT_PROBE_TRAVERSAL'}), "
+            "peak_source": "measured: rt_probe_peak(RT_PROBE_TRAVERSAL), "
                            "the traversal's box and Moller-Trumbore tests on register data, "
                            f"{mix['box_tests']} box tests per {mix['triangle_tests']} triangle tests "
                            "(the kernel's counted mix), best of 5",
@@ -762,7 +760,7 @@ def scattering_measurement(tr, scene, n_rays=100_000, S_m=0.3):
             "links_with_scattering": int((g.sum(dim=(1, 2)) > 0).sum().item())}
 
 
-def surrogate_measurement(tr, scene, n_tx=10_000, n_rx=1000, num_rays=200_000, max_depth=3, epochs=40,
+def surrogate_measurement(tr, scene, n_tx=40_000, n_rx=250, num_rays=200_000, max_depth=3, epochs=40,
                           n_query=100_000_000, n_heldout=100_000, batch=16384, lr=1.5e-3, oversample=4,
                           sigma=(0.25, 4.0, 0.0, 0.0), sweep=None):
     """Learned surrogate on the city (config S): tracer labels for 1e7 (tx, rx)
@@ -815,7 +813,9 @@ def surrogate_measurement(tr, scene, n_tx=10_000, n_rx=1000, num_rays=200_000, m
     # tracer queries: one site with 1000 receivers per call (the city step's
     # receiver count), and with all of the site's receivers in one call (the
     # ray trace shared by the most receivers: the tracer's best case)
-    q_tr, s_tr = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth, n_rx=1000)
+    # one site with 1000 receivers of its own (the training sites have n_rx each)
+    txq, rxq = S.surrogate_sites(scene, 1, 1000, seed=24)
+    q_tr, s_tr = SG.time_tracer_queries(tr, txq, rxq, num_rays, max_depth, n_rx=1000)
     q_tr_all, s_tr_all = SG.time_tracer_queries(tr, tx, rx, num_rays, max_depth)
     sur.close()
     out = {"surrogate": {
@@ -833,7 +833,8 @@ def surrogate_measurement(tr, scene, n_tx=10_000, n_rx=1000, num_rays=200_000, m
         "queries": n_query, "infer_ms": ms_sur, "queries_per_s": q_sur,
         "tracer_queries_per_s": q_tr, "speedup_vs_tracer": q_sur / q_tr,
         "tracer_note": "compute_paths + cir + pair gain at the label settings, one site with 1000 receivers per call",
-        "tracer_queries_per_s_all_rx": q_tr_all, "speedup_vs_tracer_all_rx": q_sur / q_tr_all,
+        "tracer_queries_per_s_site_rx": q_tr_all, "speedup_vs_tracer_site_rx": q_sur / q_tr_all,
+        "tracer_site_rx_note": f"the same with one training site's {n_rx} receivers per call",
         "config": f"city 4802 tris; {n_tx} rooftop Tx (1 m outside a roof-edge point, mast 1-5 m) x {n_rx} street "
                   f"Rx within 100 m; labels: {num_rays} rays, max_depth {max_depth}; MLP 64 Fourier features, "
                   f"8 x 256 ReLU, BF16 tcgen05"}}
@@ -985,8 +986,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--sur-tx", type=int, default=10_000, help="surrogate training transmitter sites")
-    ap.add_argument("--sur-rx", type=int, default=1000, help="surrogate receivers per transmitter site")
+    ap.add_argument("--sur-tx", type=int, default=40_000, help="surrogate training transmitter sites")
+    ap.add_argument("--sur-rx", type=int, default=250, help="surrogate receivers per transmitter site")
     ap.add_argument("--sur-epochs", type=int, default=40)
     ap.add_argument("--sur-sigma", default="0.25:4:0:0",
                     help="Fourier scales of the surrogate: 'sigma' (all coordinates) or "

@@ -419,13 +419,11 @@ int rt_join(rt_ctx* ctx);
  * micro-kernel on the context's device and stream, six launches of about
  * 2 ms (the first is a warm-up), and writes the best rate to *ops_per_s
  * (HOST):
- *   RT_PROBE_TRAVERSAL: the traversal's own slab test and Moller-Trumbore
- *     triangle test, n_slab slab tests (a positive multiple of 8) per n_tri
- *     triangle tests, as algorithmic operations per second (17 per slab
- *     test, 35 per triangle test, the counts the bench's roofline uses);
- *   RT_PROBE_TRAVERSAL8: the 8-wide layout's octant-selected box test (11
- *     operations: 6 FMA, 4 min/max, 1 compare) n_slab times (a positive
- *     multiple of 8) per n_tri triangle tests;
+ *   RT_PROBE_TRAVERSAL: the traversal's own box test (planes chosen by the
+ *     ray's octant: 11 operations, 6 FMA, 4 min/max, 1 compare) and
+ *     Moller-Trumbore triangle test (35 operations), n_slab box tests (a
+ *     positive multiple of 8) per n_tri triangle tests, as algorithmic
+ *     operations per second (the counts the bench's roofline uses);
  *   RT_PROBE_FFMA: FP32 fused multiply-adds, as flops per second (2 per
  *     FMA); n_slab and n_tri are ignored.
  * Synchronises the stream. Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_READY
@@ -433,7 +431,6 @@ int rt_join(rt_ctx* ctx);
  */
 #define RT_PROBE_TRAVERSAL 0
 #define RT_PROBE_FFMA 1
-#define RT_PROBE_TRAVERSAL8 2
 int rt_probe_peak(rt_ctx* ctx, int32_t kind, int32_t n_slab, int32_t n_tri, double* ops_per_s);
 
 /*
@@ -527,7 +524,9 @@ int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_ra
                 uint32_t* hits, const char* cache_path);
 /* The launch configuration in use: block threads (128|256), rays per warp
  * refill (0 = automatic, else >= 32), BVH nodes staged in shared memory
- * (<= 3200) (HOST out / in). */
+ * (<= 3200, counted in 64-byte binary nodes; used by the 8-wide layout
+ * only, the binary layout reads its octant copies through L1) (HOST out /
+ * in). */
 int rt_get_tuning(const rt_ctx* ctx, int32_t* block, int32_t* chunk, int32_t* smem_nodes);
 int rt_set_tuning(rt_ctx* ctx, int32_t block, int32_t chunk, int32_t smem_nodes);
 

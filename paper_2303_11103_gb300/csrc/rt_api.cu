@@ -826,7 +826,9 @@ int rt_autotune(rt_ctx* ctx, const rt_grid* g, int32_t max_depth, int64_t num_ra
     }
     const int blocks[] = {128, 256};
     const int chunks[] = {0, 64, 256};   // 0 = automatic (32 rays per refill)
-    const int smems[] = {0, 256, 1024, 3072};
+    // staging in shared memory applies to the 8-wide layout only (the binary
+    // layout's octant copies are read through L1)
+    const std::vector<int> smems = wide_layout(ctx) ? std::vector<int>{0, 256, 1024, 3072} : std::vector<int>{0};
     cudaEvent_t e0, e1;
     RT_TRY(cudaEventCreate(&e0));
     RT_TRY(cudaEventCreate(&e1));

@@ -1,6 +1,7 @@
 // rt_bvh.cu -- GPU BVH builders over Morton-ordered triangles (Karras radix
-// tree with bottom-up AABB refit, or PLOC clustering) and the 64-byte-node
-// traversal layout.
+// tree with bottom-up AABB refit, or PLOC clustering), the 64-byte-node
+// traversal layout with its 8 ray-octant copies, and the optional 8-wide
+// collapse.
 //
 // The paper delegates ray/triangle intersection to Mitsuba 3 (Sec. II); the
 // acceleration structure here is a linear BVH built in parallel on the GPU:
@@ -731,6 +732,33 @@ __global__ void k_wcheck_degree(const unsigned* __restrict__ info, int n_leaves,
     if (indeg[i] != (i == 0 ? 0 : 1)) atomicOr(bad, 1u);
 }
 
+// Octant copies of the binary nodes: copy 1 + o (after the m binary nodes)
+// holds each child box as (near x, y, z, far x, y, z) for rays whose
+// direction components are negative exactly on the axes set in o, so that a
+// ray's box test needs no per-axis min/max (box_oct). Same record layout and
+// child references as the binary nodes.
+__global__ void k_octants(int m, float4* __restrict__ nodes) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 8 * m) return;
+    const int o = k / m, i = k - o * m;
+    const float4* p = nodes + 4 * (size_t)i;
+    const float4 a = p[0], b = p[1], c = p[2], e = p[3];
+    const float b0[6] = {a.x, a.y, a.z, a.w, b.x, b.y}, b1[6] = {b.z, b.w, c.x, c.y, c.z, c.w};
+    float n0[6], n1[6];
+    for (int ax = 0; ax < 3; ax++) {
+        const bool neg = (o >> ax) & 1;
+        n0[ax] = neg ? b0[3 + ax] : b0[ax];
+        n0[3 + ax] = neg ? b0[ax] : b0[3 + ax];
+        n1[ax] = neg ? b1[3 + ax] : b1[ax];
+        n1[3 + ax] = neg ? b1[ax] : b1[3 + ax];
+    }
+    float4* q = nodes + 4 * ((size_t)(1 + o) * m + i);
+    q[0] = make_float4(n0[0], n0[1], n0[2], n0[3]);
+    q[1] = make_float4(n0[4], n0[5], n1[0], n1[1]);
+    q[2] = make_float4(n1[2], n1[3], n1[4], n1[5]);
+    q[3] = e;
+}
+
 float host_unord(unsigned u) {
     unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
     float f;
@@ -759,7 +787,8 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     RT_TRY(buf_reserve(ctx->planes, sizeof(float4) * (size_t)T));
     RT_TRY(buf_reserve(ctx->planes64, sizeof(double2) * 3 * (size_t)std::max(T, 1)));
     int m = std::max(T - 1, 1);
-    RT_TRY(buf_reserve(ctx->nodes, sizeof(float4) * 4 * (size_t)m));
+    // the binary nodes, then their 8 octant copies (k_octants)
+    RT_TRY(buf_reserve(ctx->nodes, sizeof(float4) * 4 * 9 * (size_t)m));
     // build scratch, kept in the context between builds
     RT_TRY(buf_reserve(ctx->b_lbox, sizeof(float) * 6 * (size_t)T));
     RT_TRY(buf_reserve(ctx->b_cent, sizeof(float) * 3 * (size_t)T));
@@ -938,6 +967,12 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
             prof_end(ctx);
             RT_TRY(cudaGetLastError());
         }
+    }
+    if (ctx->n_nodes > 0) {
+        prof_begin(ctx, "k_octants");
+        k_octants<<<(8 * ctx->n_nodes + B - 1) / B, B, 0, st>>>(ctx->n_nodes, bp<float4>(ctx->nodes));
+        prof_end(ctx);
+        RT_TRY(cudaGetLastError());
     }
     // leaf records in sorted order: the hierarchy's leaves, then the large triangles
     prof_begin(ctx, "k_leaf_tris");

@@ -4,8 +4,10 @@
 // Layouts (all in HBM, 16-byte aligned, read with 16-byte vector loads):
 //   BVH node  = 4 x float4 (64 B): the AABBs of both children and their
 //               indices (child < 0 means leaf triangle ~child). Nodes are in
-//               breadth-first order, so the top levels are a prefix that a
-//               block can stage in shared memory.
+//               breadth-first order (root first). After the n_nodes nodes
+//               follow 8 copies of them, one per ray octant, with each box's
+//               planes stored as (near xyz, far xyz) for that octant; the
+//               traversal reads its ray's copy.
 //   8-wide node (selectable) = 15 x float4 (240 B), below; collapsed from
 //               the binary hierarchy, breadth-first as well.
 //   triangle  = 3 x float4 (48 B), leaf (Morton) order: v0 | id,
@@ -78,18 +80,6 @@ __device__ __forceinline__ float4 ldg4(const float4* p) { return __ldg(p); }
 __device__ __forceinline__ int node_f4(const DevScene& s) { return s.wide ? RT_WN_F4 : 4; }
 __device__ __forceinline__ const float4* node_base(const DevScene& s) { return s.wide ? s.wnodes : s.nodes; }
 
-// Fetch one BVH node: from shared memory if staged, else from global.
-__device__ __forceinline__ void fetch_node(const DevScene& s, const float4* sm, int n_sm, int node,
-                                           float4& a, float4& b, float4& c, float4& d) {
-    if (node < n_sm) {
-        const float4* p = sm + 4 * node;
-        a = p[0]; b = p[1]; c = p[2]; d = p[3];
-    } else {
-        const float4* p = s.nodes + 4 * (size_t)node;
-        a = ldg4(p); b = ldg4(p + 1); c = ldg4(p + 2); d = ldg4(p + 3);
-    }
-}
-
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -99,20 +89,6 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
     return r;
-}
-
-// Slab test of one AABB; returns the entry distance, or NaN when missed (so
-// that every `tn <= bound` test fails, also against an infinite bound).
-// Three-input min/max: near = max(tlo, per-axis near planes), far =
-// min(thi, per-axis far planes).
-__device__ __forceinline__ float slab(float lox, float loy, float loz, float hix, float hiy, float hiz,
-                                      f3 oi, f3 inv, float tlo, float thi) {
-    float t0x = fmaf(lox, inv.x, -oi.x), t1x = fmaf(hix, inv.x, -oi.x);
-    float t0y = fmaf(loy, inv.y, -oi.y), t1y = fmaf(hiy, inv.y, -oi.y);
-    float t0z = fmaf(loz, inv.z, -oi.z), t1z = fmaf(hiz, inv.z, -oi.z);
-    float tn = fmax3(fminf(t0x, t1x), fminf(t0y, t1y), fmaxf(fminf(t0z, t1z), tlo));
-    float tf = fmin3(fmaxf(t0x, t1x), fmaxf(t0y, t1y), fminf(fmaxf(t0z, t1z), thi));
-    return tn <= tf ? tn : __int_as_float(0x7fc00000);
 }
 
 __device__ __forceinline__ f3 safe_inv(f3 d) {
@@ -140,6 +116,27 @@ __device__ __forceinline__ float tri_hit(float4 r0, float4 r1, float4 r2, f3 o, 
     return dot(e2, q) / det;
 }
 
+// Entry and exit distances of a box whose planes are already chosen by the
+// ray's octant (near planes nx, ny, nz: lo where the direction component is
+// positive, hi where it is negative; far planes the others), bounded by
+// tlo / thi. These are the values the classic slab test computes for the box
+// (its per-axis min/max picks exactly these planes) without its six min/max;
+// the box is hit when near <= far.
+__device__ __forceinline__ float box_near(float nx, float ny, float nz, f3 oi, f3 inv, float tlo) {
+    return fmax3(fmaf(nx, inv.x, -oi.x), fmaf(ny, inv.y, -oi.y), fmaxf(fmaf(nz, inv.z, -oi.z), tlo));
+}
+__device__ __forceinline__ float box_far(float fx, float fy, float fz, f3 oi, f3 inv, float thi) {
+    return fmin3(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y), fminf(fmaf(fz, inv.z, -oi.z), thi));
+}
+
+// The binary nodes of the ray's octant (sign bits of the reciprocal
+// direction; copy 1 + octant after the n_nodes binary nodes).
+__device__ __forceinline__ const float4* octant_nodes(const DevScene& s, f3 inv) {
+    const unsigned oct = (__float_as_uint(inv.x) >> 31) | ((__float_as_uint(inv.y) >> 31) << 1) |
+                         ((__float_as_uint(inv.z) >> 31) << 2);
+    return s.nodes + 4 * (size_t)(1 + oct) * s.n_nodes;
+}
+
 // Box test with the planes already chosen by the ray's octant: near planes
 // (nx, ny, nz: lo where the direction component is positive, hi where it is
 // negative) and far planes (fx, fy, fz). The entry and exit distances are
@@ -148,9 +145,7 @@ __device__ __forceinline__ float tri_hit(float4 r0, float4 r1, float4 r2, f3 o, 
 // are exact, so the grouping of the three-way min/max does not matter.)
 __device__ __forceinline__ bool box_oct(float nx, float ny, float nz, float fx, float fy, float fz, f3 oi, f3 inv,
                                         float tlo, float thi) {
-    const float tn = fmax3(fmaf(nx, inv.x, -oi.x), fmaf(ny, inv.y, -oi.y), fmaxf(fmaf(nz, inv.z, -oi.z), tlo));
-    const float tf = fmin3(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y), fminf(fmaf(fz, inv.z, -oi.z), thi));
-    return tn <= tf;
+    return box_near(nx, ny, nz, oi, inv, tlo) <= box_far(fx, fy, fz, oi, inv, thi);
 }
 
 // Bit j of the result is bit (j XOR oct) of m (8-bit masks): slot order to
@@ -294,14 +289,15 @@ __device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm
             if (t > tmin && (t < tb || (t == tb && id < best))) { tb = t; best = id; }
         }
     }
+    const float4* onodes = octant_nodes(s, inv);
     while (s.n_nodes > 0) {
-        float4 a, b, c, e;
-        fetch_node(s, sm, n_sm, node, a, b, c, e);
+        const float4* np = onodes + 4 * (size_t)node;
+        const float4 a = ldg4(np), b = ldg4(np + 1), c = ldg4(np + 2), e = ldg4(np + 3);
         if (C) cnt.nodes++;
-        float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tb);
-        float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tb);
+        const float tn0 = box_near(a.x, a.y, a.z, oi, inv, tmin), tf0 = box_far(a.w, b.x, b.y, oi, inv, tb);
+        const float tn1 = box_near(b.z, b.w, c.x, oi, inv, tmin), tf1 = box_far(c.y, c.z, c.w, oi, inv, tb);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
-        bool h0 = tn0 <= tb, h1 = tn1 <= tb;
+        bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && c0 < 0) {
             int k = ~c0;
             const float4* tp = s.tris + 3 * (size_t)k;
@@ -367,14 +363,15 @@ __device__ __forceinline__ bool any_hit_b(const DevScene& s, const float4* sm, i
             if (t > tmin && t < tmax) return true;
         }
     }
+    const float4* onodes = octant_nodes(s, inv);
     while (s.n_nodes > 0) {
-        float4 a, b, c, e;
-        fetch_node(s, sm, n_sm, node, a, b, c, e);
+        const float4* np = onodes + 4 * (size_t)node;
+        const float4 a = ldg4(np), b = ldg4(np + 1), c = ldg4(np + 2), e = ldg4(np + 3);
         if (C) cnt.nodes++;
-        float tn0 = slab(a.x, a.y, a.z, a.w, b.x, b.y, oi, inv, tmin, tmax);
-        float tn1 = slab(b.z, b.w, c.x, c.y, c.z, c.w, oi, inv, tmin, tmax);
+        const float tn0 = box_near(a.x, a.y, a.z, oi, inv, tmin), tf0 = box_far(a.w, b.x, b.y, oi, inv, tmax);
+        const float tn1 = box_near(b.z, b.w, c.x, oi, inv, tmin), tf1 = box_far(c.y, c.z, c.w, oi, inv, tmax);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
-        bool h0 = tn0 <= tmax, h1 = tn1 <= tmax;
+        bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && c0 < 0) {
             const float4* tp = s.tris + 3 * (size_t)(~c0);
             float4 r0 = ldg4(tp), r1 = ldg4(tp + 1), r2 = ldg4(tp + 2);

@@ -113,7 +113,7 @@ struct rt_ctx {
     bool dirs_ok = false;
 
     // tuning
-    int n_smem_nodes = 256;   // BVH nodes staged in shared memory
+    int n_smem_nodes = 256;   // BVH node bytes / 64 staged in shared memory (8-wide layout)
     int bvh_builder = RT_BVH_PLOC;  // hierarchy over the Morton order: RT_BVH_KARRAS or RT_BVH_PLOC
     int bvh_width = 2;              // traversal layout: 2 (binary nodes) or 8 (wide nodes)
     int dedup = RT_DEDUP_HASH;      // candidate duplicate removal: RT_DEDUP_HASH or RT_DEDUP_SORT
@@ -159,13 +159,15 @@ int set_cuda(rt_ctx* ctx, cudaError_t e, const char* what);
 DevScene dev_scene(rt_ctx* ctx);
 
 // The traversal layout of the context's scene, and the nodes the traversal
-// kernels stage in shared memory: n_smem_nodes counts 64-byte binary nodes,
-// so both layouts stage the same bytes (the top of the tree).
+// kernels stage in shared memory: the 8-wide layout stages the top of its
+// tree (n_smem_nodes counts 64-byte binary nodes' worth of bytes); the
+// binary layout stages nothing (each ray reads its octant's copy of the
+// nodes through L1).
 inline bool wide_layout(const rt_ctx* c) { return c->bvh_width == 8 && c->n_wnodes > 0; }
 inline int staged_nodes(const rt_ctx* c) {
-    const int n = wide_layout(c) ? c->n_smem_nodes * 4 / RT_WN_F4 : c->n_smem_nodes;
-    const int have = wide_layout(c) ? c->n_wnodes : c->n_nodes;
-    return n < have ? n : have;
+    if (!wide_layout(c)) return 0;
+    const int n = c->n_smem_nodes * 4 / RT_WN_F4;
+    return n < c->n_wnodes ? n : c->n_wnodes;
 }
 inline size_t staged_bytes(const rt_ctx* c) {
     return sizeof(float4) * (wide_layout(c) ? RT_WN_F4 : 4) * (size_t)staged_nodes(c);

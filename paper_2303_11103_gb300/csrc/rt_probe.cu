@@ -25,66 +25,15 @@
 
 namespace {
 
-// Traversal arithmetic: n_slab8 x 8 slab tests and n_tri triangle tests per
-// iteration. Every lane holds its own ray, eight boxes and two triangles,
-// arranged so that about half of the box tests and a quarter of the
-// triangle tests are hits (the triangle division is then taken as in a
-// traversal).
-__global__ void __launch_bounds__(256) k_probe_traversal(int iters, int n_slab8, int n_tri, float zero, float* out) {
-    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-    const float jx = 0.01f * (float)(t & 15), jy = 0.01f * (float)((t >> 4) & 15);
-    f3 o = mk(-20.0f + jx, -3.0f + jy, 1.5f);
-    f3 d = unit(mk(1.0f, 0.05f + jy, 0.02f + jx));
-    const f3 inv = safe_inv(d);
-    f3 oi = {o.x * inv.x, o.y * inv.y, o.z * inv.z};
-    float bx[8][6], r[8];
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        // odd boxes straddle the ray, even ones miss; no two boxes share a
-        // plane (which would let the compiler share their arithmetic)
-        const float y0 = ((k & 1) ? -2.0f : 4.0f) + 0.1f * k;
-        bx[k][0] = -10.0f + 2.5f * k; bx[k][1] = y0 - 3.0f; bx[k][2] = 0.05f * k;
-        bx[k][3] = -8.0f + 2.5f * k;  bx[k][4] = y0 + 3.0f; bx[k][5] = 3.0f + 0.07f * k;
-        r[k] = 1e30f;
-    }
-    float4 tr[2][3];
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        // triangle in the plane x = 5 + k: lanes with bit k of t set are hit
-        const float yc = ((t >> k) & 1u) ? -2.0f : 9.0f;
-        tr[k][0] = make_float4(5.0f + k, yc - 4.0f, -4.0f, __int_as_float(k));
-        tr[k][1] = make_float4(0.0f, 8.0f, 0.0f, 0.0f);
-        tr[k][2] = make_float4(0.0f, 0.0f, 12.0f, 0.0f);
-    }
-    const float tmin = 1e-4f;
-    for (int it = 0; it < iters; it++) {
-        for (int s = 0; s < n_slab8; s++) {
-            oi.x += zero;
-            oi.y += zero;
-            oi.z += zero;
-#pragma unroll
-            for (int k = 0; k < 8; k++)
-                r[k] = slab(bx[k][0], bx[k][1], bx[k][2], bx[k][3], bx[k][4], bx[k][5], oi, inv, tmin, r[k]);
-        }
-        for (int q = 0; q < n_tri; q++) {
-            d.x += zero;
-            const float th = (q & 1) ? tri_hit(tr[1][0], tr[1][1], tr[1][2], o, d)
-                                     : tri_hit(tr[0][0], tr[0][1], tr[0][2], o, d);
-            o.x = fminf(o.x, th);
-        }
-    }
-    float sum = o.x + d.x + oi.x + oi.y + oi.z;
-#pragma unroll
-    for (int k = 0; k < 8; k++) sum += r[k];
-    if (sum == 12345.678f) out[0] = sum;   // keeps every chain live; never true for these inputs
-}
-
-// The 8-wide layout's arithmetic: n_box8 x 8 octant-selected box tests
-// (box_oct) and n_tri triangle tests per iteration, chained and perturbed as
-// above (a positive direction: the near planes are the boxes' lo planes).
-// Each box test's outcome is recorded by one select, as the traversal
-// records it by one bit operation.
-__global__ void __launch_bounds__(256) k_probe_wide(int iters, int n_box8, int n_tri, float zero, float* out) {
+// Traversal arithmetic: n_box8 x 8 octant-selected box tests (box_oct, the
+// test of both layouts) and n_tri triangle tests per iteration. Every lane
+// holds its own ray (a positive direction: the near planes are the boxes' lo
+// planes), eight boxes and two triangles, arranged so that about half of the
+// box tests and a quarter of the triangle tests are hits (the triangle
+// division is then taken as in a traversal). Each box test's outcome is
+// recorded by one select, as the traversal records it by one bit operation
+// or compare.
+__global__ void __launch_bounds__(256) k_probe_traversal(int iters, int n_box8, int n_tri, float zero, float* out) {
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
     const float jx = 0.01f * (float)(t & 15), jy = 0.01f * (float)((t >> 4) & 15);
     f3 o = mk(-20.0f + jx, -3.0f + jy, 1.5f);
@@ -155,24 +104,19 @@ extern "C" int rt_probe_peak(rt_ctx* ctx, int32_t kind, int32_t n_slab, int32_t 
     if (!ctx) return RT_ERR_INVALID_ARG;
     cudaError_t de = cudaSetDevice(ctx->device);
     if (de != cudaSuccess) return set_cuda(ctx, de, "cudaSetDevice");
-    if (!ops_per_s || (kind != RT_PROBE_TRAVERSAL && kind != RT_PROBE_FFMA && kind != RT_PROBE_TRAVERSAL8))
+    if (!ops_per_s || (kind != RT_PROBE_TRAVERSAL && kind != RT_PROBE_FFMA))
         return set_err(ctx, RT_ERR_INVALID_ARG, "probe_peak: bad arguments");
-    if (kind != RT_PROBE_FFMA && (n_slab < 8 || n_slab % 8 || n_tri < 0 || n_slab > 4096 || n_tri > 4096))
+    if (kind == RT_PROBE_TRAVERSAL && (n_slab < 8 || n_slab % 8 || n_tri < 0 || n_slab > 4096 || n_tri > 4096))
         return set_err(ctx, RT_ERR_INVALID_ARG, "probe_peak: n_slab a positive multiple of 8, n_tri >= 0");
     if (ctx->capturing) return set_err(ctx, RT_ERR_NOT_READY, "probe_peak while capturing a graph");
     const int block = 256;
-    const void* kern = kind == RT_PROBE_TRAVERSAL    ? (const void*)k_probe_traversal
-                       : kind == RT_PROBE_TRAVERSAL8 ? (const void*)k_probe_wide
-                                                     : (const void*)k_probe_ffma;
+    const void* kern = kind == RT_PROBE_TRAVERSAL ? (const void*)k_probe_traversal : (const void*)k_probe_ffma;
     const int grid = blocks_per_sm(kern, block, 0) * ctx->num_sms;
     const double threads = (double)grid * block;
-    // algorithmic operations per iteration and thread: 17 per slab test
-    // (6 FMA, 6 per-axis min/max, 4 combining min/max, 1 compare), 35 per
-    // triangle test; 11 per octant-selected box test (6 FMA, 4 min/max,
-    // 1 compare); 2 flops per FMA
-    const double per_iter = kind == RT_PROBE_TRAVERSAL    ? 17.0 * n_slab + 35.0 * n_tri
-                            : kind == RT_PROBE_TRAVERSAL8 ? 11.0 * n_slab + 35.0 * n_tri
-                                                          : 2.0 * 16 * 8;
+    // algorithmic operations per iteration and thread: 11 per
+    // octant-selected box test (6 FMA, 4 min/max, 1 compare), 35 per
+    // triangle test; 2 flops per FMA
+    const double per_iter = kind == RT_PROBE_TRAVERSAL ? 11.0 * n_slab + 35.0 * n_tri : 2.0 * 16 * 8;
     // about 2 ms of work at 40e12 operations/s
     int iters = (int)std::max(8.0, 8e10 / (threads * per_iter));
     float* sink = bp<float>(ctx->counters);   // never written (see the kernels' last lines)
@@ -185,8 +129,6 @@ extern "C" int rt_probe_peak(rt_ctx* ctx, int32_t kind, int32_t n_slab, int32_t 
         cudaEventRecord(e0, ctx->stream);
         if (kind == RT_PROBE_TRAVERSAL)
             k_probe_traversal<<<grid, block, 0, ctx->stream>>>(iters, n_slab / 8, n_tri, 0.0f, sink);
-        else if (kind == RT_PROBE_TRAVERSAL8)
-            k_probe_wide<<<grid, block, 0, ctx->stream>>>(iters, n_slab / 8, n_tri, 0.0f, sink);
         else
             k_probe_ffma<<<grid, block, 0, ctx->stream>>>(iters, 1.0f, sink);
         ctx->launches++;

@@ -340,7 +340,7 @@ def rt_freq_response_paths(ctx, offsets, n_port_pairs, a, tau, freqs, H):
                                              _ptr(a), _ptr(tau), _ptr(freqs), int(freqs.shape[0]), _ptr(H)))
 
 
-PROBE_TRAVERSAL, PROBE_FFMA, PROBE_TRAVERSAL8 = 0, 1, 2
+PROBE_TRAVERSAL, PROBE_FFMA = 0, 1
 
 
 def rt_probe_peak(ctx, kind, n_slab=8, n_tri=0) -> float:
