@@ -431,10 +431,11 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = None
+K_COVERAGE_TRAFFIC = 20.54e6
 # L1/TEX throughput of the same launch (% of its peak, elapsed) and the
 # sector hit rate: the traversal's record reads are served by L1.
-K_COVERAGE_L1 = None
+K_COVERAGE_L1 = {"l1tex_throughput_pct": 57.0, "l1tex_sector_hit_pct": 93.4, "lts_throughput_pct": 3.5,
+                 "source": "profiles/k_coverage_city_1e6rays.md (ncu --set full, one launch)"}
 
 
 def traversal_probe(ctx, counts, n_tri=4):
