@@ -506,6 +506,9 @@ int rt_freq_response_backward(rt_ctx* ctx, const float* a, const float* tau, con
  * rt_graph_launch replays it on the context's stream, reading the buffers
  * the recorded calls named (update their contents in place between
  * replays). One graph per context; rt_graph_begin replaces the previous.
+ * A replay is refused (RT_ERR_NOT_READY) once a later call has reallocated
+ * a context buffer the graph uses (a larger scene or device set, another
+ * ray count): capture again.
  */
 int rt_graph_begin(rt_ctx* ctx);
 int rt_graph_end(rt_ctx* ctx);

@@ -722,6 +722,18 @@ int rt_pair_gain(rt_ctx* ctx, const float* a, float floor_db, float* out) {
     return pair_gain_impl(ctx, a, floor_db, out, np);
 }
 
+// Addresses of the context buffers a captured graph may read or write. A
+// later call may reallocate one of them (a larger scene, a new ray count);
+// the graph would then use freed memory, so its replay is refused.
+static std::vector<void*> graph_buffers(rt_ctx* ctx) {
+    std::vector<void*> v;
+    for (DevBuf* b : {&ctx->nodes, &ctx->wnodes, &ctx->tris, &ctx->tris_o, &ctx->planes, &ctx->planes64, &ctx->mat,
+                      &ctx->mats, &ctx->tx_pos, &ctx->tx_ypr, &ctx->rx_pos, &ctx->rx_ypr, &ctx->rx_off_d, &ctx->perm,
+                      &ctx->dirs, &ctx->counters, &ctx->status, &ctx->scat, &ctx->scat_alpha})
+        v.push_back(b->p);
+    return v;
+}
+
 int rt_graph_begin(rt_ctx* ctx) {
     CHECK_CTX(ctx);
     if (ctx->capturing) return set_err(ctx, RT_ERR_INVALID_ARG, "graph_begin: already capturing");
@@ -760,6 +772,7 @@ int rt_graph_end(rt_ctx* ctx) {
     if (e != cudaSuccess) return set_cuda(ctx, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
     cudaGraphDestroy(g);
+    ctx->graph_bufs = graph_buffers(ctx);
     if (e != cudaSuccess) {
         ctx->graph_exec = nullptr;
         return set_cuda(ctx, e, "cudaGraphInstantiate");
@@ -770,6 +783,10 @@ int rt_graph_end(rt_ctx* ctx) {
 int rt_graph_launch(rt_ctx* ctx) {
     CHECK_CTX(ctx);
     if (!ctx->graph_exec) return set_err(ctx, RT_ERR_NOT_READY, "graph_launch: no graph");
+    if (graph_buffers(ctx) != ctx->graph_bufs)
+        return set_err(ctx, RT_ERR_NOT_READY,
+                       "graph_launch: a buffer the graph uses was reallocated since capture (larger scene, "
+                       "devices or ray count); capture the graph again");
     RT_TRY(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     ctx->launches += ctx->graph_kernels;
     return RT_OK;

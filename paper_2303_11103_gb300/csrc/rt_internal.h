@@ -134,6 +134,7 @@ struct rt_ctx {
     cudaStream_t user_stream = nullptr, cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t launches_at_begin = 0, graph_kernels = 0;
+    std::vector<void*> graph_bufs;   // addresses of the buffers a graph may use, at capture
 };
 
 // Bracket one kernel launch: counts it and, when profiling, records CUDA

@@ -85,6 +85,12 @@ def test_graph_capture_replay(city):
     torch.cuda.synchronize()
     g2, h2 = tr.coverage_map(GRID, 3, 40009, 0)
     assert torch.equal(hits, h2)
+    # a later call that reallocates a buffer the graph uses (a new ray count:
+    # a larger ray order and direction table) invalidates the graph
+    tr.coverage_map(GRID, 3, 2 * 40009, 0)
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_graph_launch(tr.ctx)
+    assert e.value.code == -6 and "capture the graph again" in str(e.value)
     tr.close()
 
 
