@@ -331,12 +331,30 @@ def run_ours(args):
         with torch.cuda.stream(copy_stream):
             out_h["H"].copy_(H, non_blocking=True)
 
+    # the step's inputs packed into one pinned host buffer (16-byte aligned
+    # slots), copied to the device in one transfer per step
+    slots, off = {}, 0
+    for k, v in host.items():
+        nb = v.numel() * v.element_size()
+        slots[k] = (off, nb)
+        off += (nb + 15) // 16 * 16
+    host_blob = torch.empty(off, dtype=torch.uint8).pin_memory()
+    for k, v in host.items():
+        o, nb = slots[k]
+        host_blob[o:o + nb].copy_(v.reshape(-1).view(torch.uint8))
+    dev_blob = torch.empty(off, dtype=torch.uint8, device=dev)
+    h2d = off   # bytes copied per step (the inputs and their alignment padding)
+
+    def inputs_from(blob):
+        return {k: blob[o:o + nb].view(host[k].dtype).view(host[k].shape) for k, (o, nb) in slots.items()}
+
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        inp = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        dev_blob.copy_(host_blob, non_blocking=True)
+        inp = inputs_from(dev_blob)
         step(inp, after_freq=read_H)
         out_h["gain"].copy_(gain, non_blocking=True)
         # a and tau into pinned host buffers (grown when a step has more paths)
