@@ -8,8 +8,11 @@ pattern, 1000 receivers, 3.5 GHz):
   subcarriers of 30 kHz -> coverage map (500 x 500 cells of 1 m at 1.5 m,
   1e6 rays, max_depth 3) -> VJP of H(f) and of the CIR w.r.t. materials and
   transmitter pose.
-metric = rays*bounces/s: closest-hit ray queries (shooting-and-bouncing
-plus coverage tracing) of the whole job / time.
+metric = rays*bounces/s: ray segments tested against the scene in the whole
+job / time: closest-hit queries (shooting and bouncing, and every coverage
+segment that can reflect again) plus the coverage rays' last segments, each
+tested up to the map plane by an any-hit query. Last segments that cannot
+reach the map inside the grid are not traced and not counted.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: replicas only (each rank traces its own copy of the workload,
@@ -260,7 +263,7 @@ def run_ours(args):
     cov_counts = rt.rt_profile_report(ctx, reset=True)
     step(devin, concurrent=False)   # the second stream's map has its own work counter
     one = rt.rt_profile_report(ctx, reset=True)
-    bounces_per_step = one["closest_hit"]
+    bounces_per_step = one["closest_hit"] + one.get("plane_segments", 0)
     rt.rt_profile(ctx, False)
 
     # per-kernel breakdown: every launch bracketed by CUDA events, outside the timed region
@@ -414,6 +417,9 @@ def run_ours(args):
         "paths_per_s_note": "valid paths of compute_paths per second of the whole timed step",
         "compute_paths_counts": path_stats,
         "ray_bounces_per_step": bounces_per_step,
+        "ray_bounces_basis": {"closest_hit": one["closest_hit"], "plane_segments": one.get("plane_segments", 0),
+                              "note": "closest-hit queries plus the coverage rays' last segments tested up to "
+                                      "the map plane (any hit); untraced last segments are not counted"},
         "gpu_launches": prof["launches"],
         "kernel_ms_per_step": {k: v[1] / n_prof for k, v in sorted(breakdown.items(), key=lambda x: -x[1][1])},
         "kernel_ms_note": f"{n_prof} steps outside the timed region on one stream, every launch bracketed by "
@@ -503,8 +509,14 @@ def roofline(name, rec, sbr_counts, cov_counts, hbm, src, probe):
                                                 f"{OPS_PER_TRI} per triangle record",
             "requested_gbs": req_bytes / per_launch_s / 1e9, "hbm_peak_gbs": hbm, "hbm_peak_source": src,
             "ms_per_launch": per_launch_s * 1e3,
-            "nodes_per_query": counts["nodes"] / max(counts["closest_hit"] + counts["any_hit"], 1),
-            "tris_per_query": counts["tris"] / max(counts["closest_hit"] + counts["any_hit"], 1)}
+            "nodes_per_query": counts["nodes"] / max(queries(counts), 1),
+            "tris_per_query": counts["tris"] / max(queries(counts), 1)}
+
+
+def queries(counts):
+    """Every traversal query of a counting pass: closest hit, any hit and the
+    coverage rays' last-segment plane tests."""
+    return counts["closest_hit"] + counts["any_hit"] + counts.get("plane_segments", 0)
 
 
 def extra_measurements(tr, scene, dev, args):
@@ -525,7 +537,7 @@ def extra_measurements(tr, scene, dev, args):
     tuning_default = rt.rt_get_tuning(ctx)
     rt.rt_autotune(ctx, grid, 5, 2_000_000, gain, hits)
     tuning = rt.rt_get_tuning(ctx)
-    # closest-hit queries of one map (counting variant, untimed)
+    # ray segments of one map (counting variant, untimed)
     rt.rt_profile(ctx, rt.PROFILE_COUNT)
     rt.rt_profile_report(ctx, reset=True)
     rt.rt_coverage_map(ctx, grid, 5, n, 0, gain, hits)
@@ -557,7 +569,7 @@ def extra_measurements(tr, scene, dev, args):
             "coverage_map_config": "64 tx x 1e7 rays, max_depth 5, 500x500 cells of 1 m, one persistent launch "
                                    "in a captured CUDA graph, median of 10 replays",
             "coverage_map_tuning": {"block": tuning[0], "chunk": tuning[1], "smem_nodes": tuning[2]},
-            "coverage_map_rays_bounces_per_s": cnt["closest_hit"] / (ms / 1e3)}
+            "coverage_map_rays_bounces_per_s": (cnt["closest_hit"] + cnt.get("plane_segments", 0)) / (ms / 1e3)}
 
 
 def cir_extensions_measurement(tr, scene, dev, T=14, fs=1e6):

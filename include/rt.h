@@ -423,7 +423,10 @@ int rt_join(rt_ctx* ctx);
  *     ray's octant: 11 operations, 6 FMA, 4 min/max, 1 compare) and
  *     Moller-Trumbore triangle test (35 operations), n_slab box tests (a
  *     positive multiple of 8) per n_tri triangle tests, as algorithmic
- *     operations per second (the counts the bench's roofline uses);
+ *     operations per second (the counts the bench's roofline uses); the box
+ *     test is timed in both forms the traversal code has (two children per
+ *     packed FMA, one box per scalar FMA; six launches each) and the faster
+ *     rate is written;
  *   RT_PROBE_FFMA: FP32 fused multiply-adds, as flops per second (2 per
  *     FMA); n_slab and n_tri are ignored.
  * Synchronises the stream. Errors: RT_ERR_INVALID_ARG, RT_ERR_NOT_READY
@@ -609,8 +612,10 @@ int rt_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int
  * records. rt_profile_report: synchronises and
  * writes JSON {"launches": kernel launches since the last reset,
  * "kernels": {name: [launches, total ms]}, "closest_hit": closest-hit
- * queries, "any_hit": visibility queries, "nodes": BVH node records
- * fetched, "tris": triangle records fetched, "sbr_keys": candidate keys the
+ * queries, "any_hit": visibility queries, "plane_segments": the coverage
+ * rays' last segments tested up to the map plane (any-hit queries of the
+ * coverage kernels), "nodes": BVH node records fetched (all queries),
+ * "tris": triangle records fetched, "sbr_keys": candidate keys the
  * last shooting pass appended, "candidates": distinct candidates, "paths":
  * valid paths of the last rt_compute_paths}; reset != 0 zeroes the
  * counters afterwards. RT_ERR_CAPACITY if buf is too small (truncated).

@@ -947,6 +947,7 @@ int rt_profile_report(rt_ctx* ctx, char* buf, size_t len, int reset) {
     s += "}, \"closest_hit\": " + std::to_string(c[RT_CNT_CLOSEST]) + ", \"any_hit\": " +
          std::to_string(c[RT_CNT_ANY]) + ", \"nodes\": " + std::to_string(c[RT_CNT_NODES]) +
          ", \"tris\": " + std::to_string(c[RT_CNT_TRIS]) + ", \"sbr_keys\": " + std::to_string(c[RT_CNT_KEYS]) +
+         ", \"plane_segments\": " + std::to_string(c[RT_CNT_PLANE]) +
          ", \"candidates\": " + std::to_string(ctx->n_cand) + ", \"paths\": " + std::to_string(ctx->n_paths) + "}";
     size_t n = std::min(len - 1, s.size());
     memcpy(buf, s.data(), n);

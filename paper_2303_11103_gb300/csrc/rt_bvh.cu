@@ -733,10 +733,12 @@ __global__ void k_wcheck_degree(const unsigned* __restrict__ info, int n_leaves,
 }
 
 // Octant copies of the binary nodes: copy 1 + o (after the m binary nodes)
-// holds each child box as (near x, y, z, far x, y, z) for rays whose
+// holds each child box as near x, y, z and far x, y, z planes for rays whose
 // direction components are negative exactly on the axes set in o, so that a
-// ray's box test needs no per-axis min/max (box_oct). Same record layout and
-// child references as the binary nodes.
+// ray's box test needs no per-axis min/max (box_oct). The two children's
+// planes are interleaved in pairs (near x of child 0, near x of child 1,
+// near y ...), so that one packed FMA takes a plane of both (box_pair); the
+// fourth word holds the child references as in the binary nodes.
 __global__ void k_octants(int m, float4* __restrict__ nodes) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 8 * m) return;
@@ -753,9 +755,9 @@ __global__ void k_octants(int m, float4* __restrict__ nodes) {
         n1[3 + ax] = neg ? b1[ax] : b1[3 + ax];
     }
     float4* q = nodes + 4 * ((size_t)(1 + o) * m + i);
-    q[0] = make_float4(n0[0], n0[1], n0[2], n0[3]);
-    q[1] = make_float4(n0[4], n0[5], n1[0], n1[1]);
-    q[2] = make_float4(n1[2], n1[3], n1[4], n1[5]);
+    q[0] = make_float4(n0[0], n1[0], n0[1], n1[1]);
+    q[1] = make_float4(n0[2], n1[2], n0[3], n1[3]);
+    q[2] = make_float4(n0[4], n1[4], n0[5], n1[5]);
     q[3] = e;
 }
 

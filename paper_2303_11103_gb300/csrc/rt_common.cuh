@@ -1,13 +1,14 @@
 // rt_common.cuh -- device-side data layout, vector math and BVH traversal
 // shared by the kernels of the GB300 radio ray tracer.
 //
-// Layouts (all in HBM, 16-byte aligned, read with 16-byte vector loads):
-//   BVH node  = 4 x float4 (64 B): the AABBs of both children and their
-//               indices (child < 0 means leaf triangle ~child). Nodes are in
-//               breadth-first order (root first). After the n_nodes nodes
-//               follow 8 copies of them, one per ray octant, with each box's
-//               planes stored as (near xyz, far xyz) for that octant; the
-//               traversal reads its ray's copy.
+// Layouts (all in HBM, 16-byte aligned, read with 16- or 32-byte vector loads):
+//   BVH node  = 4 x float4 (64 B, 64-byte aligned): the AABBs of both
+//               children and their indices (child < 0 means leaf triangle
+//               ~child). Nodes are in breadth-first order (root first).
+//               After the n_nodes nodes follow 8 copies of them, one per ray
+//               octant, with the two children's planes stored in pairs
+//               (child 0, child 1) per plane: near x, y, z, far x, y, z for
+//               that octant; the traversal reads its ray's copy.
 //   8-wide node (selectable) = 15 x float4 (240 B), below; collapsed from
 //               the binary hierarchy, breadth-first as well.
 //   triangle  = 3 x float4 (48 B), leaf (Morton) order: v0 | id,
@@ -129,6 +130,67 @@ __device__ __forceinline__ float box_far(float fx, float fy, float fz, f3 oi, f3
     return fmin3(fmaf(fx, inv.x, -oi.x), fmaf(fy, inv.y, -oi.y), fminf(fmaf(fz, inv.z, -oi.z), thi));
 }
 
+// Two FMAs in one instruction: (a0 b.x + c.x, a1 b.y + c.y), each rounded
+// once, as fmaf rounds.
+__device__ __forceinline__ float2 fma2(float a0, float a1, float2 b, float2 c) {
+    unsigned long long x, y, z, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(z) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(x), "l"(y), "l"(z));
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+
+// 32 bytes in one load (p 32-byte aligned), through the read-only path.
+__device__ __forceinline__ void ldg8(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
+// Ray constants of the binary traversal, each held twice so that one packed
+// FMA takes the same plane of both children of a node.
+struct PairRay {
+    float2 ix, iy, iz;   // reciprocal direction
+    float2 mx, my, mz;   // -origin * reciprocal direction
+};
+__device__ __forceinline__ PairRay pair_ray(f3 inv, f3 oi) {
+    return {make_float2(inv.x, inv.x), make_float2(inv.y, inv.y), make_float2(inv.z, inv.z),
+            make_float2(-oi.x, -oi.x), make_float2(-oi.y, -oi.y), make_float2(-oi.z, -oi.z)};
+}
+
+// Entry and exit distances of both child boxes of an octant-copy node
+// record (a, b, c: the planes in pairs, near x, y, z, far x, y, z), bounded
+// by tlo and thi. Each value is bit for bit the one box_near / box_far
+// computes for that child: the same FMA per plane, the same min/max.
+__device__ __forceinline__ void box_pair(float4 a, float4 b, float4 c, const PairRay& r, float tlo, float thi,
+                                         float& tn0, float& tf0, float& tn1, float& tf1) {
+    const float2 nx = fma2(a.x, a.y, r.ix, r.mx), ny = fma2(a.z, a.w, r.iy, r.my), nz = fma2(b.x, b.y, r.iz, r.mz);
+    const float2 fx = fma2(b.z, b.w, r.ix, r.mx), fy = fma2(c.x, c.y, r.iy, r.my), fz = fma2(c.z, c.w, r.iz, r.mz);
+    tn0 = fmax3(nx.x, ny.x, fmaxf(nz.x, tlo));
+    tn1 = fmax3(nx.y, ny.y, fmaxf(nz.y, tlo));
+    tf0 = fmin3(fx.x, fy.x, fminf(fz.x, thi));
+    tf1 = fmin3(fx.y, fy.y, fminf(fz.y, thi));
+}
+
+// A binary node record: four 16-byte loads, or two 32-byte loads (V8).
+// Which is faster depends on the kernel around the traversal (its register
+// and L1 pressure), so each kernel picks one.
+template <bool V8>
+__device__ __forceinline__ void load_node(const float4* p, float4& a, float4& b, float4& c, float4& e) {
+    if (V8) {
+        ldg8(p, a, b);
+        ldg8(p + 2, c, e);
+    } else {
+        a = ldg4(p);
+        b = ldg4(p + 1);
+        c = ldg4(p + 2);
+        e = ldg4(p + 3);
+    }
+}
+
 // The binary nodes of the ray's octant (sign bits of the reciprocal
 // direction; copy 1 + octant after the n_nodes binary nodes).
 __device__ __forceinline__ const float4* octant_nodes(const DevScene& s, f3 inv) {
@@ -241,6 +303,7 @@ struct TravCount {
 #define RT_CNT_NODES 4
 #define RT_CNT_TRIS 5
 #define RT_CNT_KEYS 6
+#define RT_CNT_PLANE 7   // last coverage segments tested up to the map plane (any hit)
 
 __device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* counters, int query_slot) {
     unsigned long long n = c.nodes, t = c.tris, q = c.queries;
@@ -264,7 +327,7 @@ __device__ __forceinline__ void flush_counts(TravCount& c, unsigned long long* c
 // larger indices than their parent (level order), with depth below
 // RT_STACK, so the loop visits each node at most once and the stack cannot
 // overflow. C: count node / triangle records and queries in cnt.
-template <bool C>
+template <bool C, bool V8>
 __device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
                                              int exclude, float& t_out, TravCount& cnt) {
     t_out = __int_as_float(0x7f800000);
@@ -290,12 +353,17 @@ __device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm
         }
     }
     const float4* onodes = octant_nodes(s, inv);
+    const PairRay pr = pair_ray(inv, oi);
+    // the most recently deferred child stays in a register (top); the
+    // stack in memory holds the ones below it
+    const int no_top = 0x7fffffff;
+    int top = no_top;
     while (s.n_nodes > 0) {
-        const float4* np = onodes + 4 * (size_t)node;
-        const float4 a = ldg4(np), b = ldg4(np + 1), c = ldg4(np + 2), e = ldg4(np + 3);
+        float4 a, b, c, e;
+        load_node<V8>(onodes + 4 * (size_t)node, a, b, c, e);
         if (C) cnt.nodes++;
-        const float tn0 = box_near(a.x, a.y, a.z, oi, inv, tmin), tf0 = box_far(a.w, b.x, b.y, oi, inv, tb);
-        const float tn1 = box_near(b.z, b.w, c.x, oi, inv, tmin), tf1 = box_far(c.y, c.z, c.w, oi, inv, tb);
+        float tn0, tf0, tn1, tf1;
+        box_pair(a, b, c, pr, tmin, tb, tn0, tf0, tn1, tf1);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
         bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && c0 < 0) {
@@ -325,12 +393,16 @@ __device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm
         if (h0 && h1) {
             int nearc = tn0 <= tn1 ? c0 : c1;
             int farc = tn0 <= tn1 ? c1 : c0;
-            stack[sp++] = farc;
+            if (top != no_top) stack[sp++] = top;
+            top = farc;
             node = nearc;
         } else if (h0) {
             node = c0;
         } else if (h1) {
             node = c1;
+        } else if (top != no_top) {
+            node = top;
+            top = no_top;
         } else {
             if (sp == 0) break;
             node = stack[--sp];
@@ -342,7 +414,7 @@ __device__ __forceinline__ int closest_hit_b(const DevScene& s, const float4* sm
 
 // Any occluder on the open segment (tmin, tmax) along o + t d (d unit),
 // skipping original ids ex0 / ex1.
-template <bool C>
+template <bool C, bool V8>
 __device__ __forceinline__ bool any_hit_b(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d,
                                           float tmax, int ex0, int ex1, TravCount& cnt) {
     if (C) cnt.queries++;
@@ -364,12 +436,13 @@ __device__ __forceinline__ bool any_hit_b(const DevScene& s, const float4* sm, i
         }
     }
     const float4* onodes = octant_nodes(s, inv);
+    const PairRay pr = pair_ray(inv, oi);
     while (s.n_nodes > 0) {
-        const float4* np = onodes + 4 * (size_t)node;
-        const float4 a = ldg4(np), b = ldg4(np + 1), c = ldg4(np + 2), e = ldg4(np + 3);
+        float4 a, b, c, e;
+        load_node<V8>(onodes + 4 * (size_t)node, a, b, c, e);
         if (C) cnt.nodes++;
-        const float tn0 = box_near(a.x, a.y, a.z, oi, inv, tmin), tf0 = box_far(a.w, b.x, b.y, oi, inv, tmax);
-        const float tn1 = box_near(b.z, b.w, c.x, oi, inv, tmin), tf1 = box_far(c.y, c.z, c.w, oi, inv, tmax);
+        float tn0, tf0, tn1, tf1;
+        box_pair(a, b, c, pr, tmin, tmax, tn0, tf0, tn1, tf1);
         int c0 = __float_as_int(e.x), c1 = __float_as_int(e.y);
         bool h0 = tn0 <= tf0, h1 = tn1 <= tf1;
         if (h0 && c0 < 0) {
@@ -543,18 +616,20 @@ __device__ __forceinline__ bool any_hit_w(const DevScene& s, const float4* sm, i
 // binary nodes, L = 0 the scene's own (a branch, uniform across a launch).
 // The hot kernels are compiled per layout (L = 2 or 8), so each carries one
 // traversal's registers.
+// V8: binary node records read by two 32-byte loads instead of four
+// 16-byte loads (the 8-wide layout ignores it).
 #define RT_LAYOUT_ANY 0
-template <bool C, int L = RT_LAYOUT_ANY>
+template <bool C, int L = RT_LAYOUT_ANY, bool V8 = true>
 __device__ __forceinline__ int closest_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d, int exclude,
                                            float& t_out, TravCount& cnt) {
     if (L == 8 || (L == RT_LAYOUT_ANY && s.wide)) return closest_hit_w<C>(s, sm, n_sm, o, d, exclude, t_out, cnt);
-    return closest_hit_b<C>(s, sm, n_sm, o, d, exclude, t_out, cnt);
+    return closest_hit_b<C, V8>(s, sm, n_sm, o, d, exclude, t_out, cnt);
 }
-template <bool C, int L = RT_LAYOUT_ANY>
+template <bool C, int L = RT_LAYOUT_ANY, bool V8 = true>
 __device__ __forceinline__ bool any_hit(const DevScene& s, const float4* sm, int n_sm, f3 o, f3 d, float tmax,
                                         int ex0, int ex1, TravCount& cnt) {
     if (L == 8 || (L == RT_LAYOUT_ANY && s.wide)) return any_hit_w<C>(s, sm, n_sm, o, d, tmax, ex0, ex1, cnt);
-    return any_hit_b<C>(s, sm, n_sm, o, d, tmax, ex0, ex1, cnt);
+    return any_hit_b<C, V8>(s, sm, n_sm, o, d, tmax, ex0, ex1, cnt);
 }
 
 // Spherical Fibonacci lattice direction of ray i of N (global frame):

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
             const f3 d = p.dirs ? xyz(__ldg(p.dirs + i)) : fib_dir(p.N, i);
             TravCount cnt;
             float th;
-            hit = closest_hit<false, L>(p.s, nullptr, 0, o, d, -1, th, cnt);
+            hit = closest_hit<false, L, false>(p.s, nullptr, 0, o, d, -1, th, cnt);
             if (hit >= 0) {
                 m = __ldg(p.s.mat + hit);
                 sc = __ldg(p.scat + m);
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128) k_scatter(ScatParams p) {
                 if (cs > 0.0f) {
                     const f3 ks = v * (1.0f / dist);
                     TravCount cnt;
-                    if (!any_hit<false, L>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
+                    if (!any_hit<false, L, false>(p.s, nullptr, 0, P, ks, dist - p.s.tmin, hit, -1, cnt)) {
                         const float pat = am < 0 ? cs : powf(0.5f * (1.0f + dot(kr, ks)), (float)am) / fa;
                         w = (VJP ? 1.0f : s2) * pat * p.w0 / (dist * dist);
                         const Rot<float> Rr = rot_ypr(p.rx_ypr[3 * r], p.rx_ypr[3 * r + 1], p.rx_ypr[3 * r + 2]);

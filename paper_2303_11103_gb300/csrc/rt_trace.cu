@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) k_sbr(SbrParams p) {
         uint32_t epos = 0;
         if (alive) {
             float t;
-            int id = closest_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+            int id = closest_hit<C, L, false>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
             if (id < 0) {
                 alive = false;
             } else {
@@ -211,6 +211,48 @@ struct CovParams {
     uint32_t* hits;        // [n_tx*ny*nx]
 };
 
+// The map cell where the ray o + t d (t > 0) crosses the plane z = h, or -1
+// when it does not cross it inside the grid; sc receives the distance.
+__device__ __forceinline__ long long plane_cell(const CovParams& p, int tx, f3 o, f3 d, float& sc) {
+    sc = 0.0f;
+    if (d.z == 0.0f) return -1;
+    sc = (p.h - o.z) / d.z;
+    if (!(sc > 0.0f)) return -1;
+    const float fx = (o.x + sc * d.x - p.x0) * p.inv_cell;
+    const float fy = (o.y + sc * d.y - p.y0) * p.inv_cell;
+    const int ix = (int)floorf(fx), iy = (int)floorf(fy);
+    if (!(fx >= 0.0f && fy >= 0.0f && ix < p.nx && iy < p.ny)) return -1;
+    return ((long long)tx * p.ny + iy) * p.nx + ix;
+}
+
+// One segment of a coverage ray from o along d, leaving triangle `last`.
+// Returns the map cell the segment adds to (-1: none). While the ray
+// reflects again (more), the closest hit gives the next triangle (id, t)
+// and the crossing counts when it comes before that hit. The last segment
+// reflects no further, so its closest hit is not needed: an any-hit test of
+// the segment up to the crossing decides, and it is taken only when the
+// crossing lies in the grid. Both forms count the crossing exactly when no
+// triangle other than `last` is hit at a distance in (tmin, sc] (tri_hit
+// gives both the same distances). Last-segment tests are counted in cnt_pl.
+template <bool C, int L>
+__device__ __forceinline__ long long cov_segment(const CovParams& p, const float4* sm, int tx, f3 o, f3 d,
+                                                 int last, bool more, int& id, float& t, TravCount& cnt,
+                                                 TravCount& cnt_pl) {
+    float sc;
+    id = -1;
+    t = __int_as_float(0x7f800000);
+    if (more) {
+        id = closest_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
+        const long long cell = plane_cell(p, tx, o, d, sc);
+        return (cell >= 0 && (id < 0 || sc < t)) ? cell : -1;
+    }
+    const long long cell = plane_cell(p, tx, o, d, sc);
+    if (cell < 0) return -1;
+    // t <= sc  <=>  t < the next float above sc (sc is finite here)
+    const float up = nextafterf(sc, __int_as_float(0x7f800000));
+    return any_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, up, last, last, cnt_pl) ? -1 : cell;
+}
+
 template <bool C, int L>
 __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     extern __shared__ float4 sm[];
@@ -222,7 +264,7 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     Cx<float> E[3];
     const float zeta_t = p.txa.slant[p.tx_port], zeta_r = p.rxa.slant[0];
     Rot<float> Rr = rot_ypr(0.0f, 0.0f, 0.0f);
-    TravCount cnt;
+    TravCount cnt, cnt_pl;
     while (true) {
         long long kd = 0;
         long long s = feed.refill(p.c, alive, kd);
@@ -246,25 +288,18 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
         }
         if (alive) {
             float t;
-            int id = closest_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
-            if (d.z != 0.0f) {
-                float sc = (p.h - o.z) / d.z;
-                if (sc > 0.0f && (id < 0 || sc < t)) {
-                    float fx = (o.x + sc * d.x - p.x0) * p.inv_cell;
-                    float fy = (o.y + sc * d.y - p.y0) * p.inv_cell;
-                    int ix = (int)floorf(fx), iy = (int)floorf(fy);
-                    if (fx >= 0.0f && fy >= 0.0f && ix < p.nx && iy < p.ny) {
-                        V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
-                        float re = F.x * E[0].re + F.y * E[1].re + F.z * E[2].re;
-                        float im = F.x * E[0].im + F.y * E[1].im + F.z * E[2].im;
-                        float w = (re * re + im * im) * p.wscale / fabsf(d.z);
-                        size_t cell = ((size_t)tx * p.ny + iy) * p.nx + ix;
-                        atomicAdd(p.gain + cell, w);
-                        atomicAdd(p.hits + cell, 1u);
-                    }
-                }
+            int id;
+            const bool more = depth < p.D;
+            const long long cell = cov_segment<C, L>(p, sm, tx, o, d, last, more, id, t, cnt, cnt_pl);
+            if (cell >= 0) {
+                V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
+                float re = F.x * E[0].re + F.y * E[1].re + F.z * E[2].re;
+                float im = F.x * E[0].im + F.y * E[1].im + F.z * E[2].im;
+                float w = (re * re + im * im) * p.wscale / fabsf(d.z);
+                atomicAdd(p.gain + cell, w);
+                atomicAdd(p.hits + cell, 1u);
             }
-            if (id < 0 || depth >= p.D) {
+            if (id < 0 || !more) {
                 alive = false;
             } else {
                 float4 pl = __ldg(p.c.s.planes + id);
@@ -281,7 +316,10 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
             }
         }
     }
-    if (C) flush_counts(cnt, p.c.counter, RT_CNT_CLOSEST);
+    if (C) {
+        flush_counts(cnt, p.c.counter, RT_CNT_CLOSEST);
+        flush_counts(cnt_pl, p.c.counter, RT_CNT_PLANE);
+    }
 }
 
 // VJP of the coverage map with respect to the transmitters' orientation
@@ -365,28 +403,21 @@ __global__ void __launch_bounds__(256) k_coverage_vjp(CovVjpParams q) {
         }
         if (alive) {
             float t;
-            int id = closest_hit<false, L>(p.c.s, sm, p.c.n_sm, o, d, last, t, cnt);
-            if (d.z != 0.0f) {
-                float sc = (p.h - o.z) / d.z;
-                if (sc > 0.0f && (id < 0 || sc < t)) {
-                    float fx = (o.x + sc * d.x - p.x0) * p.inv_cell;
-                    float fy = (o.y + sc * d.y - p.y0) * p.inv_cell;
-                    int ix = (int)floorf(fx), iy = (int)floorf(fy);
-                    if (fx >= 0.0f && fy >= 0.0f && ix < p.nx && iy < p.ny) {
-                        const size_t cell = ((size_t)tx * p.ny + iy) * p.nx + ix;
-                        const float g = q.grad_gain[cell];
-                        if (g != 0.0f) {
-                            V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
-                            D3 re = E[0].re * F.x + E[1].re * F.y + E[2].re * F.z;
-                            D3 im = E[0].im * F.x + E[1].im * F.y + E[2].im * F.z;
-                            const float sw = g * p.wscale / fabsf(d.z);
-                            for (int k = 0; k < 3; k++)
-                                acc[k] += sw * 2.0f * (re.v * re.d[k] + im.v * im.d[k]);
-                        }
-                    }
+            int id;
+            const bool more = depth < p.D;
+            const long long cell = cov_segment<false, L>(p, sm, tx, o, d, last, more, id, t, cnt, cnt);
+            if (cell >= 0) {
+                const float g = q.grad_gain[cell];
+                if (g != 0.0f) {
+                    V3<float> F = antenna_vec<float>(p.rxa.kind, zeta_r, Rr, V3<float>{-d.x, -d.y, -d.z});
+                    D3 re = E[0].re * F.x + E[1].re * F.y + E[2].re * F.z;
+                    D3 im = E[0].im * F.x + E[1].im * F.y + E[2].im * F.z;
+                    const float sw = g * p.wscale / fabsf(d.z);
+                    for (int k = 0; k < 3; k++)
+                        acc[k] += sw * 2.0f * (re.v * re.d[k] + im.v * im.d[k]);
                 }
             }
-            if (id < 0 || depth >= p.D) {
+            if (id < 0 || !more) {
                 alive = false;
             } else {
                 float4 pl = __ldg(p.c.s.planes + id);
