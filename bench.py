@@ -224,9 +224,12 @@ def run_ours(args):
         rt.rt_set_tx(ctx, inp["txp"], inp["txy"], tx.antenna)
         rt.rt_set_rx(ctx, inp["rxp"], inp["rxy"], rx.antenna)
         rt.rt_load_scene(ctx, inp["verts"], inp["mat"], inp["mats"])
-        if concurrent:
-            rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, rt.ASYNC_AFTER_TRACE)
+        if concurrent and args.schedule == "after_trace":
+            rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, rt.ASYNC_AFTER_TRACE,
+                                     args.side_blocks)
         P = rt.rt_compute_paths(ctx, MAX_DEPTH, N_RAYS, rt.RT_LOS | rt.RT_REFLECTION)
+        if concurrent and args.schedule == "after_paths":
+            rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, 0, args.side_blocks)
         a = torch.empty((max(P, 1), nrp, ntp, 2), dtype=torch.float32, device=dev)
         tau = torch.empty(max(P, 1), dtype=torch.float32, device=dev)
         rt.rt_cir(ctx, rt.RT_LOS | rt.RT_REFLECTION, a, tau)
@@ -455,10 +458,10 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = 20.54e6
+K_COVERAGE_TRAFFIC = 20.52e6
 # L1/TEX throughput of the same launch (% of its peak, elapsed) and the
 # sector hit rate: the traversal's record reads are served by L1.
-K_COVERAGE_L1 = {"l1tex_throughput_pct": 57.0, "l1tex_sector_hit_pct": 93.4, "lts_throughput_pct": 3.5,
+K_COVERAGE_L1 = {"l1tex_throughput_pct": 61.0, "l1tex_sector_hit_pct": 87.2, "lts_throughput_pct": 2.6,
                  "source": "profiles/k_coverage_city_1e6rays.md (ncu --set full, one launch)"}
 
 
@@ -1017,6 +1020,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--schedule", default="after_trace", choices=["after_trace", "after_paths"],
+                    help="when the coverage map starts on the second stream: after the path trace (beside the "
+                         "candidate refinement) or after compute_paths returns (beside CIR, H(f) and the VJPs)")
+    ap.add_argument("--side-blocks", type=int, default=0,
+                    help="resident blocks per SM of the coverage map traced on the second stream (0: as many as fit)")
     ap.add_argument("--sur-tx", type=int, default=40_000, help="surrogate training transmitter sites")
     ap.add_argument("--sur-rx", type=int, default=250, help="surrogate receivers per transmitter site")
     ap.add_argument("--sur-epochs", type=int, default=40)

@@ -263,7 +263,7 @@ int rt_destroy(rt_ctx* ctx) {
                       &ctx->path_seq, &ctx->path_pts, &ctx->path_depth, &ctx->path_len, &ctx->path_pair,
                       &ctx->sort_hist, &ctx->scan_buf, &ctx->counters, &ctx->status, &ctx->perm, &ctx->dirs,
                       &ctx->b_lbox, &ctx->b_cent, &ctx->b_info, &ctx->b_keys, &ctx->b_keys2, &ctx->b_vals,
-                      &ctx->b_vals2, &ctx->b_child, &ctx->b_pint, &ctx->b_pleaf, &ctx->b_ibox, &ctx->b_flag,
+                      &ctx->b_vals2, &ctx->b_child, &ctx->b_pint, &ctx->b_pleaf, &ctx->b_ibox, &ctx->b_flag, &ctx->b_ploc,
                       &ctx->b_dkeys, &ctx->b_dkeys2, &ctx->b_rank, &ctx->b_wroot, &ctx->wnodes})
         buf_free(*b);
     if (ctx->host_rb) cudaFreeHost(ctx->host_rb);

@@ -15,11 +15,13 @@
 //      and leaves walk to the root, the second child to arrive at a node
 //      computing its box (atomic arrival counters); or
 //   5. (default) mutual nearest neighbours of the Morton order merge by
-//      smallest merged surface area, round by round (PLOC, below);
+//      smallest merged surface area, round by round, in levels of chunks
+//      that stop early (PLOC, below);
 //   6. the radix tree's nodes are re-numbered by depth (level order); the
-//      clustering builder's own numbering already has parents before
-//      children and the top of the tree first. Either way the top levels
-//      form a prefix that traversal blocks stage in shared memory;
+//      clustering's merges are numbered in merge order from the top, so
+//      parents come before children and the top of the tree first. Either
+//      way the top levels form a prefix that traversal blocks can stage in
+//      shared memory;
 //   7. a device check that the result is a tree with children after their
 //      parents (the traversal loop relies on it instead of an iteration cap).
 #include <algorithm>
@@ -200,17 +202,36 @@ __global__ void k_karras(const uint64_t* __restrict__ k, int n, int2* __restrict
 // lower index, so the pair that is smallest in the order (area, lower index,
 // higher index) is always mutual and every round merges at least one pair.
 //
-// Each block clusters a chunk of PLOC_C consecutive clusters in shared
-// memory until one remains (one cluster per thread, double-buffered lists);
-// the chunk roots form the next, PLOC_C times shorter list, until a single
-// block produces the root. Merges across chunk borders are thereby
-// postponed to the next level. Internal nodes are numbered m-1-c for the
-// c-th merge in (level, chunk, round, position) order, so the root is node
-// 0, the layout the Karras builder produces; boxes come out of the merges
-// (leaf boxes padded as in the refit), so no refit pass is needed.
-constexpr int PLOC_C = 1024;
+// The list is clustered in levels. At every level but the last, each block
+// takes a chunk of PLOC_C1 consecutive clusters in shared memory (one
+// cluster per PLOC_C / PLOC_C1 threads in the first rounds) and merges until
+// at most PLOC_T1 remain; the survivors of all chunks, in order, form the
+// next level's list, so the merges across chunk borders wait only until
+// then. The last level takes the whole remaining list (at most PLOC_C
+// clusters) in one block down to the root. Merges are first written to
+// provisional slots (level, chunk, merge index within the chunk); the
+// emission numbers them m-1-c for the c-th merge in (level, chunk, round,
+// position) order, so the root is node 0 and every parent precedes its
+// children, the layout the Karras builder produces. Boxes come out of the
+// merges (leaf boxes padded as in the refit), so no refit pass is needed.
+constexpr int PLOC_C = 1024;   // threads of a level block; clusters of the last level
+constexpr int PLOC_C1 = 256;   // clusters of a chunk at the other levels
+constexpr int PLOC_T1 = 16;    // a chunk there merges until at most this many remain
 constexpr int PLOC_R = 16;
-constexpr int PLOC_W = PLOC_C / 32;   // warps of a chunk block (at most 32)
+constexpr int PLOC_W = PLOC_C / 32;   // warps of a level block (at most 32)
+constexpr int PLOC_MAX_LEVELS = 8;
+constexpr int PLOC_MAX_SEG = 4096;    // chunks of a level whose survivors the next level reads
+
+// One level of the clustering: K chunks of C clusters, each merging down to
+// `target` clusters (1 at the last level); provisional node slots from
+// prov_base, C - 1 per chunk; merge counts of its chunks at group_base.
+struct PlocLevel {
+    int C, target, K, prov_base, group_base;
+};
+struct PlocPlan {
+    int n_levels, n_groups, n_prov;
+    PlocLevel lv[PLOC_MAX_LEVELS];
+};
 
 __device__ __forceinline__ float half_area(float lx, float ly, float lz, float hx, float hy, float hz) {
     float dx = hx - lx, dy = hy - ly, dz = hz - lz;
@@ -231,31 +252,89 @@ __global__ void k_ploc_leaves(int n, const uint32_t* __restrict__ leaf_tri, cons
     id[i] = ~i;
 }
 
-__global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* __restrict__ in_box,
-                                                     const int* __restrict__ in_id, float* __restrict__ out_box,
-                                                     int* __restrict__ out_id, int stride, int id_base0, int m,
-                                                     int2* __restrict__ child, int* __restrict__ par_int,
-                                                     int* __restrict__ par_leaf, float* __restrict__ ibox,
-                                                     unsigned* __restrict__ status) {
+// Exclusive prefix of n ints (read past L1: written by other blocks) into
+// out[0..n] (out[n] = the total), by one whole block.
+__device__ void block_prefix(const int* in, int n, int* out) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int j0 = 0; j0 < n; j0 += blockDim.x) {
+        int v = j0 + t < n ? __ldcg(in + j0 + t) : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        if (w == 0) {
+            int u = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, u, o);
+                if (lane >= o) u += y;
+            }
+            if (lane < nw) wsum[lane] = u;   // inclusive over warps
+        }
+        __syncthreads();
+        const int base = carry + (w > 0 ? wsum[w - 1] : 0);
+        if (j0 + t < n) out[j0 + t + 1] = base + v;
+        __syncthreads();
+        if (t == 0) carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (t == 0) out[0] = 0;
+}
+
+// One level: block b clusters positions [b C, (b + 1) C) of the level's
+// list. The list is the concatenation, in order, of the previous level's
+// chunk outputs (segment j: in_pre[j+1] - in_pre[j] clusters at slot
+// j * in_seg of the input arrays), or, when in_pre is null, the first n_in
+// clusters. Survivors go to slot b * target of the output arrays, their
+// count to out_cnt[b] and the chunk's merge count to mcnt[group_base + b].
+// The last block to finish (ticket in *done) writes the exclusive prefix of
+// out_cnt to out_pre[0..K] for the next level and, at the last level, the
+// prefix of all merge counts to gpre[0..n_groups] for the emission.
+__global__ void __launch_bounds__(PLOC_C) k_ploc_level(PlocLevel lv, const float* __restrict__ in_box,
+                                                     const int* __restrict__ in_id, const int* __restrict__ in_pre,
+                                                     int n_seg, int in_seg, int n_in, float* __restrict__ out_box,
+                                                     int* __restrict__ out_id, int* __restrict__ out_cnt,
+                                                     int* __restrict__ out_pre, int* __restrict__ mcnt,
+                                                     int* __restrict__ gpre, int n_groups, unsigned* __restrict__ done,
+                                                     int stride, int2* __restrict__ child, int* __restrict__ par_int,
+                                                     float* __restrict__ ibox, unsigned* __restrict__ status) {
     extern __shared__ float ploc_sm[];
     float* sb = ploc_sm;                                          // [2][6][PLOC_C]
     int* sid = reinterpret_cast<int*>(ploc_sm + 12 * PLOC_C);    // [2][PLOC_C]
     int* snn = sid + 2 * PLOC_C;                                  // [PLOC_C]
     __shared__ unsigned wk[PLOC_W], wm[PLOC_W];
+    __shared__ bool last_block;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int c0 = blockIdx.x * PLOC_C;
-    const int L = min(PLOC_C, count - c0);
+    const int total = in_pre ? in_pre[n_seg] : n_in;
+    const int c0 = blockIdx.x * lv.C;
+    const int L = max(0, min(lv.C, total - c0));
     if (t < L) {
-        for (int q = 0; q < 6; q++) sb[q * PLOC_C + t] = in_box[q * (size_t)stride + c0 + t];
-        sid[t] = in_id[c0 + t];
+        const int p = c0 + t;
+        int src = p;
+        if (in_pre) {
+            int lo = 0, hi = n_seg - 1;   // the last segment j with in_pre[j] <= p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (in_pre[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            src = lo * in_seg + (p - in_pre[lo]);
+        }
+        for (int q = 0; q < 6; q++) sb[q * PLOC_C + t] = in_box[q * (size_t)stride + src];
+        sid[t] = in_id[src];
     }
     __syncthreads();
-    const int id_base = id_base0 + blockIdx.x * (PLOC_C - 1);
+    const int slot_base = lv.prov_base + blockIdx.x * (lv.C - 1);
     int cur = L, created = 0, buf = 0;
-    for (int round = 0; cur > 1; round++) {
+    for (int round = 0; cur > lv.target; round++) {
         if (round >= PLOC_C) {   // unreachable for finite boxes
             if (t == 0) atomicOr(status, 1u);
-            return;
+            cur = 0;   // no survivors: the later levels stay consistent, the build fails
+            break;
         }
         const float* rb = sb + buf * 6 * PLOC_C;
         const int* ri = sid + buf * PLOC_C;
@@ -329,14 +408,14 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* _
             const int kpos = (w > 0 ? (int)wk[w - 1] : 0) + __popc(bk & lt);
             if (merge) {
                 const int mpos = (w > 0 ? (int)wm[w - 1] : 0) + __popc(bm & lt);
-                const int node = m - 1 - (id_base + created + mpos);
+                const int node = slot_base + created + mpos;   // provisional slot
                 float u[6] = {fminf(lx, rb[j]), fminf(ly, rb[PLOC_C + j]), fminf(lz, rb[2 * PLOC_C + j]),
                               fmaxf(hx, rb[3 * PLOC_C + j]), fmaxf(hy, rb[4 * PLOC_C + j]),
                               fmaxf(hz, rb[5 * PLOC_C + j])};
                 const int ca = ri[t], cb = ri[j];
                 child[node] = make_int2(ca, cb);
-                if (ca < 0) par_leaf[~ca] = node; else par_int[ca] = node;
-                if (cb < 0) par_leaf[~cb] = node; else par_int[cb] = node;
+                if (ca >= 0) par_int[ca] = node;
+                if (cb >= 0) par_int[cb] = node;
                 for (int q = 0; q < 6; q++) { ibox[6 * (size_t)node + q] = u[q]; wb[q * PLOC_C + kpos] = u[q]; }
                 wi[kpos] = node;
             } else {
@@ -348,16 +427,33 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_chunk(int count, const float* _
         __syncthreads();
         if (M == 0) {   // unreachable for finite boxes
             if (t == 0) atomicOr(status, 1u);
-            return;
+            cur = 0;
+            break;
         }
         created += M;
         cur = K;
         buf ^= 1;
     }
-    if (t == 0 && L > 0) {
-        for (int q = 0; q < 6; q++) out_box[q * (size_t)stride + blockIdx.x] = sb[(buf * 6 + q) * PLOC_C];
-        out_id[blockIdx.x] = sid[buf * PLOC_C];
-        if (gridDim.x == 1) par_int[0] = -1;   // one chunk left: its cluster is the root
+    // survivors, in order, to this chunk's output segment
+    if (t < cur) {
+        const size_t o = (size_t)blockIdx.x * lv.target + t;
+        for (int q = 0; q < 6; q++) out_box[q * (size_t)stride + o] = sb[(buf * 6 + q) * PLOC_C + t];
+        out_id[o] = sid[buf * PLOC_C + t];
+    }
+    if (t == 0) {
+        out_cnt[blockIdx.x] = cur;
+        mcnt[lv.group_base + blockIdx.x] = created;
+        // the last level leaves one cluster: the root (an internal node
+        // whenever the list had two or more clusters)
+        if (lv.target == 1 && cur == 1 && sid[buf * PLOC_C] >= 0) par_int[sid[buf * PLOC_C]] = -1;
+        __threadfence();
+        last_block = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last_block) {
+        __threadfence();
+        block_prefix(out_cnt, gridDim.x, out_pre);
+        if (lv.target == 1) block_prefix(mcnt, n_groups, gpre);
     }
 }
 
@@ -391,14 +487,15 @@ __global__ void k_refit(int n, const uint32_t* __restrict__ leaf_tri, const floa
 }
 
 // Level-order key (depth << shift) | node, depth clamped to 255 in the key
-// (a deeper tree is rejected by the stack check anyway).
+// (a deeper tree is rejected by the stack check anyway); keys may be null
+// (depth only). Slots whose parent is negative count as roots.
 __global__ void k_depth(int m, int shift, const int* __restrict__ par_int, uint64_t* __restrict__ keys,
                         int* __restrict__ maxdepth) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     int d = 0;
     for (int p = par_int[i]; p >= 0 && d < m; p = par_int[p]) d++;
-    keys[i] = ((uint64_t)min(d, 255) << shift) | (uint32_t)i;
+    if (keys) keys[i] = ((uint64_t)min(d, 255) << shift) | (uint32_t)i;
     atomicMax(maxdepth, d);
 }
 
@@ -456,25 +553,44 @@ __global__ void k_check_degree(int m, int n_leaves, const int* __restrict__ inde
     if (indeg[i] != (i == 0 ? 0 : 1)) atomicOr(bad, 1u);
 }
 
-// Nodes in the clustering's own numbering (node m-1-c for the c-th merge:
-// parents after children, root 0, the last merges, i.e. the top of the
-// tree, first): child indices are kept as they are.
-__global__ void k_emit_direct(int m, const int2* __restrict__ child, const float* __restrict__ ibox,
-                              const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri, float pad,
-                              float4* __restrict__ nodes) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
-    int2 c = child[k];
+// Final number of provisional slot s (-1: a slot no merge used): node
+// m-1-c for the c-th merge in (level, chunk, merge) order. gpre[g] = merges
+// of the groups (level chunks) before group g.
+__device__ __forceinline__ int ploc_final(const PlocPlan& pl, const int* gpre, const int* mcnt, int m, int s) {
+    for (int l = 0; l < pl.n_levels; l++) {
+        const PlocLevel& lv = pl.lv[l];
+        if (s < lv.prov_base + lv.K * (lv.C - 1)) {
+            const int b = (s - lv.prov_base) / (lv.C - 1), loc = (s - lv.prov_base) - b * (lv.C - 1);
+            const int g = lv.group_base + b;
+            return loc < mcnt[g] ? m - 1 - (gpre[g] + loc) : -1;
+        }
+    }
+    return -1;
+}
+
+// Nodes from the clustering's provisional slots, in the final numbering
+// (ploc_final): parents before children, root 0. One thread per slot.
+__global__ void k_emit_ploc(PlocPlan pl, const int* __restrict__ mcnt, const int* __restrict__ gpre, int m,
+                            const int2* __restrict__ child, const float* __restrict__ ibox,
+                            const float* __restrict__ lbox, const uint32_t* __restrict__ leaf_tri, float pad,
+                            float4* __restrict__ nodes, unsigned* __restrict__ bad) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0 && gpre[pl.n_groups] != m) atomicOr(bad, 1u);   // every internal node made exactly once
+    if (s >= pl.n_prov) return;
+    const int k = ploc_final(pl, gpre, mcnt, m, s);
+    if (k < 0 || k >= m) return;
+    const int2 c = child[s];
     float a[6], b[6];
-    if (c.x < 0) { for (int q = 0; q < 6; q++) a[q] = lbox[6 * (size_t)leaf_tri[~c.x] + q]; for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; } }
-    else { for (int q = 0; q < 6; q++) a[q] = ibox[6 * (size_t)c.x + q]; }
-    if (c.y < 0) { for (int q = 0; q < 6; q++) b[q] = lbox[6 * (size_t)leaf_tri[~c.y] + q]; for (int q = 0; q < 3; q++) { b[q] -= pad; b[3 + q] += pad; } }
-    else { for (int q = 0; q < 6; q++) b[q] = ibox[6 * (size_t)c.y + q]; }
+    int ca = c.x, cb = c.y;
+    if (ca < 0) { for (int q = 0; q < 6; q++) a[q] = lbox[6 * (size_t)leaf_tri[~ca] + q]; for (int q = 0; q < 3; q++) { a[q] -= pad; a[3 + q] += pad; } }
+    else { for (int q = 0; q < 6; q++) a[q] = ibox[6 * (size_t)ca + q]; ca = ploc_final(pl, gpre, mcnt, m, ca); }
+    if (cb < 0) { for (int q = 0; q < 6; q++) b[q] = lbox[6 * (size_t)leaf_tri[~cb] + q]; for (int q = 0; q < 3; q++) { b[q] -= pad; b[3 + q] += pad; } }
+    else { for (int q = 0; q < 6; q++) b[q] = ibox[6 * (size_t)cb + q]; cb = ploc_final(pl, gpre, mcnt, m, cb); }
     float4* p = nodes + 4 * (size_t)k;
     p[0] = make_float4(a[0], a[1], a[2], a[3]);
     p[1] = make_float4(a[4], a[5], b[0], b[1]);
     p[2] = make_float4(b[2], b[3], b[4], b[5]);
-    p[3] = make_float4(__int_as_float(c.x), __int_as_float(c.y), 0.0f, 0.0f);
+    p[3] = make_float4(__int_as_float(ca), __int_as_float(cb), 0.0f, 0.0f);
 }
 
 __global__ void k_leaf_tris(int n, const uint32_t* __restrict__ leaf_tri, const float4* __restrict__ tris_o,
@@ -859,15 +975,35 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
     } else {
         const int T = n;   // the hierarchy's triangles
         const int gT = (T + B - 1) / B;
-        RT_TRY(buf_reserve(ctx->b_child, sizeof(int2) * m));
-        RT_TRY(buf_reserve(ctx->b_pint, sizeof(int) * m));
+        // the clustering's levels: chunks of PLOC_C1 merged down to PLOC_T1
+        // clusters until at most PLOC_C remain, then one block to the root
+        PlocPlan pl{};
+        if (ctx->bvh_builder == RT_BVH_PLOC) {
+            int U = T;   // clusters entering the level, at most
+            while (true) {
+                if (pl.n_levels == PLOC_MAX_LEVELS) return set_err(ctx, RT_ERR_CAPACITY, "BVH build: too many levels");
+                PlocLevel lv;
+                if (U <= PLOC_C) lv = {PLOC_C, 1, 1, pl.n_prov, pl.n_groups};
+                else lv = {PLOC_C1, PLOC_T1, (U + PLOC_C1 - 1) / PLOC_C1, pl.n_prov, pl.n_groups};
+                pl.lv[pl.n_levels++] = lv;
+                pl.n_prov += lv.K * (lv.C - 1);
+                pl.n_groups += lv.K;
+                if (lv.target == 1) break;
+                U = lv.K * lv.target;
+            }
+        }
+        const int slots = std::max(m, pl.n_prov);   // internal nodes, or the clustering's provisional slots
+        RT_TRY(buf_reserve(ctx->b_child, sizeof(int2) * slots));
+        RT_TRY(buf_reserve(ctx->b_pint, sizeof(int) * slots));
         RT_TRY(buf_reserve(ctx->b_pleaf, sizeof(int) * T));
-        RT_TRY(buf_reserve(ctx->b_ibox, sizeof(float) * 6 * (size_t)m));
+        RT_TRY(buf_reserve(ctx->b_ibox, sizeof(float) * 6 * (size_t)slots));
         int2* child = bp<int2>(ctx->b_child);
         int* pint = bp<int>(ctx->b_pint);
         int* pleaf = bp<int>(ctx->b_pleaf);
         float* ibox = bp<float>(ctx->b_ibox);
         int gm = (m + B - 1) / B;
+        const int* gpre = nullptr;
+        const int* mcnt = nullptr;
         if (ctx->bvh_builder == RT_BVH_PLOC) {
             // two cluster lists (six box planes + ids each)
             RT_TRY(buf_reserve(ctx->b_flag, (sizeof(float) * 12 + sizeof(int) * 2) * (size_t)T));
@@ -875,25 +1011,45 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
             float* boxB = boxA + 6 * (size_t)T;
             int* idA = reinterpret_cast<int*>(boxB + 6 * (size_t)T);
             int* idB = idA + T;
+            // counts: per level a ticket, the chunks' survivor counts and their
+            // prefix; per chunk its merge count, and their prefix
+            size_t n_ints = 2 * (size_t)pl.n_groups + 1;
+            for (int l = 0; l < pl.n_levels; l++) n_ints += 1 + 2 * (size_t)pl.lv[l].K + 1;
+            RT_TRY(buf_reserve(ctx->b_ploc, sizeof(int) * n_ints));
+            RT_TRY(cudaMemsetAsync(ctx->b_ploc.p, 0, sizeof(int) * n_ints, st));
+            int* cnt = bp<int>(ctx->b_ploc);
+            int* mc = cnt;
+            int* gp = mc + pl.n_groups;
+            int* next = gp + pl.n_groups + 1;
+            mcnt = mc;
+            gpre = gp;
+            // no parent yet: negative
+            RT_TRY(cudaMemsetAsync(pint, 0xFF, sizeof(int) * (size_t)pl.n_prov, st));
             prof_begin(ctx, "k_ploc_leaves");
             k_ploc_leaves<<<gT, B, 0, st>>>(T, leaf_tri, lbox, pad, boxA, idA);
             prof_end(ctx);
             RT_TRY(cudaGetLastError());
             const size_t smem = (sizeof(float) * 12 + sizeof(int) * 3) * PLOC_C;
-            RT_TRY(ensure_smem_attr((const void*)k_ploc_chunk, smem));
-            int count = T, id_base = 0;
+            RT_TRY(ensure_smem_attr((const void*)k_ploc_level, smem));
             float *bi = boxA, *bo = boxB;
             int *ii = idA, *io = idB;
-            while (true) {
-                const int K = (count + PLOC_C - 1) / PLOC_C;
-                prof_begin(ctx, "k_ploc_chunk");
-                k_ploc_chunk<<<K, PLOC_C, smem, st>>>(count, bi, ii, bo, io, T, id_base, m, child, pint, pleaf,
-                                                      ibox, info + 14);
+            const int* in_pre = nullptr;
+            int n_seg = 0, in_seg = 0;
+            for (int l = 0; l < pl.n_levels; l++) {
+                const PlocLevel& lv = pl.lv[l];
+                unsigned* done = reinterpret_cast<unsigned*>(next);
+                int* out_cnt = next + 1;
+                int* out_pre = out_cnt + lv.K;
+                next = out_pre + lv.K + 1;
+                prof_begin(ctx, lv.target == 1 ? "k_ploc_level_top" : "k_ploc_level");
+                k_ploc_level<<<lv.K, PLOC_C, smem, st>>>(lv, bi, ii, in_pre, n_seg, in_seg, T, bo, io, out_cnt,
+                                                         out_pre, mc, gp, pl.n_groups, done, T, child, pint, ibox,
+                                                         info + 14);
                 prof_end(ctx);
                 RT_TRY(cudaGetLastError());
-                id_base += count - K;
-                if (K == 1) break;
-                count = K;
+                in_pre = out_pre;
+                n_seg = lv.K;
+                in_seg = lv.target;
                 std::swap(bi, bo);
                 std::swap(ii, io);
             }
@@ -918,17 +1074,24 @@ int bvh_build(rt_ctx* ctx, const float* verts, int64_t n_tris) {
         int shift = 1;
         while ((1ll << shift) < m) shift++;
         const uint32_t mask = (uint32_t)((1ull << shift) - 1);
-        prof_begin(ctx, "k_depth");
-        k_depth<<<gm, B, 0, st>>>(m, shift, pint, dkeys, reinterpret_cast<int*>(info + 13));
-        prof_end(ctx);
-        RT_TRY(cudaGetLastError());
         if (ctx->bvh_builder == RT_BVH_PLOC) {
-            // the clustering's numbering already puts parents before children
-            // and the top of the tree first
+            // depths over the provisional slots (unused ones have no parent)
+            prof_begin(ctx, "k_depth");
+            k_depth<<<(pl.n_prov + B - 1) / B, B, 0, st>>>(pl.n_prov, shift, pint, nullptr,
+                                                             reinterpret_cast<int*>(info + 13));
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
+            // the final numbering puts parents before children and the top of
+            // the tree first
             prof_begin(ctx, "k_emit");
-            k_emit_direct<<<gm, B, 0, st>>>(m, child, ibox, lbox, leaf_tri, pad, bp<float4>(ctx->nodes));
+            k_emit_ploc<<<(pl.n_prov + B - 1) / B, B, 0, st>>>(pl, mcnt, gpre, m, child, ibox, lbox, leaf_tri, pad,
+                                                               bp<float4>(ctx->nodes), info + 15);
             prof_end(ctx);
         } else {
+            prof_begin(ctx, "k_depth");
+            k_depth<<<gm, B, 0, st>>>(m, shift, pint, dkeys, reinterpret_cast<int*>(info + 13));
+            prof_end(ctx);
+            RT_TRY(cudaGetLastError());
             // level order: sort internal nodes by (depth, id)
             RT_TRY(radix_sort64(ctx, dkeys, bp<uint64_t>(ctx->b_dkeys2), nullptr, nullptr, m, shift + 8));
             prof_begin(ctx, "k_rank");

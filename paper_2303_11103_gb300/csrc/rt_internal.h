@@ -85,7 +85,7 @@ struct rt_ctx {
     int64_t path_cap = 0;
 
     // BVH build scratch (kept between builds: no allocation per rt_load_scene)
-    DevBuf b_lbox, b_cent, b_info, b_keys, b_keys2, b_vals, b_vals2, b_child, b_pint, b_pleaf, b_ibox, b_flag,
+    DevBuf b_lbox, b_cent, b_info, b_keys, b_keys2, b_vals, b_vals2, b_child, b_pint, b_pleaf, b_ibox, b_flag, b_ploc,
         b_dkeys, b_dkeys2, b_rank, b_wroot;
 
     // scratch
