@@ -112,6 +112,20 @@ int rt_set_bvh_builder(rt_ctx* ctx, int32_t builder);
  * RT_ERR_INVALID_ARG for another width.
  */
 int rt_set_bvh_width(rt_ctx* ctx, int32_t width);
+/*
+ * The binary hierarchy of the last rt_load_scene, for inspection (not in the
+ * paper; tests and measurement read it): node k = 16 float32 (HOST out,
+ * nodes [cap*16]): child 0 box (lo xyz, hi xyz), child 1 box (lo xyz, hi
+ * xyz), then the two child references as int32 bit patterns (>= 0:
+ * internal node, < 0: leaf ~j, j the leaf's position in Morton order), then
+ * two unused words. Node 0 is the root; every child has a larger index
+ * than its parent. *n_nodes receives the node count (0 when the scene has
+ * fewer than two triangles in the hierarchy); with nodes null or cap too
+ * small only the count is written. The large triangles tested directly by
+ * every query are not in the hierarchy. Synchronises the context's stream.
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_CUDA.
+ */
+int rt_get_bvh(rt_ctx* ctx, float* nodes, int64_t cap, int64_t* n_nodes);
 
 /*
  * Duplicate removal of the SBR candidate keys in rt_compute_paths (Sec. II-B:

@@ -353,6 +353,18 @@ int rt_set_bvh_width(rt_ctx* ctx, int32_t width) {
     return RT_OK;
 }
 
+int rt_get_bvh(rt_ctx* ctx, float* nodes, int64_t cap, int64_t* n_nodes) {
+    CHECK_CTX(ctx);
+    NO_CAPTURE(ctx, "get_bvh");
+    if (!n_nodes || cap < 0) return set_err(ctx, RT_ERR_INVALID_ARG, "get_bvh: bad arguments");
+    const int64_t n = ctx->has_scene ? ctx->n_nodes : 0;
+    *n_nodes = n;
+    if (!nodes || cap < n || n == 0) return RT_OK;
+    RT_TRY(cudaMemcpyAsync(nodes, ctx->nodes.p, sizeof(float4) * 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    RT_TRY(cudaStreamSynchronize(ctx->stream));
+    return RT_OK;
+}
+
 int rt_set_dedup(rt_ctx* ctx, int32_t mode) {
     CHECK_CTX(ctx);
     if (mode != RT_DEDUP_HASH && mode != RT_DEDUP_SORT) return set_err(ctx, RT_ERR_INVALID_ARG, "unknown dedup mode");

@@ -352,30 +352,34 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_level(PlocLevel lv, const float
             // shares are combined by (area, position), which keeps the
             // sequential scan's choice (the lowest position of the smallest
             // area), so the tree does not depend on G
-            int G = 1;
-            while (G < 32 && 2 * G * cur <= PLOC_C) G *= 2;
-            const int ci = t / G, part = t - ci * G;
+            int lg = 0;   // G = 2^lg lanes per cluster
+            while (lg < 5 && (cur << (lg + 1)) <= PLOC_C) lg++;
+            const int G = 1 << lg;
+            const int ci = t >> lg, part = t & (G - 1);
             float best = __int_as_float(0x7f800000);
             int bj = 0x7fffffff;
-            if (ci < cur) {
-                const float bx0 = rb[ci], by0 = rb[PLOC_C + ci], bz0 = rb[2 * PLOC_C + ci];
-                const float bx1 = rb[3 * PLOC_C + ci], by1 = rb[4 * PLOC_C + ci], bz1 = rb[5 * PLOC_C + ci];
-                const int per = (2 * PLOC_R) / G;   // window offsets -R..-1, 1..R in order, `per` per lane
-                for (int q = part * per; q < (part + 1) * per; q++) {
-                    const int j = ci + (q < PLOC_R ? q - PLOC_R : q - PLOC_R + 1);
-                    if (j < 0 || j >= cur) continue;
-                    float c = half_area(fminf(bx0, rb[j]), fminf(by0, rb[PLOC_C + j]), fminf(bz0, rb[2 * PLOC_C + j]),
-                                        fmaxf(bx1, rb[3 * PLOC_C + j]), fmaxf(by1, rb[4 * PLOC_C + j]),
-                                        fmaxf(bz1, rb[5 * PLOC_C + j]));
-                    if (c < best) { best = c; bj = j; }
+            // warps without a cluster skip the search (warp-uniform)
+            if ((w << 5) < (cur << lg)) {
+                if (ci < cur) {
+                    const float bx0 = rb[ci], by0 = rb[PLOC_C + ci], bz0 = rb[2 * PLOC_C + ci];
+                    const float bx1 = rb[3 * PLOC_C + ci], by1 = rb[4 * PLOC_C + ci], bz1 = rb[5 * PLOC_C + ci];
+                    const int per = (2 * PLOC_R) >> lg;   // window offsets -R..-1, 1..R in order, `per` per lane
+                    for (int q = part * per; q < (part + 1) * per; q++) {
+                        const int j = ci + (q < PLOC_R ? q - PLOC_R : q - PLOC_R + 1);
+                        if (j < 0 || j >= cur) continue;
+                        float c = half_area(fminf(bx0, rb[j]), fminf(by0, rb[PLOC_C + j]), fminf(bz0, rb[2 * PLOC_C + j]),
+                                            fmaxf(bx1, rb[3 * PLOC_C + j]), fmaxf(by1, rb[4 * PLOC_C + j]),
+                                            fmaxf(bz1, rb[5 * PLOC_C + j]));
+                        if (c < best) { best = c; bj = j; }
+                    }
                 }
+                for (int o = G >> 1; o > 0; o >>= 1) {   // G is the same for the whole block
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                    if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+                }
+                if (ci < cur && part == 0) snn[ci] = bj != 0x7fffffff ? bj : (ci > 0 ? ci - 1 : 1);
             }
-            for (int o = G >> 1; o > 0; o >>= 1) {   // G is the same for the whole block
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
-            }
-            if (ci < cur && part == 0) snn[ci] = bj != 0x7fffffff ? bj : (ci > 0 ? ci - 1 : 1);
         }
         __syncthreads();
         int j = -1;
@@ -386,8 +390,13 @@ __global__ void __launch_bounds__(PLOC_C) k_ploc_level(PlocLevel lv, const float
             keep = !(mutual && j < t);
             merge = mutual && t < j;
         }
-        // block-wide exclusive ranks of keep and merge
-        const unsigned bk = __ballot_sync(0xffffffffu, keep), bm = __ballot_sync(0xffffffffu, merge);
+        // block-wide exclusive ranks of keep and merge (warps past the
+        // clusters count zero)
+        unsigned bk = 0u, bm = 0u;
+        if ((w << 5) < cur) {
+            bk = __ballot_sync(0xffffffffu, keep);
+            bm = __ballot_sync(0xffffffffu, merge);
+        }
         if (lane == 0) { wk[w] = __popc(bk); wm[w] = __popc(bm); }
         __syncthreads();
         if (w == 0) {

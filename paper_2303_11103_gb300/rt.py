@@ -69,6 +69,7 @@ def lib():
             "rt_set_materials": [vp, vp, i32],
             "rt_set_bvh_builder": [vp, i32],
             "rt_set_bvh_width": [vp, i32],
+            "rt_get_bvh": [vp, vp, i64, ctypes.POINTER(ctypes.c_int64)],
             "rt_set_dedup": [vp, i32],
             "rt_set_tx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna)],
             "rt_set_rx": [vp, vp, vp, i32, ctypes.POINTER(rt_antenna), vp],
@@ -210,6 +211,16 @@ def rt_set_bvh_builder(ctx, builder):
 
 def rt_set_bvh_width(ctx, width):
     _check(ctx, lib().rt_set_bvh_width(ctx, int(width)))
+
+
+def rt_get_bvh(ctx):
+    """The binary hierarchy of the last load_scene: float32 [n_nodes, 16]
+    (child boxes lo/hi, then the child references as int32 bit patterns)."""
+    n = ctypes.c_int64()
+    _check(ctx, lib().rt_get_bvh(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 16), np.float32)
+    _check(ctx, lib().rt_get_bvh(ctx, out.ctypes.data_as(ctypes.c_void_p), n.value, ctypes.byref(n)))
+    return out[:n.value]
 
 
 DEDUP_HASH, DEDUP_SORT = 0, 1
