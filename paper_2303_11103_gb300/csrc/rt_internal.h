@@ -83,6 +83,7 @@ struct rt_ctx {
     DevBuf path_key, path_key_alt, path_cap_dummy;
     DevBuf path_off, path_seq, path_pts, path_depth, path_len, path_pair;
     int64_t path_cap = 0;
+    int64_t hash_hint = 0;   // hash slots the last compute_paths needed (0: read the key count first)
 
     // BVH build scratch (kept between builds: no allocation per rt_load_scene)
     DevBuf b_lbox, b_cent, b_info, b_keys, b_keys2, b_vals, b_vals2, b_child, b_pint, b_pleaf, b_ibox, b_flag, b_ploc,

@@ -90,8 +90,12 @@ struct KeyFmt {
     }
 };
 
-__global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, int n_tx, KeyFmt f) {
+// LOS keys after the shooting keys: at `at`, or at *at_dev when given (the
+// shooting pass's key count, still on the device)
+__global__ void k_write_los(uint64_t* keys, uint32_t* vals, int64_t at, const unsigned long long* at_dev, int n_tx,
+                            KeyFmt f) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (at_dev) at = (int64_t)*at_dev;
     if (t < n_tx) {
         keys[at + t] = (uint64_t)t << f.tx_shift;
         vals[at + t] = 0xFFFFFFFFu;
@@ -144,10 +148,21 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     return x;
 }
 
+// n_dev (optional): the key count is *n_dev + n on the device; when it
+// exceeds cap (a table sized from an earlier call), nothing is inserted and
+// *overflow is set, so that the host repeats the pass with the count read.
 __global__ void k_hash_insert(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+                              const unsigned long long* __restrict__ n_dev, int64_t cap, unsigned* __restrict__ overflow,
                               unsigned long long* __restrict__ tab, unsigned* __restrict__ wit, uint64_t mask) {
     // rays of one warp are coherent, so equal keys are merged in the warp first
     // (one table access and one atomicMin per distinct key of the warp)
+    if (n_dev) {
+        n += (int64_t)*n_dev;
+        if (n > cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(overflow, 1u);
+            return;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
@@ -619,6 +634,7 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
     uint32_t* vals = bp<uint32_t>(ctx->vals);
     RT_TRY(cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), st));
     int64_t nhit = 0;  // candidate keys the rays produced (one per hit)
+    bool fast = false;  // hash table sized from the previous call's key count
     if (refl) {
         int32_t* hits = nullptr;
         if (ctx->recorded_rays) {
@@ -632,58 +648,101 @@ int compute_paths_impl(rt_ctx* ctx, int D, int64_t N, uint32_t flags, int64_t* o
         // that it shares the GPU with the refinement below, not with the trace
         e = side_launch(ctx);
         if (e) return e;
-        RT_TRY(cudaMemcpyAsync(ctx->host_rb, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS,
-                               sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        RT_TRY(cudaStreamSynchronize(st));
-        nhit = (int64_t)ctx->host_rb[0];
+        // the key count is read here only when no earlier call sized the
+        // hash table; otherwise it stays on the device until the hash pass
+        fast = ctx->dedup == RT_DEDUP_HASH && ctx->key_bits < 64 && ctx->hash_hint > 0;
+        if (!fast) {
+            RT_TRY(cudaMemcpyAsync(ctx->host_rb, bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS,
+                                   sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            RT_TRY(cudaStreamSynchronize(st));
+            nhit = (int64_t)ctx->host_rb[0];
+        }
     }
-    const int64_t nkeys = nhit + (los ? ctx->n_tx : 0);
+    const int64_t extra = los ? ctx->n_tx : 0;
+    const unsigned long long* nhit_dev = bp<unsigned long long>(ctx->counters) + RT_CNT_KEYS;
+    int64_t nkeys = nhit + extra;   // with fast: known after the hash pass
     if (los) {
         prof_begin(ctx, "k_write_los");
-        k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nhit, ctx->n_tx, f);
+        k_write_los<<<(ctx->n_tx + 255) / 256, 256, 0, st>>>(keys, vals, nhit, fast ? nhit_dev : nullptr, ctx->n_tx,
+                                                            f);
         prof_end(ctx);
         RT_TRY(cudaGetLastError());
     }
-    const int64_t Ucap = std::max<int64_t>(nkeys, 1);
-    RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * Ucap));
-    RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * Ucap));
     RT_TRY(buf_reserve(ctx->cand_off, sizeof(int64_t) * (ctx->n_tx + 1)));
-    RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * Ucap));
     const uint32_t* Ud = nullptr;   // device candidate count
-    int64_t S = 1024;   // hash table slots: a power of two, at least twice the keys
-    while (S < 2 * nkeys) S <<= 1;
+    // hash table slots: a power of two, at least twice the keys
+    auto slots_for = [](int64_t n) {
+        int64_t S = 1024;
+        while (S < 2 * n) S <<= 1;
+        return S;
+    };
     // beyond 2^29 slots (6 GB) the table would outgrow the sort's scratch: sort instead
-    if (ctx->key_bits < 64 && ctx->dedup == RT_DEDUP_HASH && S <= (1ll << 29)) {
+    bool use_hash = ctx->key_bits < 64 && ctx->dedup == RT_DEDUP_HASH && (fast || slots_for(nkeys) <= (1ll << 29));
+    if (use_hash) {
         DevBuf& cnt = ctx->htab_cnt;
-        // duplicate removal by hashing, then a sort of the distinct keys only
-        RT_TRY(buf_reserve(ctx->htab_key, sizeof(uint64_t) * S));
-        RT_TRY(buf_reserve(ctx->htab_wit, sizeof(uint32_t) * S));
         RT_TRY(buf_reserve(cnt, sizeof(uint32_t) * 4));
-        RT_TRY(cudaMemsetAsync(ctx->htab_key.p, 0xFF, sizeof(uint64_t) * S, st));
-        RT_TRY(cudaMemsetAsync(ctx->htab_wit.p, 0xFF, sizeof(uint32_t) * S, st));
-        RT_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * 4, st));
-        uint32_t* cntp = bp<uint32_t>(cnt);
-        if (nkeys > 0) {
-            prof_begin(ctx, "k_hash_insert");
-            k_hash_insert<<<(unsigned)std::min<int64_t>((nkeys + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
-                keys, vals, nkeys, bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit),
-                (uint64_t)(S - 1));
-            prof_end(ctx);
-            RT_TRY(cudaGetLastError());
-            prof_begin(ctx, "k_hash_compact");
-            k_hash_compact<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
-                bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit), S, bp<uint64_t>(ctx->cand_key),
-                bp<uint32_t>(ctx->cand_wit), cntp);
-            prof_end(ctx);
-            RT_TRY(cudaGetLastError());
+        uint32_t* cntp = bp<uint32_t>(cnt);   // [0] distinct keys, [1] overflow of a table sized beforehand
+        int64_t U = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            const int64_t S = fast ? ctx->hash_hint : slots_for(nkeys);
+            const int64_t ucap = std::max<int64_t>(fast ? S / 2 : nkeys, 1);
+            RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * ucap));
+            RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * ucap));
+            RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * ucap));
+            // duplicate removal by hashing, then a sort of the distinct keys only
+            RT_TRY(buf_reserve(ctx->htab_key, sizeof(uint64_t) * S));
+            RT_TRY(buf_reserve(ctx->htab_wit, sizeof(uint32_t) * S));
+            RT_TRY(cudaMemsetAsync(ctx->htab_key.p, 0xFF, sizeof(uint64_t) * S, st));
+            RT_TRY(cudaMemsetAsync(ctx->htab_wit.p, 0xFF, sizeof(uint32_t) * S, st));
+            RT_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(uint32_t) * 4, st));
+            if (fast || nkeys > 0) {
+                const int64_t span = fast ? S / 2 : nkeys;   // keys at most
+                prof_begin(ctx, "k_hash_insert");
+                k_hash_insert<<<(unsigned)std::min<int64_t>((span + 255) / 256, 8 * ctx->num_sms), 256, 0, st>>>(
+                    keys, vals, fast ? extra : nkeys, fast ? nhit_dev : nullptr, S / 2, cntp + 1,
+                    bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit), (uint64_t)(S - 1));
+                prof_end(ctx);
+                RT_TRY(cudaGetLastError());
+                prof_begin(ctx, "k_hash_compact");
+                k_hash_compact<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(
+                    bp<unsigned long long>(ctx->htab_key), bp<unsigned>(ctx->htab_wit), S,
+                    bp<uint64_t>(ctx->cand_key), bp<uint32_t>(ctx->cand_wit), cntp);
+                prof_end(ctx);
+                RT_TRY(cudaGetLastError());
+            }
+            // one read: distinct keys and overflow, and the shooting pass's key count
+            RT_TRY(cudaMemcpyAsync(ctx->host_rb, cntp, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            if (fast)
+                RT_TRY(cudaMemcpyAsync(ctx->host_rb + 1, nhit_dev, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            RT_TRY(cudaStreamSynchronize(st));
+            U = reinterpret_cast<uint32_t*>(ctx->host_rb)[0];
+            const bool overflow = reinterpret_cast<uint32_t*>(ctx->host_rb)[1] != 0;
+            if (fast) {
+                nhit = (int64_t)ctx->host_rb[1];
+                nkeys = nhit + extra;
+                fast = false;
+                if (overflow) {
+                    // the table was too small: again, sized by the count just
+                    // read (or by sorting, for a table beyond 2^29 slots)
+                    use_hash = slots_for(nkeys) <= (1ll << 29);
+                    if (use_hash) continue;
+                }
+            }
+            break;
         }
-        RT_TRY(cudaMemcpyAsync(ctx->host_rb, cntp, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        RT_TRY(cudaStreamSynchronize(st));
-        const int64_t U = *reinterpret_cast<uint32_t*>(ctx->host_rb);
-        RT_TRY(radix_sort64(ctx, bp<uint64_t>(ctx->cand_key), bp<uint64_t>(ctx->keys_alt), bp<uint32_t>(ctx->cand_wit),
-                            bp<uint32_t>(ctx->vals_alt), U, ctx->key_bits));
-        Ud = cntp;
-    } else {
+        if (use_hash) {
+            ctx->hash_hint = slots_for(nkeys);
+            RT_TRY(radix_sort64(ctx, bp<uint64_t>(ctx->cand_key), bp<uint64_t>(ctx->keys_alt),
+                                bp<uint32_t>(ctx->cand_wit), bp<uint32_t>(ctx->vals_alt), U, ctx->key_bits));
+            Ud = cntp;
+        }
+    }
+    if (!use_hash) {
+        ctx->hash_hint = 0;
+        const int64_t ucap = std::max<int64_t>(nkeys, 1);
+        RT_TRY(buf_reserve(ctx->cand_key, sizeof(uint64_t) * ucap));
+        RT_TRY(buf_reserve(ctx->cand_wit, sizeof(uint32_t) * ucap));
+        RT_TRY(buf_reserve(ctx->cand_img, sizeof(float) * 3 * f.D * ucap));
         RT_TRY(radix_sort64(ctx, keys, bp<uint64_t>(ctx->keys_alt), vals, bp<uint32_t>(ctx->vals_alt), nkeys,
                             ctx->key_bits));
         // duplicate removal of the sorted keys
