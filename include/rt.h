@@ -408,8 +408,15 @@ int rt_coverage_map_accumulate(rt_ctx* ctx, const rt_grid* g, int32_t max_depth,
  *     next rt_compute_paths, beside its candidate refinement and the calls
  *     after it, instead of competing with the trace for the SMs; a call
  *     that needs the map earlier starts it at that point.
- *   blocks_per_sm caps the map's resident blocks per SM (0 = as many as
- *     fit), leaving room for the other stream's kernels.
+ *   blocks_per_sm 0 (the default): the map runs as short-lived blocks (each
+ *     warp traces one refill of 32 rays, then its block ends), so that SM
+ *     slots keep freeing while it traces and kernels of the context's
+ *     stream take them first when that stream has the higher priority. The
+ *     second stream is created at the lowest stream priority, so give the
+ *     context's stream a higher one (cudaStreamCreateWithPriority) for the
+ *     calls beside the map to run alongside it instead of after it.
+ *   blocks_per_sm > 0: one persistent launch with at most that many resident
+ *     blocks per SM.
  * rt_join(ctx) orders the context's stream after the map; read gain and hits
  * only after it, and keep them allocated until then. rt_destroy waits for a
  * started map and drops one still waiting for a path trace. The calls that change

@@ -186,10 +186,12 @@ int side_launch(rt_ctx* ctx) {
     std::swap(ctx->status, ctx->side_status);
     const int cap = ctx->grid_cap;
     ctx->grid_cap = r.blocks_per_sm;
+    ctx->side_yield = r.blocks_per_sm == 0;
     cudaError_t me = cudaMemsetAsync(ctx->status.p, 0, sizeof(unsigned), ctx->stream);
     int e = me != cudaSuccess ? set_cuda(ctx, me, "cudaMemsetAsync")
                               : launch_coverage(ctx, &r.g, r.D, r.N, 0, r.N, true, r.tx_port, r.gain, r.hits);
     ctx->grid_cap = cap;
+    ctx->side_yield = false;
     std::swap(ctx->stream, ctx->side);
     std::swap(ctx->counters, ctx->side_counters);
     std::swap(ctx->status, ctx->side_status);

@@ -99,6 +99,7 @@ struct rt_ctx {
     DevBuf side_counters, side_status;
     // a map requested with RT_ASYNC_AFTER_TRACE, not launched yet
     bool side_deferred = false;
+    bool side_yield = false;   // the second stream's map is being launched as short-lived blocks
     struct SideReq {
         rt_grid g;
         int32_t D, tx_port, blocks_per_sm;

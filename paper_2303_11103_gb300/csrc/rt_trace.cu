@@ -53,6 +53,7 @@ struct TraceCommon {
     const float4* dirs;   // [N] with perm: (direction of lattice ray perm[k], perm[k] as bits), or null
     unsigned long long* counter;
     int chunk;            // rays per warp refill
+    int quota;            // refills per warp before it stops (0: until the rays run out)
     int n_sm;             // staged BVH nodes
     unsigned* status;
 };
@@ -67,6 +68,7 @@ __device__ __forceinline__ void stage_nodes(const TraceCommon& c, float4* sm) {
 // global ray slot (tx * N + lattice index) for a refilled lane, -1 otherwise.
 struct WarpFeed {
     long long next = 0, end = 0;
+    int fetched = 0;
     bool exhausted = false;
     // k_out receives the ray's index in the trace order (its slot in c.dirs).
     __device__ __forceinline__ long long refill(const TraceCommon& c, bool alive, long long& k_out) {
@@ -75,6 +77,13 @@ struct WarpFeed {
         long long slot = -1;
         if (dead == 0 || exhausted) return slot;
         if (next >= end) {
+            // a warp with a refill quota stops after it (its block then ends
+            // and frees its SM slot for other work)
+            if (c.quota > 0 && fetched >= c.quota) {
+                exhausted = true;
+                return slot;
+            }
+            fetched++;
             unsigned long long base = 0;
             if ((threadIdx.x & 31) == 0) base = atomicAdd(c.counter, (unsigned long long)c.chunk);
             base = __shfl_sync(full, base, 0);
@@ -528,6 +537,7 @@ static TraceCommon make_common(rt_ctx* ctx, int64_t N, int64_t first, int64_t co
     c.dirs = (c.perm && ctx->dirs_ok) ? bp<float4>(ctx->dirs) : nullptr;
     c.counter = bp<unsigned long long>(ctx->counters);
     c.chunk = ctx->warp_chunk;
+    c.quota = 0;
     c.n_sm = staged_nodes(ctx);
     c.status = bp<unsigned>(ctx->status);
     return c;
@@ -599,6 +609,16 @@ int launch_coverage(rt_ctx* ctx, const rt_grid* g, int D, int64_t N, int64_t fir
     RT_TRY(cudaMemsetAsync(ctx->counters.p, 0, sizeof(unsigned long long), ctx->stream));
     int grid = trace_grid(ctx, (const void*)kern, smem);
     p.c.chunk = pick_chunk(ctx, p.c.total, grid);
+    if (ctx->side_yield) {
+        // a map beside other work: short-lived blocks, one refill of 32 rays
+        // per warp, so that kernels of the context's stream (given a higher
+        // priority) take the SM slots these blocks free as they end
+        p.c.quota = 1;
+        p.c.chunk = 32;
+        const long long warps = (p.c.total + 31) / 32;
+        const int wpb = ctx->trace_block / 32;
+        grid = (int)std::max<long long>(1, (warps + wpb - 1) / wpb);
+    }
     prof_begin(ctx, "k_coverage");
     kern<<<grid, ctx->trace_block, smem, ctx->stream>>>(p);
     prof_end(ctx);

@@ -70,6 +70,36 @@ def test_async_map_beside_paths(city, after_trace):
 
 
 @pytest.mark.parametrize("after_trace", [False, True])
+def test_yielding_map_beside_paths_on_a_high_priority_stream(city, after_trace):
+    """The default async map (short-lived blocks) beside the path calls of a
+    higher-priority stream, as the bench runs it: paths, CIR, H(f) and the map
+    equal those of the calls in order."""
+    tr = city[0]
+    freqs = torch.linspace(-15e6, 15e6, 64, dtype=torch.float64, device=tr.device)
+    ref_map = tr.coverage_map(GRID, D, N_RAYS)
+    tr.compute_paths(D, N_RAYS)
+    ref_sets = gpu_paths(tr)[0]
+    a0, t0 = tr.cir()
+    h0 = tr.freq_response(a0, t0, freqs)
+    a0, t0, h0 = a0.clone(), t0.clone(), h0.clone()
+    torch.cuda.synchronize()
+    hi = torch.cuda.Stream(device=tr.device, priority=-1)
+    with torch.cuda.stream(hi):
+        for _ in range(2):
+            m = tr.coverage_map_async(GRID, D, N_RAYS, after_trace=after_trace)
+            tr.compute_paths(D, N_RAYS)
+            a, t = tr.cir()
+            h = tr.freq_response(a, t, freqs)
+            tr.join()
+            hi.synchronize()
+            assert gpu_paths(tr)[0] == ref_sets
+            assert torch.equal(a, a0) and torch.equal(t, t0) and torch.equal(h, h0)
+            _same_map(ref_map, m)
+    torch.cuda.synchronize()
+    tr.sync_stream()
+
+
+@pytest.mark.parametrize("after_trace", [False, True])
 def test_mutators_join_first(city, after_trace):
     """A scene load, a transmitter move or a frequency change right after
     the async map waits for it (a deferred map is started first): the map is
