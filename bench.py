@@ -233,6 +233,8 @@ def run_ours(args):
         if concurrent and args.schedule == "after_trace":
             rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, rt.ASYNC_AFTER_TRACE,
                                      args.side_blocks)
+        if concurrent and args.schedule == "with_trace":
+            rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, 0, args.side_blocks)
         P = rt.rt_compute_paths(ctx, MAX_DEPTH, N_RAYS, rt.RT_LOS | rt.RT_REFLECTION)
         if concurrent and args.schedule == "after_paths":
             rt.rt_coverage_map_async(ctx, grid, MAX_DEPTH, N_RAYS, 0, gain, hits, 0, args.side_blocks)
@@ -1039,9 +1041,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--schedule", default="after_trace", choices=["after_trace", "after_paths"],
+    ap.add_argument("--schedule", default="after_trace", choices=["after_trace", "after_paths", "with_trace"],
                     help="when the coverage map starts on the second stream: after the path trace (beside the "
-                         "candidate refinement) or after compute_paths returns (beside CIR, H(f) and the VJPs)")
+                         "candidate refinement), after compute_paths returns (beside CIR, H(f) and the VJPs), "
+                         "or before compute_paths (beside the path trace too)")
     ap.add_argument("--side-blocks", type=int, default=0,
                     help="coverage map on the second stream: 0 = short-lived blocks that free SM slots for the "
                          "context's (higher-priority) stream; N > 0 = one persistent launch with N blocks per SM")
