@@ -262,10 +262,25 @@ __device__ __forceinline__ long long cov_segment(const CovParams& p, const float
     return any_hit<C, L>(p.c.s, sm, p.c.n_sm, o, d, up, last, last, cnt_pl) ? -1 : cell;
 }
 
+// Transmitter rotations a coverage block keeps in shared memory (more
+// transmitters: computed per ray).
+#define RT_ROT_CACHE 64
+
 template <bool C, int L>
 __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
     extern __shared__ float4 sm[];
-    stage_nodes(p.c, sm);
+    // each transmitter's rotation once per block instead of once per ray
+    // (the same function, so the same values)
+    __shared__ float s_rot[RT_ROT_CACHE * 9];
+    const long long n_tx = p.c.total / (p.c.count > 0 ? p.c.count : 1);
+    const bool rot_cached = n_tx <= RT_ROT_CACHE;
+    if (rot_cached) {
+        for (int k = threadIdx.x; k < (int)n_tx; k += blockDim.x) {
+            const Rot<float> R = rot_ypr(p.c.tx_ypr[3 * k], p.c.tx_ypr[3 * k + 1], p.c.tx_ypr[3 * k + 2]);
+            for (int q = 0; q < 9; q++) s_rot[9 * k + q] = R.m[q / 3][q % 3];
+        }
+    }
+    stage_nodes(p.c, sm);   // ends with a block barrier
     WarpFeed feed;
     bool alive = false;
     f3 o = mk(0, 0, 0), d = mk(0, 0, 1);
@@ -282,7 +297,12 @@ __global__ void __launch_bounds__(256) k_coverage(CovParams p) {
             tx = (int)t64;
             o = mk(p.c.tx_pos[3 * tx], p.c.tx_pos[3 * tx + 1], p.c.tx_pos[3 * tx + 2]);
             d = ray_dir(p.c, kd, i);
-            Rot<float> Rt = rot_ypr(p.c.tx_ypr[3 * tx], p.c.tx_ypr[3 * tx + 1], p.c.tx_ypr[3 * tx + 2]);
+            Rot<float> Rt;
+            if (rot_cached) {
+                for (int q = 0; q < 9; q++) Rt.m[q / 3][q % 3] = s_rot[9 * tx + q];
+            } else {
+                Rt = rot_ypr(p.c.tx_ypr[3 * tx], p.c.tx_ypr[3 * tx + 1], p.c.tx_ypr[3 * tx + 2]);
+            }
             V3<float> f = antenna_vec<float>(p.txa.kind, zeta_t, Rt, V3<float>{d.x, d.y, d.z});
             E[0] = {f.x, 0.0f};
             E[1] = {f.y, 0.0f};
