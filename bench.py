@@ -479,10 +479,10 @@ ALU_PEAK_GOPS = 152 * 128 * 2.070
 # DRAM bytes (read + write) of one k_coverage launch of this workload, from
 # the ncu capture summarised in profiles/k_coverage_city_1e6rays.md; set to
 # None whenever the kernel changes until it is captured again.
-K_COVERAGE_TRAFFIC = 20.52e6
+K_COVERAGE_TRAFFIC = 20.60e6
 # L1/TEX throughput of the same launch (% of its peak, elapsed) and the
 # sector hit rate: the traversal's record reads are served by L1.
-K_COVERAGE_L1 = {"l1tex_throughput_pct": 61.0, "l1tex_sector_hit_pct": 87.2, "lts_throughput_pct": 2.6,
+K_COVERAGE_L1 = {"l1tex_throughput_pct": 61.3, "l1tex_sector_hit_pct": 85.9, "lts_throughput_pct": 2.8,
                  "source": "profiles/k_coverage_city_1e6rays.md (ncu --set full, one launch)"}
 
 
